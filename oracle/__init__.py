@@ -1,0 +1,249 @@
+"""FP64 CPU oracle for the direct-summation Hermite hot path (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product library never loads it and
+has no CPU fallback; the two share no code. The arithmetic lives in
+``oracle.c`` (plain C, binary64); this module compiles it with gcc on first use
+and marshals numpy arrays through ctypes.
+
+Every routine follows a passage of the paper (Portegies Zwart & Bedorf,
+"Computational Gravitational Dynamics with Modern Numerical Accelerators"):
+
+- ``force`` / ``force_ext``: direct summation of softened gravity from the
+  j-set onto an i-set that is part of it or disjoint from it (Sect. III.A);
+- ``predict``: prediction of the j particles to the block time (Sect. III.A);
+- ``correct_one``, ``aarseth_dt``, ``initial_dt``, ``quantize``: the
+  4th-order Hermite predictor-corrector with individual block steps
+  (Sect. II, III, VI);
+- ``hermite_run``: the block-step (or shared-step) integration loop;
+- ``energy``: kinetic plus softened potential energy.
+
+Parity pins live in ``tests/test_oracle_*.py``; none is unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc flags of the oracle: binary64 as written (no FMA contraction, no fast-math)."""
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` beside it."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    return compile_source(_SRC, _LIB)
+
+
+def use_library(path=None):
+    """Point the wrapper at another build of oracle.c (a planted-mistake copy in the
+    mutation tests); None restores the default library. Returns the previous one."""
+    global _lib
+    with _lock:
+        prev = _lib
+        _lib = None if path is None else _bind(ctypes.CDLL(path))
+    return prev
+
+
+def _restore(lib):
+    global _lib
+    with _lock:
+        _lib = lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    lib.orc_force_idx.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                  _I, _D, _D, _D]
+    lib.orc_force_ext.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                  _D, _D, _D, _D, _D]
+    lib.orc_predict.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
+    lib.orc_correct_one.argtypes = [ctypes.c_double] + [_D] * 10
+    lib.orc_aarseth_dt.argtypes = [_D, _D, _D, _D, ctypes.c_double]
+    lib.orc_aarseth_dt.restype = ctypes.c_double
+    lib.orc_initial_dt.argtypes = [_D, _D, ctypes.c_double]
+    lib.orc_initial_dt.restype = ctypes.c_double
+    lib.orc_quantize.argtypes = [ctypes.c_double] * 5
+    lib.orc_quantize.restype = ctypes.c_double
+    lib.orc_hermite_run.argtypes = ([ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]
+                                    + [ctypes.c_double] * 7
+                                    + [ctypes.c_long, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_long), _D])
+    lib.orc_hermite_run.restype = ctypes.c_int
+    lib.orc_energy.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D, _D]
+    lib.orc_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(_D)
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops use (OMP_NUM_THREADS, else all cores)."""
+    return int(_load().orc_num_threads())
+
+
+def force(m, pos, vel, eps2, idx=None):
+    """acc, jerk (ni,3) and pot (ni,) on i = idx[k] (all if None) from every j != i."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    pos = _f64(pos, (n, 3))
+    vel = _f64(vel, (n, 3))
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.size and (idx.min() < 0 or idx.max() >= n):
+            raise IndexError("idx out of range")
+        ni, ip = idx.shape[0], idx.ctypes.data_as(_I)
+    acc = np.zeros((ni, 3))
+    jerk = np.zeros((ni, 3))
+    pot = np.zeros(ni)
+    lib.orc_force_idx(n, _p(m), _p(pos), _p(vel), float(eps2), ni, ip, _p(acc), _p(jerk), _p(pot))
+    return acc, jerk, pot
+
+
+def force_ext(m, pos, vel, eps2, ipos, ivel):
+    """acc, jerk, pot on an external i-set (no self-exclusion)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    pos = _f64(pos, (n, 3))
+    vel = _f64(vel, (n, 3))
+    ipos = _f64(ipos).reshape(-1, 3)
+    ivel = _f64(ivel, ipos.shape)
+    ni = ipos.shape[0]
+    acc = np.zeros((ni, 3))
+    jerk = np.zeros((ni, 3))
+    pot = np.zeros(ni)
+    lib.orc_force_ext(n, _p(m), _p(pos), _p(vel), float(eps2), ni, _p(ipos), _p(ivel),
+                      _p(acc), _p(jerk), _p(pot))
+    return acc, jerk, pot
+
+
+def predict(t, tj, pos, vel, acc, jerk):
+    """Predicted (pos, vel) of every particle at time t from its own time tj."""
+    lib = _load()
+    tj = _f64(tj)
+    n = tj.shape[0]
+    pos, vel, acc, jerk = (_f64(a, (n, 3)) for a in (pos, vel, acc, jerk))
+    pp = np.zeros((n, 3))
+    vp = np.zeros((n, 3))
+    lib.orc_predict(n, float(t), _p(tj), _p(pos), _p(vel), _p(acc), _p(jerk), _p(pp), _p(vp))
+    return pp, vp
+
+
+def correct_one(dt, xp, vp, a0, j0, a1, j1):
+    """Hermite corrector for one particle: (x1, v1, a2_end, a3_end)."""
+    lib = _load()
+    args = [_f64(a, (3,)) for a in (xp, vp, a0, j0, a1, j1)]
+    outs = [np.zeros(3) for _ in range(4)]
+    lib.orc_correct_one(float(dt), *[_p(a) for a in args], *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def aarseth_dt(a, j, a2, a3, eta):
+    lib = _load()
+    return float(lib.orc_aarseth_dt(*[_p(_f64(v, (3,))) for v in (a, j, a2, a3)], float(eta)))
+
+
+def initial_dt(a, j, eta_s):
+    lib = _load()
+    return float(lib.orc_initial_dt(_p(_f64(a, (3,))), _p(_f64(j, (3,))), float(eta_s)))
+
+
+def quantize(dt_raw, dt_old, t_new, dt_min, dt_max):
+    return float(_load().orc_quantize(float(dt_raw), float(dt_old), float(t_new), float(dt_min),
+                                      float(dt_max)))
+
+
+class State:
+    """Integrator state of one system (copies of the caller's arrays)."""
+
+    def __init__(self, m, pos, vel, t0=0.0, acc=None, jerk=None, t=None, dt=None):
+        self.m = _f64(m).copy()
+        n = self.m.shape[0]
+        self.pos = _f64(pos, (n, 3)).copy()
+        self.vel = _f64(vel, (n, 3)).copy()
+        self.acc = np.zeros((n, 3)) if acc is None else _f64(acc, (n, 3)).copy()
+        self.jerk = np.zeros((n, 3)) if jerk is None else _f64(jerk, (n, 3)).copy()
+        self.t = np.full(n, float(t0)) if t is None else _f64(t).copy()
+        self.dt = np.zeros(n) if dt is None else _f64(dt).copy()
+        self.initialised = acc is not None
+
+    @property
+    def n(self):
+        return self.m.shape[0]
+
+
+def hermite_run(state: State, t_end, eps2, eta=0.01, eta_s=None, dt_min=2.0 ** -30,
+                dt_max=1.0 / 16, dt_shared=0.0, max_steps=0):
+    """Advance ``state`` in place with block (or shared, dt_shared > 0) steps to t_end.
+
+    Returns (n_block_steps, n_interactions)."""
+    lib = _load()
+    if eta_s is None:
+        eta_s = eta
+    steps = ctypes.c_long(0)
+    inter = ctypes.c_double(0.0)
+    init = 0 if state.initialised else 1
+    rc = lib.orc_hermite_run(state.n, _p(state.m), _p(state.pos), _p(state.vel), _p(state.acc),
+                             _p(state.jerk), _p(state.t), _p(state.dt), float(eps2), float(eta),
+                             float(eta_s), float(dt_min), float(dt_max), float(dt_shared),
+                             float(t_end), int(max_steps), init, ctypes.byref(steps),
+                             ctypes.byref(inter))
+    if rc != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    state.initialised = True
+    return int(steps.value), float(inter.value)
+
+
+def energy(m, pos, vel, eps2):
+    """(K, W): kinetic and softened potential energy (pairwise sum over i<j)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    kin = ctypes.c_double()
+    w = ctypes.c_double()
+    lib.orc_energy(n, _p(m), _p(_f64(pos, (n, 3))), _p(_f64(vel, (n, 3))), float(eps2),
+                   ctypes.byref(kin), ctypes.byref(w))
+    return float(kin.value), float(w.value)

@@ -1,0 +1,469 @@
+/*
+ * FP64 CPU oracle for the direct-summation Hermite hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference the CUDA
+ * path is checked against. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product library never links,
+ * calls or falls back to it, and it shares no code with the CUDA sources.
+ *
+ * What it computes (paper: Portegies Zwart & Bedorf, "Computational
+ * Gravitational Dynamics with Modern Numerical Accelerators"):
+ *   - the force that a j-set exerts on an i-set, by direct summation over
+ *     every (i, j) pair (Sect. III.A: i particles receive, j particles exert,
+ *     the two sets may coincide or be disjoint; cost N_i * N_j);
+ *   - the pair interaction is Newton's softened gravity (Sect. II), with the
+ *     acceleration, its time derivative (the jerk) and the potential that a
+ *     4th-order Hermite integrator needs (Sect. II: >= 4th-order integrators
+ *     with individual steps for direct codes; Sect. VI: ph4, a 4th-order
+ *     Hermite predictor-corrector);
+ *   - the prediction of the j particles to the current time (Sect. III.A,
+ *     the optional prediction step on the j particles);
+ *   - the Hermite corrector and the individual block time steps, where only
+ *     the particles that are due at time t are advanced (Sect. III and
+ *     III.A: individual/block time steps, N_i << N_j).
+ * The paper prints none of these formulas; they are the textbook forms it
+ * names (Makino & Aarseth 1992 Hermite scheme, Aarseth's step criterion),
+ * written out here plainly. Readings of the paper are listed in the design
+ * notes at the repository root.
+ *
+ * Arithmetic: IEEE binary64, round to nearest, compiled without FMA
+ * contraction (-ffp-contract=off) and without fast-math, so x86 and Arm hosts
+ * give the same bits. Force sums are plain j-ascending loops accumulated with
+ * Neumaier's compensated summation, so that the oracle's own rounding error
+ * (~1e-16 relative) is far below every tolerance it is used to check.
+ *
+ * Layout: positions, velocities, accelerations and jerks are row-major
+ * (n, 3) arrays of doubles; masses, potentials, times and steps are length-n
+ * arrays.
+ *
+ * Parity pins (tests/test_oracle_*.py): closed-form two-body values, exact
+ * symmetric configurations, Newton's third law (sum m a = sum m jerk = 0),
+ * finite-difference checks that acc = -grad(pot) and jerk = d(acc)/dt,
+ * brute force in 50-digit arithmetic on tiny N, Kepler's equation and the
+ * softened circular orbit for the integrator, 4th-order convergence and
+ * energy conservation.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- compensated (Neumaier) summation ---------------------------------- */
+
+typedef struct {
+    double s; /* running sum */
+    double c; /* accumulated rounding error */
+} ksum;
+
+static void ks_add(ksum *k, double x)
+{
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x))
+        k->c += (k->s - t) + x;
+    else
+        k->c += (x - t) + k->s;
+    k->s = t;
+}
+
+static double ks_val(const ksum *k) { return k->s + k->c; }
+
+/* ---- pair interaction (Sect. II: Newtonian gravity, softened) ----------- */
+
+/*
+ * Contribution of particle j (mass mj, position xj, velocity vj) to particle
+ * i (position xi, velocity vi). With r = xj - xi, v = vj - vi and
+ * s2 = |r|^2 + eps2:
+ *   acc  = mj r / s2^(3/2)
+ *   jerk = mj [ v / s2^(3/2) - 3 (r.v) r / s2^(5/2) ]     (d acc / dt)
+ *   pot  = -mj / s2^(1/2)
+ */
+static void pair_terms(double mj, const double *xj, const double *vj,
+                       const double *xi, const double *vi, double eps2,
+                       double acc[3], double jerk[3], double *pot)
+{
+    double r[3], v[3];
+    for (int c = 0; c < 3; c++) {
+        r[c] = xj[c] - xi[c];
+        v[c] = vj[c] - vi[c];
+    }
+    double s2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps2;
+    double s = sqrt(s2);
+    double inv_s3 = 1.0 / (s2 * s);
+    double rv = r[0] * v[0] + r[1] * v[1] + r[2] * v[2];
+    for (int c = 0; c < 3; c++) {
+        acc[c] = mj * r[c] * inv_s3;
+        jerk[c] = mj * (v[c] * inv_s3 - 3.0 * rv * r[c] * inv_s3 / s2);
+    }
+    *pot = -mj / s;
+}
+
+/* Sum over all j of the pair terms on one i-particle; j == skip is left out
+ * (skip < 0 means none is left out). */
+static void sum_over_j(int nj, const double *m, const double *pos,
+                       const double *vel, const double *xi, const double *vi,
+                       double eps2, int skip, double acc[3], double jerk[3],
+                       double *pot)
+{
+    ksum ka[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum kj[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum kp = {0, 0};
+    for (int j = 0; j < nj; j++) {
+        if (j == skip)
+            continue;
+        double a[3], jk[3], p;
+        pair_terms(m[j], pos + 3 * (size_t)j, vel + 3 * (size_t)j, xi, vi,
+                   eps2, a, jk, &p);
+        for (int c = 0; c < 3; c++) {
+            ks_add(&ka[c], a[c]);
+            ks_add(&kj[c], jk[c]);
+        }
+        ks_add(&kp, p);
+    }
+    for (int c = 0; c < 3; c++) {
+        acc[c] = ks_val(&ka[c]);
+        jerk[c] = ks_val(&kj[c]);
+    }
+    *pot = ks_val(&kp);
+}
+
+/*
+ * Force on i-particles that are members of the j-set (Sect. III.A, same-set
+ * case): i = idx[k] (idx == NULL means i = k for k < ni), summing over every
+ * j != i. Outputs are indexed by k.
+ */
+void orc_force_idx(int nj, const double *m, const double *pos,
+                   const double *vel, double eps2, int ni, const int *idx,
+                   double *acc, double *jerk, double *pot)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < ni; k++) {
+        int i = idx ? idx[k] : k;
+        sum_over_j(nj, m, pos, vel, pos + 3 * (size_t)i, vel + 3 * (size_t)i,
+                   eps2, i, acc + 3 * (size_t)k, jerk + 3 * (size_t)k,
+                   pot + k);
+    }
+}
+
+/*
+ * Force on an external i-set, disjoint from the j-set (Sect. III.A,
+ * different-set case): no pair is left out.
+ */
+void orc_force_ext(int nj, const double *m, const double *pos,
+                   const double *vel, double eps2, int ni, const double *ipos,
+                   const double *ivel, double *acc, double *jerk, double *pot)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < ni; k++)
+        sum_over_j(nj, m, pos, vel, ipos + 3 * (size_t)k,
+                   ivel + 3 * (size_t)k, eps2, -1, acc + 3 * (size_t)k,
+                   jerk + 3 * (size_t)k, pot + k);
+}
+
+/* ---- predictor (Sect. III.A: prediction of the j particles) ------------- */
+
+/*
+ * Taylor prediction of every particle from its own time tj[i] to time t:
+ *   xp = x + v d + a d^2/2 + jerk d^3/6,   vp = v + a d + jerk d^2/2,
+ * with d = t - tj[i].
+ */
+void orc_predict(int n, double t, const double *tj, const double *pos,
+                 const double *vel, const double *acc, const double *jerk,
+                 double *pos_p, double *vel_p)
+{
+    for (int i = 0; i < n; i++) {
+        double d = t - tj[i];
+        for (int c = 0; c < 3; c++) {
+            size_t q = 3 * (size_t)i + c;
+            pos_p[q] = pos[q] + vel[q] * d + acc[q] * d * d / 2.0 +
+                       jerk[q] * d * d * d / 6.0;
+            vel_p[q] = vel[q] + acc[q] * d + jerk[q] * d * d / 2.0;
+        }
+    }
+}
+
+/* ---- corrector (4th-order Hermite, Sect. II and VI) --------------------- */
+
+/*
+ * Hermite corrector for one particle over a step of length dt, from the
+ * predicted state (xp, vp), the start-of-step acc/jerk (a0, j0) and the
+ * end-of-step acc/jerk (a1, j1). The 2nd and 3rd derivatives of the
+ * acceleration at the start of the step follow from the cubic Hermite
+ * interpolant through (a0, j0) and (a1, j1):
+ *   a2 = (-6 (a0 - a1) - dt (4 j0 + 2 j1)) / dt^2
+ *   a3 = (12 (a0 - a1) + 6 dt (j0 + j1)) / dt^3
+ *   x1 = xp + a2 dt^4/24 + a3 dt^5/120,   v1 = vp + a2 dt^3/6 + a3 dt^4/24.
+ * Returns a2 and a3 moved to the end of the step (a2 + dt a3, a3), which the
+ * step criterion uses.
+ */
+void orc_correct_one(double dt, const double xp[3], const double vp[3],
+                     const double a0[3], const double j0[3],
+                     const double a1[3], const double j1[3], double x1[3],
+                     double v1[3], double a2_end[3], double a3_end[3])
+{
+    for (int c = 0; c < 3; c++) {
+        double a2 = (-6.0 * (a0[c] - a1[c]) - dt * (4.0 * j0[c] + 2.0 * j1[c])) /
+                    (dt * dt);
+        double a3 = (12.0 * (a0[c] - a1[c]) + 6.0 * dt * (j0[c] + j1[c])) /
+                    (dt * dt * dt);
+        x1[c] = xp[c] + a2 * dt * dt * dt * dt / 24.0 +
+                a3 * dt * dt * dt * dt * dt / 120.0;
+        v1[c] = vp[c] + a2 * dt * dt * dt / 6.0 + a3 * dt * dt * dt * dt / 24.0;
+        a2_end[c] = a2 + dt * a3;
+        a3_end[c] = a3;
+    }
+}
+
+/* ---- time steps (Sect. III, III.A: individual and block steps) ---------- */
+
+static double norm3(const double *u)
+{
+    return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
+/*
+ * Aarseth's step criterion:
+ *   dt = sqrt( eta (|a| |a2| + |j|^2) / (|j| |a3| + |a2|^2) ).
+ * A zero denominator (no higher derivatives, e.g. an isolated particle)
+ * gives +inf, which the quantizer turns into dt_max.
+ */
+double orc_aarseth_dt(const double a[3], const double j[3], const double a2[3],
+                      const double a3[3], double eta)
+{
+    double na = norm3(a), nj = norm3(j), n2 = norm3(a2), n3 = norm3(a3);
+    double num = na * n2 + nj * nj;
+    double den = nj * n3 + n2 * n2;
+    if (den == 0.0)
+        return INFINITY;
+    return sqrt(eta * num / den);
+}
+
+/* Initial step without higher derivatives: dt0 = eta_s |a| / |j|. */
+double orc_initial_dt(const double a[3], const double j[3], double eta_s)
+{
+    double nj = norm3(j);
+    if (nj == 0.0)
+        return INFINITY;
+    return eta_s * norm3(a) / nj;
+}
+
+/*
+ * Block quantization of a raw step into a power of two:
+ *   - the largest power of two <= dt_raw (dt_max when dt_raw is +inf);
+ *   - at most twice the previous step (dt_old > 0), i.e. growth by one level;
+ *   - clamped to [dt_min, dt_max];
+ *   - halved until it divides the particle's new time t_new, so block times
+ *     stay commensurate (exact in binary64 for dyadic times).
+ */
+double orc_quantize(double dt_raw, double dt_old, double t_new, double dt_min,
+                    double dt_max)
+{
+    double d;
+    if (!(dt_raw < dt_max)) {
+        d = dt_max;
+    } else {
+        int e;
+        frexp(dt_raw, &e); /* dt_raw = f 2^e, f in [0.5, 1) */
+        d = ldexp(1.0, e - 1);
+    }
+    if (dt_old > 0.0 && d > 2.0 * dt_old)
+        d = 2.0 * dt_old;
+    if (d > dt_max)
+        d = dt_max;
+    if (d < dt_min)
+        d = dt_min;
+    while (d > dt_min && fmod(t_new, d) != 0.0)
+        d = d / 2.0;
+    return d;
+}
+
+/* ---- integrator state ---------------------------------------------------- */
+
+/*
+ * Full state of a system: mass, position, velocity, acceleration, jerk, own
+ * time and own step per particle. The force and correction steps act on the
+ * 'active' particles (all of them in shared-step mode).
+ */
+typedef struct {
+    int n;
+    double eps2;
+    double *m, *pos, *vel, *acc, *jerk, *t, *dt;
+} orc_state;
+
+/* Evaluate acc and jerk of all particles at their current (synchronous)
+ * positions and assign the initial block step. */
+static void initialise(orc_state *s, double eta_s, double dt_min,
+                       double dt_max, double dt_shared, double *pot_scratch)
+{
+    orc_force_idx(s->n, s->m, s->pos, s->vel, s->eps2, s->n, NULL, s->acc,
+                  s->jerk, pot_scratch);
+    for (int i = 0; i < s->n; i++) {
+        if (dt_shared > 0.0) {
+            s->dt[i] = dt_shared;
+        } else {
+            double raw = orc_initial_dt(s->acc + 3 * (size_t)i,
+                                        s->jerk + 3 * (size_t)i, eta_s);
+            s->dt[i] = orc_quantize(raw, 0.0, s->t[i], dt_min, dt_max);
+        }
+    }
+}
+
+/*
+ * One block step (shared-step mode is the special case where all particles
+ * share one dt and all are due together):
+ *   1. t_next = min_i (t_i + dt_i); active = {i : t_i + dt_i == t_next}, in
+ *      ascending index order;
+ *   2. predict every particle to t_next;
+ *   3. evaluate acc/jerk on the active particles from the predicted set;
+ *   4. correct the active particles and give them a new step.
+ * Returns the number of active particles, sets *t_out = t_next.
+ */
+static int block_step(orc_state *s, double eta, double dt_min, double dt_max,
+                      double dt_shared, int *active, double *pp, double *vp,
+                      double *a1, double *j1, double *p1, double *t_out)
+{
+    int n = s->n;
+    double t_next = INFINITY;
+    for (int i = 0; i < n; i++)
+        if (s->t[i] + s->dt[i] < t_next)
+            t_next = s->t[i] + s->dt[i];
+    int na = 0;
+    for (int i = 0; i < n; i++)
+        if (s->t[i] + s->dt[i] == t_next)
+            active[na++] = i;
+
+    orc_predict(n, t_next, s->t, s->pos, s->vel, s->acc, s->jerk, pp, vp);
+    orc_force_idx(n, s->m, pp, vp, s->eps2, na, active, a1, j1, p1);
+
+    for (int k = 0; k < na; k++) {
+        int i = active[k];
+        size_t q = 3 * (size_t)i, r = 3 * (size_t)k;
+        double dt = t_next - s->t[i];
+        double x1[3], v1[3], a2[3], a3[3];
+        orc_correct_one(dt, pp + q, vp + q, s->acc + q, s->jerk + q, a1 + r,
+                        j1 + r, x1, v1, a2, a3);
+        double dt_new;
+        if (dt_shared > 0.0) {
+            dt_new = dt_shared;
+        } else {
+            double raw = orc_aarseth_dt(a1 + r, j1 + r, a2, a3, eta);
+            dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
+        }
+        for (int c = 0; c < 3; c++) {
+            s->pos[q + c] = x1[c];
+            s->vel[q + c] = v1[c];
+            s->acc[q + c] = a1[r + c];
+            s->jerk[q + c] = j1[r + c];
+        }
+        s->t[i] = t_next;
+        s->dt[i] = dt_new;
+    }
+    *t_out = t_next;
+    return na;
+}
+
+/*
+ * Integrate a system with 4th-order Hermite and block (or shared) steps
+ * until every particle reaches t_end, or until max_steps block steps have
+ * been taken (max_steps <= 0: no limit).
+ *
+ * In/out arrays: pos, vel (n,3); acc, jerk (n,3); t, dt (n). When init != 0
+ * the acc/jerk are evaluated at the start and dt is assigned (t must then be
+ * the same for all particles); otherwise acc, jerk, t and dt are taken as
+ * given (a resumed run).
+ * dt_shared > 0 selects shared-step mode with that step.
+ * Counters: *n_block_steps, *n_interactions (sum over steps of N_active * N,
+ * the initial evaluation included when init != 0).
+ * Returns 0, or -1 if a scratch allocation failed.
+ */
+int orc_hermite_run(int n, const double *m, double *pos, double *vel,
+                    double *acc, double *jerk, double *t, double *dt,
+                    double eps2, double eta, double eta_s, double dt_min,
+                    double dt_max, double dt_shared, double t_end,
+                    long max_steps, int init, long *n_block_steps,
+                    double *n_interactions)
+{
+    orc_state s = {n, eps2, (double *)m, pos, vel, acc, jerk, t, dt};
+    int *active = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *buf = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 15);
+    if (!active || !buf) {
+        free(active);
+        free(buf);
+        return -1;
+    }
+    double *pp = buf, *vp = buf + 3 * (size_t)n, *a1 = buf + 6 * (size_t)n;
+    double *j1 = buf + 9 * (size_t)n, *p1 = buf + 12 * (size_t)n;
+    long steps = 0;
+    double inter = 0.0;
+    if (init && n > 0) {
+        initialise(&s, eta_s, dt_min, dt_max, dt_shared, p1);
+        inter += (double)n * (double)n;
+    }
+    while (n > 0 && (max_steps <= 0 || steps < max_steps)) {
+        double t_next = INFINITY;
+        for (int i = 0; i < n; i++)
+            if (t[i] + dt[i] < t_next)
+                t_next = t[i] + dt[i];
+        if (t_next > t_end)
+            break;
+        double tn;
+        int na = block_step(&s, eta, dt_min, dt_max, dt_shared, active, pp, vp,
+                            a1, j1, p1, &tn);
+        inter += (double)na * (double)n;
+        steps++;
+    }
+    *n_block_steps = steps;
+    *n_interactions = inter;
+    free(active);
+    free(buf);
+    return 0;
+}
+
+/* ---- energy diagnostic -------------------------------------------------- */
+
+/*
+ * Kinetic and softened potential energy of a synchronised system:
+ *   K = sum_i m_i |v_i|^2 / 2,   W = -sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps2),
+ * the potential written as the sum over distinct pairs (not through the
+ * per-particle potential), so it also cross-checks the force routine's pot.
+ */
+void orc_energy(int n, const double *m, const double *pos, const double *vel,
+                double eps2, double *kin, double *wpot)
+{
+    ksum kk = {0, 0}, kw = {0, 0};
+    for (int i = 0; i < n; i++) {
+        const double *v = vel + 3 * (size_t)i;
+        ks_add(&kk, 0.5 * m[i] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    }
+    double *rowsum = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int i = 0; i < n; i++) {
+        ksum kr = {0, 0};
+        for (int j = i + 1; j < n; j++) {
+            double r2 = eps2;
+            for (int c = 0; c < 3; c++) {
+                double d = pos[3 * (size_t)j + c] - pos[3 * (size_t)i + c];
+                r2 += d * d;
+            }
+            ks_add(&kr, -m[i] * m[j] / sqrt(r2));
+        }
+        rowsum[i] = ks_val(&kr);
+    }
+    for (int i = 0; i < n; i++)
+        ks_add(&kw, rowsum[i]);
+    free(rowsum);
+    *kin = ks_val(&kk);
+    *wpot = ks_val(&kw);
+}
+
+/* Number of threads the force loops run on. */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,100 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case copies ``oracle/oracle.c``, plants one plausible slip (a wrong factor,
+sign, power, operand order, dropped term), compiles the copy on the CPU, points
+the oracle wrapper at it and runs the pin tests of ``test_oracle_force.py`` and
+``test_oracle_hermite.py``; at least one pin must fail for every mutant. The
+unmodified source must pass them all.
+"""
+import os
+
+import pytest
+
+import oracle
+
+from . import test_oracle_force as F
+from . import test_oracle_hermite as H
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = [
+    ("jerk radial factor 3 -> 2", "3.0 * rv * r[c] * inv_s3 / s2", "2.0 * rv * r[c] * inv_s3 / s2"),
+    ("jerk radial term sign", "v[c] * inv_s3 - 3.0", "v[c] * inv_s3 + 3.0"),
+    ("acc power of distance", "inv_s3 = 1.0 / (s2 * s);", "inv_s3 = 1.0 / (s2);"),
+    ("separation transposed", "r[c] = xj[c] - xi[c];", "r[c] = xi[c] - xj[c];"),
+    ("relative velocity transposed", "v[c] = vj[c] - vi[c];", "v[c] = vi[c] - vj[c];"),
+    ("pot sign", "*pot = -mj / s;", "*pot = mj / s;"),
+    ("softening dropped", "r[2] * r[2] + eps2;", "r[2] * r[2];"),
+    ("self pair kept", "if (j == skip)", "if (j == skip && j < 0)"),
+    ("predictor jerk term 1/6 -> 1/2", "jerk[q] * d * d * d / 6.0", "jerk[q] * d * d * d / 2.0"),
+    ("predictor velocity jerk term dropped", "vel_p[q] = vel[q] + acc[q] * d + jerk[q] * d * d / 2.0;",
+     "vel_p[q] = vel[q] + acc[q] * d;"),
+    ("corrector a3 coefficient", "a3 * dt * dt * dt * dt * dt / 120.0", "a3 * dt * dt * dt * dt * dt / 24.0"),
+    ("corrector j0/j1 transposed", "4.0 * j0[c] + 2.0 * j1[c]", "2.0 * j0[c] + 4.0 * j1[c]"),
+    ("corrector velocity a2 term", "v1[c] = vp[c] + a2 * dt * dt * dt / 6.0", "v1[c] = vp[c] + a2 * dt * dt * dt / 2.0"),
+    ("a2 not moved to end of step", "a2_end[c] = a2 + dt * a3;", "a2_end[c] = a2;"),
+    ("Aarseth numerator", "double num = na * n2 + nj * nj;", "double num = na * n2 + na * na;"),
+    ("growth limit x2 -> x4", "d > 2.0 * dt_old", "d > 4.0 * dt_old"),
+    ("commensurability dropped", "fmod(t_new, d) != 0.0", "fmod(t_new, d) != fmod(t_new, d)"),
+    ("scheduler takes a particle early", "if (s->t[i] + s->dt[i] == t_next)\n            active[na++] = i;",
+     "if (s->t[i] + s->dt[i] <= t_next + s->dt[i] / 2)\n            active[na++] = i;"),
+    ("kinetic energy factor", "0.5 * m[i] * (v[0]", "m[i] * (v[0]"),
+]
+
+
+def _pins():
+    out = [(f"two_body[{i}]", lambda i=i: F.test_two_body_closed_forms(i)) for i in range(3)]
+    out += [
+        ("ext", F.test_external_i_set_matches_member_case),
+        ("cube0", lambda: F.test_cube_vertices(0.0)),
+        ("cube_eps", lambda: F.test_cube_vertices(0.3)),
+        ("triangle", F.test_equilateral_triangle),
+        ("third_law", lambda: F.test_newton_third_law(1e-2)),
+        ("pot_vs_energy", lambda: F.test_pot_matches_pairwise_energy(1e-2)),
+        ("grad_pot", lambda: F.test_acc_is_minus_grad_pot(2e-2)),
+        ("jerk_fd", lambda: F.test_jerk_is_time_derivative_of_acc(2e-2)),
+        ("rotation", F.test_rigid_rotation_jerk),
+        ("homology", F.test_homologous_expansion_jerk),
+        ("single", F.test_single_particle_and_empty),
+        ("predictor", H.test_predictor_exact_for_cubic),
+        ("corrector", H.test_corrector_exact_for_quintic),
+        ("aarseth", H.test_aarseth_criterion_hand_values),
+        ("quantize", H.test_quantize_cases),
+        ("circular", H.test_softened_circular_orbit_and_convergence),
+        ("kepler", H.test_kepler_ellipse_and_convergence),
+        ("momentum", H.test_shared_step_momentum_conservation),
+        ("dyadic", lambda: H.test_block_times_are_dyadic(H.make_block_run())),
+        ("equal_block_shared", H.test_equal_block_steps_equal_shared_steps),
+        ("schedule_counts", H.test_block_schedule_counts_two_binaries),
+        ("energy_order", H.test_energy_convergence_order),
+    ]
+    return out
+
+
+def _failures():
+    failed = []
+    for name, fn in _pins():
+        try:
+            fn()
+        except Exception:  # an AssertionError, or a NaN tripping a comparison
+            failed.append(name)
+    return failed
+
+
+def test_unmodified_source_passes_all_pins():
+    assert _failures() == []
+
+
+@pytest.mark.parametrize("desc,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, desc, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    lib = oracle.compile_source(str(path), str(tmp_path / "libmutant.so"))
+    prev = oracle.use_library(lib)
+    try:
+        failed = _failures()
+    finally:
+        oracle._restore(prev)
+    assert failed, f"no pin caught: {desc}"
