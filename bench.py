@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the direct-summation Hermite hot path on GB300.
+
+Default workload: a Plummer sphere of N = 65536 equal masses, eps = 1e-3,
+block time steps (Aarseth eta = 0.01, dt_max = 1/16), FP32 pair math with
+double-single relative coordinates and accumulation (NB_F32DS), FP64 state.
+One bench step advances the system by 1/16 N-body time unit through nb_step:
+every block step inside runs the scheduler (K5), the j-predictor (K1), the
+pair-force kernel (K2) with its partial-sum reduction (K3) and the Hermite
+corrector (K4). The metric is pair interactions (N_active * N summed over the
+block steps) per second, in G/s, and its fraction of FP32 peak at 60 flops per
+acc+jerk interaction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload block65536|full2p20|small1024]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only under torchrun). Multi-GPU runs are
+independent replicas (the workload does not shard; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G pair-interactions/s (acc+jerk)"
+UNIT = "G interactions/s"
+FLOPS_PER_INTERACTION = 60
+L2_FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "block65536": dict(n=65536, eps=1e-3, eta=0.01, dt_max=1.0 / 16, shared_dt=0.0,
+                       variant="f32ds", masses="equal", step_t=1.0 / 16, kind="evolve",
+                       desc="Plummer N=65536 equal masses, eps=1e-3, block steps "
+                            "(Aarseth eta=0.01, dt_max=1/16); one bench step = 1/16 time unit"),
+    "full2p20": dict(n=2 ** 20, eps=1e-4, variant="f32ds", masses="lognormal", kind="force",
+                     desc="Plummer N=2^20 log-normal masses (sigma 0.5), eps=1e-4; one bench "
+                          "step = one full N^2 acc/jerk/pot evaluation (predict + force)"),
+    "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
+                      variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
+                      desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
+                           "step = 16 shared steps"),
+}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="block65536")
+    ap.add_argument("--variant", choices=["f32", "f32ds", "f64"], default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: a barrier and a max over ranks, no data path)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(per_rank):
+    """Whole-job numbers from per-rank (units, seconds) pairs: units summed over the
+    replicas, time the slowest rank's."""
+    units = sum(u for u, _ in per_rank)
+    secs = max(s for _, s in per_rank)
+    return units, secs
+
+
+class Dist:
+    def __init__(self, world, backend):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def gather_pairs(self, units, secs, device=None):
+        if self.world == 1:
+            return [(units, secs)]
+        import torch
+        t = torch.tensor([units, secs], dtype=torch.float64, device=device)
+        out = [torch.zeros_like(t) for _ in range(self.world)]
+        self.dist.all_gather(out, t)
+        return [(float(o[0]), float(o[1])) for o in out]
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = sorted({self.NAMES[k] for _, _, fl in rows for k, v in enumerate(fl)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# peaks
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except ValueError:
+            return {}
+    return {}
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """FP32 peak: SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+ORACLE_BLOCK_STEPS = 64
+
+
+def oracle_sample(wl, particles):
+    """One bounded oracle sample of the workload; returns (interactions, seconds, desc)."""
+    import oracle
+    eps2 = wl["eps"] ** 2
+    if wl["kind"] == "force":
+        import numpy as np
+        rng = np.random.default_rng(2014)
+        ni = 4096
+        idx = rng.choice(particles.n, size=ni, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.force(particles.m, particles.pos, particles.vel, eps2, idx=idx)
+        dt = time.perf_counter() - t0
+        return float(ni) * particles.n, dt, (
+            f"oracle force on a seeded {ni}-particle i-subset against all {particles.n} j")
+    st = oracle.State(particles.m, particles.pos, particles.vel)
+    t0 = time.perf_counter()
+    if wl.get("shared_dt", 0.0) > 0:
+        steps, inter = oracle.hermite_run(st, math.inf, eps2, dt_shared=wl["shared_dt"],
+                                          max_steps=16)
+        desc = "oracle shared-step Hermite: initial evaluation + 16 steps from t=0"
+    else:
+        steps, inter = oracle.hermite_run(st, math.inf, eps2, eta=wl["eta"],
+                                          dt_max=wl["dt_max"], max_steps=ORACLE_BLOCK_STEPS)
+        desc = (f"oracle block-step Hermite of the same system from t=0: initial full "
+                f"evaluation + first {ORACLE_BLOCK_STEPS} block steps")
+    dt = time.perf_counter() - t0
+    return inter, dt, desc
+
+
+def make_particles(wl):
+    from paper_1409_5474_gb300 import ic
+    return ic.plummer(wl["n"], ic.MASTER_SEED + (3 if wl["n"] == 2 ** 20 else 0),
+                      masses=wl["masses"])
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def config_of(wl, name, variant):
+    c = {"workload": name, "n": wl["n"], "eps": wl["eps"], "variant": variant,
+         "desc": wl["desc"], "inputs": "seeded synthetic Plummer sphere",
+         "l2": "flushed between timed steps (256 MB write)"}
+    if wl["kind"] == "evolve":
+        c.update({"eta": wl["eta"], "dt_max": wl["dt_max"], "shared_dt": wl["shared_dt"],
+                  "step_time_units": wl["step_t"]})
+    return c
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    wl = WORKLOADS[args.workload]
+    variant = args.variant or wl["variant"]
+    p = make_particles(wl)
+    inter_t = secs_t = 0.0
+    desc = ""
+    for k in range(args.warmup + args.steps):
+        inter, secs, desc = oracle_sample(wl, p)
+        if k >= args.warmup:
+            inter_t += inter
+            secs_t += secs
+    value = inter_t / secs_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, args.workload, variant),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": desc + " (per step)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU path)")
+    torch.cuda.set_device(local)
+    dist = Dist(world, "nccl")
+    from paper_1409_5474_gb300 import nbody
+
+    nbody.load()
+    wl = WORKLOADS[args.workload]
+    variant = args.variant or wl["variant"]
+    p = make_particles(wl)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    cfg = dict(variant=variant, eps=wl["eps"], device=local, flags=nbody.NB_FLAG_TIMING)
+    if wl["kind"] == "evolve":
+        cfg.update(eta=wl["eta"], dt_max=wl["dt_max"], shared_dt=wl["shared_dt"])
+    sysm = nbody.System(p.m, p.pos, p.vel, **cfg)
+    h = sysm.h
+    nbody.nb_set_stream(h, stream.cuda_stream)
+    n = p.n
+
+    def one_step(k, host_state):
+        """One bench step; returns (interactions, device_ms, wall_s, launches, stats, state)."""
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if wl["kind"] == "evolve":
+            w0 = time.perf_counter()
+            if host_state is not None:
+                nbody.nb_set_state(h, host_state)          # H2D of the whole state
+            e0.record(stream)
+            st = nbody.nb_step(h, (k + 1) * wl["step_t"])
+            e1.record(stream)
+            out = nbody.nb_get_state(h)                    # D2H of the whole state
+            w1 = time.perf_counter()
+            stream.synchronize()
+            return st["interactions"], e0.elapsed_time(e1), w1 - w0, st["kernel_launches"], st, out
+        # full evaluation: predict to t0 and one N^2 force
+        before = nbody.nb_get_stats(h)
+        w0 = time.perf_counter()
+        if host_state is not None:
+            nbody.nb_set_particles(h, p.m, p.pos.T, p.vel.T, 0.0)
+        e0.record(stream)
+        nbody.nb_predict(h, 0.0)
+        nbody.nb_force_dev(h, 0, n, bufs[0:3].data_ptr(), bufs[3:6].data_ptr(), bufs[6].data_ptr())
+        e1.record(stream)
+        host = bufs.cpu()                                  # D2H of acc, jerk, pot
+        w1 = time.perf_counter()
+        stream.synchronize()
+        after = nbody.nb_get_stats(h)
+        d = {k_: after[k_] - before[k_] for k_ in ("interactions", "force_ms", "reduce_ms",
+                                                    "predict_ms", "kernel_launches",
+                                                    "force_launches")}
+        return d["interactions"], e0.elapsed_time(e1), w1 - w0, d["kernel_launches"], d, host
+
+    bufs = torch.empty((7, n), dtype=torch.float64, device="cuda") if wl["kind"] == "force" else None
+    host_state = None
+    for k in range(args.warmup):
+        one_step(k, None)
+    if wl["kind"] == "evolve":
+        host_state = nbody.nb_get_state(h)
+    else:
+        host_state = True
+    nbody.nb_reset_stats(h)
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    tot_inter = tot_ms = tot_wall = 0.0
+    launches = 0
+    force_ms = reduce_ms = 0.0
+    force_launches = 0
+    for k in range(args.warmup, args.warmup + args.steps):
+        flush.fill_(float(k))                              # L2 flush between timed steps
+        inter, ms, wall, nl, st, host_state = one_step(k, host_state)
+        tot_inter += inter
+        tot_ms += ms
+        tot_wall += wall
+        launches += nl
+        force_ms += st["force_ms"]
+        reduce_ms += st["reduce_ms"]
+        force_launches += st["force_launches"]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    dist.barrier()
+    pairs = dist.gather_pairs(tot_inter, tot_ms / 1e3, device="cuda")
+    units, secs = aggregate(pairs)
+    wall_pairs = dist.gather_pairs(tot_inter, tot_wall, device="cuda")
+    e2e_units, e2e_secs = aggregate(wall_pairs)
+    if rank != 0:
+        sysm.close()
+        dist.close()
+        return 0
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    value = units / secs / 1e9
+    achieved = FLOPS_PER_INTERACTION * tot_inter / (force_ms / 1e3) / 1e12 if force_ms else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if variant == "f64" else "f32",
+        "data": "synthetic (seeded Plummer sphere, N-body units)",
+        "config": dict(config_of(wl, args.workload, variant),
+                       parallelism=("replicas%d" % world) if world > 1 else "single GPU"),
+        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+        "roofline": {"bound": "alu", "kernel": "k_force_tile32/k_force_jmode32 (pair force)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived; "
+                                    "FP32 is not in MEASURED_PEAKS.json)" % sm_max,
+                     "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "force_ms": force_ms, "reduce_ms": reduce_ms,
+                     "force_launches": force_launches},
+        "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8,
+                "d2h_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8},
+        "gpu_launches": launches,
+        "interactions": tot_inter,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        inter, secs_c, desc = oracle_sample(wl, p)
+        line["cpu_baseline"] = {"value": inter / secs_c / 1e9, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle", "sample": desc,
+                                "seconds": secs_c}
+    print(json.dumps(line), flush=True)
+    sysm.close()
+    dist.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * nbody.h - C ABI of libnbody.so, the GB300-native direct-summation Hermite
+ * N-body core (CUDA kernels for sm_103a).
+ *
+ * Paper: S. Portegies Zwart & J. Bedorf, "Computational Gravitational Dynamics
+ * with Modern Numerical Accelerators". The problem the calls follow is the
+ * one stated in Sect. III.A: a j-set of particles exerts a softened
+ * Newtonian force (Sect. II) on an i-set, which may be a subset of the j-set
+ * (the particles that are due at the current block time, Sect. III) or a
+ * disjoint set; a 4th-order Hermite predictor-corrector (Sect. II, VI: ph4)
+ * with individual block time steps (Sect. III) drives the evaluations.
+ *
+ * Conventions
+ *  - Every call returns an int status (NB_OK = 0 or an NB_ERR_* code). The
+ *    message of the last failure on a handle is nb_last_error(h).
+ *  - Handles are opaque. The library owns all device memory it allocates;
+ *    the caller owns every host buffer it passes, which the library only
+ *    reads or writes during the call.
+ *  - Arrays are structure-of-arrays, binary64: a vector field over n
+ *    particles (positions, velocities, accelerations, jerks) is ONE buffer
+ *    of 3*n doubles laid out x[0..n), y[0..n), z[0..n). Masses, potentials,
+ *    times and steps are n doubles. Indices are 0-based int32.
+ *  - Host-pointer calls are synchronous: they return after the result is in
+ *    the caller's buffer. *_dev calls take device pointers, run on the
+ *    handle's stream (nb_set_stream) and return without waiting.
+ *  - A handle is not thread-safe; use one handle per thread. The server
+ *    calls (nb_submit / nb_poll / nb_cancel / nb_result_release) are
+ *    thread-safe.
+ *  - No call falls back to the CPU: without a usable CUDA device nb_create
+ *    fails with NB_ERR_CUDA.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define NB_OK 0
+#define NB_ERR_ARG 1        /* invalid argument (size, NULL, range, order) */
+#define NB_ERR_OOM 2        /* device allocation failed */
+#define NB_ERR_BUDGET 3     /* request exceeds the handle's memory budget */
+#define NB_ERR_CUDA 4       /* a CUDA runtime call failed */
+#define NB_ERR_TIMEOUT 5    /* a bounded device-side wait gave up */
+#define NB_ERR_NONFINITE 6  /* non-finite input, or a force that overflowed
+                               (e.g. coincident particles with eps = 0) */
+#define NB_ERR_BUSY 7       /* server queue full */
+#define NB_ERR_NOTFOUND 8   /* unknown ticket */
+#define NB_ERR_STATE 9      /* call out of order (e.g. nb_correct with no force) */
+
+/* ---- pair-arithmetic variants (Sect. III.A: emulated vs native FP64) ---- */
+#define NB_F32 0   /* FP32 pair math, FP32 positions and sums (reported only) */
+#define NB_F32DS 1 /* FP32 pair math; double-single (hi+lo FP32) relative
+                      coordinates and double-single accumulation of acc, jerk
+                      and pot (the paper's emulated double precision for the
+                      inter-particle distance); FP64 state */
+#define NB_F64 2   /* IEEE FP64 pair math (the paper's native double path for
+                      extreme mass ratios) */
+
+/* ---- configuration ------------------------------------------------------ */
+#define NB_FLAG_TIMING 1 /* time every kernel launch with CUDA events (nb_stats) */
+
+typedef struct nb_config {
+    int n_max;           /* particle capacity of the handle, >= 1 */
+    int variant;         /* NB_F32, NB_F32DS or NB_F64 */
+    double eps;          /* Plummer softening length, >= 0 */
+    double eta;          /* Aarseth step-criterion accuracy, > 0 */
+    double eta_s;        /* initial-step parameter (dt0 = eta_s |a|/|jerk|); 0 means eta */
+    double dt_max;       /* largest block step: a power of two */
+    double dt_min;       /* smallest block step: a power of two, <= dt_max */
+    double shared_dt;    /* > 0: shared-step mode with this step; 0: block steps */
+    size_t budget_bytes; /* device-memory cap for the handle; 0 = none */
+    int device;          /* CUDA device ordinal */
+    int flags;           /* NB_FLAG_* */
+} nb_config;
+
+/* Fills cfg with: n_max 1024, NB_F32DS, eps 0, eta 0.01, eta_s 0 (= eta),
+ * dt_max 1/16, dt_min 2^-30, shared_dt 0, budget 0, device 0, flags 0. */
+void nb_config_default(nb_config *cfg);
+
+/* Counters of a handle since creation or nb_reset_stats. Kernel times are
+ * filled only with NB_FLAG_TIMING. */
+typedef struct nb_stats {
+    long long block_steps;      /* block (or shared) steps taken */
+    long long force_launches;   /* force evaluations launched */
+    double interactions;        /* sum over evaluations of N_i * N_j */
+    double force_ms;            /* pair-force kernel time (CUDA events) */
+    double reduce_ms;           /* partial-sum reduction kernel time */
+    double predict_ms;          /* j-prediction kernel time */
+    double correct_ms;          /* corrector + step kernel time */
+    double sched_ms;            /* block scheduler kernel time */
+    long long dt_min_hits;      /* corrections whose step was clamped at dt_min */
+    long long active_hist[32];  /* block steps by floor(log2(N_active)) */
+    long long kernel_launches;  /* CUDA kernels this library launched */
+} nb_stats;
+
+typedef struct nb_handle_s *nb_handle;
+
+/* Human-readable name of a status code (static storage). */
+const char *nb_status_string(int status);
+
+/* Message of the last failure on h (static or handle-owned storage; valid
+ * until the next call on h). With h == NULL: the last nb_create failure. */
+const char *nb_last_error(nb_handle h);
+
+/* Version string of the library. */
+const char *nb_version(void);
+
+/* ---- lifetime ------------------------------------------------------------
+ * nb_create allocates the device state for cfg->n_max particles on
+ * cfg->device. Rejects eps < 0, eta <= 0, dt_max or dt_min not a power of
+ * two, dt_min > dt_max, shared_dt < 0, n_max < 1, an unknown variant
+ * (NB_ERR_ARG), and a state larger than budget_bytes (NB_ERR_BUDGET).
+ * nb_destroy frees everything; it is a no-op on NULL. */
+int nb_create(const nb_config *cfg, nb_handle *out);
+int nb_destroy(nb_handle h);
+
+/* Stream for all later device work of h (a cudaStream_t; NULL = the
+ * library's own stream). The caller keeps the stream alive. */
+int nb_set_stream(nb_handle h, void *stream);
+
+/* ---- state ----------------------------------------------------------------
+ * nb_set_particles copies n particles (m[n], pos[3n], vel[3n]) and sets every
+ * own time t_i = t0. acc, jerk and steps are left unset until nb_init (or the
+ * first nb_step, which calls it). Rejects n < 1 or n > n_max (NB_ERR_ARG),
+ * negative masses (NB_ERR_ARG) and non-finite values (NB_ERR_NONFINITE). */
+int nb_set_particles(nb_handle h, int n, const double *m, const double *pos,
+                     const double *vel, double t0);
+
+/* Evaluate acc and jerk of every particle at its current (common) time and
+ * assign the initial block steps dt0 = eta_s |a|/|jerk| (quantized), or the
+ * shared step. One full N*N evaluation. */
+int nb_init(nb_handle h);
+
+/* Copy out masses and the current (corrected, not predicted) positions and
+ * velocities. Any pointer may be NULL to skip it. */
+int nb_get_particles(nb_handle h, double *m, double *pos, double *vel);
+
+/* Full integrator state for checkpoint / resume: m[n], pos[3n], vel[3n],
+ * acc[3n], jerk[3n], own time t[n], own step dt[n]. nb_set_state restores a
+ * state taken by nb_get_state (same n <= n_max), after which nb_step resumes
+ * bit-identically. Any output pointer of nb_get_state may be NULL. */
+int nb_get_state(nb_handle h, int *n, double *m, double *pos, double *vel,
+                 double *acc, double *jerk, double *t, double *dt);
+int nb_set_state(nb_handle h, int n, const double *m, const double *pos,
+                 const double *vel, const double *acc, const double *jerk,
+                 const double *t, const double *dt);
+
+/* ---- the hot path ----------------------------------------------------------
+ * nb_predict (Sect. III.A, prediction of the j particles): every particle is
+ * moved by its Taylor series from its own time t_i to time t,
+ *   xp = x + v d + a d^2/2 + jerk d^3/6,  vp = v + a d + jerk d^2/2,  d = t - t_i.
+ * Rejects t < t_i for any particle (NB_ERR_ARG). */
+int nb_predict(nb_handle h, double t);
+
+/* nb_force (Sect. III.A): acc, jerk and pot of the i-particles idx[0..n_i)
+ * (members of the j-set; idx == NULL means all particles in order) from
+ * every predicted j-particle, the pair i == j left out:
+ *   r = x_j - x_i, v = v_j - v_i, s2 = |r|^2 + eps^2,
+ *   acc_i  += m_j r / s2^(3/2)
+ *   jerk_i += m_j (v - 3 (r.v) r / s2) / s2^(3/2)
+ *   pot_i  -= m_j / s2^(1/2).
+ * Outputs: acc[3 n_i], jerk[3 n_i], pot[n_i] (any may be NULL), indexed by
+ * position k in idx. Duplicate indices are allowed. Requires a preceding
+ * nb_predict (NB_ERR_STATE). Coincident particles with eps = 0 give
+ * NB_ERR_NONFINITE. n_i = 0 is a no-op. */
+int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk,
+             double *pot);
+
+/* nb_force with device buffers (idx_dev: n_i int32 or NULL; outputs as
+ * nb_force but device memory, any may be NULL), asynchronous on the handle's
+ * stream. Errors found on the device (non-finite results) are reported by
+ * the next synchronous call. */
+int nb_force_dev(nb_handle h, const int *idx_dev, int n_i, double *acc_dev,
+                 double *jerk_dev, double *pot_dev);
+
+/* nb_force_ext (Sect. III.A, disjoint i-set): the force of the predicted
+ * j-set on n_i external particles (pos[3 n_i], vel[3 n_i]); no pair is left
+ * out. Outputs as nb_force. */
+int nb_force_ext(nb_handle h, int n_i, const double *pos, const double *vel,
+                 double *acc, double *jerk, double *pot);
+
+/* nb_correct (4th-order Hermite corrector, Sect. II/VI): advance the
+ * particles of the last nb_force (idx, n_i must repeat that call's list,
+ * without duplicates; NB_ERR_ARG otherwise) from their own times to t using
+ * their predicted state and the new acc/jerk, then give each a new step:
+ * Aarseth's criterion quantized to a power of two in [dt_min, dt_max] that
+ * divides t (block mode), or the shared step. */
+int nb_correct(nb_handle h, const int *idx, int n_i, double t);
+
+/* nb_step: block-step Hermite loop (Sect. III, III.A) until every particle
+ * reaches t_end (t_end must be a multiple of the current steps, e.g. of
+ * dt_max). Each block step: t_next = min_i(t_i + dt_i); the due particles
+ * (t_i + dt_i == t_next, ascending index) are the i-set; predict all j,
+ * force on the i-set, correct. Calls nb_init first if needed. st (may be
+ * NULL) receives the counters of this call only. */
+int nb_step(nb_handle h, double t_end, nb_stats *st);
+
+/* Kinetic and potential energy of the synchronised system (all t_i equal,
+ * else NB_ERR_STATE): K = sum m v^2/2, W = sum m_i pot_i / 2 with pot from an
+ * FP64 evaluation at the current positions. */
+int nb_energy(nb_handle h, double *kin, double *pot);
+
+/* Counters accumulated since creation or the last reset. */
+int nb_get_stats(nb_handle h, nb_stats *st);
+int nb_reset_stats(nb_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

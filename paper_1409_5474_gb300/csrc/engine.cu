@@ -1,0 +1,949 @@
+// C ABI of the single-system engine (nbody.h): handles, device state, the
+// block-step Hermite loop and the host <-> device boundary.
+//
+// Device state of a handle is one slab of FP64 structure-of-arrays with row
+// stride ld = capacity rounded up to 64 (plus 64 doubles of padding, so that
+// bulk copies rounded up to 16 bytes stay inside the slab):
+//   m[ld], pos/vel/acc/jerk[3][ld], t[ld], dt[ld], pos_p/vel_p[3][ld],
+//   f_acc/f_jerk[3][ld], f_pot[ld], DS j-records rec[ld][3] (float4), act[ld].
+// The block-step loop (paper Sect. III, III.A) runs one scheduler kernel per
+// block step, reads t_next and N_active from a mapped-memory mailbox, and
+// launches predictor, force (+ reduction) and corrector for that N_active.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nb;
+
+namespace {
+
+std::mutex g_create_mu;
+std::string g_create_msg;
+
+bool is_pow2(double x)
+{
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    int e;
+    double f = std::frexp(x, &e);
+    return f == 0.5;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Timing: pairs of events recorded around launches, harvested at sync points.
+enum TimerKind { T_FORCE = 0, T_REDUCE, T_PREDICT, T_CORRECT, T_SCHED, T_NKIND };
+
+struct Timer {
+    std::vector<cudaEvent_t> free_ev;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double ms[T_NKIND] = {0, 0, 0, 0, 0};
+
+    cudaEvent_t get()
+    {
+        if (!free_ev.empty()) {
+            cudaEvent_t e = free_ev.back();
+            free_ev.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void add(int kind, cudaEvent_t a, cudaEvent_t b) { pending.push_back({kind, a, b}); }
+    void harvest()
+    {
+        for (auto &p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.kind] += t;
+            free_ev.push_back(p.a);
+            free_ev.push_back(p.b);
+        }
+        pending.clear();
+        cudaGetLastError();
+    }
+    ~Timer()
+    {
+        for (auto &p : pending) {
+            free_ev.push_back(p.a);
+            free_ev.push_back(p.b);
+        }
+        for (auto e : free_ev) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct nb_handle_s {
+    nb_config cfg{};
+    int dev = 0;
+    int num_sms = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+
+    int n = 0;
+    int cap = 0;
+    long long ld = 0;
+    void *slab = nullptr;
+    size_t slab_bytes = 0;
+    double *m = nullptr, *pos = nullptr, *vel = nullptr, *acc = nullptr, *jerk = nullptr;
+    double *t = nullptr, *dt = nullptr, *pos_p = nullptr, *vel_p = nullptr;
+    double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
+    float4 *rec = nullptr;
+    int *act = nullptr;
+
+    // growable scratch
+    double *part = nullptr;
+    size_t part_cap = 0;  // doubles
+    double *io = nullptr; // host-API staging: [7][n_i] outputs, ext inputs
+    size_t io_cap = 0;    // doubles
+    int *d_idx = nullptr;
+    size_t idx_cap = 0;   // ints
+    float4 *ext_rec = nullptr;
+    size_t ext_rec_cap = 0;  // records
+
+    unsigned *d_err = nullptr;
+    unsigned long long *d_dtmin = nullptr;
+    double *d_energy = nullptr;
+    Mailbox *mail_h = nullptr, *mail_d = nullptr;
+
+    size_t bytes = 0;  // device bytes held
+
+    bool have_particles = false, initialised = false, predicted = false;
+    double t_pred = 0.0;
+    int last_force_n = -1;
+    std::vector<int> last_idx;
+    bool last_force_all = false;
+
+    nb_stats stats{};
+    Timer timer;
+    std::string msg;
+};
+
+namespace {
+
+int fail(nb_handle h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->msg = buf;
+    else {
+        std::lock_guard<std::mutex> lk(g_create_mu);
+        g_create_msg = buf;
+    }
+    return code;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), NB_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+StateDev state_of(nb_handle h)
+{
+    StateDev s;
+    s.n = h->n;
+    s.ld = h->ld;
+    s.m = h->m;
+    s.pos = h->pos;
+    s.vel = h->vel;
+    s.acc = h->acc;
+    s.jerk = h->jerk;
+    s.t = h->t;
+    s.dt = h->dt;
+    s.pos_p = h->pos_p;
+    s.vel_p = h->vel_p;
+    s.rec = h->rec;
+    return s;
+}
+
+StepParams params_of(nb_handle h)
+{
+    StepParams p;
+    p.eta = h->cfg.eta;
+    p.eta_s = h->cfg.eta_s > 0.0 ? h->cfg.eta_s : h->cfg.eta;
+    p.dt_min = h->cfg.dt_min;
+    p.dt_max = h->cfg.dt_max;
+    p.shared_dt = h->cfg.shared_dt;
+    return p;
+}
+
+JSet jset_of(nb_handle h)
+{
+    JSet j;
+    j.n = h->n;
+    j.rec32 = h->rec;
+    j.pos64 = h->pos_p;
+    j.vel64 = h->vel_p;
+    j.m64 = h->m;
+    j.ld = h->ld;
+    return j;
+}
+
+ISet members_of(nb_handle h, const int *idx_dev, int n_i)
+{
+    ISet is;
+    is.n = n_i;
+    is.idx = idx_dev;
+    is.member = true;
+    is.rec32 = h->rec;
+    is.pos64 = h->pos_p;
+    is.vel64 = h->vel_p;
+    is.m64 = h->m;
+    is.ld64 = h->ld;
+    is.nj = h->n;
+    return is;
+}
+
+bool timing(nb_handle h) { return (h->cfg.flags & NB_FLAG_TIMING) != 0; }
+
+// Grow a device buffer (synchronising first so no kernel still uses it).
+template <typename T>
+int grow(nb_handle h, T **buf, size_t *cap, size_t need)
+{
+    if (need <= *cap) return NB_OK;
+    size_t want = std::max(need, *cap * 2);
+    const size_t add = want * sizeof(T) - *cap * sizeof(T);
+    if (h->cfg.budget_bytes && h->bytes + add > h->cfg.budget_bytes) {
+        want = need;
+        const size_t add2 = want * sizeof(T) - *cap * sizeof(T);
+        if (h->bytes + add2 > h->cfg.budget_bytes)
+            return fail(h, NB_ERR_BUDGET, "scratch of %zu bytes exceeds the budget of %zu bytes",
+                        want * sizeof(T), h->cfg.budget_bytes);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (*buf) {
+        cudaFree(*buf);
+        h->bytes -= *cap * sizeof(T);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    T *p = nullptr;
+    if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, NB_ERR_OOM, "cudaMalloc of %zu bytes failed", want * sizeof(T));
+    }
+    *buf = p;
+    *cap = want;
+    h->bytes += want * sizeof(T);
+    return NB_OK;
+}
+
+// Read and clear the device error word; translate it into a status.
+int check_err(nb_handle h)
+{
+    unsigned e = 0;
+    CK(h, cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (timing(h)) h->timer.harvest();
+    if (!e) return NB_OK;
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
+    if (e & DERR_TIMEOUT) return fail(h, NB_ERR_TIMEOUT, "a device-side wait timed out");
+    if (e & DERR_BADINDEX) return fail(h, NB_ERR_ARG, "an i-set index is outside [0, n)");
+    if (e & DERR_BACKWARD)
+        return fail(h, NB_ERR_ARG, "prediction time is before some particle's own time");
+    return fail(h, NB_ERR_NONFINITE,
+                "non-finite force or state (coincident particles with eps = 0?)");
+}
+
+int ensure_part(nb_handle h, const ForcePlan &p, int n_i)
+{
+    return grow(h, &h->part, &h->part_cap, std::max<size_t>(plan_partial_doubles(p, n_i), 1));
+}
+
+// Force on an i-set into out; plans, grows scratch, records timers.
+int run_force(nb_handle h, int variant, const ISet &is, Out3 out)
+{
+    if (is.n <= 0) return NB_OK;
+    ForcePlan p = plan_force(variant, is.n, h->n, h->num_sms);
+    int rc = ensure_part(h, p, is.n);
+    if (rc) return rc;
+    cudaEvent_t ev[4];
+    cudaEvent_t *evp = nullptr;
+    if (timing(h)) {
+        for (auto &e : ev) e = h->timer.get();
+        evp = ev;
+    }
+    const double eps2 = h->cfg.eps * h->cfg.eps;
+    CK(h, launch_force(variant, p, jset_of(h), is, eps2, h->part, out, h->d_err, h->stream, evp));
+    h->stats.kernel_launches += (p.nsplit > 1) ? 2 : 1;
+    if (evp) {
+        h->timer.add(T_FORCE, ev[0], ev[1]);
+        h->timer.add(T_REDUCE, ev[2], ev[3]);
+    }
+    h->stats.force_launches++;
+    h->stats.interactions += (double)is.n * (double)h->n;
+    return NB_OK;
+}
+
+template <typename F>
+int timed(nb_handle h, int kind, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (timing(h)) {
+        a = h->timer.get();
+        b = h->timer.get();
+        cudaEventRecord(a, h->stream);
+    }
+    cudaError_t e = launch();
+    h->stats.kernel_launches++;
+    if (timing(h)) {
+        cudaEventRecord(b, h->stream);
+        h->timer.add(kind, a, b);
+    }
+    if (e != cudaSuccess) return fail(h, NB_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return NB_OK;
+}
+
+int predict_to(nb_handle h, double t)
+{
+    const bool rec = h->cfg.variant != NB_F64;
+    StateDev s = state_of(h);
+    int rc = timed(h, T_PREDICT, [&] { return launch_predict(s, t, rec, h->d_err, h->stream); });
+    if (rc) return rc;
+    h->predicted = true;
+    h->t_pred = t;
+    return NB_OK;
+}
+
+int do_init(nb_handle h)
+{
+    // all own times are equal at set-up: predict with d = 0 builds the records
+    double t0 = 0.0;
+    CK(h, cudaMemcpyAsync(&t0, h->t, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    int rc = predict_to(h, t0);
+    if (rc) return rc;
+    Out3 f{h->f_acc, h->f_jerk, h->f_pot, h->ld};
+    rc = run_force(h, h->cfg.variant, members_of(h, nullptr, h->n), f);
+    if (rc) return rc;
+    StateDev s = state_of(h);
+    StepParams p = params_of(h);
+    CK(h, launch_init_steps(s, f, p, h->d_err, h->stream));
+    h->stats.kernel_launches++;
+    rc = check_err(h);
+    if (rc) return rc;
+    h->initialised = true;
+    h->predicted = false;
+    return NB_OK;
+}
+
+void sync_stats_counters(nb_handle h)
+{
+    unsigned long long hits = 0;
+    if (cudaMemcpyAsync(&hits, h->d_dtmin, sizeof hits, cudaMemcpyDeviceToHost, h->stream) ==
+            cudaSuccess &&
+        cudaStreamSynchronize(h->stream) == cudaSuccess)
+        h->stats.dt_min_hits = (long long)hits;
+    if (timing(h)) {
+        h->timer.harvest();
+        h->stats.force_ms = h->timer.ms[T_FORCE];
+        h->stats.reduce_ms = h->timer.ms[T_REDUCE];
+        h->stats.predict_ms = h->timer.ms[T_PREDICT];
+        h->stats.correct_ms = h->timer.ms[T_CORRECT];
+        h->stats.sched_ms = h->timer.ms[T_SCHED];
+    }
+}
+
+int validate_host(nb_handle h, int n, const double *m, const double *pos, const double *vel)
+{
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(m[i])) return fail(h, NB_ERR_NONFINITE, "mass %d is not finite", i);
+        if (m[i] < 0.0) return fail(h, NB_ERR_ARG, "mass %d is negative", i);
+    }
+    for (long long q = 0; q < 3LL * n; ++q) {
+        if (!std::isfinite(pos[q]) || !std::isfinite(vel[q]))
+            return fail(h, NB_ERR_NONFINITE, "position/velocity entry %lld is not finite", q);
+    }
+    return NB_OK;
+}
+
+// Copy a host [rows][n] block into device rows of stride ld.
+cudaError_t h2d_rows(double *dst, long long ld, const double *src, int n, int rows,
+                     cudaStream_t st)
+{
+    return cudaMemcpy2DAsync(dst, ld * sizeof(double), src, n * sizeof(double), n * sizeof(double),
+                             rows, cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t d2h_rows(double *dst, const double *src, long long ld, int n, int rows,
+                     cudaStream_t st)
+{
+    return cudaMemcpy2DAsync(dst, n * sizeof(double), src, ld * sizeof(double), n * sizeof(double),
+                             rows, cudaMemcpyDeviceToHost, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void nb_config_default(nb_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->n_max = 1024;
+    cfg->variant = NB_F32DS;
+    cfg->eps = 0.0;
+    cfg->eta = 0.01;
+    cfg->eta_s = 0.0;
+    cfg->dt_max = 1.0 / 16;
+    cfg->dt_min = std::ldexp(1.0, -30);
+    cfg->shared_dt = 0.0;
+    cfg->budget_bytes = 0;
+    cfg->device = 0;
+    cfg->flags = 0;
+}
+
+const char *nb_status_string(int status)
+{
+    switch (status) {
+    case NB_OK: return "NB_OK";
+    case NB_ERR_ARG: return "NB_ERR_ARG";
+    case NB_ERR_OOM: return "NB_ERR_OOM";
+    case NB_ERR_BUDGET: return "NB_ERR_BUDGET";
+    case NB_ERR_CUDA: return "NB_ERR_CUDA";
+    case NB_ERR_TIMEOUT: return "NB_ERR_TIMEOUT";
+    case NB_ERR_NONFINITE: return "NB_ERR_NONFINITE";
+    case NB_ERR_BUSY: return "NB_ERR_BUSY";
+    case NB_ERR_NOTFOUND: return "NB_ERR_NOTFOUND";
+    case NB_ERR_STATE: return "NB_ERR_STATE";
+    default: return "NB_ERR_UNKNOWN";
+    }
+}
+
+const char *nb_last_error(nb_handle h)
+{
+    if (h) return h->msg.c_str();
+    std::lock_guard<std::mutex> lk(g_create_mu);
+    return g_create_msg.c_str();
+}
+
+const char *nb_version(void) { return "nbody-gb300 0.1 (sm_103a)"; }
+
+int nb_create(const nb_config *cfg, nb_handle *out)
+{
+    if (!cfg || !out) return fail(nullptr, NB_ERR_ARG, "cfg and out must not be NULL");
+    *out = nullptr;
+    if (cfg->n_max < 1) return fail(nullptr, NB_ERR_ARG, "n_max must be >= 1");
+    if (cfg->variant < NB_F32 || cfg->variant > NB_F64)
+        return fail(nullptr, NB_ERR_ARG, "unknown variant %d", cfg->variant);
+    if (!(cfg->eps >= 0.0) || !std::isfinite(cfg->eps))
+        return fail(nullptr, NB_ERR_ARG, "eps must be finite and >= 0");
+    if (!(cfg->eta > 0.0) || !std::isfinite(cfg->eta))
+        return fail(nullptr, NB_ERR_ARG, "eta must be > 0");
+    if (cfg->eta_s < 0.0) return fail(nullptr, NB_ERR_ARG, "eta_s must be >= 0");
+    if (!is_pow2(cfg->dt_max)) return fail(nullptr, NB_ERR_ARG, "dt_max must be a power of two");
+    if (!is_pow2(cfg->dt_min) || cfg->dt_min > cfg->dt_max)
+        return fail(nullptr, NB_ERR_ARG, "dt_min must be a power of two <= dt_max");
+    if (!(cfg->shared_dt >= 0.0) || !std::isfinite(cfg->shared_dt))
+        return fail(nullptr, NB_ERR_ARG, "shared_dt must be finite and >= 0");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, NB_ERR_CUDA, "no CUDA device available");
+    }
+    if (cfg->device < 0 || cfg->device >= ndev)
+        return fail(nullptr, NB_ERR_ARG, "device %d out of range (%d devices)", cfg->device, ndev);
+
+    nb_handle h = new nb_handle_s();
+    h->cfg = *cfg;
+    h->dev = cfg->device;
+    h->cap = cfg->n_max;
+    h->ld = ((long long)cfg->n_max + 63) / 64 * 64;
+
+    auto bail = [&](int code) {
+        nb_destroy(h);
+        return code;
+    };
+    if (cudaSetDevice(h->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, NB_ERR_CUDA, "cudaSetDevice(%d) failed", cfg->device);
+    }
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev);
+
+    const size_t row = (size_t)h->ld;
+    const size_t vec = align256((3 * row + 64) * sizeof(double));
+    const size_t sca = align256((row + 64) * sizeof(double));
+    const size_t recb = align256(row * DS_REC * sizeof(float4));
+    const size_t actb = align256(row * sizeof(int));
+    h->slab_bytes = 6 * vec + 4 * sca + 2 * vec + recb + actb;  // see layout in the file header
+    const size_t small = 256 * 3;
+    if (cfg->budget_bytes && h->slab_bytes + small > cfg->budget_bytes) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "state of %zu bytes exceeds the budget of %zu bytes",
+                      h->slab_bytes, cfg->budget_bytes);
+        delete h;
+        return fail(nullptr, NB_ERR_BUDGET, "%s", msg);
+    }
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, NB_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    h->stream = h->own_stream;
+    if (cudaMalloc(&h->slab, h->slab_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        int code = fail(nullptr, NB_ERR_OOM, "cudaMalloc of %zu bytes failed", h->slab_bytes);
+        bail(code);
+        return code;
+    }
+    h->bytes = h->slab_bytes;
+    char *p = static_cast<char *>(h->slab);
+    auto take = [&](size_t b) {
+        char *q = p;
+        p += b;
+        return q;
+    };
+    h->pos = (double *)take(vec);
+    h->vel = (double *)take(vec);
+    h->acc = (double *)take(vec);
+    h->jerk = (double *)take(vec);
+    h->pos_p = (double *)take(vec);
+    h->vel_p = (double *)take(vec);
+    h->m = (double *)take(sca);
+    h->t = (double *)take(sca);
+    h->dt = (double *)take(sca);
+    h->f_pot = (double *)take(sca);
+    h->f_acc = (double *)take(vec);
+    h->f_jerk = (double *)take(vec);
+    h->rec = (float4 *)take(recb);
+    h->act = (int *)take(actb);
+    if (cudaMemsetAsync(h->slab, 0, h->slab_bytes, h->stream) != cudaSuccess ||
+        cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMalloc(&h->d_dtmin, 256) != cudaSuccess ||
+        cudaMalloc(&h->d_energy, 256) != cudaSuccess ||
+        cudaMemsetAsync(h->d_err, 0, 256, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->d_dtmin, 0, 256, h->stream) != cudaSuccess ||
+        cudaHostAlloc(&h->mail_h, sizeof(Mailbox), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&h->mail_d, h->mail_h, 0) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        int code = fail(nullptr, NB_ERR_CUDA, "device set-up failed");
+        bail(code);
+        return code;
+    }
+    h->bytes += 3 * 256;
+    *out = h;
+    return NB_OK;
+}
+
+int nb_destroy(nb_handle h)
+{
+    if (!h) return NB_OK;
+    cudaSetDevice(h->dev);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->timer.harvest();
+    cudaFree(h->slab);
+    cudaFree(h->part);
+    cudaFree(h->io);
+    cudaFree(h->d_idx);
+    cudaFree(h->ext_rec);
+    cudaFree(h->d_err);
+    cudaFree(h->d_dtmin);
+    cudaFree(h->d_energy);
+    if (h->mail_h) cudaFreeHost(h->mail_h);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    cudaGetLastError();
+    delete h;
+    return NB_OK;
+}
+
+int nb_set_stream(nb_handle h, void *stream)
+{
+    if (!h) return NB_ERR_ARG;
+    cudaSetDevice(h->dev);
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    return NB_OK;
+}
+
+int nb_set_particles(nb_handle h, int n, const double *m, const double *pos, const double *vel,
+                     double t0)
+{
+    if (!h) return NB_ERR_ARG;
+    if (n < 1 || n > h->cap) return fail(h, NB_ERR_ARG, "n = %d outside [1, n_max = %d]", n, h->cap);
+    if (!m || !pos || !vel) return fail(h, NB_ERR_ARG, "m, pos and vel must not be NULL");
+    if (!std::isfinite(t0)) return fail(h, NB_ERR_NONFINITE, "t0 is not finite");
+    int rc = validate_host(h, n, m, pos, vel);
+    if (rc) return rc;
+    cudaSetDevice(h->dev);
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->n = n;
+    CK(h, cudaMemcpyAsync(h->m, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, h2d_rows(h->pos, h->ld, pos, n, 3, h->stream));
+    CK(h, h2d_rows(h->vel, h->ld, vel, n, 3, h->stream));
+    std::vector<double> tt(n, t0);
+    CK(h, cudaMemcpyAsync(h->t, tt.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->dt, 0, n * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->acc, 0, 3 * h->ld * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->jerk, 0, 3 * h->ld * sizeof(double), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->have_particles = true;
+    h->initialised = false;
+    h->predicted = false;
+    h->last_force_n = -1;
+    return NB_OK;
+}
+
+int nb_init(nb_handle h)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(h->dev);
+    return do_init(h);
+}
+
+int nb_get_particles(nb_handle h, double *m, double *pos, double *vel)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(h->dev);
+    const int n = h->n;
+    if (m) CK(h, cudaMemcpyAsync(m, h->m, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (pos) CK(h, d2h_rows(pos, h->pos, h->ld, n, 3, h->stream));
+    if (vel) CK(h, d2h_rows(vel, h->vel, h->ld, n, 3, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return NB_OK;
+}
+
+int nb_get_state(nb_handle h, int *n_out, double *m, double *pos, double *vel, double *acc,
+                 double *jerk, double *t, double *dt)
+{
+    if (!h) return NB_ERR_ARG;
+    if (n_out) *n_out = h->n;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(h->dev);
+    const int n = h->n;
+    if (m) CK(h, cudaMemcpyAsync(m, h->m, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (pos) CK(h, d2h_rows(pos, h->pos, h->ld, n, 3, h->stream));
+    if (vel) CK(h, d2h_rows(vel, h->vel, h->ld, n, 3, h->stream));
+    if (acc) CK(h, d2h_rows(acc, h->acc, h->ld, n, 3, h->stream));
+    if (jerk) CK(h, d2h_rows(jerk, h->jerk, h->ld, n, 3, h->stream));
+    if (t) CK(h, cudaMemcpyAsync(t, h->t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (dt) CK(h, cudaMemcpyAsync(dt, h->dt, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return NB_OK;
+}
+
+int nb_set_state(nb_handle h, int n, const double *m, const double *pos, const double *vel,
+                 const double *acc, const double *jerk, const double *t, const double *dt)
+{
+    if (!h) return NB_ERR_ARG;
+    if (n < 1 || n > h->cap) return fail(h, NB_ERR_ARG, "n = %d outside [1, n_max = %d]", n, h->cap);
+    if (!m || !pos || !vel || !acc || !jerk || !t || !dt)
+        return fail(h, NB_ERR_ARG, "nb_set_state needs every array");
+    int rc = validate_host(h, n, m, pos, vel);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(t[i]) || !is_pow2(dt[i]))
+            return fail(h, NB_ERR_ARG, "particle %d: t must be finite and dt a power of two", i);
+    }
+    cudaSetDevice(h->dev);
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->n = n;
+    CK(h, cudaMemcpyAsync(h->m, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, h2d_rows(h->pos, h->ld, pos, n, 3, h->stream));
+    CK(h, h2d_rows(h->vel, h->ld, vel, n, 3, h->stream));
+    CK(h, h2d_rows(h->acc, h->ld, acc, n, 3, h->stream));
+    CK(h, h2d_rows(h->jerk, h->ld, jerk, n, 3, h->stream));
+    CK(h, cudaMemcpyAsync(h->t, t, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->dt, dt, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->have_particles = true;
+    h->initialised = true;
+    h->predicted = false;
+    h->last_force_n = -1;
+    return NB_OK;
+}
+
+int nb_predict(nb_handle h, double t)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    if (!std::isfinite(t)) return fail(h, NB_ERR_ARG, "t is not finite");
+    cudaSetDevice(h->dev);
+    int rc = predict_to(h, t);
+    if (rc) return rc;
+    rc = check_err(h);
+    if (rc) h->predicted = false;
+    return rc;
+}
+
+int nb_force_dev(nb_handle h, const int *idx_dev, int n_i, double *acc_dev, double *jerk_dev,
+                 double *pot_dev)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->predicted) return fail(h, NB_ERR_STATE, "nb_force needs a preceding nb_predict");
+    if (n_i < 0) return fail(h, NB_ERR_ARG, "n_i < 0");
+    if (!idx_dev && n_i > h->n) return fail(h, NB_ERR_ARG, "n_i > n with idx == NULL");
+    if (n_i == 0) return NB_OK;
+    cudaSetDevice(h->dev);
+    Out3 out{acc_dev, jerk_dev, pot_dev, n_i};
+    h->last_force_n = -1;  // device buffers: nb_correct cannot use them
+    return run_force(h, h->cfg.variant, members_of(h, idx_dev, n_i), out);
+}
+
+int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, double *pot)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->predicted) return fail(h, NB_ERR_STATE, "nb_force needs a preceding nb_predict");
+    if (n_i < 0) return fail(h, NB_ERR_ARG, "n_i < 0");
+    if (!idx && n_i > h->n) return fail(h, NB_ERR_ARG, "n_i > n with idx == NULL");
+    if (idx) {
+        for (int k = 0; k < n_i; ++k)
+            if (idx[k] < 0 || idx[k] >= h->n)
+                return fail(h, NB_ERR_ARG, "idx[%d] = %d outside [0, %d)", k, idx[k], h->n);
+    }
+    h->last_force_n = -1;
+    if (n_i == 0) return NB_OK;
+    cudaSetDevice(h->dev);
+    int rc = grow(h, &h->io, &h->io_cap, 7 * (size_t)n_i);
+    if (rc) return rc;
+    const int *idx_dev = nullptr;
+    if (idx) {
+        rc = grow(h, &h->d_idx, &h->idx_cap, (size_t)n_i);
+        if (rc) return rc;
+        CK(h, cudaMemcpyAsync(h->d_idx, idx, n_i * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        idx_dev = h->d_idx;
+    }
+    Out3 out{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i, n_i};
+    rc = run_force(h, h->cfg.variant, members_of(h, idx_dev, n_i), out);
+    if (rc) return rc;
+    std::vector<double> buf(7 * (size_t)n_i);
+    CK(h, cudaMemcpyAsync(buf.data(), h->io, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    rc = check_err(h);
+    if (rc) return rc;
+    if (acc) std::memcpy(acc, buf.data(), 3 * n_i * sizeof(double));
+    if (jerk) std::memcpy(jerk, buf.data() + 3 * (size_t)n_i, 3 * n_i * sizeof(double));
+    if (pot) std::memcpy(pot, buf.data() + 6 * (size_t)n_i, n_i * sizeof(double));
+    h->last_force_n = n_i;
+    h->last_force_all = (idx == nullptr);
+    if (idx)
+        h->last_idx.assign(idx, idx + n_i);
+    else
+        h->last_idx.clear();
+    return NB_OK;
+}
+
+int nb_force_ext(nb_handle h, int n_i, const double *pos, const double *vel, double *acc,
+                 double *jerk, double *pot)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->predicted) return fail(h, NB_ERR_STATE, "nb_force_ext needs a preceding nb_predict");
+    if (n_i < 0 || (n_i > 0 && (!pos || !vel)))
+        return fail(h, NB_ERR_ARG, "n_i < 0 or NULL pos/vel");
+    for (long long q = 0; q < 3LL * n_i; ++q)
+        if (!std::isfinite(pos[q]) || !std::isfinite(vel[q]))
+            return fail(h, NB_ERR_NONFINITE, "external position/velocity %lld is not finite", q);
+    if (n_i == 0) return NB_OK;
+    cudaSetDevice(h->dev);
+    // io layout: [7][n_i] outputs, then [6][n_i] inputs (pos rows, vel rows)
+    int rc = grow(h, &h->io, &h->io_cap, 13 * (size_t)n_i);
+    if (rc) return rc;
+    double *in_pos = h->io + 7 * (size_t)n_i;
+    double *in_vel = h->io + 10 * (size_t)n_i;
+    CK(h, cudaMemcpyAsync(in_pos, pos, 3 * n_i * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(in_vel, vel, 3 * n_i * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    ISet is{};
+    is.n = n_i;
+    is.idx = nullptr;
+    is.member = false;
+    is.pos64 = in_pos;
+    is.vel64 = in_vel;
+    is.m64 = nullptr;
+    is.ld64 = n_i;
+    is.nj = h->n;
+    if (h->cfg.variant != NB_F64) {
+        rc = grow(h, &h->ext_rec, &h->ext_rec_cap, (size_t)n_i * DS_REC);
+        if (rc) return rc;
+        CK(h, launch_make_rec(n_i, in_pos, in_vel, n_i, h->ext_rec, h->stream));
+        is.rec32 = h->ext_rec;
+    }
+    Out3 out{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i, n_i};
+    rc = run_force(h, h->cfg.variant, is, out);
+    if (rc) return rc;
+    std::vector<double> buf(7 * (size_t)n_i);
+    CK(h, cudaMemcpyAsync(buf.data(), h->io, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    rc = check_err(h);
+    if (rc) return rc;
+    if (acc) std::memcpy(acc, buf.data(), 3 * n_i * sizeof(double));
+    if (jerk) std::memcpy(jerk, buf.data() + 3 * (size_t)n_i, 3 * n_i * sizeof(double));
+    if (pot) std::memcpy(pot, buf.data() + 6 * (size_t)n_i, n_i * sizeof(double));
+    h->last_force_n = -1;
+    return NB_OK;
+}
+
+int nb_correct(nb_handle h, const int *idx, int n_i, double t)
+{
+    if (!h) return NB_ERR_ARG;
+    if (h->last_force_n < 0 || !h->predicted)
+        return fail(h, NB_ERR_STATE, "nb_correct needs a preceding host nb_force");
+    if (n_i != h->last_force_n) return fail(h, NB_ERR_ARG, "idx must repeat the last nb_force list");
+    if (!std::isfinite(t) || t != h->t_pred)
+        return fail(h, NB_ERR_ARG, "t must equal the prediction time of the last nb_predict");
+    if ((idx == nullptr) != h->last_force_all)
+        return fail(h, NB_ERR_ARG, "idx must repeat the last nb_force list");
+    if (idx) {
+        if (!std::equal(idx, idx + n_i, h->last_idx.begin()))
+            return fail(h, NB_ERR_ARG, "idx must repeat the last nb_force list");
+        std::vector<char> seen(h->n, 0);
+        for (int k = 0; k < n_i; ++k) {
+            if (seen[idx[k]]) return fail(h, NB_ERR_ARG, "duplicate index %d in nb_correct", idx[k]);
+            seen[idx[k]] = 1;
+        }
+    }
+    if (n_i == 0) return NB_OK;
+    cudaSetDevice(h->dev);
+    Out3 f{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i, n_i};
+    StateDev s = state_of(h);
+    StepParams p = params_of(h);
+    int rc = timed(h, T_CORRECT, [&] {
+        return launch_correct(s, idx ? h->d_idx : nullptr, n_i, t, f, p, h->d_err, h->d_dtmin,
+                              h->stream);
+    });
+    if (rc) return rc;
+    h->predicted = false;
+    h->last_force_n = -1;
+    h->initialised = true;
+    return check_err(h);
+}
+
+int nb_step(nb_handle h, double t_end, nb_stats *st)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    if (!std::isfinite(t_end)) return fail(h, NB_ERR_ARG, "t_end is not finite");
+    cudaSetDevice(h->dev);
+    sync_stats_counters(h);
+    const nb_stats before = h->stats;
+    int rc;
+    if (!h->initialised) {
+        rc = do_init(h);
+        if (rc) return rc;
+    }
+    StateDev s = state_of(h);
+    StepParams prm = params_of(h);
+    const bool rec = h->cfg.variant != NB_F64;
+    Out3 f{h->f_acc, h->f_jerk, h->f_pot, h->ld};
+    volatile Mailbox *mb = h->mail_h;
+    for (;;) {
+        rc = timed(h, T_SCHED, [&] { return launch_sched(s, h->act, h->mail_d, h->stream); });
+        if (rc) return rc;
+        CK(h, cudaStreamSynchronize(h->stream));
+        const double t_next = mb->t_next;
+        const int na = mb->n_active;
+        if (!(t_next <= t_end)) break;
+        rc = timed(h, T_PREDICT, [&] { return launch_predict(s, t_next, rec, h->d_err, h->stream); });
+        if (rc) return rc;
+        rc = run_force(h, h->cfg.variant, members_of(h, h->act, na), f);
+        if (rc) return rc;
+        rc = timed(h, T_CORRECT, [&] {
+            return launch_correct(s, h->act, na, t_next, f, prm, h->d_err, h->d_dtmin, h->stream);
+        });
+        if (rc) return rc;
+        h->stats.block_steps++;
+        int lg = 0;
+        while ((2LL << lg) <= na && lg < 31) ++lg;
+        h->stats.active_hist[lg]++;
+    }
+    h->predicted = false;
+    h->last_force_n = -1;
+    rc = check_err(h);
+    sync_stats_counters(h);
+    if (st) {
+        nb_stats d = h->stats;
+        d.block_steps -= before.block_steps;
+        d.force_launches -= before.force_launches;
+        d.interactions -= before.interactions;
+        d.force_ms -= before.force_ms;
+        d.reduce_ms -= before.reduce_ms;
+        d.predict_ms -= before.predict_ms;
+        d.correct_ms -= before.correct_ms;
+        d.sched_ms -= before.sched_ms;
+        d.dt_min_hits -= before.dt_min_hits;
+        for (int k = 0; k < 32; ++k) d.active_hist[k] -= before.active_hist[k];
+        d.kernel_launches -= before.kernel_launches;
+        *st = d;
+    }
+    return rc;
+}
+
+int nb_energy(nb_handle h, double *kin, double *pot)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(h->dev);
+    const int n = h->n;
+    std::vector<double> tt(n);
+    CK(h, cudaMemcpyAsync(tt.data(), h->t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int i = 1; i < n; ++i)
+        if (tt[i] != tt[0]) return fail(h, NB_ERR_STATE, "particles are not synchronised");
+    int rc = predict_to(h, tt[0]);  // d = 0: the predicted state is the current state
+    if (rc) return rc;
+    const bool was_pred = h->predicted;
+    (void)was_pred;
+    Out3 f{h->f_acc, h->f_jerk, h->f_pot, h->ld};
+    // FP64 pair potential: the diagnostic is kept in binary64 whatever the variant
+    const int saved = h->cfg.variant;
+    ISet is = members_of(h, nullptr, n);
+    rc = run_force(h, NB_F64, is, f);
+    h->cfg.variant = saved;
+    if (rc) return rc;
+    CK(h, launch_energy(n, h->m, h->vel, h->ld, h->f_pot, h->d_energy, h->stream));
+    h->stats.kernel_launches++;
+    double e2[2] = {0, 0};
+    CK(h, cudaMemcpyAsync(e2, h->d_energy, sizeof e2, cudaMemcpyDeviceToHost, h->stream));
+    rc = check_err(h);
+    if (rc) return rc;
+    if (kin) *kin = e2[0];
+    if (pot) *pot = e2[1];
+    h->predicted = false;
+    return NB_OK;
+}
+
+int nb_get_stats(nb_handle h, nb_stats *st)
+{
+    if (!h || !st) return NB_ERR_ARG;
+    cudaSetDevice(h->dev);
+    cudaStreamSynchronize(h->stream);
+    sync_stats_counters(h);
+    *st = h->stats;
+    return NB_OK;
+}
+
+int nb_reset_stats(nb_handle h)
+{
+    if (!h) return NB_ERR_ARG;
+    cudaSetDevice(h->dev);
+    cudaStreamSynchronize(h->stream);
+    h->timer.harvest();
+    for (double &x : h->timer.ms) x = 0.0;
+    std::memset(&h->stats, 0, sizeof h->stats);
+    cudaMemsetAsync(h->d_dtmin, 0, sizeof(unsigned long long), h->stream);
+    cudaStreamSynchronize(h->stream);
+    return NB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,960 @@
+// Pair-force kernels (K2) and the partial-sum reduction (K3).
+//
+// Direct summation of softened gravity from a j-set onto an i-set (paper
+// Sect. III.A): for every i and every j != i,
+//   r = x_j - x_i, v = v_j - v_i, s2 = |r|^2 + eps^2, rinv = s2^(-1/2),
+//   acc += m_j rinv^3 r,  jerk += m_j rinv^3 (v - 3 (r.v) rinv^2 r),  pot -= m_j rinv.
+//
+// Two mappings of the (i, j) work onto the GPU, as the paper discusses:
+//  - tile kernels ("i-parallel", Sect. III.A): each thread owns IPT
+//    i-particles in registers; the CTA streams its j-range through shared
+//    memory in tiles of JT records, staged by 1-D bulk copies (the TMA engine,
+//    cp.async.bulk) into an NS-deep ring of mbarrier-guarded buffers. The
+//    j-range is split across grid.y (the paper's j-parallel split for small
+//    N_i, after Makino's scheme), and the partial sums are reduced by K3.
+//  - j-parallel warp kernels for tiny i-sets (N_i <= 32, block-step tails):
+//    every thread holds the same few i-particles and a different j; partial
+//    sums are combined by warp shuffles, then across warps in FP64, then
+//    across CTAs by K3.
+//
+// Precision variants (Sect. III.A: emulated double precision for the
+// inter-particle distance, native FP64 for extreme mass ratios):
+//  - NB_F32DS: positions as double-single (hi + lo FP32) records; the relative
+//    coordinate is (x_j.hi - x_i.hi) + (x_j.lo - x_i.lo), which keeps close
+//    pairs far from the origin accurate; pair math in FP32 with rsqrtf on the
+//    SFU; per-tile FP32 sums folded into double-single accumulators (TwoSum).
+//  - NB_F32: the same kernel with FP32 positions (hi only) and FP32 sums.
+//  - NB_F64: IEEE binary64 throughout.
+//
+// Self pair: for i-particles that are members of the j-set the i == j pair is
+// masked by index (its potential term m_i/eps would otherwise swamp the FP32
+// sums, and with eps = 0 it is 0/0). The mask is applied only in the j-tiles
+// that contain one of the warp's own i-particles (a warp-uniform branch), so
+// the inner loop of every other tile carries no compare.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "nb_internal.cuh"
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier + bulk copies (TMA engine), all waits bounded.
+// ---------------------------------------------------------------------------
+
+static constexpr unsigned long long WAIT_LIMIT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Global -> shared bulk copy, completion signalled on bar (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of bar; gives up after WAIT_LIMIT_NS.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        for (int k = 0; k < 32; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Double-single accumulation (Knuth/Moller TwoSum + fast renormalisation).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void ds_add(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (x - bb);
+    const float t = lo + e;
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
+__device__ __forceinline__ bool finite7(const double *v)
+{
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) ok = ok && isfinite(v[c]);
+    return ok;
+}
+
+// Write the 7 totals of slot k: acc (3), jerk (3) and the positive potential
+// sum P (pot = -P).
+__device__ __forceinline__ void write_final(const Out3 &out, int k, double v[7], unsigned *err)
+{
+    v[6] = -v[6];
+    if (!finite7(v)) atomicOr(err, DERR_NONFINITE);
+    if (out.acc) {
+        out.acc[k] = v[0];
+        out.acc[out.ld + k] = v[1];
+        out.acc[2 * out.ld + k] = v[2];
+    }
+    if (out.jerk) {
+        out.jerk[k] = v[3];
+        out.jerk[out.ld + k] = v[4];
+        out.jerk[2 * out.ld + k] = v[5];
+    }
+    if (out.pot) out.pot[k] = v[6];
+}
+
+// Member index of slot k; an index outside the j-set is flagged and replaced by 0.
+__device__ __forceinline__ int member_index(const ISet &is, int k, unsigned *err)
+{
+    const int r = is.idx ? __ldg(is.idx + k) : k;
+    if ((unsigned)r >= (unsigned)is.nj) {
+        atomicOr(err, DERR_BADINDEX);
+        return 0;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 / double-single tile kernel.
+// ---------------------------------------------------------------------------
+
+template <int VAR, int IPT, int NT, int JT, int NS>
+__global__ void __launch_bounds__(NT)
+    k_force_tile32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f, int ntiles,
+                   double *__restrict__ part, long long pld, Out3 out, unsigned *err)
+{
+    extern __shared__ __align__(128) float4 s_tile[];  // NS * JT * DS_REC
+    __shared__ __align__(8) uint64_t s_full[NS];
+    __shared__ int s_abort;
+
+    constexpr bool DS = (VAR == NB_F32DS);
+    const int tid = threadIdx.x;
+    const int nsplit = gridDim.y;
+    const int split = blockIdx.y;
+    const int tile0 = (int)((long long)ntiles * split / nsplit);
+    const int tile1 = (int)((long long)ntiles * (split + 1) / nsplit);
+    const int my_tiles = tile1 - tile0;
+
+    // i-particles of this thread
+    float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+    float mi[IPT];
+    int iid[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        int k = blockIdx.x * (NT * IPT) + p * NT + tid;
+        if (k >= is.n) k = is.n - 1;  // idle slots compute a copy, never written
+        const int r = is.member ? member_index(is, k, err) : k;
+        const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
+        const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
+        const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
+        xh[p] = a.x; yh[p] = a.y; zh[p] = a.z; mi[p] = a.w;
+        xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+        vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+        iid[p] = is.member ? r : -1;
+    }
+
+    // running totals: double-single (DS) or plain FP32
+    float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A_h[p][c] = A_l[p][c] = J_h[p][c] = J_l[p][c] = 0.f;
+        P_h[p] = P_l[p] = 0.f;
+    }
+
+    if (tid == 0) {
+        s_abort = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) mbar_init(&s_full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int kt) {
+        const int stage = kt % NS;
+        const int t = tile0 + kt;
+        const int cnt = min(JT, nj - t * JT);
+        const uint32_t bytes = (uint32_t)cnt * DS_REC * 16u;
+        mbar_expect_tx(&s_full[stage], bytes);
+        bulk_g2s(s_tile + (size_t)stage * JT * DS_REC, jrec + (size_t)t * JT * DS_REC, bytes,
+                 &s_full[stage]);
+    };
+    if (tid == 0) {
+        for (int kt = 0; kt < NS && kt < my_tiles; ++kt) issue(kt);
+    }
+
+    for (int kt = 0; kt < my_tiles; ++kt) {
+        const int stage = kt % NS;
+        const uint32_t parity = (uint32_t)((kt / NS) & 1);
+        if (!mbar_wait(&s_full[stage], parity)) s_abort = 1;
+        const float4 *T = s_tile + (size_t)stage * JT * DS_REC;
+        const int jbase = (tile0 + kt) * JT;
+        const int cnt = min(JT, nj - jbase);
+
+        float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
+            tp[p] = 0.f;
+        }
+
+        // self pair in this tile for any lane of the warp? (warp-uniform)
+        bool own = false;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) own = own || (iid[p] >= jbase && iid[p] < jbase + cnt);
+        own = __any_sync(0xffffffffu, own);
+
+        auto body = [&](int jj, auto masked_tag) {
+            constexpr bool MASKED = decltype(masked_tag)::value;
+            const float4 a = T[DS_REC * jj];
+            const float4 c = T[DS_REC * jj + 2];
+            float4 b;
+            if (DS) b = T[DS_REC * jj + 1];
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (a.x - xh[p]) + (b.x - xl[p]);
+                    dy = (a.y - yh[p]) + (b.y - yl[p]);
+                    dz = (a.z - zh[p]) + (b.z - zl[p]);
+                } else {
+                    dx = a.x - xh[p];
+                    dy = a.y - yh[p];
+                    dz = a.z - zh[p];
+                }
+                const float dvx = c.x - vx[p], dvy = c.y - vy[p], dvz = c.z - vz[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float rinv = rsqrtf(r2);
+                if (MASKED) rinv = (jbase + jj == iid[p]) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = a.w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float beta = (mr3 * rinv2) * rv;
+                tp[p] += mrinv;
+                ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                tja[p][0] = fmaf(mr3, dvx, tja[p][0]);
+                tja[p][1] = fmaf(mr3, dvy, tja[p][1]);
+                tja[p][2] = fmaf(mr3, dvz, tja[p][2]);
+                tjb[p][0] = fmaf(beta, dx, tjb[p][0]);
+                tjb[p][1] = fmaf(beta, dy, tjb[p][1]);
+                tjb[p][2] = fmaf(beta, dz, tjb[p][2]);
+            }
+        };
+        if (own) {
+            for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
+        } else if (cnt == JT) {
+#pragma unroll 4
+            for (int jj = 0; jj < JT; ++jj) body(jj, std::false_type{});
+        } else {
+#pragma unroll 2
+            for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
+        }
+
+        // fold the tile sums into the running totals
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float jt = fmaf(-3.f, tjb[p][c], tja[p][c]);
+                if (DS) {
+                    ds_add(A_h[p][c], A_l[p][c], ta[p][c]);
+                    ds_add(J_h[p][c], J_l[p][c], jt);
+                } else {
+                    A_h[p][c] += ta[p][c];
+                    J_h[p][c] += jt;
+                }
+            }
+            if (DS)
+                ds_add(P_h[p], P_l[p], tp[p]);
+            else
+                P_h[p] += tp[p];
+        }
+
+        __syncthreads();  // every warp is done with this stage
+        if (s_abort) break;
+        if (tid == 0 && kt + NS < my_tiles) issue(kt + NS);
+    }
+    if (s_abort) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        return;
+    }
+
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        const int k = blockIdx.x * (NT * IPT) + p * NT + tid;
+        if (k >= is.n) continue;
+        double v[7];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = (double)A_h[p][c] + (double)A_l[p][c];
+            v[3 + c] = (double)J_h[p][c] + (double)J_l[p][c];
+        }
+        v[6] = (double)P_h[p] + (double)P_l[p];
+        if (nsplit == 1) {
+            write_final(out, k, v, err);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) part[((size_t)split * 7 + c) * pld + k] = v[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 tile kernel.
+// ---------------------------------------------------------------------------
+
+template <int IPT, int NT, int JT, int NS>
+__global__ void __launch_bounds__(NT)
+    k_force_tile64(JSet js, ISet is, double eps2, int ntiles, double *__restrict__ part,
+                   long long pld, Out3 out, unsigned *err)
+{
+    extern __shared__ __align__(128) double s_t64[];  // NS * 7 * JT
+    __shared__ __align__(8) uint64_t s_full[NS];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int nsplit = gridDim.y;
+    const int split = blockIdx.y;
+    const int tile0 = (int)((long long)ntiles * split / nsplit);
+    const int tile1 = (int)((long long)ntiles * (split + 1) / nsplit);
+    const int my_tiles = tile1 - tile0;
+    const int nj = js.n;
+
+    double xi[IPT][3], vi[IPT][3], mi[IPT];
+    int iid[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        int k = blockIdx.x * (NT * IPT) + p * NT + tid;
+        if (k >= is.n) k = is.n - 1;
+        const int r = is.member ? member_index(is, k, err) : k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xi[p][c] = __ldg(is.pos64 + c * is.ld64 + r);
+            vi[p][c] = __ldg(is.vel64 + c * is.ld64 + r);
+        }
+        mi[p] = is.member ? __ldg(is.m64 + r) : 0.0;
+        iid[p] = is.member ? r : -1;
+    }
+
+    double A[IPT][3], J[IPT][3], P[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[p][c] = J[p][c] = 0.0;
+        P[p] = 0.0;
+    }
+
+    if (tid == 0) {
+        s_abort = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) mbar_init(&s_full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // 7 rows per stage: x, y, z, vx, vy, vz, m
+    auto issue = [&](int kt) {
+        const int stage = kt % NS;
+        const int t = tile0 + kt;
+        const int cnt = min(JT, nj - t * JT);
+        const uint32_t bytes = (uint32_t)(((cnt * 8) + 15) & ~15);  // rows are padded
+        mbar_expect_tx(&s_full[stage], 7u * bytes);
+        double *dst = s_t64 + (size_t)stage * 7 * JT;
+        const size_t off = (size_t)t * JT;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            bulk_g2s(dst + c * JT, js.pos64 + c * js.ld + off, bytes, &s_full[stage]);
+            bulk_g2s(dst + (3 + c) * JT, js.vel64 + c * js.ld + off, bytes, &s_full[stage]);
+        }
+        bulk_g2s(dst + 6 * JT, js.m64 + off, bytes, &s_full[stage]);
+    };
+    if (tid == 0) {
+        for (int kt = 0; kt < NS && kt < my_tiles; ++kt) issue(kt);
+    }
+
+    for (int kt = 0; kt < my_tiles; ++kt) {
+        const int stage = kt % NS;
+        const uint32_t parity = (uint32_t)((kt / NS) & 1);
+        if (!mbar_wait(&s_full[stage], parity)) s_abort = 1;
+        const double *T = s_t64 + (size_t)stage * 7 * JT;
+        const int jbase = (tile0 + kt) * JT;
+        const int cnt = min(JT, nj - jbase);
+        double ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.0;
+            tp[p] = 0.0;
+        }
+        bool own = false;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) own = own || (iid[p] >= jbase && iid[p] < jbase + cnt);
+        own = __any_sync(0xffffffffu, own);
+#pragma unroll 2
+        for (int jj = 0; jj < cnt; ++jj) {
+            const double xj = T[jj], yj = T[JT + jj], zj = T[2 * JT + jj];
+            const double uj = T[3 * JT + jj], wj = T[4 * JT + jj], qj = T[5 * JT + jj];
+            const double mj = T[6 * JT + jj];
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                const double dx = xj - xi[p][0], dy = yj - xi[p][1], dz = zj - xi[p][2];
+                const double dvx = uj - vi[p][0], dvy = wj - vi[p][1], dvz = qj - vi[p][2];
+                double r2 = fma(dx, dx, eps2);
+                r2 = fma(dy, dy, r2);
+                r2 = fma(dz, dz, r2);
+                double rv = dx * dvx;
+                rv = fma(dy, dvy, rv);
+                rv = fma(dz, dvz, rv);
+                double rinv = rsqrt(r2);
+                if (own) rinv = (jbase + jj == iid[p]) ? 0.0 : rinv;
+                const double rinv2 = rinv * rinv;
+                const double mrinv = mj * rinv;
+                const double mr3 = mrinv * rinv2;
+                const double beta = (mr3 * rinv2) * rv;
+                tp[p] += mrinv;
+                ta[p][0] = fma(mr3, dx, ta[p][0]);
+                ta[p][1] = fma(mr3, dy, ta[p][1]);
+                ta[p][2] = fma(mr3, dz, ta[p][2]);
+                tja[p][0] = fma(mr3, dvx, tja[p][0]);
+                tja[p][1] = fma(mr3, dvy, tja[p][1]);
+                tja[p][2] = fma(mr3, dvz, tja[p][2]);
+                tjb[p][0] = fma(beta, dx, tjb[p][0]);
+                tjb[p][1] = fma(beta, dy, tjb[p][1]);
+                tjb[p][2] = fma(beta, dz, tjb[p][2]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                A[p][c] += ta[p][c];
+                J[p][c] += fma(-3.0, tjb[p][c], tja[p][c]);
+            }
+            P[p] += tp[p];
+        }
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && kt + NS < my_tiles) issue(kt + NS);
+    }
+    if (s_abort) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        return;
+    }
+
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        const int k = blockIdx.x * (NT * IPT) + p * NT + tid;
+        if (k >= is.n) continue;
+        double v[7] = {A[p][0], A[p][1], A[p][2], J[p][0], J[p][1], J[p][2], P[p]};
+        if (nsplit == 1) {
+            write_final(out, k, v, err);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) part[((size_t)split * 7 + c) * pld + k] = v[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// j-parallel kernels for tiny i-sets: thread = j, all threads share IPT i's.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int VAR, int IPT, int NT>
+__global__ void __launch_bounds__(NT)
+    k_force_jmode32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f,
+                    double *__restrict__ part, long long pld, Out3 out, unsigned *err)
+{
+    constexpr bool DS = (VAR == NB_F32DS);
+    constexpr int NW = NT / 32;
+    __shared__ float s_red[NW][IPT][7];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsplit = gridDim.x, split = blockIdx.x;
+    const int j0 = (int)((long long)nj * split / nsplit);
+    const int j1 = (int)((long long)nj * (split + 1) / nsplit);
+
+    for (int g0 = 0; g0 < is.n; g0 += IPT) {
+        float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+        float mi[IPT];
+        int iid[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = min(g0 + p, is.n - 1);
+            const int r = is.member ? member_index(is, k, err) : k;
+            const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
+            const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
+            const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
+            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z; mi[p] = a.w;
+            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+            iid[p] = is.member ? r : -1;
+        }
+        float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
+            tp[p] = 0.f;
+        }
+        for (int j = j0 + tid; j < j1; j += NT) {
+            const float4 a = __ldg(jrec + (size_t)DS_REC * j);
+            const float4 c = __ldg(jrec + (size_t)DS_REC * j + 2);
+            float4 b;
+            if (DS) b = __ldg(jrec + (size_t)DS_REC * j + 1);
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (a.x - xh[p]) + (b.x - xl[p]);
+                    dy = (a.y - yh[p]) + (b.y - yl[p]);
+                    dz = (a.z - zh[p]) + (b.z - zl[p]);
+                } else {
+                    dx = a.x - xh[p];
+                    dy = a.y - yh[p];
+                    dz = a.z - zh[p];
+                }
+                const float dvx = c.x - vx[p], dvy = c.y - vy[p], dvz = c.z - vz[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float rinv = rsqrtf(r2);
+                rinv = (j == iid[p]) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = a.w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float beta = (mr3 * rinv2) * rv;
+                tp[p] += mrinv;
+                ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                tja[p][0] = fmaf(mr3, dvx, tja[p][0]);
+                tja[p][1] = fmaf(mr3, dvy, tja[p][1]);
+                tja[p][2] = fmaf(mr3, dvz, tja[p][2]);
+                tjb[p][0] = fmaf(beta, dx, tjb[p][0]);
+                tjb[p][1] = fmaf(beta, dy, tjb[p][1]);
+                tjb[p][2] = fmaf(beta, dz, tjb[p][2]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            float v[7];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = ta[p][c];
+                v[3 + c] = fmaf(-3.f, tjb[p][c], tja[p][c]);
+            }
+            v[6] = tp[p];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const float w = warp_sum(v[c]);
+                if (lane == 0) s_red[warp][p][c] = w;
+            }
+        }
+        __syncthreads();
+        if (tid < IPT * 7) {
+            const int p = tid / 7, c = tid % 7;
+            const int k = g0 + p;
+            if (k < is.n) {
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) s += (double)s_red[w][p][c];
+                if (nsplit == 1) {
+                    if (c == 6) {
+                        s = -s;
+                        if (out.pot) out.pot[k] = s;
+                    } else if (c < 3) {
+                        if (out.acc) out.acc[c * out.ld + k] = s;
+                    } else {
+                        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
+                    }
+                    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
+                } else {
+                    part[((size_t)split * 7 + c) * pld + k] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int IPT, int NT>
+__global__ void __launch_bounds__(NT)
+    k_force_jmode64(JSet js, ISet is, double eps2, double *__restrict__ part, long long pld,
+                    Out3 out, unsigned *err)
+{
+    constexpr int NW = NT / 32;
+    __shared__ double s_red[NW][IPT][7];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsplit = gridDim.x, split = blockIdx.x;
+    const int nj = js.n;
+    const int j0 = (int)((long long)nj * split / nsplit);
+    const int j1 = (int)((long long)nj * (split + 1) / nsplit);
+
+    for (int g0 = 0; g0 < is.n; g0 += IPT) {
+        double xi[IPT][3], vi[IPT][3], mi[IPT];
+        int iid[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = min(g0 + p, is.n - 1);
+            const int r = is.member ? member_index(is, k, err) : k;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xi[p][c] = __ldg(is.pos64 + c * is.ld64 + r);
+                vi[p][c] = __ldg(is.vel64 + c * is.ld64 + r);
+            }
+            mi[p] = is.member ? __ldg(is.m64 + r) : 0.0;
+            iid[p] = is.member ? r : -1;
+        }
+        double ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.0;
+            tp[p] = 0.0;
+        }
+        for (int j = j0 + tid; j < j1; j += NT) {
+            const double xj = __ldg(js.pos64 + j), yj = __ldg(js.pos64 + js.ld + j),
+                         zj = __ldg(js.pos64 + 2 * js.ld + j);
+            const double uj = __ldg(js.vel64 + j), wj = __ldg(js.vel64 + js.ld + j),
+                         qj = __ldg(js.vel64 + 2 * js.ld + j);
+            const double mj = __ldg(js.m64 + j);
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                const double dx = xj - xi[p][0], dy = yj - xi[p][1], dz = zj - xi[p][2];
+                const double dvx = uj - vi[p][0], dvy = wj - vi[p][1], dvz = qj - vi[p][2];
+                double r2 = fma(dx, dx, eps2);
+                r2 = fma(dy, dy, r2);
+                r2 = fma(dz, dz, r2);
+                double rv = dx * dvx;
+                rv = fma(dy, dvy, rv);
+                rv = fma(dz, dvz, rv);
+                double rinv = rsqrt(r2);
+                rinv = (j == iid[p]) ? 0.0 : rinv;
+                const double rinv2 = rinv * rinv;
+                const double mrinv = mj * rinv;
+                const double mr3 = mrinv * rinv2;
+                const double beta = (mr3 * rinv2) * rv;
+                tp[p] += mrinv;
+                ta[p][0] = fma(mr3, dx, ta[p][0]);
+                ta[p][1] = fma(mr3, dy, ta[p][1]);
+                ta[p][2] = fma(mr3, dz, ta[p][2]);
+                tja[p][0] = fma(mr3, dvx, tja[p][0]);
+                tja[p][1] = fma(mr3, dvy, tja[p][1]);
+                tja[p][2] = fma(mr3, dvz, tja[p][2]);
+                tjb[p][0] = fma(beta, dx, tjb[p][0]);
+                tjb[p][1] = fma(beta, dy, tjb[p][1]);
+                tjb[p][2] = fma(beta, dz, tjb[p][2]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            double v[7];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = ta[p][c];
+                v[3 + c] = fma(-3.0, tjb[p][c], tja[p][c]);
+            }
+            v[6] = tp[p];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const double w = warp_sum(v[c]);
+                if (lane == 0) s_red[warp][p][c] = w;
+            }
+        }
+        __syncthreads();
+        if (tid < IPT * 7) {
+            const int p = tid / 7, c = tid % 7;
+            const int k = g0 + p;
+            if (k < is.n) {
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) s += s_red[w][p][c];
+                if (nsplit == 1) {
+                    if (c == 6) {
+                        s = -s;
+                        if (out.pot) out.pot[k] = s;
+                    } else if (c < 3) {
+                        if (out.acc) out.acc[c * out.ld + k] = s;
+                    } else {
+                        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
+                    }
+                    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
+                } else {
+                    part[((size_t)split * 7 + c) * pld + k] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: sum the nsplit partials of every (slot, component) in fixed order s = 0..
+// ---------------------------------------------------------------------------
+
+// Store the reduced value s of component c of slot k (c == 6: the positive
+// potential sum, stored negated).
+__device__ __forceinline__ void store_component(const Out3 &out, int c, int k, double s,
+                                                unsigned *err)
+{
+    if (c == 6) {
+        s = -s;
+        if (out.pot) out.pot[k] = s;
+    } else if (c < 3) {
+        if (out.acc) out.acc[c * out.ld + k] = s;
+    } else {
+        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
+    }
+    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
+}
+
+// One thread per (k, c) - for few splits.
+__global__ void k_reduce_thread(int ni, int nsplit, const double *__restrict__ part, long long pld,
+                                Out3 out, unsigned *err)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 7LL * ni) return;
+    const int c = (int)(q / ni), k = (int)(q % ni);
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * 7 + c) * pld + k];
+    store_component(out, c, k, s, err);
+}
+
+// One warp per (k, c) - for many splits: lane l sums s = l, l+32, ... then a
+// fixed xor tree.
+__global__ void k_reduce_warp(int ni, int nsplit, const double *__restrict__ part, long long pld,
+                              Out3 out, unsigned *err)
+{
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= 7LL * ni) return;
+    const int c = (int)(w / ni), k = (int)(w % ni);
+    double s = 0.0;
+    for (int sp = lane; sp < nsplit; sp += 32) s += part[((size_t)sp * 7 + c) * pld + k];
+    s = warp_sum(s);
+    if (lane == 0) store_component(out, c, k, s, err);
+}
+
+// ---------------------------------------------------------------------------
+// Plans and launchers.
+// ---------------------------------------------------------------------------
+
+constexpr int JT32 = 128;
+constexpr int NS32 = 3;
+constexpr int JT64 = 64;
+constexpr int NS64 = 3;
+
+ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
+{
+    ForcePlan p{};
+    if (n_i <= 32) {
+        p.kind = 1;
+        p.ipt = n_i <= 1 ? 1 : n_i <= 2 ? 2 : n_i <= 4 ? 4 : 8;
+        if (variant == NB_F64 && p.ipt > 4) p.ipt = 4;  // FP64 registers
+        p.threads = (variant == NB_F64) ? 128 : 256;
+        const int per_thread = 4;
+        long long g = (n_j + (long long)p.threads * per_thread - 1) / ((long long)p.threads * per_thread);
+        if (g > 2LL * num_sms) g = 2LL * num_sms;
+        if (g < 1) g = 1;
+        p.nsplit = (int)g;
+        p.jt = 0;
+        return p;
+    }
+    p.kind = 0;
+    if (variant == NB_F64) {
+        p.ipt = 1;
+        p.threads = 128;
+        p.jt = JT64;
+    } else {
+        p.ipt = 2;
+        p.jt = JT32;
+        p.threads = n_i >= 16384 ? 256 : (n_i >= 1024 ? 128 : 64);
+    }
+    const long long ib = (long long)p.threads * p.ipt;
+    const long long nblk = (n_i + ib - 1) / ib;
+    const long long ntiles = (n_j + p.jt - 1) / p.jt;
+    const long long resident = (p.threads >= 256) ? 2 : (p.threads == 128 ? 4 : 8);
+    const long long target = 4LL * num_sms * resident;
+    long long ns = (target + nblk - 1) / nblk;
+    if (ns > ntiles) ns = ntiles;
+    if (ns < 1) ns = 1;
+    p.nsplit = (int)ns;
+    return p;
+}
+
+size_t plan_partial_doubles(const ForcePlan &p, int n_i)
+{
+    if (p.nsplit <= 1) return 0;
+    return (size_t)p.nsplit * 7 * (size_t)n_i;
+}
+
+template <int VAR, int IPT, int NT>
+static cudaError_t go_tile32(const JSet &js, const ISet &is, float eps2f, int nsplit,
+                             double *part, Out3 out, unsigned *err, cudaStream_t st)
+{
+    auto kern = k_force_tile32<VAR, IPT, NT, JT32, NS32>;
+    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);  // 18 KB, below 48 KB
+    const int ntiles = (js.n + JT32 - 1) / JT32;
+    dim3 grid((is.n + NT * IPT - 1) / (NT * IPT), nsplit);
+    kern<<<grid, NT, smem, st>>>(js.rec32, js.n, is, eps2f, ntiles, part, is.n, out, err);
+    return cudaGetLastError();
+}
+
+template <int IPT, int NT>
+static cudaError_t go_tile64(const JSet &js, const ISet &is, double eps2, int nsplit, double *part,
+                             Out3 out, unsigned *err, cudaStream_t st)
+{
+    auto kern = k_force_tile64<IPT, NT, JT64, NS64>;
+    const size_t smem = (size_t)NS64 * 7 * JT64 * sizeof(double);  // 10.5 KB
+    const int ntiles = (js.n + JT64 - 1) / JT64;
+    dim3 grid((is.n + NT * IPT - 1) / (NT * IPT), nsplit);
+    kern<<<grid, NT, smem, st>>>(js, is, eps2, ntiles, part, is.n, out, err);
+    return cudaGetLastError();
+}
+
+template <int VAR>
+static cudaError_t dispatch32(const ForcePlan &p, const JSet &js, const ISet &is, float eps2f,
+                              double *part, Out3 out, unsigned *err, cudaStream_t st)
+{
+    if (p.kind == 1) {
+        const int g = p.nsplit;
+#define JM(I) \
+    k_force_jmode32<VAR, I, 256><<<g, 256, 0, st>>>(js.rec32, js.n, is, eps2f, part, is.n, out, err)
+        switch (p.ipt) {
+        case 1: JM(1); break;
+        case 2: JM(2); break;
+        case 4: JM(4); break;
+        default: JM(8); break;
+        }
+#undef JM
+        return cudaGetLastError();
+    }
+    switch (p.threads) {
+    case 256: return go_tile32<VAR, 2, 256>(js, is, eps2f, p.nsplit, part, out, err, st);
+    case 128: return go_tile32<VAR, 2, 128>(js, is, eps2f, p.nsplit, part, out, err, st);
+    default: return go_tile32<VAR, 2, 64>(js, is, eps2f, p.nsplit, part, out, err, st);
+    }
+}
+
+static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is, double eps2,
+                              double *part, Out3 out, unsigned *err, cudaStream_t st)
+{
+    if (p.kind == 1) {
+        const int g = p.nsplit;
+#define JM(I) k_force_jmode64<I, 128><<<g, 128, 0, st>>>(js, is, eps2, part, is.n, out, err)
+        switch (p.ipt) {
+        case 1: JM(1); break;
+        case 2: JM(2); break;
+        default: JM(4); break;
+        }
+#undef JM
+        return cudaGetLastError();
+    }
+    return go_tile64<1, 128>(js, is, eps2, p.nsplit, part, out, err, st);
+}
+
+cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, const ISet &is,
+                         double eps2, double *part, Out3 out, unsigned *err, cudaStream_t st,
+                         cudaEvent_t *ev)
+{
+    if (is.n <= 0) return cudaSuccess;
+    const float eps2f = (float)eps2;
+    cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (variant == NB_F64)
+        e = dispatch64(plan, js, is, eps2, part, out, err, st);
+    else if (variant == NB_F32DS)
+        e = dispatch32<NB_F32DS>(plan, js, is, eps2f, part, out, err, st);
+    else
+        e = dispatch32<NB_F32>(plan, js, is, eps2f, part, out, err, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    if (plan.nsplit > 1) {
+        const long long nout = 7LL * is.n;
+        const int bs = 256;
+        if (plan.nsplit >= 64) {
+            const long long threads = nout * 32;
+            k_reduce_warp<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(is.n, plan.nsplit,
+                                                                               part, is.n, out, err);
+        } else {
+            k_reduce_thread<<<(unsigned)((nout + bs - 1) / bs), bs, 0, st>>>(is.n, plan.nsplit,
+                                                                             part, is.n, out, err);
+        }
+        e = cudaGetLastError();
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    return e;
+}
+
+}  // namespace nb

@@ -1,0 +1,134 @@
+// Internal declarations of libnbody: device helpers, launch plans and the
+// kernel launchers shared by the engine, batch and server translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+namespace nb {
+
+// ---- device error word bits (OR-ed by kernels, read by the host) ----------
+enum : unsigned {
+    DERR_NONFINITE = 1u,  // a force or corrected state that is not finite
+    DERR_TIMEOUT = 2u,    // a bounded mbarrier wait gave up
+    DERR_BACKWARD = 4u,   // prediction to a time before a particle's own time
+    DERR_BADINDEX = 8u,   // an i-set index outside [0, n_j) (replaced by 0)
+};
+
+// Double-single j-record, 48 bytes per particle (see DS_REC):
+//   r[0] = {x_hi, y_hi, z_hi, m}, r[1] = {x_lo, y_lo, z_lo, 0}, r[2] = {vx, vy, vz, 0}
+// with x = x_hi + x_lo to ~48 bits and FP32 velocity.
+constexpr int DS_REC = 3;  // float4 per record
+
+// Vector-field output with a row stride: component c of slot k is p[c*ld + k].
+struct Out3 {
+    double *acc;
+    double *jerk;
+    double *pot;
+    long long ld;
+};
+
+// The i-set of an evaluation. Members of the j-set are given by idx (slot k ->
+// particle idx[k], or k when idx is null) and read from the j-records; an
+// external i-set brings its own records (rec32 / soa64) and has no self pair.
+struct ISet {
+    int n;
+    const int *idx;        // member indices (nullptr: identity)
+    bool member;           // true: i is a member of the j-set (self pair removed)
+    const float4 *rec32;   // F32/DS records of the i-set (members: the j-records)
+    const double *pos64;   // FP64 SoA [3][ld64] (members: predicted positions)
+    const double *vel64;
+    const double *m64;     // masses (members only; used for the self term)
+    long long ld64;
+    int nj;                // bound of member indices (the j-set size)
+};
+
+// The j-set of an evaluation: predicted FP64 SoA and the DS records.
+struct JSet {
+    int n;
+    const float4 *rec32;   // n DS records
+    const double *pos64;   // [3][ld]
+    const double *vel64;
+    const double *m64;
+    long long ld;
+};
+
+// A force launch plan.
+struct ForcePlan {
+    int kind;     // 0: i-parallel tiles (K2 tile), 1: j-parallel warps (K2 jmode)
+    int ipt;      // i-particles per thread
+    int threads;  // CTA size
+    int nsplit;   // j-splits (grid.y for tiles, grid.x for jmode)
+    int jt;       // j-tile depth (tile kind)
+};
+
+// Choose a plan for n_i i-particles against n_j j-particles.
+ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms);
+
+// Scratch doubles the plan needs for partial sums (0 when nsplit == 1).
+size_t plan_partial_doubles(const ForcePlan &p, int n_i);
+
+// Launch K2 (+ K3 when nsplit > 1). part must hold plan_partial_doubles.
+// eps2: softening squared. Results go to out (slot-indexed). Non-finite
+// results set DERR_NONFINITE in *err. ev (optional, 4 events) brackets the
+// force kernel (ev[0], ev[1]) and the reduction (ev[2], ev[3]).
+cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, const ISet &is,
+                         double eps2, double *part, Out3 out, unsigned *err,
+                         cudaStream_t st, cudaEvent_t *ev);
+
+// ---- per-particle kernels (K1, K4, K5) -------------------------------------
+
+struct StateDev {
+    int n;
+    long long ld;      // row stride of the SoA vector fields (capacity)
+    double *m;
+    double *pos, *vel, *acc, *jerk;   // [3][ld]
+    double *t, *dt;
+    double *pos_p, *vel_p;            // predicted [3][ld]
+    float4 *rec;                      // DS records [n][3]
+};
+
+struct StepParams {
+    double eta, eta_s, dt_min, dt_max, shared_dt;
+};
+
+// Mailbox the scheduler writes (mapped host memory) after each block step.
+struct Mailbox {
+    double t_next;
+    int n_active;
+    int pad;
+};
+
+// K1: predict all particles of s to time t (FP64), writing pos_p, vel_p and,
+// when want_rec, the DS records.
+cudaError_t launch_predict(const StateDev &s, double t, bool want_rec, unsigned *err,
+                           cudaStream_t st);
+
+// K4: Hermite corrector + new step for the n_a particles act[k] to time t_new,
+// with the new acc/jerk in f (slot-indexed). dtmin_hits counts clamps.
+cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new,
+                           const Out3 &f, const StepParams &p, unsigned *err,
+                           unsigned long long *dtmin_hits, cudaStream_t st);
+
+// K4 at start-up: initial steps from acc/jerk (slot k = particle k), or the shared step.
+cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams &p,
+                              unsigned *err, cudaStream_t st);
+
+// K5: t_next = min(t_i + dt_i) and the due particles in ascending order.
+cudaError_t launch_sched(const StateDev &s, int *act, Mailbox *mail_dev, cudaStream_t st);
+
+// Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
+cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,
+                          const double *pot, double *out2, cudaStream_t st);
+
+// DS records of an external i-set from FP64 SoA positions/velocities (mass 0).
+cudaError_t launch_make_rec(int n, const double *pos, const double *vel, long long ld,
+                            float4 *rec, cudaStream_t st);
+
+// Check every value of n finite doubles (3 rows of stride ld, or 1 row when rows == 1).
+cudaError_t launch_check_finite(const double *p, int n, int rows, long long ld, unsigned *err,
+                                cudaStream_t st);
+
+}  // namespace nb

@@ -1,0 +1,352 @@
+"""ctypes binding of libnbody.so (include/nbody.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; the force, predictor, corrector and scheduler run in the
+library's CUDA kernels. If the library has not been built, ``load()`` raises:
+there is no CPU fallback.
+
+Array conventions follow the C ABI: a vector field over n particles is a
+(3, n) float64 array (rows x, y, z); masses, potentials, times and steps are
+(n,) float64 arrays; indices are int32. Host-array calls copy in and out;
+``nb_force_dev`` takes device pointers (e.g. ``tensor.data_ptr()``) and runs
+on the handle's stream (``nb_set_stream``, e.g. ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnbody.so")
+
+NB_OK = 0
+NB_ERR_ARG = 1
+NB_ERR_OOM = 2
+NB_ERR_BUDGET = 3
+NB_ERR_CUDA = 4
+NB_ERR_TIMEOUT = 5
+NB_ERR_NONFINITE = 6
+NB_ERR_BUSY = 7
+NB_ERR_NOTFOUND = 8
+NB_ERR_STATE = 9
+
+NB_F32 = 0
+NB_F32DS = 1
+NB_F64 = 2
+VARIANTS = {"f32": NB_F32, "f32ds": NB_F32DS, "f64": NB_F64}
+
+NB_FLAG_TIMING = 1
+
+
+class NBodyError(RuntimeError):
+    def __init__(self, status, func, msg):
+        self.status = status
+        self.func = func
+        super().__init__(f"{func}: status {status}: {msg}")
+
+
+class nb_config(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int), ("variant", ctypes.c_int), ("eps", ctypes.c_double),
+                ("eta", ctypes.c_double), ("eta_s", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("dt_min", ctypes.c_double), ("shared_dt", ctypes.c_double),
+                ("budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class nb_stats(ctypes.Structure):
+    _fields_ = [("block_steps", ctypes.c_longlong), ("force_launches", ctypes.c_longlong),
+                ("interactions", ctypes.c_double), ("force_ms", ctypes.c_double),
+                ("reduce_ms", ctypes.c_double), ("predict_ms", ctypes.c_double),
+                ("correct_ms", ctypes.c_double), ("sched_ms", ctypes.c_double),
+                ("dt_min_hits", ctypes.c_longlong), ("active_hist", ctypes.c_longlong * 32),
+                ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "active_hist"}
+        d["active_hist"] = list(self.active_hist)
+        return d
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_H = ctypes.c_void_p
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes); restype int means a status to check
+_SIGS = [
+    ("nb_config_default", None, [ctypes.POINTER(nb_config)]),
+    ("nb_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("nb_last_error", ctypes.c_char_p, [_H]),
+    ("nb_version", ctypes.c_char_p, []),
+    ("nb_create", ctypes.c_int, [ctypes.POINTER(nb_config), ctypes.POINTER(_H)]),
+    ("nb_destroy", ctypes.c_int, [_H]),
+    ("nb_set_stream", ctypes.c_int, [_H, ctypes.c_void_p]),
+    ("nb_set_particles", ctypes.c_int, [_H, ctypes.c_int, _D, _D, _D, ctypes.c_double]),
+    ("nb_init", ctypes.c_int, [_H]),
+    ("nb_get_particles", ctypes.c_int, [_H, _D, _D, _D]),
+    ("nb_get_state", ctypes.c_int, [_H, _I, _D, _D, _D, _D, _D, _D, _D]),
+    ("nb_set_state", ctypes.c_int, [_H, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]),
+    ("nb_predict", ctypes.c_int, [_H, ctypes.c_double]),
+    ("nb_force", ctypes.c_int, [_H, _I, ctypes.c_int, _D, _D, _D]),
+    ("nb_force_dev", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    ("nb_force_ext", ctypes.c_int, [_H, ctypes.c_int, _D, _D, _D, _D, _D]),
+    ("nb_correct", ctypes.c_int, [_H, _I, ctypes.c_int, ctypes.c_double]),
+    ("nb_step", ctypes.c_int, [_H, ctypes.c_double, ctypes.POINTER(nb_stats)]),
+    ("nb_energy", ctypes.c_int, [_H, _D, _D]),
+    ("nb_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_stats)]),
+    ("nb_reset_stats", ctypes.c_int, [_H]),
+]
+
+
+def load(path: str | None = None):
+    """Load libnbody.so (raises if it is missing; it is never replaced by a CPU path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} is not built: run `python -m paper_1409_5474_gb300.build`")
+            lib = ctypes.CDLL(p)
+            for name, res, args in _SIGS:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def declared_symbols():
+    """Names of the entry points this binding declares."""
+    return [s[0] for s in _SIGS]
+
+
+def _check(rc, func, h=None):
+    if rc != NB_OK:
+        lib = load()
+        msg = lib.nb_last_error(h)
+        raise NBodyError(rc, func, msg.decode() if msg else "")
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape):
+    out = np.ascontiguousarray(a, dtype=np.float64)
+    return out.reshape(shape)
+
+
+def nb_config_default(**kw) -> nb_config:
+    cfg = nb_config()
+    load().nb_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        setattr(cfg, k, v)
+    return cfg
+
+
+def nb_version() -> str:
+    return load().nb_version().decode()
+
+
+def nb_status_string(rc: int) -> str:
+    return load().nb_status_string(rc).decode()
+
+
+def nb_create(cfg: nb_config) -> int:
+    h = _H()
+    rc = load().nb_create(ctypes.byref(cfg), ctypes.byref(h))
+    _check(rc, "nb_create", None)
+    return h.value
+
+
+def nb_destroy(h) -> None:
+    load().nb_destroy(h)
+
+
+def nb_set_stream(h, stream_ptr) -> None:
+    _check(load().nb_set_stream(h, stream_ptr), "nb_set_stream", h)
+
+
+def nb_set_particles(h, m, pos, vel, t0=0.0) -> None:
+    m = _f64(m, (-1,))
+    n = m.shape[0]
+    pos = _f64(pos, (3, n))
+    vel = _f64(vel, (3, n))
+    _check(load().nb_set_particles(h, n, _dp(m), _dp(pos), _dp(vel), float(t0)),
+           "nb_set_particles", h)
+
+
+def nb_init(h) -> None:
+    _check(load().nb_init(h), "nb_init", h)
+
+
+def _n(h) -> int:
+    n = ctypes.c_int(0)
+    load().nb_get_state(h, ctypes.byref(n), None, None, None, None, None, None, None)
+    return n.value
+
+
+def nb_get_particles(h):
+    n = _n(h)
+    m = np.empty(n)
+    pos = np.empty((3, n))
+    vel = np.empty((3, n))
+    _check(load().nb_get_particles(h, _dp(m), _dp(pos), _dp(vel)), "nb_get_particles", h)
+    return m, pos, vel
+
+
+def nb_get_state(h):
+    """dict with m, pos, vel, acc, jerk (3, n), t, dt (n,)."""
+    n = _n(h)
+    out = {"m": np.empty(n), "pos": np.empty((3, n)), "vel": np.empty((3, n)),
+           "acc": np.empty((3, n)), "jerk": np.empty((3, n)), "t": np.empty(n), "dt": np.empty(n)}
+    nn = ctypes.c_int(0)
+    _check(load().nb_get_state(h, ctypes.byref(nn), *[_dp(out[k]) for k in
+                                                       ("m", "pos", "vel", "acc", "jerk", "t", "dt")]),
+           "nb_get_state", h)
+    return out
+
+
+def nb_set_state(h, st) -> None:
+    n = np.asarray(st["m"]).shape[0]
+    arrs = [_f64(st["m"], (n,)), _f64(st["pos"], (3, n)), _f64(st["vel"], (3, n)),
+            _f64(st["acc"], (3, n)), _f64(st["jerk"], (3, n)), _f64(st["t"], (n,)),
+            _f64(st["dt"], (n,))]
+    _check(load().nb_set_state(h, n, *[_dp(a) for a in arrs]), "nb_set_state", h)
+
+
+def nb_predict(h, t) -> None:
+    _check(load().nb_predict(h, float(t)), "nb_predict", h)
+
+
+def nb_force(h, idx=None, n_i=None):
+    """acc (3, n_i), jerk (3, n_i), pot (n_i,) on members idx (None: all particles)."""
+    if idx is None:
+        n_i = _n(h) if n_i is None else int(n_i)
+        ip = None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        n_i = idx.shape[0]
+        ip = idx.ctypes.data_as(_I)
+    acc = np.empty((3, n_i))
+    jerk = np.empty((3, n_i))
+    pot = np.empty(n_i)
+    _check(load().nb_force(h, ip, n_i, _dp(acc), _dp(jerk), _dp(pot)), "nb_force", h)
+    return acc, jerk, pot
+
+
+def nb_force_dev(h, idx_ptr, n_i, acc_ptr, jerk_ptr, pot_ptr) -> None:
+    """Device-pointer force: pointers are ints (0 for NULL); outputs are (3, n_i) rows."""
+    _check(load().nb_force_dev(h, idx_ptr or None, int(n_i), acc_ptr or None, jerk_ptr or None,
+                               pot_ptr or None), "nb_force_dev", h)
+
+
+def nb_force_ext(h, pos, vel):
+    pos = _f64(pos, (3, -1))
+    n_i = pos.shape[1]
+    vel = _f64(vel, (3, n_i))
+    acc = np.empty((3, n_i))
+    jerk = np.empty((3, n_i))
+    pot = np.empty(n_i)
+    _check(load().nb_force_ext(h, n_i, _dp(pos), _dp(vel), _dp(acc), _dp(jerk), _dp(pot)),
+           "nb_force_ext", h)
+    return acc, jerk, pot
+
+
+def nb_correct(h, idx, t, n_i=None) -> None:
+    if idx is None:
+        n_i = _n(h) if n_i is None else int(n_i)
+        ip = None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        n_i = idx.shape[0]
+        ip = idx.ctypes.data_as(_I)
+    _check(load().nb_correct(h, ip, n_i, float(t)), "nb_correct", h)
+
+
+def nb_step(h, t_end) -> dict:
+    st = nb_stats()
+    _check(load().nb_step(h, float(t_end), ctypes.byref(st)), "nb_step", h)
+    return st.as_dict()
+
+
+def nb_energy(h):
+    k = ctypes.c_double()
+    w = ctypes.c_double()
+    _check(load().nb_energy(h, ctypes.byref(k), ctypes.byref(w)), "nb_energy", h)
+    return k.value, w.value
+
+
+def nb_get_stats(h) -> dict:
+    st = nb_stats()
+    _check(load().nb_get_stats(h, ctypes.byref(st)), "nb_get_stats", h)
+    return st.as_dict()
+
+
+def nb_reset_stats(h) -> None:
+    _check(load().nb_reset_stats(h), "nb_reset_stats", h)
+
+
+class System:
+    """One N-body system on the GPU (owns an nb_handle)."""
+
+    def __init__(self, m, pos, vel, t0=0.0, n_max=None, **cfg):
+        """m (n,), pos and vel (n, 3) as ``ic.Particles`` holds them; cfg: nb_config fields."""
+        m = np.asarray(m, dtype=np.float64)
+        n = m.shape[0]
+        cfg.setdefault("n_max", n if n_max is None else n_max)
+        self.cfg = nb_config_default(**cfg)
+        self.h = nb_create(self.cfg)
+        try:
+            nb_set_particles(self.h, m, _f64(pos, (n, 3)).T, _f64(vel, (n, 3)).T, t0)
+        except Exception:
+            self.close()
+            raise
+
+    def close(self):
+        if getattr(self, "h", None):
+            nb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def predict(self, t):
+        nb_predict(self.h, t)
+
+    def force(self, idx=None):
+        return nb_force(self.h, idx)
+
+    def force_ext(self, pos, vel):
+        return nb_force_ext(self.h, pos, vel)
+
+    def correct(self, idx, t):
+        nb_correct(self.h, idx, t)
+
+    def step(self, t_end):
+        return nb_step(self.h, t_end)
+
+    def energy(self):
+        return nb_energy(self.h)
+
+    def state(self):
+        return nb_get_state(self.h)
+
+    def set_state(self, st):
+        nb_set_state(self.h, st)

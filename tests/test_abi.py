@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/*.h declares (no compute call: this runs without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1409_5474_gb300 import build as nb_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(nb_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = nb_build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for core in ("nb_create", "nb_set_particles", "nb_predict", "nb_force", "nb_correct",
+                 "nb_step", "nb_destroy"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1409_5474_gb300 import nbody
+    assert set(_declared()) <= set(nbody.declared_symbols()) | set()
+
+
+def test_status_strings_and_create_without_device(lib):
+    from paper_1409_5474_gb300 import nbody
+    nbody.load()
+    assert nbody.nb_status_string(0) == "NB_OK"
+    assert nbody.nb_status_string(6) == "NB_ERR_NONFINITE"
+    assert "sm_103a" in nbody.nb_version()
+    cfg = nbody.nb_config_default(n_max=16)
+    assert cfg.variant == nbody.NB_F32DS and cfg.dt_max == 1.0 / 16 and cfg.eta == 0.01
+    # argument checks run before any device work
+    for bad in ({"eps": -1.0}, {"eta": 0.0}, {"dt_max": 0.1}, {"n_max": 0}, {"variant": 7},
+                {"dt_min": 0.25, "dt_max": 0.125}):
+        kw = dict(n_max=16)
+        kw.update(bad)
+        c = nbody.nb_config_default(**kw)
+        with pytest.raises(nbody.NBodyError) as ei:
+            nbody.nb_create(c)
+        assert ei.value.status == nbody.NB_ERR_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No library means an error, never a CPU fallback."""
+    from paper_1409_5474_gb300 import nbody
+    saved = nbody._lib
+    nbody._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            nbody.load(str(tmp_path / "none.so"))
+    finally:
+        nbody._lib = saved

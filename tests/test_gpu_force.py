@@ -1,0 +1,194 @@
+"""Parity of the CUDA force path (K1 predict + K2 pair kernels + K3 reduction)
+with the FP64 CPU oracle, through the C ABI.
+
+Gates (relative RMS over the i-set, sqrt(sum |d|^2 / sum |ref|^2)):
+  F64 pairs:          acc, jerk, pot <= 1e-12
+  F32 double-single:  acc, pot <= 1e-6; jerk <= 1e-5 (FP32 velocities; the
+                      jerk's v - 3(r.v)r/s2 cancels)
+  F32 plain:          reported, sanity bound 1e-3 only
+Sizes span the tile and warp edges (1, 2, 3, 31, 32, 33, 1023, 4097 = 32*128+1)
+and every launch mode (j-parallel warps for N_i <= 32, tiles with and without
+a j-split above).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1409_5474_gb300 import ic
+
+pytestmark = pytest.mark.gpu
+
+GATES = {"f64": (1e-12, 1e-12, 1e-12), "f32ds": (1e-6, 1e-5, 1e-6), "f32": (1e-3, 1e-2, 1e-3)}
+
+
+def rel_rms(got, ref):
+    ref = np.asarray(ref)
+    den = float((ref ** 2).sum())
+    num = float(((np.asarray(got) - ref) ** 2).sum())
+    return np.sqrt(num / den) if den > 0 else np.sqrt(num)
+
+
+def _system(n, seed, spread=1.0, offset=0.0):
+    p = ic.plummer(n, seed, masses="lognormal") if n > 1 else ic.Particles(
+        np.array([1.0]), np.array([[0.1, -0.2, 0.3]]), np.array([[0.0, 0.1, 0.0]]))
+    return p.m, p.pos * spread + offset, p.vel
+
+
+def _check(nb, variant, m, pos, vel, eps, idx=None):
+    eps2 = eps * eps
+    with nb.System(m, pos, vel, variant=variant, eps=eps, device=0) as s:
+        s.predict(0.0)
+        acc, jerk, pot = s.force(idx)
+    ra, rj, rp = oracle.force(m, pos, vel, eps2, idx=idx)
+    ga, gj, gp = GATES[variant]
+    ea, ej, ep = rel_rms(acc.T, ra), rel_rms(jerk.T, rj), rel_rms(pot, rp)
+    assert ea <= ga and ej <= gj and ep <= gp, (variant, len(m), ea, ej, ep)
+    return ea, ej, ep
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds", "f32"])
+@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 1023, 4097])
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_full_set_parity(nb, variant, n, eps):
+    m, pos, vel = _system(n, 100 + n)
+    _check(nb, variant, m, pos, vel, eps)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+@pytest.mark.parametrize("n_i", [1, 2, 3, 5, 8, 9, 17, 32, 33, 100, 1000, 4097])
+def test_active_subset_parity(nb, variant, n_i):
+    """Random active subsets (with duplicates) against N = 4097: covers the j-parallel
+    warp kernel (N_i <= 32), the tile kernel with a j-split, and the ragged last tile."""
+    m, pos, vel = _system(4097, 7)
+    rng = np.random.default_rng(n_i)
+    idx = rng.integers(0, 4097, size=n_i).astype(np.int32)
+    if n_i > 3:
+        idx[1] = idx[0]  # a duplicate
+    _check(nb, variant, m, pos, vel, 1e-3, idx=idx)
+
+
+def test_single_particle(nb):
+    m, pos, vel = _system(1, 0)
+    for variant in ("f64", "f32ds"):
+        with nb.System(m, pos, vel, variant=variant, eps=0.1, device=0) as s:
+            s.predict(0.0)
+            acc, jerk, pot = s.force()
+        np.testing.assert_array_equal(acc, 0.0)
+        np.testing.assert_array_equal(jerk, 0.0)
+        assert abs(pot[0]) < 1e-12  # the self term is removed exactly up to rounding
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+def test_far_from_origin_double_single(nb, variant):
+    """A compact cluster centred at x = 1000: FP32 positions lose the separations, the
+    double-single relative coordinate keeps them (paper Sect. III.A)."""
+    m, pos, vel = _system(512, 9, spread=1e-3, offset=1000.0)
+    ea, ej, ep = _check(nb, variant, m, pos, vel, 1e-6)
+    with nb.System(m, pos, vel, variant="f32", eps=1e-6, device=0) as s:
+        s.predict(0.0)
+        acc, _, _ = s.force()
+    ra, _, _ = oracle.force(m, pos, vel, 1e-12)
+    assert rel_rms(acc.T, ra) > 100 * ea  # plain FP32 is visibly worse here
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+def test_external_i_set(nb, variant):
+    m, pos, vel = _system(2000, 10)
+    rng = np.random.default_rng(3)
+    ipos = rng.normal(size=(37, 3))
+    ivel = rng.normal(size=(37, 3))
+    eps = 0.01
+    with nb.System(m, pos, vel, variant=variant, eps=eps, device=0) as s:
+        s.predict(0.0)
+        acc, jerk, pot = s.force_ext(ipos.T, ivel.T)
+    ra, rj, rp = oracle.force_ext(m, pos, vel, eps * eps, ipos, ivel)
+    ga, gj, gp = GATES[variant]
+    assert rel_rms(acc.T, ra) <= ga and rel_rms(jerk.T, rj) <= gj and rel_rms(pot, rp) <= gp
+
+
+def test_predictor_parity(nb):
+    """nb_predict + nb_force at t > t0 equals the oracle's prediction followed by its force."""
+    p = ic.plummer(700, 12)
+    eps = 0.02
+    with nb.System(p.m, p.pos, p.vel, variant="f64", eps=eps, device=0) as s:
+        nb.nb_init(s.h)  # acc, jerk at t0 (and the first steps)
+        st = s.state()
+        s.predict(0.01)
+        acc, jerk, pot = s.force()
+    pp, vp = oracle.predict(0.01, st["t"], st["pos"].T, st["vel"].T, st["acc"].T, st["jerk"].T)
+    ra, rj, rp = oracle.force(p.m, pp, vp, eps * eps)
+    assert rel_rms(acc.T, ra) < 1e-12 and rel_rms(jerk.T, rj) < 1e-12
+
+
+def test_errors(nb):
+    m, pos, vel = _system(64, 13)
+    with nb.System(m, pos, vel, variant="f32ds", eps=0.01, device=0) as s:
+        with pytest.raises(nb.NBodyError) as e:
+            s.force()
+        assert e.value.status == nb.NB_ERR_STATE
+        s.predict(0.0)
+        with pytest.raises(nb.NBodyError) as e:
+            s.force(np.array([0, 64], dtype=np.int32))
+        assert e.value.status == nb.NB_ERR_ARG
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nb_set_particles(s.h, np.ones(65), np.zeros((3, 65)), np.zeros((3, 65)))
+        assert e.value.status == nb.NB_ERR_ARG
+        bad = pos.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nb_set_particles(s.h, m, bad.T, vel.T)
+        assert e.value.status == nb.NB_ERR_NONFINITE
+    # coincident distinct particles without softening overflow: reported, not returned
+    pos2 = pos.copy()
+    pos2[5] = pos2[6]
+    with nb.System(m, pos2, vel, variant="f64", eps=0.0, device=0) as s:
+        s.predict(0.0)
+        with pytest.raises(nb.NBodyError) as e:
+            s.force()
+        assert e.value.status == nb.NB_ERR_NONFINITE
+    with pytest.raises(nb.NBodyError) as e:
+        nb.System(m, pos, vel, budget_bytes=1000, device=0)
+    assert e.value.status == nb.NB_ERR_BUDGET
+
+
+def test_force_dev_matches_host_call(nb):
+    torch = pytest.importorskip("torch")
+    m, pos, vel = _system(3000, 14)
+    idx = np.arange(0, 3000, 7, dtype=np.int32)
+    with nb.System(m, pos, vel, variant="f32ds", eps=0.01, device=0) as s:
+        nb.nb_set_stream(s.h, torch.cuda.current_stream().cuda_stream)
+        s.predict(0.0)
+        acc_h, jerk_h, pot_h = s.force(idx)
+        d_idx = torch.from_numpy(idx).cuda()
+        out = torch.empty((7, idx.size), dtype=torch.float64, device="cuda")
+        nb.nb_force_dev(s.h, d_idx.data_ptr(), idx.size, out[0:3].data_ptr(), out[3:6].data_ptr(),
+                        out[6].data_ptr())
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        nb.nb_set_stream(s.h, 0)
+    np.testing.assert_array_equal(got[0:3], acc_h)
+    np.testing.assert_array_equal(got[3:6], jerk_h)
+    np.testing.assert_array_equal(got[6], pot_h)
+
+
+@pytest.mark.slow
+def test_full_size_sampled_2pow20(nb):
+    """The N = 2^20 single full evaluation (eps = 1e-4, log-normal masses), every variant,
+    checked on a seeded 1024-particle i-subset (the oracle evaluates it one i at a time)."""
+    p = ic.plummer(2 ** 20, ic.MASTER_SEED + 3, masses="lognormal")
+    eps = 1e-4
+    rng = np.random.default_rng(2014)
+    sample = np.sort(rng.choice(2 ** 20, size=1024, replace=False)).astype(np.int32)
+    ra, rj, rp = oracle.force(p.m, p.pos, p.vel, eps * eps, idx=sample)
+    for variant in ("f32ds", "f32", "f64"):
+        with nb.System(p.m, p.pos, p.vel, variant=variant, eps=eps, device=0) as s:
+            s.predict(0.0)
+            if variant == "f64":
+                acc, jerk, pot = s.force(sample)   # FP64 on the sample only
+            else:
+                acc, jerk, pot = s.force()          # the full N^2 launch, sampled afterwards
+                acc, jerk, pot = acc[:, sample], jerk[:, sample], pot[sample]
+        ga, gj, gp = GATES[variant]
+        ea, ej, ep = rel_rms(acc.T, ra), rel_rms(jerk.T, rj), rel_rms(pot, rp)
+        print(variant, ea, ej, ep)
+        assert ea <= ga and ej <= gj and ep <= gp, (variant, ea, ej, ep)

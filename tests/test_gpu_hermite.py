@@ -1,0 +1,156 @@
+"""Parity of the CUDA block-step Hermite path (K1-K5 through nb_step) with the
+FP64 CPU oracle, plus the invariants that hold at any size.
+
+Trajectories of N-body systems diverge exponentially (paper Sect. VI), so
+long-horizon comparisons use energy and invariants; short horizons compare
+states directly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1409_5474_gb300 import ic
+
+pytestmark = pytest.mark.gpu
+
+
+def _energy_oracle(m, pos, vel, eps2):
+    k, w = oracle.energy(m, pos, vel, eps2)
+    return k + w
+
+
+def test_small_case_shared_steps_fp64(nb):
+    """N = 1024 Plummer, eps = 1/64, shared dt = 1/256, FP64 pairs, one time unit:
+    energy drift <= 1e-6; state close to the oracle's; per-step force parity 1e-12."""
+    p = ic.plummer(1024)
+    eps = 1.0 / 64
+    eps2 = eps * eps
+    st = oracle.State(p.m, p.pos, p.vel)
+    e0 = _energy_oracle(p.m, p.pos, p.vel, eps2)
+    oracle.hermite_run(st, 0.25, eps2, dt_shared=1.0 / 256)
+    with nb.System(p.m, p.pos, p.vel, variant="f64", eps=eps, shared_dt=1.0 / 256, device=0) as s:
+        k0, w0 = s.energy()
+        assert abs((k0 + w0) - e0) < 1e-13
+        stats = s.step(0.25)
+        assert stats["block_steps"] == 64
+        g = s.state()
+        # state after a quarter time unit agrees with the oracle's run
+        assert np.abs(g["pos"].T - st.pos).max() < 1e-9
+        # per-evaluation parity on the GPU's own state
+        s.predict(0.25)
+        acc, jerk, pot = s.force()
+        ra, rj, rp = oracle.force(p.m, g["pos"].T, g["vel"].T, eps2)
+        assert np.sqrt(((acc.T - ra) ** 2).sum() / (ra ** 2).sum()) < 1e-12
+        assert np.sqrt(((jerk.T - rj) ** 2).sum() / (rj ** 2).sum()) < 1e-12
+        s.step(1.0)
+        k1, w1 = s.energy()
+    assert abs((k1 + w1 - e0) / e0) < 1e-6
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+def test_block_steps_short_horizon(nb, variant):
+    """Block steps (eta = 0.02, dt_max = 1/16) over 1/16 time unit: same schedule as the
+    oracle (block-step count and interactions within a few percent), positions close."""
+    p = ic.plummer(512, 31)
+    eps = 0.01
+    st = oracle.State(p.m, p.pos, p.vel)
+    o_steps, o_inter = oracle.hermite_run(st, 1.0 / 16, eps * eps, eta=0.02, dt_max=1.0 / 16)
+    with nb.System(p.m, p.pos, p.vel, variant=variant, eps=eps, eta=0.02, dt_max=1.0 / 16,
+                   device=0) as s:
+        stats = s.step(1.0 / 16)
+        g = s.state()
+    np.testing.assert_array_equal(g["t"], 1.0 / 16)
+    if variant == "f64":
+        assert stats["block_steps"] == o_steps
+        assert abs(stats["interactions"] - o_inter) <= 0.02 * o_inter
+        assert np.abs(g["pos"].T - st.pos).max() < 1e-8
+        assert (g["dt"] == st.dt).mean() > 0.99
+    else:
+        assert abs(stats["block_steps"] - o_steps) <= 0.05 * o_steps
+        assert np.abs(g["pos"].T - st.pos).max() < 1e-5
+
+
+def test_block_invariants_and_energy(nb):
+    p = ic.plummer(2048, 32)
+    eps = 1e-3
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.01, dt_max=1.0 / 16,
+                   device=0) as s:
+        k0, w0 = s.energy()
+        stats = s.step(0.125)
+        g = s.state()
+        k1, w1 = s.energy()
+    np.testing.assert_array_equal(g["t"], 0.125)
+    lg = np.log2(g["dt"])
+    np.testing.assert_array_equal(lg, np.round(lg))
+    np.testing.assert_array_equal(np.fmod(g["t"], g["dt"]), 0.0)
+    assert stats["block_steps"] >= 8 and sum(stats["active_hist"]) == stats["block_steps"]
+    assert abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0) < 1e-5
+
+
+def test_schedule_counts_two_binaries(nb):
+    """Exact scheduler counts: tight binary 128 steps, wide binary 16 over 2^-6."""
+    pos, vel = [], []
+    import math
+    for cx, d in ((-5.0, 0.01), (5.0, 0.04)):
+        w = math.sqrt(0.5 / d ** 3)
+        pos += [[cx - d / 2, 0, 0], [cx + d / 2, 0, 0]]
+        vel += [[0, -w * d / 2, 0], [0, w * d / 2, 0]]
+    with nb.System(np.full(4, 0.25), np.array(pos), np.array(vel), variant="f64", eps=0.0,
+                   eta=0.01, eta_s=0.1, dt_max=1.0 / 16, device=0) as s:
+        stats = s.step(2.0 ** -6)
+        g = s.state()
+    np.testing.assert_array_equal(g["dt"], [2.0 ** -13] * 2 + [2.0 ** -10] * 2)
+    assert stats["block_steps"] == 128
+    assert stats["interactions"] == 16 + 4 * (2 * 128 + 2 * 16)
+
+
+def test_checkpoint_resume_bitwise(nb):
+    p = ic.plummer(800, 33)
+    kw = dict(variant="f32ds", eps=0.01, eta=0.02, device=0)
+    with nb.System(p.m, p.pos, p.vel, **kw) as a:
+        a.step(1.0 / 16)
+        ck = a.state()
+        a.step(1.0 / 8)
+        full = a.state()
+    with nb.System(ck["m"], ck["pos"].T, ck["vel"].T, **kw) as b:
+        b.set_state(ck)
+        b.step(1.0 / 8)
+        res = b.state()
+    for k in ("pos", "vel", "acc", "jerk", "dt"):
+        np.testing.assert_array_equal(res[k], full[k])
+
+
+def test_equal_block_steps_equal_shared_steps(nb):
+    p = ic.plummer(300, 34)
+    dt = 1.0 / 256
+    with nb.System(p.m, p.pos, p.vel, variant="f64", eps=0.01, shared_dt=dt, device=0) as a:
+        a.step(16 * dt)
+        sa = a.state()
+    with nb.System(p.m, p.pos, p.vel, variant="f64", eps=0.01, dt_min=dt, dt_max=dt,
+                   device=0) as b:
+        b.step(16 * dt)
+        sb = b.state()
+    np.testing.assert_array_equal(sa["pos"], sb["pos"])
+    np.testing.assert_array_equal(sa["vel"], sb["vel"])
+
+
+def test_manual_calls_equal_one_block_step(nb):
+    """nb_predict + nb_force(due set) + nb_correct reproduce the first block step of nb_step."""
+    p = ic.plummer(400, 35)
+    kw = dict(variant="f64", eps=0.01, eta=0.02, device=0)
+    with nb.System(p.m, p.pos, p.vel, **kw) as a:
+        nb.nb_init(a.h)
+        s0 = a.state()
+        t_next = float((s0["t"] + s0["dt"]).min())
+        due = np.nonzero(s0["t"] + s0["dt"] == t_next)[0].astype(np.int32)
+        a.predict(t_next)
+        a.force(due)
+        a.correct(due, t_next)
+        ma = a.state()
+    with nb.System(p.m, p.pos, p.vel, **kw) as b:
+        nb.nb_init(b.h)
+        stats = b.step(t_next)
+        mb = b.state()
+    assert stats["block_steps"] == 1
+    for k in ("pos", "vel", "acc", "jerk", "t", "dt"):
+        np.testing.assert_array_equal(ma[k], mb[k])
