@@ -209,6 +209,40 @@ int nb_energy(nb_handle h, double *kin, double *pot);
 int nb_get_stats(nb_handle h, nb_stats *st);
 int nb_reset_stats(nb_handle h);
 
+/* ---- allocation-free force evaluation -----------------------------------
+ * The paper has no counterpart of this call; it exists for callers that
+ * cannot call cudaMalloc: a host code that gives all of its device memory to
+ * its own pool allocator (a tree code coupled to this library, say) and bars
+ * other allocations, since cudaMalloc synchronises the device and fragments
+ * the pool, or code that runs where no allocation is allowed.
+ *
+ * nb_force_static computes what nb_force computes with FP64 pair arithmetic
+ * (NB_F64), but on caller-owned device buffers and with no handle:
+ *   n_j            j-particles; m[n_j], pos and vel as 3 rows of stride ld
+ *                  (x at pos[0..n_j), y at pos[ld..), z at pos[2 ld..)), ld >= n_j;
+ *   n_i, idx       i-set: device int32 indices into the j-set (NULL: 0..n_i-1,
+ *                  then n_i <= n_j); the pair i == j is left out;
+ *   eps            softening (>= 0);
+ *   acc, jerk      outputs, 3 rows of stride n_i each; pot: n_i values (device;
+ *                  any may be NULL);
+ *   stream         cudaStream_t of the work (NULL: the legacy default stream).
+ * The call returns after the results are in the output buffers.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the partial
+ * sums of its j-split live in a file-scope device array of
+ * NB_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU which loads the
+ * library holds until the process exits. The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other
+ * threads) race: serialise them. Sizes: n_i <= NB_STATIC_MAX_NI, else
+ * NB_ERR_ARG; an index outside [0, n_j) gives NB_ERR_ARG, a non-finite result
+ * NB_ERR_NONFINITE, a CUDA failure NB_ERR_CUDA. */
+#define NB_STATIC_MAX_NI 1024
+#define NB_STATIC_SCRATCH_DOUBLES (1 << 20)
+int nb_force_static(int n_j, const double *m, const double *pos, const double *vel,
+                    long long ld, int n_i, const int *idx, double eps, double *acc,
+                    double *jerk, double *pot, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

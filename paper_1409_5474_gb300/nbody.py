@@ -100,6 +100,10 @@ _SIGS = [
     ("nb_energy", ctypes.c_int, [_H, _D, _D]),
     ("nb_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_stats)]),
     ("nb_reset_stats", ctypes.c_int, [_H]),
+    ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 
@@ -292,6 +296,20 @@ def nb_get_stats(h) -> dict:
 
 def nb_reset_stats(h) -> None:
     _check(load().nb_reset_stats(h), "nb_reset_stats", h)
+
+
+NB_STATIC_MAX_NI = 1024
+
+
+def nb_force_static(n_j, m_ptr, pos_ptr, vel_ptr, ld, n_i, idx_ptr, eps, acc_ptr, jerk_ptr,
+                    pot_ptr, stream_ptr=0) -> None:
+    """Allocation-free FP64 force on caller-owned device buffers (pointers as ints, 0 = NULL).
+    For callers that cannot allocate device memory; see nbody.h."""
+    rc = load().nb_force_static(int(n_j), m_ptr, pos_ptr, vel_ptr, int(ld), int(n_i),
+                                idx_ptr or None, float(eps), acc_ptr or None, jerk_ptr or None,
+                                pot_ptr or None, stream_ptr or None)
+    if rc != NB_OK:
+        raise NBodyError(rc, "nb_force_static", nb_status_string(rc))
 
 
 class System:
