@@ -62,8 +62,18 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="block65536")
     ap.add_argument("--variant", choices=["f32", "f32ds", "f64"], default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="override the workload's particle count (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
+
+
+def workload(args):
+    wl = dict(WORKLOADS[args.workload])
+    if args.n:
+        wl["n"] = args.n
+        wl["desc"] = wl["desc"] + " [N overridden to %d]" % args.n
+    return wl
 
 
 # ---------------------------------------------------------------------------
@@ -222,7 +232,7 @@ def oracle_sample(wl, particles):
 
 def make_particles(wl):
     from paper_1409_5474_gb300 import ic
-    return ic.plummer(wl["n"], ic.MASTER_SEED + (3 if wl["n"] == 2 ** 20 else 0),
+    return ic.plummer(wl["n"], ic.MASTER_SEED + (3 if wl["masses"] == "lognormal" else 0),
                       masses=wl["masses"])
 
 
@@ -245,7 +255,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    wl = WORKLOADS[args.workload]
+    wl = workload(args)
     variant = args.variant or wl["variant"]
     p = make_particles(wl)
     inter_t = secs_t = 0.0
@@ -281,10 +291,11 @@ def run_ours(args):
     from paper_1409_5474_gb300 import nbody
 
     nbody.load()
-    wl = WORKLOADS[args.workload]
+    wl = workload(args)
     variant = args.variant or wl["variant"]
     p = make_particles(wl)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
+    torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     cfg = dict(variant=variant, eps=wl["eps"], device=local, flags=nbody.NB_FLAG_TIMING)
     if wl["kind"] == "evolve":

@@ -119,8 +119,9 @@ const char *nb_version(void);
 int nb_create(const nb_config *cfg, nb_handle *out);
 int nb_destroy(nb_handle h);
 
-/* Stream for all later device work of h (a cudaStream_t; NULL = the
- * library's own stream). The caller keeps the stream alive. */
+/* Stream for all later device work of h (a cudaStream_t; NULL selects the
+ * CUDA default stream). A new handle works on a non-blocking stream of its
+ * own. The caller keeps the stream alive. */
 int nb_set_stream(nb_handle h, void *stream);
 
 /* ---- state ----------------------------------------------------------------

@@ -572,7 +572,7 @@ int nb_set_stream(nb_handle h, void *stream)
     if (!h) return NB_ERR_ARG;
     cudaSetDevice(h->dev);
     CK(h, cudaStreamSynchronize(h->stream));
-    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    h->stream = static_cast<cudaStream_t>(stream);  // NULL: the default stream
     return NB_OK;
 }
 

@@ -165,7 +165,6 @@ def test_force_dev_matches_host_call(nb):
                         out[6].data_ptr())
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        nb.nb_set_stream(s.h, 0)
     np.testing.assert_array_equal(got[0:3], acc_h)
     np.testing.assert_array_equal(got[3:6], jerk_h)
     np.testing.assert_array_equal(got[6], pot_h)
