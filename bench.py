@@ -355,6 +355,8 @@ def run_ours(args):
     launches = 0
     force_ms = reduce_ms = 0.0
     force_launches = 0
+    other_ms = {"sched_ms": 0.0, "predict_ms": 0.0, "correct_ms": 0.0}
+    block_steps = 0
     for k in range(args.warmup, args.warmup + args.steps):
         flush.fill_(float(k))                              # L2 flush between timed steps
         inter, ms, wall, nl, st, host_state = one_step(k, host_state)
@@ -365,6 +367,9 @@ def run_ours(args):
         force_ms += st["force_ms"]
         reduce_ms += st["reduce_ms"]
         force_launches += st["force_launches"]
+        for key in other_ms:
+            other_ms[key] += st.get(key, 0.0)
+        block_steps += st.get("block_steps", 0)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     dist.barrier()
@@ -399,6 +404,8 @@ def run_ours(args):
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "force_ms": force_ms, "reduce_ms": reduce_ms,
                      "force_launches": force_launches},
+        "kernel_ms": dict(other_ms, force_ms=force_ms, reduce_ms=reduce_ms),
+        "block_steps": block_steps,
         "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8,
                 "d2h_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8},

@@ -118,6 +118,12 @@ struct nb_handle_s {
     unsigned long long *d_dtmin = nullptr;
     double *d_energy = nullptr;
     Mailbox *mail_h = nullptr, *mail_d = nullptr;
+    SchedDev *sd = nullptr;                // scheduler state on the device
+    unsigned long long *sched_status = nullptr;  // look-back words, one per tile
+    unsigned long long seq_next = 1;       // host mirror of sd->seq
+    bool sched_valid = false;              // sd->t_cur / hist match the particles
+    double t_cur = 0.0;                    // host mirror of the last block time
+    cudaEvent_t ev_sched = nullptr;
 
     size_t bytes = 0;  // device bytes held
 
@@ -324,6 +330,70 @@ int predict_to(nb_handle h, double t)
     return NB_OK;
 }
 
+int level_of(double dt, double dt_max)
+{
+    int k = std::ilogb(dt_max) - std::ilogb(dt);
+    return k < 0 ? 0 : (k >= NLEVEL ? NLEVEL - 1 : k);
+}
+
+// Build the scheduler state from host copies of t and dt: the last block time
+// t_cur = max t_i and the level histogram. Block steps need every t_i to be a
+// multiple of its dt_i and t_cur < t_i + dt_i (no particle overdue); shared
+// steps need all t_i equal.
+int load_sched(nb_handle h, const double *t, const double *dt)
+{
+    const int n = h->n;
+    double tc = t[0];
+    for (int i = 1; i < n; ++i) tc = std::max(tc, t[i]);
+    std::vector<int> hist(NLEVEL, 0);
+    if (h->cfg.shared_dt > 0.0) {
+        for (int i = 0; i < n; ++i)
+            if (t[i] != tc) return fail(h, NB_ERR_STATE, "shared steps need equal particle times");
+    } else {
+        for (int i = 0; i < n; ++i) {
+            if (std::fmod(t[i], dt[i]) != 0.0 || !(tc < t[i] + dt[i]))
+                return fail(h, NB_ERR_STATE,
+                            "particle %d: t = %.17g is not a block time of its step %.17g "
+                            "(or it is overdue at t = %.17g)", i, t[i], dt[i], tc);
+            if (dt[i] > h->cfg.dt_max || dt[i] < h->cfg.dt_min)
+                return fail(h, NB_ERR_STATE, "particle %d: step outside [dt_min, dt_max]", i);
+            hist[level_of(dt[i], h->cfg.dt_max)]++;
+        }
+    }
+    CK(h, cudaMemcpyAsync(&h->sd->t_cur, &tc, sizeof tc, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->sd->hist, hist.data(), NLEVEL * sizeof(int), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->t_cur = tc;
+    h->sched_valid = true;
+    return NB_OK;
+}
+
+int rebuild_sched(nb_handle h)
+{
+    const int n = h->n;
+    std::vector<double> t(n), dt(n);
+    CK(h, cudaMemcpyAsync(t.data(), h->t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(dt.data(), h->dt, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return load_sched(h, t.data(), dt.data());
+}
+
+// Wait until the scheduler launch number `epoch` has published its mailbox.
+int wait_mail(nb_handle h, unsigned long long epoch)
+{
+    volatile Mailbox *mb = h->mail_h;
+    for (int spin = 0; spin < 20000; ++spin)
+        if (mb->seq == epoch) return NB_OK;
+    CK(h, cudaEventSynchronize(h->ev_sched));
+    if (mb->seq != epoch) {
+        int rc = check_err(h);
+        if (rc) return rc;
+        return fail(h, NB_ERR_CUDA, "scheduler %llu did not publish its result", epoch);
+    }
+    return NB_OK;
+}
+
 int do_init(nb_handle h)
 {
     // all own times are equal at set-up: predict with d = 0 builds the records
@@ -337,12 +407,15 @@ int do_init(nb_handle h)
     if (rc) return rc;
     StateDev s = state_of(h);
     StepParams p = params_of(h);
-    CK(h, launch_init_steps(s, f, p, h->d_err, h->stream));
+    CK(h, cudaMemsetAsync(h->sd->hist, 0, NLEVEL * sizeof(int), h->stream));
+    CK(h, launch_init_steps(s, f, p, h->sd, h->d_err, h->stream));
     h->stats.kernel_launches++;
     rc = check_err(h);
     if (rc) return rc;
     h->initialised = true;
     h->predicted = false;
+    h->t_cur = t0;
+    h->sched_valid = true;
     return NB_OK;
 }
 
@@ -535,13 +608,33 @@ int nb_create(const nb_config *cfg, nb_handle *out)
         cudaMemsetAsync(h->d_dtmin, 0, 256, h->stream) != cudaSuccess ||
         cudaHostAlloc(&h->mail_h, sizeof(Mailbox), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(&h->mail_d, h->mail_h, 0) != cudaSuccess ||
+        cudaMalloc(&h->sd, sizeof(SchedDev)) != cudaSuccess ||
+        cudaMemsetAsync(h->sd, 0, sizeof(SchedDev), h->stream) != cudaSuccess ||
+        cudaMalloc(&h->sched_status, sizeof(unsigned long long) *
+                                         ((h->cap + SCHED_TILE - 1) / SCHED_TILE)) != cudaSuccess ||
+        cudaMemsetAsync(h->sched_status, 0, sizeof(unsigned long long) *
+                                                ((h->cap + SCHED_TILE - 1) / SCHED_TILE),
+                        h->stream) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_sched, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
         int code = fail(nullptr, NB_ERR_CUDA, "device set-up failed");
         bail(code);
         return code;
     }
-    h->bytes += 3 * 256;
+    h->bytes += 3 * 256 + sizeof(SchedDev) +
+                sizeof(unsigned long long) * ((h->cap + SCHED_TILE - 1) / SCHED_TILE);
+    {
+        const unsigned long long one = 1;
+        std::memset((void *)h->mail_h, 0, sizeof(Mailbox));
+        if (cudaMemcpy(&h->sd->seq, &one, sizeof one, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            int code = fail(nullptr, NB_ERR_CUDA, "device set-up failed");
+            bail(code);
+            return code;
+        }
+        h->seq_next = 1;
+    }
     *out = h;
     return NB_OK;
 }
@@ -560,6 +653,9 @@ int nb_destroy(nb_handle h)
     cudaFree(h->d_err);
     cudaFree(h->d_dtmin);
     cudaFree(h->d_energy);
+    cudaFree(h->sd);
+    cudaFree(h->sched_status);
+    if (h->ev_sched) cudaEventDestroy(h->ev_sched);
     if (h->mail_h) cudaFreeHost(h->mail_h);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     cudaGetLastError();
@@ -600,6 +696,7 @@ int nb_set_particles(nb_handle h, int n, const double *m, const double *pos, con
     h->have_particles = true;
     h->initialised = false;
     h->predicted = false;
+    h->sched_valid = false;
     h->last_force_n = -1;
     return NB_OK;
 }
@@ -654,12 +751,22 @@ int nb_set_state(nb_handle h, int n, const double *m, const double *pos, const d
     int rc = validate_host(h, n, m, pos, vel);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
-        if (!std::isfinite(t[i]) || !is_pow2(dt[i]))
-            return fail(h, NB_ERR_ARG, "particle %d: t must be finite and dt a power of two", i);
+        if (!std::isfinite(t[i]) || !(dt[i] > 0.0) || !std::isfinite(dt[i]))
+            return fail(h, NB_ERR_ARG, "particle %d: t must be finite and dt > 0", i);
+        if (h->cfg.shared_dt <= 0.0 && !is_pow2(dt[i]))
+            return fail(h, NB_ERR_ARG, "particle %d: block steps must be powers of two", i);
     }
     cudaSetDevice(h->dev);
     CK(h, cudaStreamSynchronize(h->stream));
+    const int n_prev = h->n;
     h->n = n;
+    {
+        int rc2 = load_sched(h, t, dt);
+        if (rc2) {
+            h->n = n_prev;
+            return rc2 == NB_ERR_STATE ? fail(h, NB_ERR_ARG, "%s", h->msg.c_str()) : rc2;
+        }
+    }
     CK(h, cudaMemcpyAsync(h->m, m, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, h2d_rows(h->pos, h->ld, pos, n, 3, h->stream));
     CK(h, h2d_rows(h->vel, h->ld, vel, n, 3, h->stream));
@@ -819,13 +926,14 @@ int nb_correct(nb_handle h, const int *idx, int n_i, double t)
     StateDev s = state_of(h);
     StepParams p = params_of(h);
     int rc = timed(h, T_CORRECT, [&] {
-        return launch_correct(s, idx ? h->d_idx : nullptr, n_i, t, f, p, h->d_err, h->d_dtmin,
-                              h->stream);
+        return launch_correct(s, idx ? h->d_idx : nullptr, n_i, t, f, p, h->sd, h->d_err,
+                              h->d_dtmin, h->stream);
     });
     if (rc) return rc;
     h->predicted = false;
     h->last_force_n = -1;
     h->initialised = true;
+    h->sched_valid = false;
     return check_err(h);
 }
 
@@ -842,30 +950,77 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         rc = do_init(h);
         if (rc) return rc;
     }
+    if (!h->sched_valid) {
+        rc = rebuild_sched(h);
+        if (rc) return rc;
+    }
     StateDev s = state_of(h);
     StepParams prm = params_of(h);
     const bool rec = h->cfg.variant != NB_F64;
     Out3 f{h->f_acc, h->f_jerk, h->f_pot, h->ld};
-    volatile Mailbox *mb = h->mail_h;
-    for (;;) {
-        rc = timed(h, T_SCHED, [&] { return launch_sched(s, h->act, h->mail_d, h->stream); });
-        if (rc) return rc;
-        CK(h, cudaStreamSynchronize(h->stream));
-        const double t_next = mb->t_next;
-        const int na = mb->n_active;
-        if (!(t_next <= t_end)) break;
-        rc = timed(h, T_PREDICT, [&] { return launch_predict(s, t_next, rec, h->d_err, h->stream); });
-        if (rc) return rc;
-        rc = run_force(h, h->cfg.variant, members_of(h, h->act, na), f);
-        if (rc) return rc;
-        rc = timed(h, T_CORRECT, [&] {
-            return launch_correct(s, h->act, na, t_next, f, prm, h->d_err, h->d_dtmin, h->stream);
-        });
-        if (rc) return rc;
+    auto count_step = [&](int na) {
         h->stats.block_steps++;
         int lg = 0;
         while ((2LL << lg) <= na && lg < 31) ++lg;
         h->stats.active_hist[lg]++;
+    };
+    if (prm.shared_dt > 0.0) {
+        // shared steps: every particle is due at t_cur + dt; the host knows the
+        // schedule, so the launches are queued without waiting on the device
+        const ISet all = members_of(h, nullptr, h->n);
+        for (;;) {
+            const double t_next = h->t_cur + prm.shared_dt;
+            if (!(t_next <= t_end)) break;
+            rc = timed(h, T_PREDICT,
+                       [&] { return launch_predict(s, t_next, rec, h->d_err, h->stream); });
+            if (rc) return rc;
+            rc = run_force(h, h->cfg.variant, all, f);
+            if (rc) return rc;
+            rc = timed(h, T_CORRECT, [&] {
+                return launch_correct(s, nullptr, h->n, t_next, f, prm, h->sd, h->d_err,
+                                      h->d_dtmin, h->stream);
+            });
+            if (rc) return rc;
+            h->t_cur = t_next;
+            count_step(h->n);
+        }
+    } else {
+        // block steps: the fused scheduler + predictor publishes (t_next, N_active)
+        // to the mailbox; the force, corrector and the next scheduler launch are
+        // queued as soon as it is read
+        auto launch_sched = [&]() -> int {
+            const unsigned long long ep = h->seq_next++;
+            int r = timed(h, T_SCHED, [&] {
+                return launch_sched_predict(s, h->sd, h->sched_status, h->act, h->mail_d,
+                                            prm.dt_max, rec, h->d_err, h->stream);
+            });
+            if (r) return r;
+            CK(h, cudaEventRecord(h->ev_sched, h->stream));
+            (void)ep;
+            return NB_OK;
+        };
+        rc = launch_sched();
+        if (rc) return rc;
+        for (;;) {
+            rc = wait_mail(h, h->seq_next - 1);
+            if (rc) return rc;
+            const double t_next = h->mail_h->t_next;
+            const int na = h->mail_h->n_active;
+            if (!(t_next <= t_end)) break;
+            if (na < 1 || na > h->n)
+                return fail(h, NB_ERR_STATE, "scheduler returned %d due particles", na);
+            rc = run_force(h, h->cfg.variant, members_of(h, h->act, na), f);
+            if (rc) return rc;
+            rc = timed(h, T_CORRECT, [&] {
+                return launch_correct(s, h->act, na, t_next, f, prm, h->sd, h->d_err, h->d_dtmin,
+                                      h->stream);
+            });
+            if (rc) return rc;
+            h->t_cur = t_next;
+            count_step(na);
+            rc = launch_sched();
+            if (rc) return rc;
+        }
     }
     h->predicted = false;
     h->last_force_n = -1;

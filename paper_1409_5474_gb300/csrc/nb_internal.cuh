@@ -94,12 +94,33 @@ struct StepParams {
     double eta, eta_s, dt_min, dt_max, shared_dt;
 };
 
-// Mailbox the scheduler writes (mapped host memory) after each block step.
-struct Mailbox {
-    double t_next;
-    int n_active;
+// Step levels: dt = dt_max * 2^-k, k in [0, NLEVEL).
+constexpr int NLEVEL = 64;
+
+// Device-side state of the block scheduler.
+struct SchedDev {
+    double t_cur;                 // time of the last block step (max_i t_i)
+    unsigned long long seq;       // number of the next scheduler launch (look-back epoch)
+    unsigned ticket;              // tile tickets handed out in the running launch
+    unsigned done;                // CTAs finished in the running launch
+    int n_active;                 // due count, written by the CTA of the last tile
     int pad;
+    int hist[NLEVEL];             // particles per step level
 };
+
+// Mailbox the scheduler writes (mapped host memory) after each launch: the
+// host polls seq, then reads t_next and n_active.
+struct Mailbox {
+    volatile unsigned long long seq;
+    volatile double t_next;
+    volatile int n_active;
+    volatile int pad;
+};
+
+// Particles per scheduler CTA (256 threads x 8).
+constexpr int SCHED_THREADS = 256;
+constexpr int SCHED_PER_THREAD = 8;
+constexpr int SCHED_TILE = SCHED_THREADS * SCHED_PER_THREAD;
 
 // K1: predict all particles of s to time t (FP64), writing pos_p, vel_p and,
 // when want_rec, the DS records.
@@ -107,17 +128,27 @@ cudaError_t launch_predict(const StateDev &s, double t, bool want_rec, unsigned 
                            cudaStream_t st);
 
 // K4: Hermite corrector + new step for the n_a particles act[k] to time t_new,
-// with the new acc/jerk in f (slot-indexed). dtmin_hits counts clamps.
+// with the new acc/jerk in f (slot-indexed). dtmin_hits counts clamps. Keeps
+// the level histogram of sd up to date and sets sd->t_cur = t_new.
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new,
-                           const Out3 &f, const StepParams &p, unsigned *err,
+                           const Out3 &f, const StepParams &p, SchedDev *sd, unsigned *err,
                            unsigned long long *dtmin_hits, cudaStream_t st);
 
-// K4 at start-up: initial steps from acc/jerk (slot k = particle k), or the shared step.
+// K4 at start-up: initial steps from acc/jerk (slot k = particle k), or the
+// shared step; adds every particle to the level histogram (zeroed by the caller).
 cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams &p,
-                              unsigned *err, cudaStream_t st);
+                              SchedDev *sd, unsigned *err, cudaStream_t st);
 
-// K5: t_next = min(t_i + dt_i) and the due particles in ascending order.
-cudaError_t launch_sched(const StateDev &s, int *act, Mailbox *mail_dev, cudaStream_t st);
+// K5 + K1 fused (block steps): t_next from the level histogram and t_cur (the
+// next multiple of the smallest occupied step after t_cur, which equals
+// min_i(t_i + dt_i) when every t_i is a multiple of dt_i and t_i <= t_cur <
+// t_i + dt_i); predicts every particle to t_next (FP64 + DS records); writes
+// the due particles (t_i + dt_i == t_next) to act in ascending index with a
+// single-pass decoupled look-back scan over tiles; the last CTA publishes
+// (seq, t_next, n_active) to the mailbox. status: one word per tile.
+cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long long *status,
+                                 int *act, Mailbox *mail_dev, double dt_max, bool want_rec,
+                                 unsigned *err, cudaStream_t st);
 
 // Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
 cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,

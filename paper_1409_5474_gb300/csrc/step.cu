@@ -32,7 +32,7 @@ __global__ void k_predict(StateDev s, double t, unsigned *err)
     for (int c = 0; c < 3; ++c) {
         const long long q = c * s.ld + i;
         const double x = s.pos[q], v = s.vel[q], a = s.acc[q], j = s.jerk[q];
-        xp[c] = x + d * (v + d * (0.5 * a + d * (j / 6.0)));
+        xp[c] = x + d * (v + d * (0.5 * a + d * (j * (1.0 / 6.0))));
         vp[c] = v + d * (a + d * (0.5 * j));
         s.pos_p[q] = xp[c];
         s.vel_p[q] = vp[c];
@@ -71,6 +71,14 @@ __device__ __forceinline__ double norm3(double x, double y, double z)
     return sqrt(x * x + y * y + z * z);
 }
 
+// t is a whole multiple of the power of two d: t / d is exact, so test it for an
+// integer (equivalent to fmod(t, d) == 0 for power-of-two d, and cheaper).
+__device__ __forceinline__ bool divides(double t, double d)
+{
+    const double q = t * (1.0 / d);
+    return q == trunc(q);
+}
+
 // Largest power of two <= raw (dt_max for raw >= dt_max or +inf), at most twice
 // dt_old, clamped to [dt_min, dt_max], halved until it divides t_new.
 __device__ double quantize(double raw, double dt_old, double t_new, double dt_min, double dt_max,
@@ -91,19 +99,40 @@ __device__ double quantize(double raw, double dt_old, double t_new, double dt_mi
         d = dt_min;
         *clamped = true;
     }
-    while (d > dt_min && fmod(t_new, d) != 0.0) d = 0.5 * d;
+    while (d > dt_min && !divides(t_new, d)) d = 0.5 * d;
     return d;
+}
+
+// Level of a power-of-two step: dt = dt_max * 2^-k.
+__device__ __forceinline__ int step_level(double dt, double dt_max)
+{
+    int k = ilogb(dt_max) - ilogb(dt);
+    return k < 0 ? 0 : (k >= NLEVEL ? NLEVEL - 1 : k);
+}
+
+// hist[level] += delta, one atomic per group of lanes with the same level.
+__device__ __forceinline__ void hist_add(int *hist, int level, int delta)
+{
+    const unsigned act = __activemask();
+    const unsigned same = __match_any_sync(act, level);
+    const int lane = threadIdx.x & 31;
+    if (lane == __ffs(same) - 1) atomicAdd(hist + level, delta * __popc(same));
 }
 
 // ---- K4 --------------------------------------------------------------------
 
 __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
-                          StepParams prm, unsigned *err, unsigned long long *dtmin_hits)
+                          StepParams prm, SchedDev *sd, unsigned *err,
+                          unsigned long long *dtmin_hits)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) sd->t_cur = t_new;
     if (k >= na) return;
     const int i = act ? act[k] : k;
     const double dt = t_new - s.t[i];
+    const double dt_old = s.dt[i];
+    // one division per particle; the rest are products (exact for power-of-two dt)
+    const double idt = 1.0 / dt, idt2 = idt * idt, idt3 = idt2 * idt;
     const double dt2 = dt * dt, dt3 = dt2 * dt, dt4 = dt3 * dt, dt5 = dt4 * dt;
     double a1v[3], j1v[3], a2e[3], a3e[3];
     bool finite = true;
@@ -112,10 +141,10 @@ __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, doubl
         const long long q = c * s.ld + i;
         const double a0 = s.acc[q], j0 = s.jerk[q];
         const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
-        const double a2 = (-6.0 * (a0 - a1) - dt * (4.0 * j0 + 2.0 * j1)) / dt2;
-        const double a3 = (12.0 * (a0 - a1) + 6.0 * dt * (j0 + j1)) / dt3;
-        const double x1 = s.pos_p[q] + a2 * dt4 / 24.0 + a3 * dt5 / 120.0;
-        const double v1 = s.vel_p[q] + a2 * dt3 / 6.0 + a3 * dt4 / 24.0;
+        const double a2 = (-6.0 * (a0 - a1) - dt * (4.0 * j0 + 2.0 * j1)) * idt2;
+        const double a3 = (12.0 * (a0 - a1) + 6.0 * dt * (j0 + j1)) * idt3;
+        const double x1 = s.pos_p[q] + a2 * dt4 * (1.0 / 24.0) + a3 * dt5 * (1.0 / 120.0);
+        const double v1 = s.vel_p[q] + a2 * dt3 * (1.0 / 6.0) + a3 * dt4 * (1.0 / 24.0);
         s.pos[q] = x1;
         s.vel[q] = v1;
         s.acc[q] = a1;
@@ -141,23 +170,28 @@ __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, doubl
         bool clamped;
         dt_new = quantize(raw, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
         if (clamped && dtmin_hits) atomicAdd(dtmin_hits, 1ull);
+        const int lo = step_level(dt_old, prm.dt_max), ln = step_level(dt_new, prm.dt_max);
+        if (lo != ln) {
+            hist_add(sd->hist, lo, -1);
+            hist_add(sd->hist, ln, +1);
+        }
     }
     s.t[i] = t_new;
     s.dt[i] = dt_new;
 }
 
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new, const Out3 &f,
-                           const StepParams &p, unsigned *err, unsigned long long *dtmin_hits,
-                           cudaStream_t st)
+                           const StepParams &p, SchedDev *sd, unsigned *err,
+                           unsigned long long *dtmin_hits, cudaStream_t st)
 {
     if (n_a <= 0) return cudaSuccess;
     const int bs = 128;
-    k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, err, dtmin_hits);
+    k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits);
     return cudaGetLastError();
 }
 
 // Initial step: acc/jerk of particle k are in f (slot k = particle k) and in s.
-__global__ void k_init_steps(StateDev s, Out3 f, StepParams prm, unsigned *err)
+__global__ void k_init_steps(StateDev s, Out3 f, StepParams prm, SchedDev *sd, unsigned *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
@@ -177,80 +211,233 @@ __global__ void k_init_steps(StateDev s, Out3 f, StepParams prm, unsigned *err)
         const double raw = (nj_ == 0.0) ? INFINITY : prm.eta_s * norm3(a[0], a[1], a[2]) / nj_;
         bool clamped;
         dt = quantize(raw, 0.0, s.t[i], prm.dt_min, prm.dt_max, &clamped);
+        hist_add(sd->hist, step_level(dt, prm.dt_max), 1);
     }
     s.dt[i] = dt;
+    if (i == 0) sd->t_cur = s.t[0];
 }
 
-cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams &p, unsigned *err,
-                              cudaStream_t st)
+cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams &p, SchedDev *sd,
+                              unsigned *err, cudaStream_t st)
 {
     if (s.n <= 0) return cudaSuccess;
     const int bs = 256;
-    k_init_steps<<<(s.n + bs - 1) / bs, bs, 0, st>>>(s, f, p, err);
+    k_init_steps<<<(s.n + bs - 1) / bs, bs, 0, st>>>(s, f, p, sd, err);
     return cudaGetLastError();
 }
 
-// ---- K5 --------------------------------------------------------------------
+// ---- K5 + K1: fused block scheduler and predictor -----------------------
 
-constexpr int SCHED_T = 1024;
-
-// One CTA: min reduction, then an ordered compaction in chunks of SCHED_T.
-__global__ void __launch_bounds__(SCHED_T) k_sched(StateDev s, int *__restrict__ act, Mailbox *mail)
+__device__ __forceinline__ unsigned long long globaltimer_ns()
 {
-    __shared__ double s_min[SCHED_T / 32];
-    __shared__ int s_cnt[SCHED_T / 32];
-    __shared__ int s_total;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long LOOKBACK_LIMIT_NS = 4000000000ull;  // 4 s
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+constexpr unsigned ST_AGG = 1u, ST_PREFIX = 2u;
+
+__device__ __forceinline__ unsigned long long st_word(unsigned epoch, unsigned flag, unsigned v)
+{
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | v;
+}
+
+template <bool REC>
+__global__ void __launch_bounds__(SCHED_THREADS)
+    k_sched_predict(StateDev s, SchedDev *sd, unsigned long long *status, int *act,
+                    Mailbox *mail, double dt_max, unsigned *err)
+{
+    constexpr int NWORD = SCHED_TILE / 32;
+    __shared__ unsigned s_flags[NWORD];
+    __shared__ int s_woff[NWORD];
+    __shared__ int s_wtot[NWORD / 32];
+    __shared__ int s_tile, s_agg, s_excl;
+    __shared__ unsigned s_epoch;
+    __shared__ unsigned s_occ[NLEVEL / 32];
+    __shared__ double s_tnext;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = s.n;
+    const int ntiles = gridDim.x;
 
-    double mn = INFINITY;
-    for (int i = tid; i < n; i += SCHED_T) mn = fmin(mn, s.t[i] + s.dt[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if (lane == 0) s_min[warp] = mn;
-    __syncthreads();
-    if (warp == 0) {
-        double v = s_min[lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) s_min[0] = v;
-    }
-    __syncthreads();
-    const double tn = s_min[0];
-
-    int base = 0;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int c0 = 0; c0 < n; c0 += SCHED_T) {
-        const int i = c0 + tid;
-        const bool due = (i < n) && (s.t[i] + s.dt[i] == tn);
-        const unsigned b = __ballot_sync(0xffffffffu, due);
-        if (lane == 0) s_cnt[warp] = __popc(b);
-        __syncthreads();
-        if (warp == 0) {
-            const int v = s_cnt[lane];
-            int incl = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
-            }
-            s_cnt[lane] = incl - v;
-            if (lane == 31) s_total = incl;
-        }
-        __syncthreads();
-        if (due) act[base + s_cnt[warp] + __popc(b & lt)] = i;
-        base += s_total;
-        __syncthreads();
+    // occupied step levels -> t_next
+    static_assert(NLEVEL % 32 == 0 && NLEVEL / 32 <= SCHED_THREADS / 32, "levels");
+    if (warp < NLEVEL / 32) {
+        const bool occ = ((volatile int *)sd->hist)[warp * 32 + lane] > 0;
+        const unsigned b = __ballot_sync(0xffffffffu, occ);
+        if (lane == 0) s_occ[warp] = b;
     }
     if (tid == 0) {
-        mail->t_next = tn;
-        mail->n_active = base;
+        s_tile = (int)atomicAdd(&sd->ticket, 1u);  // tiles in start order
+        s_epoch = (unsigned)(*(volatile unsigned long long *)&sd->seq);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int kmax = 0;
+        for (int w = 0; w < NLEVEL / 32; ++w)
+            if (s_occ[w]) kmax = w * 32 + 31 - __clz(s_occ[w]);
+        const double dm = ldexp(dt_max, -kmax);
+        const double tc = *(volatile double *)&sd->t_cur;
+        s_tnext = tc - fmod(tc, dm) + dm;
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    const double tn = s_tnext;
+    const int base = tile * SCHED_TILE;
+
+    // predict + due flags (one ballot word per warp and round)
+#pragma unroll 2
+    for (int r = 0; r < SCHED_PER_THREAD; ++r) {
+        const int i = base + r * SCHED_THREADS + tid;
+        bool due = false;
+        if (i < s.n) {
+            const double ti = s.t[i];
+            const double d = tn - ti;
+            due = (ti + s.dt[i] == tn);
+            double xp[3], vp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long q = c * s.ld + i;
+                const double x = s.pos[q], v = s.vel[q], a = s.acc[q], j = s.jerk[q];
+                xp[c] = x + d * (v + d * (0.5 * a + d * (j * (1.0 / 6.0))));
+                vp[c] = v + d * (a + d * (0.5 * j));
+                s.pos_p[q] = xp[c];
+                s.vel_p[q] = vp[c];
+            }
+            if (REC) {
+                float hi[3], lo[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    hi[c] = (float)xp[c];
+                    lo[c] = (float)(xp[c] - (double)hi[c]);
+                }
+                float4 *rr = s.rec + (size_t)DS_REC * i;
+                rr[0] = make_float4(hi[0], hi[1], hi[2], (float)s.m[i]);
+                rr[1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+                rr[2] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, due);
+        if (lane == 0) s_flags[r * (SCHED_THREADS / 32) + warp] = b;
+    }
+    __syncthreads();
+
+    // exclusive offsets of the flag words in index order, and the tile aggregate
+    static_assert(NWORD % 32 == 0 && NWORD / 32 <= SCHED_THREADS / 32, "flag words");
+    if (warp < NWORD / 32) {
+        const int w = warp * 32 + lane;
+        const int v = __popc(s_flags[w]);
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        s_woff[w] = incl - v;
+        if (lane == 31) s_wtot[warp] = incl;
+    }
+    __syncthreads();
+    if (warp < NWORD / 32) {
+        int carry = 0;
+        for (int q = 0; q < warp; ++q) carry += s_wtot[q];
+        s_woff[warp * 32 + lane] += carry;
+    }
+    if (tid == 0) {
+        int a = 0;
+        for (int q = 0; q < NWORD / 32; ++q) a += s_wtot[q];
+        s_agg = a;
+    }
+    __syncthreads();
+    const int agg = s_agg;
+
+    // decoupled look-back over the tiles in front of this one
+    if (tid == 0) {
+        const unsigned ep = s_epoch;
+        if (tile == 0) {
+            st_release_u64(status + tile, st_word(ep, ST_PREFIX, (unsigned)agg));
+            s_excl = 0;
+        } else {
+            st_release_u64(status + tile, st_word(ep, ST_AGG, (unsigned)agg));
+            int excl = 0;
+            int t = tile - 1;
+            const unsigned long long t0 = globaltimer_ns();
+            bool ok = true;
+            while (t >= 0) {
+                const unsigned long long wd = ld_acquire_u64(status + t);
+                if ((unsigned)(wd >> 32) != ep) {
+                    if (globaltimer_ns() - t0 > LOOKBACK_LIMIT_NS) {
+                        ok = false;
+                        break;
+                    }
+                    continue;
+                }
+                const unsigned flag = (unsigned)(wd >> 30) & 3u;
+                excl += (int)(wd & 0x3fffffffu);
+                if (flag == ST_PREFIX) break;
+                --t;
+            }
+            if (!ok) atomicOr(err, DERR_TIMEOUT);
+            st_release_u64(status + tile, st_word(ep, ST_PREFIX, (unsigned)(excl + agg)));
+            s_excl = excl;
+        }
+        if (tile == ntiles - 1) {
+            sd->n_active = s_excl + agg;
+        }
+    }
+    __syncthreads();
+    const int excl = s_excl;
+
+    // scatter the due indices in ascending order
+#pragma unroll 2
+    for (int r = 0; r < SCHED_PER_THREAD; ++r) {
+        const int w = r * (SCHED_THREADS / 32) + warp;
+        const unsigned b = s_flags[w];
+        if (b & (1u << lane)) {
+            const int i = base + r * SCHED_THREADS + tid;
+            act[excl + s_woff[w] + __popc(b & ((1u << lane) - 1u))] = i;
+        }
+    }
+
+    // the last CTA to finish publishes the result and re-arms the launch state
+    if (tid == 0) {
+        __threadfence();
+        const unsigned fin = atomicAdd(&sd->done, 1u);
+        if (fin == (unsigned)ntiles - 1) {
+            __threadfence();
+            const int na = *(volatile int *)&sd->n_active;
+            mail->t_next = tn;
+            mail->n_active = na;
+            __threadfence_system();
+            mail->seq = (unsigned long long)s_epoch;
+            sd->ticket = 0;
+            sd->done = 0;
+            sd->seq = (unsigned long long)s_epoch + 1ull;
+        }
     }
 }
 
-cudaError_t launch_sched(const StateDev &s, int *act, Mailbox *mail_dev, cudaStream_t st)
+cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long long *status,
+                                 int *act, Mailbox *mail_dev, double dt_max, bool want_rec,
+                                 unsigned *err, cudaStream_t st)
 {
-    k_sched<<<1, SCHED_T, 0, st>>>(s, act, mail_dev);
+    const int g = (s.n + SCHED_TILE - 1) / SCHED_TILE;
+    if (want_rec)
+        k_sched_predict<true><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, mail_dev, dt_max,
+                                                           err);
+    else
+        k_sched_predict<false><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, mail_dev, dt_max,
+                                                            err);
     return cudaGetLastError();
 }
 

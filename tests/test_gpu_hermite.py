@@ -71,7 +71,7 @@ def test_block_steps_short_horizon(nb, variant):
 
 
 def test_block_invariants_and_energy(nb):
-    p = ic.plummer(2048, 32)
+    p = ic.plummer(5000, 32)  # three scheduler tiles of 2048
     eps = 1e-3
     with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.01, dt_max=1.0 / 16,
                    device=0) as s:
@@ -135,8 +135,10 @@ def test_equal_block_steps_equal_shared_steps(nb):
 
 
 def test_manual_calls_equal_one_block_step(nb):
-    """nb_predict + nb_force(due set) + nb_correct reproduce the first block step of nb_step."""
-    p = ic.plummer(400, 35)
+    """nb_predict + nb_force(due set) + nb_correct reproduce the first block step of nb_step:
+    the due set the scheduler compacts (over several tiles) is the one t_i + dt_i == t_next
+    defines."""
+    p = ic.plummer(5000, 35)
     kw = dict(variant="f64", eps=0.01, eta=0.02, device=0)
     with nb.System(p.m, p.pos, p.vel, **kw) as a:
         nb.nb_init(a.h)
@@ -154,3 +156,38 @@ def test_manual_calls_equal_one_block_step(nb):
     assert stats["block_steps"] == 1
     for k in ("pos", "vel", "acc", "jerk", "t", "dt"):
         np.testing.assert_array_equal(ma[k], mb[k])
+
+
+def test_block_steps_multi_tile_vs_oracle(nb):
+    """N = 6000 (three scheduler tiles), FP64 pairs, 1/64 time unit: the same block-step
+    schedule as the oracle and states that agree to 1e-9."""
+    p = ic.plummer(6000, 36)
+    eps = 0.01
+    st = oracle.State(p.m, p.pos, p.vel)
+    o_steps, o_inter = oracle.hermite_run(st, 1.0 / 64, eps * eps, eta=0.02, dt_max=1.0 / 16)
+    with nb.System(p.m, p.pos, p.vel, variant="f64", eps=eps, eta=0.02, dt_max=1.0 / 16,
+                   device=0) as s:
+        stats = s.step(1.0 / 64)
+        g = s.state()
+    assert stats["block_steps"] == o_steps
+    assert abs(stats["interactions"] - o_inter) <= 1e-3 * o_inter
+    np.testing.assert_array_equal(g["t"], st.t)
+    assert (g["dt"] == st.dt).mean() > 0.999
+    assert np.abs(g["pos"].T - st.pos).max() < 1e-9
+
+
+def test_set_state_rejects_broken_block_invariant(nb):
+    p = ic.plummer(100, 37)
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=0.01, device=0) as s:
+        s.step(1.0 / 32)
+        ck = s.state()
+        bad = dict(ck)
+        bad["t"] = ck["t"].copy()
+        bad["dt"] = ck["dt"].copy()
+        bad["dt"][3] = 1.0 / 16
+        bad["t"][3] = 1.0 / 32 + 1.0 / 64   # not a multiple of its step
+        with pytest.raises(nb.NBodyError) as e:
+            s.set_state(bad)
+        assert e.value.status == nb.NB_ERR_ARG
+        s.set_state(ck)                     # the genuine checkpoint is accepted
+        s.step(1.0 / 16)
