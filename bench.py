@@ -64,6 +64,8 @@ def parse_args(argv=None):
     ap.add_argument("--variant", choices=["f32", "f32ds", "f64"], default=None)
     ap.add_argument("--n", type=int, default=None,
                     help="override the workload's particle count (profiling of smaller cases)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the library's autotuner (nb_autotune) in the untimed set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -304,6 +306,7 @@ def run_ours(args):
     h = sysm.h
     nbody.nb_set_stream(h, stream.cuda_stream)
     n = p.n
+    plan_table = nbody.nb_autotune(h, 3) if args.autotune else None
 
     def one_step(k, host_state):
         """One bench step; returns (interactions, device_ms, wall_s, launches, stats, state)."""
@@ -357,6 +360,7 @@ def run_ours(args):
     force_launches = 0
     other_ms = {"sched_ms": 0.0, "predict_ms": 0.0, "correct_ms": 0.0}
     block_steps = 0
+    hist = {"active_hist": [0] * 32, "force_ms_hist": [0.0] * 32, "inter_hist": [0.0] * 32}
     for k in range(args.warmup, args.warmup + args.steps):
         flush.fill_(float(k))                              # L2 flush between timed steps
         inter, ms, wall, nl, st, host_state = one_step(k, host_state)
@@ -370,6 +374,9 @@ def run_ours(args):
         for key in other_ms:
             other_ms[key] += st.get(key, 0.0)
         block_steps += st.get("block_steps", 0)
+        for key in hist:
+            for b, x in enumerate(st.get(key, [0] * 32)):
+                hist[key][b] += x
     torch.cuda.synchronize()
     clocks = sampler.stop()
     dist.barrier()
@@ -406,10 +413,13 @@ def run_ours(args):
                      "force_launches": force_launches},
         "kernel_ms": dict(other_ms, force_ms=force_ms, reduce_ms=reduce_ms),
         "block_steps": block_steps,
+        "by_log2_active": {k: [round(x, 3) if isinstance(x, float) else x for x in v]
+                           for k, v in hist.items()},
         "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8,
                 "d2h_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8},
         "gpu_launches": launches,
+        "plans": "autotuned (nb_autotune)" if plan_table else "built-in heuristic",
         "interactions": tot_inter,
         "clocks": clocks,
     }

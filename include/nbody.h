@@ -96,6 +96,8 @@ typedef struct nb_stats {
     long long dt_min_hits;      /* corrections whose step was clamped at dt_min */
     long long active_hist[32];  /* block steps by floor(log2(N_active)) */
     long long kernel_launches;  /* CUDA kernels this library launched */
+    double force_ms_hist[32];   /* force kernel time by floor(log2(N_i)) (NB_FLAG_TIMING) */
+    double inter_hist[32];      /* interactions by floor(log2(N_i)) */
 } nb_stats;
 
 typedef struct nb_handle_s *nb_handle;
@@ -209,6 +211,43 @@ int nb_energy(nb_handle h, double *kin, double *pot);
 /* Counters accumulated since creation or the last reset. */
 int nb_get_stats(nb_handle h, nb_stats *st);
 int nb_reset_stats(nb_handle h);
+
+/* ---- launch plans and the autotuner ---------------------------------------
+ * How a force evaluation of n_i i-particles is laid out on the GPU (the
+ * paper's i-parallel and j-parallel mappings, Sect. III.A):
+ *   kind 0: tiles - a CTA of 256 threads holds 2 i-particles per thread in
+ *           256/nwj/32 warp columns; nwj warp rows share each j-tile;
+ *           nsplit CTAs split the j-range (FP32 kinds: nwj in {1, 4, 8});
+ *   kind 1: j-parallel warp groups - each warp holds up to 2 i-particles (FP64:
+ *           all threads share up to 4) and its lanes stride over j; nsplit
+ *           CTAs split the j-range;
+ *   kind 2: tiny i-sets (FP32 kinds) - all threads share up to 4 i-particles
+ *           and each holds up to 4 j-records; the split count follows from
+ *           the j-set size (nsplit is ignored).
+ * A plan changes only the order in which pair terms are summed, not which are
+ * summed. Plans are looked up by bucket b = ceil(log2(n_i)) (0..31). */
+typedef struct nb_plan {
+    int kind;   /* 0 tiles, 1 warp groups, 2 tiny sets, -1 = built-in heuristic */
+    int nwj;    /* warp rows per CTA (kind 0) */
+    int nsplit; /* j-range splits (>= 1; clamped to the j-set) */
+} nb_plan;
+
+/* The plan used for an evaluation of n_i i-particles on the current j-set. */
+int nb_plan_for(nb_handle h, int n_i, nb_plan *out);
+
+/* Set the plan table (n <= 32 entries, entry b for bucket b; kind -1 entries
+ * and buckets >= n use the heuristic); table == NULL restores the heuristic.
+ * Rejects malformed entries (NB_ERR_ARG). */
+int nb_set_plan_table(nb_handle h, const nb_plan *table, int n);
+int nb_get_plan_table(nb_handle h, nb_plan *table /* 32 entries */);
+
+/* Autotuner: for every bucket up to the current N, times candidate plans
+ * (kind, nwj, nsplit around the heuristic) on the handle's own particles with
+ * CUDA events, reps repetitions each, and stores the fastest in the plan
+ * table. The particle state is left unchanged; the prediction is not (the
+ * j-set is predicted to the latest own time), so call nb_predict again before
+ * a manual nb_force. */
+int nb_autotune(nb_handle h, int reps);
 
 /* ---- allocation-free force evaluation -----------------------------------
  * The paper has no counterpart of this call; it exists for callers that

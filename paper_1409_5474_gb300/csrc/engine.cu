@@ -47,9 +47,11 @@ struct Timer {
     struct Pending {
         int kind;
         cudaEvent_t a, b;
+        int bucket;  // floor(log2 n_i) for force launches, else -1
     };
     std::vector<Pending> pending;
     double ms[T_NKIND] = {0, 0, 0, 0, 0};
+    double force_hist[32] = {0};
 
     cudaEvent_t get()
     {
@@ -62,12 +64,18 @@ struct Timer {
         cudaEventCreate(&e);
         return e;
     }
-    void add(int kind, cudaEvent_t a, cudaEvent_t b) { pending.push_back({kind, a, b}); }
+    void add(int kind, cudaEvent_t a, cudaEvent_t b, int bucket = -1)
+    {
+        pending.push_back({kind, a, b, bucket});
+    }
     void harvest()
     {
         for (auto &p : pending) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.kind] += t;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                ms[p.kind] += t;
+                if (p.bucket >= 0) force_hist[p.bucket] += t;
+            }
             free_ev.push_back(p.a);
             free_ev.push_back(p.b);
         }
@@ -102,11 +110,14 @@ struct nb_handle_s {
     double *t = nullptr, *dt = nullptr, *pos_p = nullptr, *vel_p = nullptr;
     double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
     float4 *rec = nullptr;
+    float4 *irec = nullptr;  // records of the due set, gathered by the scheduler
     int *act = nullptr;
 
     // growable scratch
     double *part = nullptr;
     size_t part_cap = 0;  // doubles
+    unsigned *split_cnt = nullptr;  // per-i-block counters of the folded split reduction
+    size_t split_cnt_cap = 0;
     double *io = nullptr; // host-API staging: [7][n_i] outputs, ext inputs
     size_t io_cap = 0;    // doubles
     int *d_idx = nullptr;
@@ -136,6 +147,7 @@ struct nb_handle_s {
     nb_stats stats{};
     Timer timer;
     std::string msg;
+    nb_plan plans[32];  // plan table by bucket ceil(log2 n_i); kind -1 = heuristic
 };
 
 namespace {
@@ -216,6 +228,19 @@ ISet members_of(nb_handle h, const int *idx_dev, int n_i)
     is.m64 = h->m;
     is.ld64 = h->ld;
     is.nj = h->n;
+    is.gathered = false;
+    return is;
+}
+
+// The due set of a block step: for FP32 kinds the gathered records (one row
+// per slot, the index in the record); FP64 reads the predicted state by index.
+ISet due_set(nb_handle h, int n_a)
+{
+    ISet is = members_of(h, h->act, n_a);
+    if (h->cfg.variant != NB_F64) {
+        is.gathered = true;
+        is.rec32 = h->irec;
+    }
     return is;
 }
 
@@ -262,6 +287,8 @@ int check_err(nb_handle h)
     if (timing(h)) h->timer.harvest();
     if (!e) return NB_OK;
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
+    if (h->split_cnt)  // an aborted force launch may leave a split counter armed
+        CK(h, cudaMemsetAsync(h->split_cnt, 0, h->split_cnt_cap * sizeof(unsigned), h->stream));
     if (e & DERR_TIMEOUT) return fail(h, NB_ERR_TIMEOUT, "a device-side wait timed out");
     if (e & DERR_BADINDEX) return fail(h, NB_ERR_ARG, "an i-set index is outside [0, n)");
     if (e & DERR_BACKWARD)
@@ -272,14 +299,53 @@ int check_err(nb_handle h)
 
 int ensure_part(nb_handle h, const ForcePlan &p, int n_i)
 {
-    return grow(h, &h->part, &h->part_cap, std::max<size_t>(plan_partial_doubles(p, n_i), 1));
+    int rc = grow(h, &h->part, &h->part_cap, std::max<size_t>(plan_partial_doubles(p, n_i), 1));
+    if (rc) return rc;
+    const size_t need = std::max<size_t>(plan_counters(p, n_i), 64);
+    if (need > h->split_cnt_cap) {
+        rc = grow(h, &h->split_cnt, &h->split_cnt_cap, need);
+        if (rc) return rc;
+        CK(h, cudaMemsetAsync(h->split_cnt, 0, h->split_cnt_cap * sizeof(unsigned), h->stream));
+    }
+    return NB_OK;
 }
+
+int bucket_of(int n_i)
+{
+    int b = 0;
+    while ((1LL << b) < n_i && b < 31) ++b;
+    return b;
+}
+
+ForcePlan plan_for(nb_handle h, int variant, int n_i)
+{
+    const nb_plan &e = h->plans[bucket_of(n_i)];
+    if (e.kind >= 0 && variant == h->cfg.variant) return plan_from_entry(e, variant, n_i, h->n);
+    return plan_force(variant, n_i, h->n, h->num_sms);
+}
+
+nb_plan entry_of(const ForcePlan &p)
+{
+    nb_plan e;
+    e.kind = p.kind;
+    e.nwj = p.nwj;
+    e.nsplit = p.nsplit;
+    return e;
+}
+
+// Force on an i-set into out with a given plan; grows scratch, records timers.
+int run_force_plan(nb_handle h, int variant, const ForcePlan &p, const ISet &is, Out3 out);
 
 // Force on an i-set into out; plans, grows scratch, records timers.
 int run_force(nb_handle h, int variant, const ISet &is, Out3 out)
 {
     if (is.n <= 0) return NB_OK;
-    ForcePlan p = plan_force(variant, is.n, h->n, h->num_sms);
+    return run_force_plan(h, variant, plan_for(h, variant, is.n), is, out);
+}
+
+int run_force_plan(nb_handle h, int variant, const ForcePlan &p, const ISet &is, Out3 out)
+{
+    if (is.n <= 0) return NB_OK;
     int rc = ensure_part(h, p, is.n);
     if (rc) return rc;
     cudaEvent_t ev[4];
@@ -289,14 +355,19 @@ int run_force(nb_handle h, int variant, const ISet &is, Out3 out)
         evp = ev;
     }
     const double eps2 = h->cfg.eps * h->cfg.eps;
-    CK(h, launch_force(variant, p, jset_of(h), is, eps2, h->part, out, h->d_err, h->stream, evp));
-    h->stats.kernel_launches += (p.nsplit > 1) ? 2 : 1;
+    CK(h, launch_force(variant, p, jset_of(h), is, eps2, h->part, h->split_cnt, out, h->d_err,
+                       h->stream, evp));
+    h->stats.kernel_launches += 1;
+    int lg = 0;
+    while ((2LL << lg) <= is.n && lg < 31) ++lg;
     if (evp) {
-        h->timer.add(T_FORCE, ev[0], ev[1]);
-        h->timer.add(T_REDUCE, ev[2], ev[3]);
+        h->timer.add(T_FORCE, ev[0], ev[1], lg);
+        h->timer.free_ev.push_back(ev[2]);
+        h->timer.free_ev.push_back(ev[3]);
     }
     h->stats.force_launches++;
     h->stats.interactions += (double)is.n * (double)h->n;
+    h->stats.inter_hist[lg] += (double)is.n * (double)h->n;
     return NB_OK;
 }
 
@@ -433,6 +504,7 @@ void sync_stats_counters(nb_handle h)
         h->stats.predict_ms = h->timer.ms[T_PREDICT];
         h->stats.correct_ms = h->timer.ms[T_CORRECT];
         h->stats.sched_ms = h->timer.ms[T_SCHED];
+        for (int k = 0; k < 32; ++k) h->stats.force_ms_hist[k] = h->timer.force_hist[k];
     }
 }
 
@@ -539,6 +611,7 @@ int nb_create(const nb_config *cfg, nb_handle *out)
 
     nb_handle h = new nb_handle_s();
     h->cfg = *cfg;
+    for (auto &e : h->plans) e = nb_plan{-1, 1, 1};
     h->dev = cfg->device;
     h->cap = cfg->n_max;
     h->ld = ((long long)cfg->n_max + 63) / 64 * 64;
@@ -559,7 +632,7 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     const size_t sca = align256((row + 64) * sizeof(double));
     const size_t recb = align256(row * DS_REC * sizeof(float4));
     const size_t actb = align256(row * sizeof(int));
-    h->slab_bytes = 6 * vec + 4 * sca + 2 * vec + recb + actb;  // see layout in the file header
+    h->slab_bytes = 6 * vec + 4 * sca + 2 * vec + 2 * recb + actb;  // see the file header
     const size_t small = 256 * 3;
     if (cfg->budget_bytes && h->slab_bytes + small > cfg->budget_bytes) {
         char msg[160];
@@ -600,6 +673,7 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     h->f_acc = (double *)take(vec);
     h->f_jerk = (double *)take(vec);
     h->rec = (float4 *)take(recb);
+    h->irec = (float4 *)take(recb);
     h->act = (int *)take(actb);
     if (cudaMemsetAsync(h->slab, 0, h->slab_bytes, h->stream) != cudaSuccess ||
         cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMalloc(&h->d_dtmin, 256) != cudaSuccess ||
@@ -647,6 +721,7 @@ int nb_destroy(nb_handle h)
     h->timer.harvest();
     cudaFree(h->slab);
     cudaFree(h->part);
+    cudaFree(h->split_cnt);
     cudaFree(h->io);
     cudaFree(h->d_idx);
     cudaFree(h->ext_rec);
@@ -880,6 +955,7 @@ int nb_force_ext(nb_handle h, int n_i, const double *pos, const double *vel, dou
     is.m64 = nullptr;
     is.ld64 = n_i;
     is.nj = h->n;
+    is.gathered = false;
     if (h->cfg.variant != NB_F64) {
         rc = grow(h, &h->ext_rec, &h->ext_rec_cap, (size_t)n_i * DS_REC);
         if (rc) return rc;
@@ -991,8 +1067,8 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         auto launch_sched = [&]() -> int {
             const unsigned long long ep = h->seq_next++;
             int r = timed(h, T_SCHED, [&] {
-                return launch_sched_predict(s, h->sd, h->sched_status, h->act, h->mail_d,
-                                            prm.dt_max, rec, h->d_err, h->stream);
+                return launch_sched_predict(s, h->sd, h->sched_status, h->act, h->irec,
+                                            h->mail_d, prm.dt_max, rec, h->d_err, h->stream);
             });
             if (r) return r;
             CK(h, cudaEventRecord(h->ev_sched, h->stream));
@@ -1009,7 +1085,7 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             if (!(t_next <= t_end)) break;
             if (na < 1 || na > h->n)
                 return fail(h, NB_ERR_STATE, "scheduler returned %d due particles", na);
-            rc = run_force(h, h->cfg.variant, members_of(h, h->act, na), f);
+            rc = run_force(h, h->cfg.variant, due_set(h, na), f);
             if (rc) return rc;
             rc = timed(h, T_CORRECT, [&] {
                 return launch_correct(s, h->act, na, t_next, f, prm, h->sd, h->d_err, h->d_dtmin,
@@ -1037,7 +1113,11 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         d.correct_ms -= before.correct_ms;
         d.sched_ms -= before.sched_ms;
         d.dt_min_hits -= before.dt_min_hits;
-        for (int k = 0; k < 32; ++k) d.active_hist[k] -= before.active_hist[k];
+        for (int k = 0; k < 32; ++k) {
+            d.active_hist[k] -= before.active_hist[k];
+            d.force_ms_hist[k] -= before.force_ms_hist[k];
+            d.inter_hist[k] -= before.inter_hist[k];
+        }
         d.kernel_launches -= before.kernel_launches;
         *st = d;
     }
@@ -1095,10 +1175,149 @@ int nb_reset_stats(nb_handle h)
     cudaStreamSynchronize(h->stream);
     h->timer.harvest();
     for (double &x : h->timer.ms) x = 0.0;
+    for (double &x : h->timer.force_hist) x = 0.0;
     std::memset(&h->stats, 0, sizeof h->stats);
     cudaMemsetAsync(h->d_dtmin, 0, sizeof(unsigned long long), h->stream);
     cudaStreamSynchronize(h->stream);
     return NB_OK;
+}
+
+int nb_plan_for(nb_handle h, int n_i, nb_plan *out)
+{
+    if (!h || !out || n_i < 1) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    *out = entry_of(plan_for(h, h->cfg.variant, n_i));
+    return NB_OK;
+}
+
+int nb_set_plan_table(nb_handle h, const nb_plan *table, int n)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!table) {
+        for (auto &e : h->plans) e = nb_plan{-1, 1, 1};
+        return NB_OK;
+    }
+    if (n < 0 || n > 32) return fail(h, NB_ERR_ARG, "plan table has %d entries (max 32)", n);
+    for (int b = 0; b < n; ++b) {
+        const nb_plan &e = table[b];
+        if (e.kind < -1 || e.kind > 2 || (e.kind >= 0 && e.nsplit < 1))
+            return fail(h, NB_ERR_ARG, "plan entry %d is malformed", b);
+        if (e.kind == 0 && !(e.nwj == 1 || e.nwj == 4 || e.nwj == 8))
+            return fail(h, NB_ERR_ARG, "plan entry %d: nwj must be 1, 4 or 8", b);
+    }
+    for (int b = 0; b < 32; ++b) h->plans[b] = b < n ? table[b] : nb_plan{-1, 1, 1};
+    return NB_OK;
+}
+
+int nb_get_plan_table(nb_handle h, nb_plan *table)
+{
+    if (!h || !table) return NB_ERR_ARG;
+    for (int b = 0; b < 32; ++b) table[b] = h->plans[b];
+    return NB_OK;
+}
+
+int nb_autotune(nb_handle h, int reps)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    if (reps < 1) reps = 1;
+    cudaSetDevice(h->dev);
+    const int n = h->n;
+    const int variant = h->cfg.variant;
+    // predict the j-set to the latest own time (valid for every particle)
+    std::vector<double> tt(n);
+    CK(h, cudaMemcpyAsync(tt.data(), h->t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double tmax = tt[0];
+    for (int i = 1; i < n; ++i) tmax = std::max(tmax, tt[i]);
+    int rc = predict_to(h, tmax);
+    if (rc) return rc;
+    const int saved_flags = h->cfg.flags;
+    h->cfg.flags &= ~NB_FLAG_TIMING;  // the tuner's own events only
+    const nb_stats saved_stats = h->stats;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    const int bmax = bucket_of(n);
+    for (int b = 0; b <= bmax && rc == NB_OK; ++b) {
+        const int n_i = (int)std::min<long long>(1LL << b, n);
+        std::vector<int> idx(n_i);
+        for (int k = 0; k < n_i; ++k) idx[k] = (int)((long long)k * n / n_i);
+        rc = grow(h, &h->d_idx, &h->idx_cap, (size_t)n_i);
+        if (rc) break;
+        rc = grow(h, &h->io, &h->io_cap, 7 * (size_t)n_i);
+        if (rc) break;
+        CK(h, cudaMemcpyAsync(h->d_idx, idx.data(), n_i * sizeof(int), cudaMemcpyHostToDevice,
+                              h->stream));
+        const ISet is = members_of(h, h->d_idx, n_i);
+        Out3 out{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i, n_i};
+        // candidates around the heuristic plan
+        std::vector<ForcePlan> cand;
+        const ForcePlan base = plan_force(variant, n_i, n, h->num_sms);
+        std::vector<nb_plan> entries;
+        if (variant != NB_F64 && n_i <= 32) entries.push_back(nb_plan{2, 1, 1});
+        const int kinds_nwj[4][2] = {{1, 1}, {0, 1}, {0, 4}, {0, 8}};
+        for (auto &kn : kinds_nwj) {
+            const int kind = kn[0], nwj = kn[1];
+            if (kind == 1 && n_i > 8192) continue;
+            if (kind == 0 && n_i < 16) continue;
+            if (variant == NB_F64 && nwj != 1) continue;
+            if (variant == NB_F64 && kind == 1 && n_i > 32) continue;
+            nb_plan probe{kind, nwj, 1};
+            ForcePlan one = plan_from_entry(probe, variant, n_i, n);
+            long long g;
+            if (kind == 1) {
+                const long long groups = variant == NB_F64 ? 1 : (n_i + one.ipt - 1) / one.ipt;
+                g = std::max(1LL, (16LL * h->num_sms + groups - 1) / groups);
+            } else {
+                const long long ib = (long long)(one.threads / one.nwj) * one.ipt;
+                const long long nblk = (n_i + ib - 1) / ib;
+                g = std::max(1LL, (4LL * h->num_sms + nblk - 1) / nblk);
+            }
+            for (long long f : {1LL, 2LL, 4LL, 8LL, 16LL}) {
+                for (int dir = 0; dir < 2; ++dir) {
+                    long long ns = dir ? g * f : g / f;
+                    if (ns < 1 || (dir && f == 1)) continue;
+                    entries.push_back(nb_plan{kind, nwj, (int)ns});
+                }
+            }
+        }
+        entries.push_back(entry_of(base));
+        double best = 1e30;
+        nb_plan best_e = entry_of(base);
+        for (const nb_plan &e : entries) {
+            const ForcePlan p = plan_from_entry(e, variant, n_i, n);
+            rc = run_force_plan(h, variant, p, is, out);  // warm-up
+            if (rc) break;
+            std::vector<float> ms;
+            for (int r = 0; r < reps; ++r) {
+                CK(h, cudaEventRecord(e0, h->stream));
+                rc = run_force_plan(h, variant, p, is, out);
+                if (rc) break;
+                CK(h, cudaEventRecord(e1, h->stream));
+                CK(h, cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(h, cudaEventElapsedTime(&t, e0, e1));
+                ms.push_back(t);
+            }
+            if (rc) break;
+            std::sort(ms.begin(), ms.end());
+            const double med = ms[ms.size() / 2];
+            if (med < best) {
+                best = med;
+                best_e = entry_of(p);
+            }
+        }
+        if (rc == NB_OK) h->plans[b] = best_e;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg.flags = saved_flags;
+    h->stats = saved_stats;
+    h->predicted = false;
+    h->last_force_n = -1;
+    if (rc) return rc;
+    return check_err(h);
 }
 
 }  // extern "C"

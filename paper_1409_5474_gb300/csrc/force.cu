@@ -128,6 +128,32 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float x)
     lo = t - (hi - s);
 }
 
+// A double-single value hi + lo (two FP32 numbers). On GB300 a warp-wide FP64
+// instruction holds an SMSP's FP64 pipe for ~64 cycles, so partial sums are
+// combined in double-single FP32 arithmetic and only final results are FP64.
+struct dsf {
+    float hi, lo;
+};
+
+// a += b for double-single values (TwoSum of the high parts, low parts added,
+// renormalised).
+__device__ __forceinline__ void ds_acc(dsf &a, dsf b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    a.hi = s + e;
+    a.lo = e - (a.hi - s);
+}
+
+__device__ __forceinline__ dsf ds_shfl_xor(dsf a, int o)
+{
+    return dsf{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+__device__ __forceinline__ double ds_to_double(dsf a) { return (double)a.hi + (double)a.lo; }
+
 __device__ __forceinline__ bool finite7(const double *v)
 {
     bool ok = true;
@@ -156,6 +182,133 @@ __device__ __forceinline__ void write_final(const Out3 &out, int k, double v[7],
 }
 
 // Member index of slot k; an index outside the j-set is flagged and replaced by 0.
+// Store the reduced value s of component c of slot k (c == 6: the positive
+// potential sum, stored negated).
+__device__ __forceinline__ void store_component(const Out3 &out, int c, int k, double s,
+                                                unsigned *err)
+{
+    if (c == 6) {
+        s = -s;
+        if (out.pot) out.pot[k] = s;
+    } else if (c < 3) {
+        if (out.acc) out.acc[c * out.ld + k] = s;
+    } else {
+        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
+    }
+    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
+}
+
+// K3, folded into the force kernels: after a CTA has written its partial sums
+// for slots [slot0, slot0 + nslots), the last of the nsplit CTAs that share
+// these slots (counted in *counter) reduces them and re-arms the counter. One
+// warp per (slot, component): lane l adds splits l, l + 32, ... in order, then a
+// fixed xor tree, so the result does not depend on which CTA finished last.
+// The same with double-single partials (float2 {hi, lo} in the part buffer)
+// combined in FP32 arithmetic; the final value is converted once.
+template <int NT>
+__device__ __forceinline__ void finish_split_ds(int nsplit, int slot0, int nslots, int n_i,
+                                                const float2 *part, long long pld,
+                                                unsigned *counter, const Out3 &out,
+                                                unsigned *err)
+{
+    __shared__ int s_last_ds;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last_ds = (atomicAdd(counter, 1u) == (unsigned)nsplit - 1u);
+    __syncthreads();
+    if (!s_last_ds) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int valid = min(nslots, n_i - slot0);
+    const int total = valid * 7;
+    constexpr int U = 8;
+    for (int q0 = warp * U; q0 < total; q0 += (NT / 32) * U) {
+        dsf acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = dsf{0.f, 0.f};
+        for (int sp = lane; sp < nsplit; sp += 32) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                if (q < total) {
+                    const int c = q / valid, k = slot0 + q % valid;
+                    const float2 v = __ldcg(part + ((size_t)sp * 7 + c) * pld + k);
+                    ds_acc(acc[u], dsf{v.x, v.y});
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            dsf v = acc[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ds_acc(v, ds_shfl_xor(v, o));
+            const int q = q0 + u;
+            if (lane == 0 && q < total)
+                store_component(out, q / valid, slot0 + q % valid, ds_to_double(v), err);
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <int NT>
+__device__ __forceinline__ void finish_split(int nsplit, int slot0, int nslots, int n_i,
+                                             const double *part, long long pld,
+                                             unsigned *counter, const Out3 &out, unsigned *err)
+{
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == (unsigned)nsplit - 1u);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int valid = min(nslots, n_i - slot0);
+    const int total = valid * 7;
+    constexpr int U = 8;  // outputs per warp pass: 8 independent loads in flight per lane
+    for (int q0 = warp * U; q0 < total; q0 += (NT / 32) * U) {
+        double acc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] = 0.0;
+        for (int sp = lane; sp < nsplit; sp += 32) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + u;
+                if (q < total) {
+                    const int c = q / valid, k = slot0 + q % valid;
+                    acc[u] += __ldcg(part + ((size_t)sp * 7 + c) * pld + k);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            double v = acc[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            const int q = q0 + u;
+            if (lane == 0 && q < total) store_component(out, q / valid, slot0 + q % valid, v, err);
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Record row of i-slot k: the slot itself for a gathered or external i-set,
+// else the member's particle index.
+__device__ __forceinline__ int member_index(const ISet &is, int k, unsigned *err);
+__device__ __forceinline__ int i_row(const ISet &is, int k, unsigned *err)
+{
+    if (is.gathered || !is.member) return k;
+    return member_index(is, k, err);
+}
+
+// Particle index of an i-record (self-pair mask): from the record for a
+// gathered set, the row for members, none (-1) for an external set.
+__device__ __forceinline__ int i_id(const ISet &is, int row, float id_bits)
+{
+    if (is.gathered) return __float_as_int(id_bits);
+    return is.member ? row : -1;
+}
+
 __device__ __forceinline__ int member_index(const ISet &is, int k, unsigned *err)
 {
     const int r = is.idx ? __ldg(is.idx + k) : k;
@@ -168,19 +321,32 @@ __device__ __forceinline__ int member_index(const ISet &is, int k, unsigned *err
 
 // ---------------------------------------------------------------------------
 // FP32 / double-single tile kernel.
+//
+// A CTA is NWI x NWJ warps. The NWI warp columns own different i-particles
+// (IPT per lane, an i-block of IB = 32 NWI IPT); the NWJ warp rows hold the
+// same i-particles and share out every j-tile (row g takes j = g, g + NWJ,
+// ...), so that a few hundred i-particles still fill an SM without cutting
+// the j-range into many grid-level pieces. Rows are added in shared memory at
+// the end, in fixed order.
 // ---------------------------------------------------------------------------
 
-template <int VAR, int IPT, int NT, int JT, int NS>
-__global__ void __launch_bounds__(NT)
+template <int VAR, int IPT, int NWI, int NWJ, int JT, int NS>
+__global__ void __launch_bounds__(32 * NWI * NWJ)
     k_force_tile32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f, int ntiles,
-                   double *__restrict__ part, long long pld, Out3 out, unsigned *err)
+                   double *__restrict__ part, long long pld, unsigned *counters, Out3 out,
+                   unsigned *err)
 {
     extern __shared__ __align__(128) float4 s_tile[];  // NS * JT * DS_REC
     __shared__ __align__(8) uint64_t s_full[NS];
     __shared__ int s_abort;
 
     constexpr bool DS = (VAR == NB_F32DS);
-    const int tid = threadIdx.x;
+    constexpr int NT = 32 * NWI * NWJ;
+    constexpr int IB = 32 * NWI * IPT;
+    // tiles per FP32 partial sum: about 128 pairs per thread between folds
+    constexpr int FOLD = (128 * NWJ / JT) > 1 ? (128 * NWJ / JT) : 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wi = warp % NWI, wj = warp / NWI;
     const int nsplit = gridDim.y;
     const int split = blockIdx.y;
     const int tile0 = (int)((long long)ntiles * split / nsplit);
@@ -193,16 +359,16 @@ __global__ void __launch_bounds__(NT)
     int iid[IPT];
 #pragma unroll
     for (int p = 0; p < IPT; ++p) {
-        int k = blockIdx.x * (NT * IPT) + p * NT + tid;
+        int k = blockIdx.x * IB + p * (32 * NWI) + wi * 32 + lane;
         if (k >= is.n) k = is.n - 1;  // idle slots compute a copy, never written
-        const int r = is.member ? member_index(is, k, err) : k;
+        const int r = i_row(is, k, err);
         const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
         const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
         const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
         xh[p] = a.x; yh[p] = a.y; zh[p] = a.z; mi[p] = a.w;
         xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
         vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
-        iid[p] = is.member ? r : -1;
+        iid[p] = i_id(is, r, b.w);
     }
 
     // running totals: double-single (DS) or plain FP32
@@ -212,6 +378,14 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
         for (int c = 0; c < 3; ++c) A_h[p][c] = A_l[p][c] = J_h[p][c] = J_l[p][c] = 0.f;
         P_h[p] = P_l[p] = 0.f;
+    }
+    // FP32 partial sums between folds
+    float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
+        tp[p] = 0.f;
     }
 
     if (tid == 0) {
@@ -242,14 +416,6 @@ __global__ void __launch_bounds__(NT)
         const float4 *T = s_tile + (size_t)stage * JT * DS_REC;
         const int jbase = (tile0 + kt) * JT;
         const int cnt = min(JT, nj - jbase);
-
-        float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
-#pragma unroll
-        for (int p = 0; p < IPT; ++p) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
-            tp[p] = 0.f;
-        }
 
         // self pair in this tile for any lane of the warp? (warp-uniform)
         bool own = false;
@@ -301,16 +467,17 @@ __global__ void __launch_bounds__(NT)
             }
         };
         if (own) {
-            for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
+            for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::true_type{});
         } else if (cnt == JT) {
 #pragma unroll 4
-            for (int jj = 0; jj < JT; ++jj) body(jj, std::false_type{});
+            for (int jj = wj; jj < JT; jj += NWJ) body(jj, std::false_type{});
         } else {
 #pragma unroll 2
-            for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
+            for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::false_type{});
         }
 
-        // fold the tile sums into the running totals
+        // fold the FP32 partial sums into the running totals
+        if ((kt + 1) % FOLD == 0 || kt + 1 == my_tiles) {
 #pragma unroll
         for (int p = 0; p < IPT; ++p) {
 #pragma unroll
@@ -328,6 +495,10 @@ __global__ void __launch_bounds__(NT)
                 ds_add(P_h[p], P_l[p], tp[p]);
             else
                 P_h[p] += tp[p];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
+            tp[p] = 0.f;
+        }
         }
 
         __syncthreads();  // every warp is done with this stage
@@ -339,25 +510,63 @@ __global__ void __launch_bounds__(NT)
         return;
     }
 
+    dsf v[IPT][7];
 #pragma unroll
     for (int p = 0; p < IPT; ++p) {
-        const int k = blockIdx.x * (NT * IPT) + p * NT + tid;
-        if (k >= is.n) continue;
-        double v[7];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            v[c] = (double)A_h[p][c] + (double)A_l[p][c];
-            v[3 + c] = (double)J_h[p][c] + (double)J_l[p][c];
+            v[p][c] = dsf{A_h[p][c], A_l[p][c]};
+            v[p][3 + c] = dsf{J_h[p][c], J_l[p][c]};
         }
-        v[6] = (double)P_h[p] + (double)P_l[p];
-        if (nsplit == 1) {
-            write_final(out, k, v, err);
-        } else {
+        v[p][6] = dsf{P_h[p], P_l[p]};
+    }
+    if (NWJ > 1) {
+        // add the warp rows in order 0..NWJ-1 (the tile ring is free: all tiles consumed)
+        float2 *s_red = reinterpret_cast<float2 *>(s_tile);  // [NWJ][7][IB]
 #pragma unroll
-            for (int c = 0; c < 7; ++c) part[((size_t)split * 7 + c) * pld + k] = v[c];
+        for (int p = 0; p < IPT; ++p) {
+            const int slot = p * (32 * NWI) + wi * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < 7; ++c)
+                s_red[(wj * 7 + c) * IB + slot] = make_float2(v[p][c].hi, v[p][c].lo);
+        }
+        __syncthreads();
+        if (wj == 0) {
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                const int slot = p * (32 * NWI) + wi * 32 + lane;
+#pragma unroll
+                for (int c = 0; c < 7; ++c)
+                    for (int g = 1; g < NWJ; ++g) {
+                        const float2 w = s_red[(g * 7 + c) * IB + slot];
+                        ds_acc(v[p][c], dsf{w.x, w.y});
+                    }
+            }
         }
     }
+    if (wj == 0) {
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = blockIdx.x * IB + p * (32 * NWI) + wi * 32 + lane;
+            if (k >= is.n) continue;
+            if (nsplit == 1) {
+                double d[7];
+#pragma unroll
+                for (int c = 0; c < 7; ++c) d[c] = ds_to_double(v[p][c]);
+                write_final(out, k, d, err);
+            } else {
+                float2 *pp = reinterpret_cast<float2 *>(part);
+#pragma unroll
+                for (int c = 0; c < 7; ++c)
+                    pp[((size_t)split * 7 + c) * pld + k] = make_float2(v[p][c].hi, v[p][c].lo);
+            }
+        }
+    }
+    if (nsplit > 1)
+        finish_split_ds<NT>(nsplit, blockIdx.x * IB, IB, is.n, reinterpret_cast<float2 *>(part),
+                            pld, counters + blockIdx.x, out, err);
 }
+
 
 // ---------------------------------------------------------------------------
 // FP64 tile kernel.
@@ -366,7 +575,7 @@ __global__ void __launch_bounds__(NT)
 template <int IPT, int NT, int JT, int NS>
 __global__ void __launch_bounds__(NT)
     k_force_tile64(JSet js, ISet is, double eps2, int ntiles, double *__restrict__ part,
-                   long long pld, Out3 out, unsigned *err)
+                   long long pld, unsigned *counters, Out3 out, unsigned *err)
 {
     extern __shared__ __align__(128) double s_t64[];  // NS * 7 * JT
     __shared__ __align__(8) uint64_t s_full[NS];
@@ -513,10 +722,13 @@ __global__ void __launch_bounds__(NT)
             for (int c = 0; c < 7; ++c) part[((size_t)split * 7 + c) * pld + k] = v[c];
         }
     }
+    if (nsplit > 1)
+        finish_split<NT>(nsplit, blockIdx.x * (NT * IPT), NT * IPT, is.n, part, pld,
+                         counters + blockIdx.x, out, err);
 }
 
 // ---------------------------------------------------------------------------
-// j-parallel kernels for tiny i-sets: thread = j, all threads share IPT i's.
+// j-parallel kernels for small i-sets (lanes over j).
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -527,35 +739,52 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-template <int VAR, int IPT, int NT>
-__global__ void __launch_bounds__(NT)
-    k_force_jmode32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f,
-                    double *__restrict__ part, long long pld, Out3 out, unsigned *err)
+// FP32 / double-single warp-group kernel for small and mid-size i-sets: each
+// warp owns its own IPT i-particles (every lane holds the same ones) and its
+// lanes stride over the CTA's j-range, reading the j-records straight from
+// L1/L2 (the warps of a CTA share one j-range, so it is read from L2 once per
+// CTA). A warp needs no block barrier: its lanes' sums meet in one xor tree.
+// Grid: i-groups of NWARP warps (x) times j-splits (y); the splits are reduced
+// by the last CTA of each group (finish_split).
+template <int VAR, int IPT, int NWARP>
+__global__ void __launch_bounds__(32 * NWARP)
+    k_force_wgrp32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f,
+                   double *__restrict__ part, long long pld, unsigned *counters, Out3 out,
+                   unsigned *err)
 {
     constexpr bool DS = (VAR == NB_F32DS);
-    constexpr int NW = NT / 32;
-    __shared__ float s_red[NW][IPT][7];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nsplit = gridDim.x, split = blockIdx.x;
+    constexpr int NT = 32 * NWARP;
+    constexpr int CHUNK = 32 * 32;  // j per FP32 partial sum (32 per lane)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nsplit = gridDim.y, split = blockIdx.y;
     const int j0 = (int)((long long)nj * split / nsplit);
     const int j1 = (int)((long long)nj * (split + 1) / nsplit);
+    const int slot0 = (blockIdx.x * NWARP + warp) * IPT;
 
-    for (int g0 = 0; g0 < is.n; g0 += IPT) {
-        float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
-        float mi[IPT];
-        int iid[IPT];
+    float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+    int iid[IPT];
 #pragma unroll
-        for (int p = 0; p < IPT; ++p) {
-            const int k = min(g0 + p, is.n - 1);
-            const int r = is.member ? member_index(is, k, err) : k;
-            const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
-            const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
-            const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
-            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z; mi[p] = a.w;
-            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
-            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
-            iid[p] = is.member ? r : -1;
-        }
+    for (int p = 0; p < IPT; ++p) {
+        const int k = min(slot0 + p, is.n - 1);
+        const int r = i_row(is, k, err);
+        const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
+        const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
+        const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
+        xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
+        xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+        vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+        iid[p] = i_id(is, r, b.w);
+    }
+    float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A_h[p][c] = A_l[p][c] = J_h[p][c] = J_l[p][c] = 0.f;
+        P_h[p] = P_l[p] = 0.f;
+    }
+
+    for (int c0 = j0; c0 < j1; c0 += CHUNK) {
+        const int c1 = min(c0 + CHUNK, j1);
         float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
 #pragma unroll
         for (int p = 0; p < IPT; ++p) {
@@ -563,7 +792,8 @@ __global__ void __launch_bounds__(NT)
             for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
             tp[p] = 0.f;
         }
-        for (int j = j0 + tid; j < j1; j += NT) {
+#pragma unroll 4
+        for (int j = c0 + lane; j < c1; j += 32) {
             const float4 a = __ldg(jrec + (size_t)DS_REC * j);
             const float4 c = __ldg(jrec + (size_t)DS_REC * j + 2);
             float4 b;
@@ -607,50 +837,205 @@ __global__ void __launch_bounds__(NT)
         }
 #pragma unroll
         for (int p = 0; p < IPT; ++p) {
-            float v[7];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                v[c] = ta[p][c];
-                v[3 + c] = fmaf(-3.f, tjb[p][c], tja[p][c]);
+                const float jt = fmaf(-3.f, tjb[p][c], tja[p][c]);
+                if (DS) {
+                    ds_add(A_h[p][c], A_l[p][c], ta[p][c]);
+                    ds_add(J_h[p][c], J_l[p][c], jt);
+                } else {
+                    A_h[p][c] += ta[p][c];
+                    J_h[p][c] += jt;
+                }
             }
-            v[6] = tp[p];
+            if (DS)
+                ds_add(P_h[p], P_l[p], tp[p]);
+            else
+                P_h[p] += tp[p];
+        }
+    }
+
+    // lanes -> warp total (double-single xor tree); lane 0 stores
 #pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                const float w = warp_sum(v[c]);
-                if (lane == 0) s_red[warp][p][c] = w;
+    for (int p = 0; p < IPT; ++p) {
+        dsf v[7];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = dsf{A_h[p][c], A_l[p][c]};
+            v[3 + c] = dsf{J_h[p][c], J_l[p][c]};
+        }
+        v[6] = dsf{P_h[p], P_l[p]};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) ds_acc(v[c], ds_shfl_xor(v[c], o));
+        const int k = slot0 + p;
+        if (lane == 0 && k < is.n) {
+            if (nsplit == 1) {
+                double d[7];
+#pragma unroll
+                for (int c = 0; c < 7; ++c) d[c] = ds_to_double(v[c]);
+                write_final(out, k, d, err);
+            } else {
+                float2 *pp = reinterpret_cast<float2 *>(part);
+#pragma unroll
+                for (int c = 0; c < 7; ++c)
+                    pp[((size_t)split * 7 + c) * pld + k] = make_float2(v[c].hi, v[c].lo);
             }
+        }
+    }
+    if (nsplit > 1)
+        finish_split_ds<NT>(nsplit, blockIdx.x * NWARP * IPT, NWARP * IPT, is.n,
+                            reinterpret_cast<float2 *>(part), pld, counters + blockIdx.x, out,
+                            err);
+}
+
+
+// FP32 / double-single kernel for tiny i-sets (block-step tails): every thread
+// holds the same IPT i-particles and JPT j-records of its own, all loaded
+// before any arithmetic so the whole j-set costs one L2 round trip; sums go
+// through a double-single warp tree, then across the CTA's warps, one
+// partial per CTA.
+// Groups of IPT (<= 4) i-particles are processed in turn (the j-records stay
+// in registers).
+template <int VAR, int IPT, int JPT>
+__global__ void __launch_bounds__(256)
+    k_force_tiny32(const float4 *__restrict__ jrec, int nj, ISet is, float eps2f,
+                   double *__restrict__ part, long long pld, unsigned *counters, Out3 out,
+                   unsigned *err)
+{
+    constexpr bool DS = (VAR == NB_F32DS);
+    constexpr int NT = 256, NW = NT / 32;
+    __shared__ float2 s_red[NW][IPT * 7];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsplit = gridDim.x, split = blockIdx.x;
+
+    // this thread's j-records: j = split * NT * JPT + r * NT + tid
+    float4 ja[JPT], jb[JPT], jc[JPT];
+    int jidx[JPT];
+#pragma unroll
+    for (int r = 0; r < JPT; ++r) {
+        const int j = split * NT * JPT + r * NT + tid;
+        jidx[r] = j;
+        if (j < nj) {
+            ja[r] = __ldg(jrec + (size_t)DS_REC * j);
+            jc[r] = __ldg(jrec + (size_t)DS_REC * j + 2);
+            if (DS) jb[r] = __ldg(jrec + (size_t)DS_REC * j + 1);
+        } else {
+            ja[r] = make_float4(0.f, 0.f, 0.f, 0.f);  // massless: contributes nothing
+            jc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            jb[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            jidx[r] = -2;
+        }
+    }
+
+    for (int g0 = 0; g0 < is.n; g0 += IPT) {
+        float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+        int iid[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = min(g0 + p, is.n - 1);
+            const int r = i_row(is, k, err);
+            const float4 a = __ldg(is.rec32 + (size_t)DS_REC * r);
+            const float4 b = __ldg(is.rec32 + (size_t)DS_REC * r + 1);
+            const float4 c = __ldg(is.rec32 + (size_t)DS_REC * r + 2);
+            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
+            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+            iid[p] = i_id(is, r, b.w);
+        }
+        dsf v[IPT][7];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            float ta0 = 0.f, ta1 = 0.f, ta2 = 0.f, tj0 = 0.f, tj1 = 0.f, tj2 = 0.f;
+            float tb0 = 0.f, tb1 = 0.f, tb2 = 0.f, tp = 0.f;
+#pragma unroll
+            for (int r = 0; r < JPT; ++r) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (ja[r].x - xh[p]) + (jb[r].x - xl[p]);
+                    dy = (ja[r].y - yh[p]) + (jb[r].y - yl[p]);
+                    dz = (ja[r].z - zh[p]) + (jb[r].z - zl[p]);
+                } else {
+                    dx = ja[r].x - xh[p];
+                    dy = ja[r].y - yh[p];
+                    dz = ja[r].z - zh[p];
+                }
+                const float dvx = jc[r].x - vx[p], dvy = jc[r].y - vy[p], dvz = jc[r].z - vz[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float rinv = rsqrtf(r2);
+                // self pair and padding records (jidx -2) contribute nothing
+                rinv = (jidx[r] == iid[p] || jidx[r] < 0) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = ja[r].w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float beta = (mr3 * rinv2) * rv;
+                tp += mrinv;
+                ta0 = fmaf(mr3, dx, ta0);
+                ta1 = fmaf(mr3, dy, ta1);
+                ta2 = fmaf(mr3, dz, ta2);
+                tj0 = fmaf(mr3, dvx, tj0);
+                tj1 = fmaf(mr3, dvy, tj1);
+                tj2 = fmaf(mr3, dvz, tj2);
+                tb0 = fmaf(beta, dx, tb0);
+                tb1 = fmaf(beta, dy, tb1);
+                tb2 = fmaf(beta, dz, tb2);
+            }
+            v[p][0] = dsf{ta0, 0.f};
+            v[p][1] = dsf{ta1, 0.f};
+            v[p][2] = dsf{ta2, 0.f};
+            v[p][3] = dsf{fmaf(-3.f, tb0, tj0), 0.f};
+            v[p][4] = dsf{fmaf(-3.f, tb1, tj1), 0.f};
+            v[p][5] = dsf{fmaf(-3.f, tb2, tj2), 0.f};
+            v[p][6] = dsf{tp, 0.f};
+        }
+        // double-single xor tree across the lanes, all chains interleaved
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int p = 0; p < IPT; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) ds_acc(v[p][c], ds_shfl_xor(v[p][c], o));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int p = 0; p < IPT; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c)
+                    s_red[warp][p * 7 + c] = make_float2(v[p][c].hi, v[p][c].lo);
         }
         __syncthreads();
         if (tid < IPT * 7) {
             const int p = tid / 7, c = tid % 7;
             const int k = g0 + p;
-            if (k < is.n) {
-                double s = 0.0;
+            dsf sum{0.f, 0.f};
 #pragma unroll
-                for (int w = 0; w < NW; ++w) s += (double)s_red[w][p][c];
-                if (nsplit == 1) {
-                    if (c == 6) {
-                        s = -s;
-                        if (out.pot) out.pot[k] = s;
-                    } else if (c < 3) {
-                        if (out.acc) out.acc[c * out.ld + k] = s;
-                    } else {
-                        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
-                    }
-                    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
-                } else {
-                    part[((size_t)split * 7 + c) * pld + k] = s;
-                }
+            for (int w = 0; w < NW; ++w) ds_acc(sum, dsf{s_red[w][tid].x, s_red[w][tid].y});
+            if (k < is.n) {
+                if (nsplit == 1)
+                    store_component(out, c, k, ds_to_double(sum), err);
+                else
+                    reinterpret_cast<float2 *>(part)[((size_t)split * 7 + c) * pld + k] =
+                        make_float2(sum.hi, sum.lo);
             }
         }
         __syncthreads();
     }
+    if (nsplit > 1)
+        finish_split_ds<NT>(nsplit, 0, is.n, is.n, reinterpret_cast<float2 *>(part), pld, counters,
+                            out, err);
 }
 
+// FP64 j-parallel kernel: thread = j, all threads share IPT i's.
 template <int IPT, int NT>
 __global__ void __launch_bounds__(NT)
     k_force_jmode64(JSet js, ISet is, double eps2, double *__restrict__ part, long long pld,
-                    Out3 out, unsigned *err)
+                    unsigned *counters, Out3 out, unsigned *err)
 {
     constexpr int NW = NT / 32;
     __shared__ double s_red[NW][IPT][7];
@@ -756,53 +1141,7 @@ __global__ void __launch_bounds__(NT)
         }
         __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------------------
-// K3: sum the nsplit partials of every (slot, component) in fixed order s = 0..
-// ---------------------------------------------------------------------------
-
-// Store the reduced value s of component c of slot k (c == 6: the positive
-// potential sum, stored negated).
-__device__ __forceinline__ void store_component(const Out3 &out, int c, int k, double s,
-                                                unsigned *err)
-{
-    if (c == 6) {
-        s = -s;
-        if (out.pot) out.pot[k] = s;
-    } else if (c < 3) {
-        if (out.acc) out.acc[c * out.ld + k] = s;
-    } else {
-        if (out.jerk) out.jerk[(c - 3) * out.ld + k] = s;
-    }
-    if (!isfinite(s)) atomicOr(err, DERR_NONFINITE);
-}
-
-// One thread per (k, c) - for few splits.
-__global__ void k_reduce_thread(int ni, int nsplit, const double *__restrict__ part, long long pld,
-                                Out3 out, unsigned *err)
-{
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= 7LL * ni) return;
-    const int c = (int)(q / ni), k = (int)(q % ni);
-    double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += part[((size_t)sp * 7 + c) * pld + k];
-    store_component(out, c, k, s, err);
-}
-
-// One warp per (k, c) - for many splits: lane l sums s = l, l+32, ... then a
-// fixed xor tree.
-__global__ void k_reduce_warp(int ni, int nsplit, const double *__restrict__ part, long long pld,
-                              Out3 out, unsigned *err)
-{
-    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= 7LL * ni) return;
-    const int c = (int)(w / ni), k = (int)(w % ni);
-    double s = 0.0;
-    for (int sp = lane; sp < nsplit; sp += 32) s += part[((size_t)sp * 7 + c) * pld + k];
-    s = warp_sum(s);
-    if (lane == 0) store_component(out, c, k, s, err);
+    if (nsplit > 1) finish_split<NT>(nsplit, 0, is.n, is.n, part, pld, counters, out, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -814,20 +1153,96 @@ constexpr int NS32 = 3;
 constexpr int JT64 = 64;
 constexpr int NS64 = 3;
 
+// Warp-group layout (FP32 kind 1): ipt i-particles per warp, nwarp warps per CTA.
+static void wgrp_shape(int n_i, ForcePlan &p)
+{
+    p.ipt = n_i <= 1 ? 1 : 2;
+    const int groups = (n_i + p.ipt - 1) / p.ipt;
+    const int nwarp = groups <= 1 ? 1 : groups <= 2 ? 2 : groups <= 4 ? 4 : 8;
+    p.threads = 32 * nwarp;
+}
+
+static long long clampll(long long v, long long lo, long long hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Tiny-set layout (FP32 kind 2): ipt i-particles per pass, jt = j per thread;
+// one j-split per CTA of 256 threads.
+static void tiny_shape(int n_i, int n_j, ForcePlan &p)
+{
+    p.kind = 2;
+    p.ipt = n_i <= 1 ? 1 : (n_i <= 2 ? 2 : 4);
+    p.threads = 256;
+    p.jt = n_j >= 256 * 4 * 32 ? 4 : (n_j >= 256 * 2 * 32 ? 2 : 1);
+    p.nsplit = (n_j + 256 * p.jt - 1) / (256 * p.jt);
+}
+
 ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
 {
     ForcePlan p{};
-    if (n_i <= 32) {
+    p.nwj = 1;
+    if (variant == NB_F64) {
+        if (n_i <= 32) {  // FP64 j-parallel kernel
+            p.kind = 1;
+            p.ipt = n_i <= 1 ? 1 : n_i <= 2 ? 2 : 4;
+            p.threads = 128;
+            p.nsplit = (int)clampll((n_j + 128LL * 4 - 1) / (128LL * 4), 1, 2LL * num_sms);
+            return p;
+        }
+        p.kind = 0;
+        p.ipt = 1;
+        p.threads = 128;
+        p.jt = JT64;
+        const long long nblk = (n_i + 127) / 128;
+        const long long ntiles = (n_j + JT64 - 1) / JT64;
+        p.nsplit = (int)clampll((16LL * num_sms + nblk - 1) / nblk, 1,
+                                ntiles / 2 > 1 ? ntiles / 2 : 1);
+        return p;
+    }
+    if (n_i <= 4) {
+        tiny_shape(n_i, n_j, p);
+        return p;
+    }
+    if (n_i <= 4096) {
+        // warp groups: about 16 warps per SM in total, at least 256 j per split
         p.kind = 1;
-        p.ipt = n_i <= 1 ? 1 : n_i <= 2 ? 2 : n_i <= 4 ? 4 : 8;
-        if (variant == NB_F64 && p.ipt > 4) p.ipt = 4;  // FP64 registers
-        p.threads = (variant == NB_F64) ? 128 : 256;
-        const int per_thread = 4;
-        long long g = (n_j + (long long)p.threads * per_thread - 1) / ((long long)p.threads * per_thread);
-        if (g > 2LL * num_sms) g = 2LL * num_sms;
-        if (g < 1) g = 1;
-        p.nsplit = (int)g;
-        p.jt = 0;
+        wgrp_shape(n_i, p);
+        const long long groups = (n_i + p.ipt - 1) / p.ipt;
+        const long long cap = n_j / 256 > 1 ? n_j / 256 : 1;
+        p.nsplit = (int)clampll((16LL * num_sms + groups - 1) / groups, 1, cap);
+        return p;
+    }
+    // tiles: 256 threads, 2 i per thread; warp rows share j-tiles below 8192 i
+    p.kind = 0;
+    p.ipt = 2;
+    p.threads = 256;
+    p.jt = JT32;
+    p.nwj = n_i >= 8192 ? 1 : 4;
+    const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
+    const long long nblk = (n_i + ib - 1) / ib;
+    const long long ntiles = (n_j + p.jt - 1) / p.jt;
+    p.nsplit = (int)clampll((4LL * num_sms + nblk - 1) / nblk, 1, ntiles / 2 > 1 ? ntiles / 2 : 1);
+    return p;
+}
+
+ForcePlan plan_from_entry(const nb_plan &e, int variant, int n_i, int n_j)
+{
+    ForcePlan p{};
+    p.nwj = 1;
+    if (e.kind == 2 && variant != NB_F64) {
+        tiny_shape(n_i, n_j, p);  // its split count follows from the j per thread
+        return p;
+    }
+    if (e.kind == 1 || e.kind == 2) {
+        p.kind = 1;
+        if (variant == NB_F64) {
+            p.ipt = n_i <= 1 ? 1 : n_i <= 2 ? 2 : 4;
+            p.threads = 128;
+        } else {
+            wgrp_shape(n_i, p);
+        }
+        p.nsplit = (int)clampll(e.nsplit, 1, n_j);
         return p;
     }
     p.kind = 0;
@@ -837,18 +1252,12 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
         p.jt = JT64;
     } else {
         p.ipt = 2;
+        p.threads = 256;
         p.jt = JT32;
-        p.threads = n_i >= 16384 ? 256 : (n_i >= 1024 ? 128 : 64);
+        p.nwj = (e.nwj == 4 || e.nwj == 8) ? e.nwj : 1;
     }
-    const long long ib = (long long)p.threads * p.ipt;
-    const long long nblk = (n_i + ib - 1) / ib;
-    const long long ntiles = (n_j + p.jt - 1) / p.jt;
-    const long long resident = (p.threads >= 256) ? 2 : (p.threads == 128 ? 4 : 8);
-    const long long target = 4LL * num_sms * resident;
-    long long ns = (target + nblk - 1) / nblk;
-    if (ns > ntiles) ns = ntiles;
-    if (ns < 1) ns = 1;
-    p.nsplit = (int)ns;
+    const int ntiles = (n_j + p.jt - 1) / p.jt;
+    p.nsplit = (int)clampll(e.nsplit, 1, ntiles);
     return p;
 }
 
@@ -858,60 +1267,105 @@ size_t plan_partial_doubles(const ForcePlan &p, int n_i)
     return (size_t)p.nsplit * 7 * (size_t)n_i;
 }
 
-template <int VAR, int IPT, int NT>
+template <int VAR, int IPT, int NWI, int NWJ>
 static cudaError_t go_tile32(const JSet &js, const ISet &is, float eps2f, int nsplit,
-                             double *part, Out3 out, unsigned *err, cudaStream_t st)
+                             double *part, unsigned *cnt, Out3 out, unsigned *err,
+                             cudaStream_t st)
 {
-    auto kern = k_force_tile32<VAR, IPT, NT, JT32, NS32>;
-    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);  // 18 KB, below 48 KB
+    auto kern = k_force_tile32<VAR, IPT, NWI, NWJ, JT32, NS32>;
+    constexpr int NT = 32 * NWI * NWJ;
+    constexpr int IB = 32 * NWI * IPT;
+    const size_t ring = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);  // 18 KB
+    const size_t red = NWJ > 1 ? (size_t)NWJ * 7 * IB * sizeof(double) : 0;  // <= 28 KB
+    const size_t smem = ring > red ? ring : red;
     const int ntiles = (js.n + JT32 - 1) / JT32;
-    dim3 grid((is.n + NT * IPT - 1) / (NT * IPT), nsplit);
-    kern<<<grid, NT, smem, st>>>(js.rec32, js.n, is, eps2f, ntiles, part, is.n, out, err);
+    dim3 grid((is.n + IB - 1) / IB, nsplit);
+    kern<<<grid, NT, smem, st>>>(js.rec32, js.n, is, eps2f, ntiles, part, is.n, cnt, out, err);
     return cudaGetLastError();
+}
+
+template <int VAR, int IPT, int NWARP>
+static cudaError_t go_wgrp32(const JSet &js, const ISet &is, float eps2f, int nsplit,
+                             double *part, unsigned *cnt, Out3 out, unsigned *err,
+                             cudaStream_t st)
+{
+    const int groups = (is.n + IPT - 1) / IPT;
+    dim3 grid((groups + NWARP - 1) / NWARP, nsplit);
+    k_force_wgrp32<VAR, IPT, NWARP><<<grid, 32 * NWARP, 0, st>>>(js.rec32, js.n, is, eps2f, part,
+                                                                  is.n, cnt, out, err);
+    return cudaGetLastError();
+}
+
+template <int VAR, int IPT, int JPT>
+static cudaError_t go_tiny32(const JSet &js, const ISet &is, float eps2f, double *part,
+                             unsigned *cnt, Out3 out, unsigned *err, cudaStream_t st)
+{
+    const int g = (js.n + 256 * JPT - 1) / (256 * JPT);
+    k_force_tiny32<VAR, IPT, JPT><<<g, 256, 0, st>>>(js.rec32, js.n, is, eps2f, part, is.n, cnt,
+                                                      out, err);
+    return cudaGetLastError();
+}
+
+template <int VAR, int IPT>
+static cudaError_t go_tiny32_j(int jpt, const JSet &js, const ISet &is, float eps2f,
+                               double *part, unsigned *cnt, Out3 out, unsigned *err,
+                               cudaStream_t st)
+{
+    switch (jpt) {
+    case 1: return go_tiny32<VAR, IPT, 1>(js, is, eps2f, part, cnt, out, err, st);
+    case 2: return go_tiny32<VAR, IPT, 2>(js, is, eps2f, part, cnt, out, err, st);
+    default: return go_tiny32<VAR, IPT, 4>(js, is, eps2f, part, cnt, out, err, st);
+    }
 }
 
 template <int IPT, int NT>
 static cudaError_t go_tile64(const JSet &js, const ISet &is, double eps2, int nsplit, double *part,
-                             Out3 out, unsigned *err, cudaStream_t st)
+                             unsigned *cnt, Out3 out, unsigned *err, cudaStream_t st)
 {
     auto kern = k_force_tile64<IPT, NT, JT64, NS64>;
     const size_t smem = (size_t)NS64 * 7 * JT64 * sizeof(double);  // 10.5 KB
     const int ntiles = (js.n + JT64 - 1) / JT64;
     dim3 grid((is.n + NT * IPT - 1) / (NT * IPT), nsplit);
-    kern<<<grid, NT, smem, st>>>(js, is, eps2, ntiles, part, is.n, out, err);
+    kern<<<grid, NT, smem, st>>>(js, is, eps2, ntiles, part, is.n, cnt, out, err);
     return cudaGetLastError();
 }
 
 template <int VAR>
 static cudaError_t dispatch32(const ForcePlan &p, const JSet &js, const ISet &is, float eps2f,
-                              double *part, Out3 out, unsigned *err, cudaStream_t st)
+                              double *part, unsigned *cnt, Out3 out, unsigned *err,
+                              cudaStream_t st)
 {
-    if (p.kind == 1) {
-        const int g = p.nsplit;
-#define JM(I) \
-    k_force_jmode32<VAR, I, 256><<<g, 256, 0, st>>>(js.rec32, js.n, is, eps2f, part, is.n, out, err)
+    if (p.kind == 2) {
         switch (p.ipt) {
-        case 1: JM(1); break;
-        case 2: JM(2); break;
-        case 4: JM(4); break;
-        default: JM(8); break;
+        case 1: return go_tiny32_j<VAR, 1>(p.jt, js, is, eps2f, part, cnt, out, err, st);
+        case 2: return go_tiny32_j<VAR, 2>(p.jt, js, is, eps2f, part, cnt, out, err, st);
+        default: return go_tiny32_j<VAR, 4>(p.jt, js, is, eps2f, part, cnt, out, err, st);
         }
-#undef JM
-        return cudaGetLastError();
     }
-    switch (p.threads) {
-    case 256: return go_tile32<VAR, 2, 256>(js, is, eps2f, p.nsplit, part, out, err, st);
-    case 128: return go_tile32<VAR, 2, 128>(js, is, eps2f, p.nsplit, part, out, err, st);
-    default: return go_tile32<VAR, 2, 64>(js, is, eps2f, p.nsplit, part, out, err, st);
+    if (p.kind == 1) {
+        const int nw = p.threads / 32;
+        if (p.ipt == 1) return go_wgrp32<VAR, 1, 1>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+        switch (nw) {
+        case 1: return go_wgrp32<VAR, 2, 1>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+        case 2: return go_wgrp32<VAR, 2, 2>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+        case 4: return go_wgrp32<VAR, 2, 4>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+        default: return go_wgrp32<VAR, 2, 8>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+        }
+    }
+    switch (p.nwj) {
+    case 1: return go_tile32<VAR, 2, 8, 1>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+    case 4: return go_tile32<VAR, 2, 2, 4>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
+    default: return go_tile32<VAR, 2, 1, 8>(js, is, eps2f, p.nsplit, part, cnt, out, err, st);
     }
 }
 
 static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is, double eps2,
-                              double *part, Out3 out, unsigned *err, cudaStream_t st)
+                              double *part, unsigned *cnt, Out3 out, unsigned *err,
+                              cudaStream_t st)
 {
     if (p.kind == 1) {
         const int g = p.nsplit;
-#define JM(I) k_force_jmode64<I, 128><<<g, 128, 0, st>>>(js, is, eps2, part, is.n, out, err)
+#define JM(I) k_force_jmode64<I, 128><<<g, 128, 0, st>>>(js, is, eps2, part, is.n, cnt, out, err)
         switch (p.ipt) {
         case 1: JM(1); break;
         case 2: JM(2); break;
@@ -920,40 +1374,36 @@ static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is
 #undef JM
         return cudaGetLastError();
     }
-    return go_tile64<1, 128>(js, is, eps2, p.nsplit, part, out, err, st);
+    return go_tile64<1, 128>(js, is, eps2, p.nsplit, part, cnt, out, err, st);
+}
+
+size_t plan_counters(const ForcePlan &p, int n_i)
+{
+    if (p.nsplit <= 1) return 1;
+    if (p.kind == 2) return 1;
+    long long ib;
+    if (p.kind == 1)
+        ib = (long long)(p.threads / 32) * p.ipt;  // FP32 warp groups (FP64 j-parallel: one)
+    else
+        ib = (long long)(p.threads / p.nwj) * p.ipt;
+    return (size_t)((n_i + ib - 1) / ib);
 }
 
 cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, const ISet &is,
-                         double eps2, double *part, Out3 out, unsigned *err, cudaStream_t st,
-                         cudaEvent_t *ev)
+                         double eps2, double *part, unsigned *counters, Out3 out, unsigned *err,
+                         cudaStream_t st, cudaEvent_t *ev)
 {
     if (is.n <= 0) return cudaSuccess;
     const float eps2f = (float)eps2;
     cudaError_t e;
     if (ev) cudaEventRecord(ev[0], st);
     if (variant == NB_F64)
-        e = dispatch64(plan, js, is, eps2, part, out, err, st);
+        e = dispatch64(plan, js, is, eps2, part, counters, out, err, st);
     else if (variant == NB_F32DS)
-        e = dispatch32<NB_F32DS>(plan, js, is, eps2f, part, out, err, st);
+        e = dispatch32<NB_F32DS>(plan, js, is, eps2f, part, counters, out, err, st);
     else
-        e = dispatch32<NB_F32>(plan, js, is, eps2f, part, out, err, st);
+        e = dispatch32<NB_F32>(plan, js, is, eps2f, part, counters, out, err, st);
     if (ev) cudaEventRecord(ev[1], st);
-    if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[2], st);
-    if (plan.nsplit > 1) {
-        const long long nout = 7LL * is.n;
-        const int bs = 256;
-        if (plan.nsplit >= 64) {
-            const long long threads = nout * 32;
-            k_reduce_warp<<<(unsigned)((threads + bs - 1) / bs), bs, 0, st>>>(is.n, plan.nsplit,
-                                                                               part, is.n, out, err);
-        } else {
-            k_reduce_thread<<<(unsigned)((nout + bs - 1) / bs), bs, 0, st>>>(is.n, plan.nsplit,
-                                                                             part, is.n, out, err);
-        }
-        e = cudaGetLastError();
-    }
-    if (ev) cudaEventRecord(ev[3], st);
     return e;
 }
 

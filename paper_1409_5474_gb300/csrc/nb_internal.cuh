@@ -18,8 +18,9 @@ enum : unsigned {
 };
 
 // Double-single j-record, 48 bytes per particle (see DS_REC):
-//   r[0] = {x_hi, y_hi, z_hi, m}, r[1] = {x_lo, y_lo, z_lo, 0}, r[2] = {vx, vy, vz, 0}
-// with x = x_hi + x_lo to ~48 bits and FP32 velocity.
+//   r[0] = {x_hi, y_hi, z_hi, m}, r[1] = {x_lo, y_lo, z_lo, id}, r[2] = {vx, vy, vz, 0}
+// with x = x_hi + x_lo to ~48 bits, FP32 velocity, and id the particle index
+// stored as int bits (read only to recognise the self pair of a gathered i-set).
 constexpr int DS_REC = 3;  // float4 per record
 
 // Vector-field output with a row stride: component c of slot k is p[c*ld + k].
@@ -43,6 +44,8 @@ struct ISet {
     const double *m64;     // masses (members only; used for the self term)
     long long ld64;
     int nj;                // bound of member indices (the j-set size)
+    bool gathered;         // FP32 kinds: rec32 holds one record per slot (a gathered
+                           // copy) whose r[1].w carries the particle index bits
 };
 
 // The j-set of an evaluation: predicted FP64 SoA and the DS records.
@@ -62,20 +65,29 @@ struct ForcePlan {
     int threads;  // CTA size
     int nsplit;   // j-splits (grid.y for tiles, grid.x for jmode)
     int jt;       // j-tile depth (tile kind)
+    int nwj;      // warp rows sharing each j-tile (FP32 tile kind)
 };
 
 // Choose a plan for n_i i-particles against n_j j-particles.
 ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms);
 
+// A plan from a plan-table entry (kind 0 or 1; sizes clamped to the sets).
+ForcePlan plan_from_entry(const nb_plan &e, int variant, int n_i, int n_j);
+
 // Scratch doubles the plan needs for partial sums (0 when nsplit == 1).
 size_t plan_partial_doubles(const ForcePlan &p, int n_i);
 
-// Launch K2 (+ K3 when nsplit > 1). part must hold plan_partial_doubles.
+// Counters the split reduction needs: one per i-block (zero at allocation;
+// every launch leaves them at zero again).
+size_t plan_counters(const ForcePlan &p, int n_i);
+
+// Launch K2 with the K3 reduction folded in: when nsplit > 1 each CTA writes
+// its partial sums to part (plan_partial_doubles) and the last CTA of every
+// i-block (counted in counters) sums them in the fixed order s = 0..nsplit-1.
 // eps2: softening squared. Results go to out (slot-indexed). Non-finite
-// results set DERR_NONFINITE in *err. ev (optional, 4 events) brackets the
-// force kernel (ev[0], ev[1]) and the reduction (ev[2], ev[3]).
+// results set DERR_NONFINITE in *err. ev (optional, 2 events) brackets the launch.
 cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, const ISet &is,
-                         double eps2, double *part, Out3 out, unsigned *err,
+                         double eps2, double *part, unsigned *counters, Out3 out, unsigned *err,
                          cudaStream_t st, cudaEvent_t *ev);
 
 // ---- per-particle kernels (K1, K4, K5) -------------------------------------
@@ -119,7 +131,7 @@ struct Mailbox {
 
 // Particles per scheduler CTA (256 threads x 8).
 constexpr int SCHED_THREADS = 256;
-constexpr int SCHED_PER_THREAD = 8;
+constexpr int SCHED_PER_THREAD = 1;
 constexpr int SCHED_TILE = SCHED_THREADS * SCHED_PER_THREAD;
 
 // K1: predict all particles of s to time t (FP64), writing pos_p, vel_p and,
@@ -144,11 +156,12 @@ cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams
 // min_i(t_i + dt_i) when every t_i is a multiple of dt_i and t_i <= t_cur <
 // t_i + dt_i); predicts every particle to t_next (FP64 + DS records); writes
 // the due particles (t_i + dt_i == t_next) to act in ascending index with a
-// single-pass decoupled look-back scan over tiles; the last CTA publishes
+// single-pass decoupled look-back scan over tiles, and (when want_rec) their
+// records to irec in the same order; the last CTA publishes
 // (seq, t_next, n_active) to the mailbox. status: one word per tile.
 cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long long *status,
-                                 int *act, Mailbox *mail_dev, double dt_max, bool want_rec,
-                                 unsigned *err, cudaStream_t st);
+                                 int *act, float4 *irec, Mailbox *mail_dev, double dt_max,
+                                 bool want_rec, unsigned *err, cudaStream_t st);
 
 // Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
 cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,

@@ -25,12 +25,15 @@ constexpr int kMaxDevices = 64;
 
 // Partial sums of the j-split: 7 values per (split, i-particle).
 __device__ __align__(256) double g_static_part[NB_STATIC_SCRATCH_DOUBLES];
-// Device error word of these calls (cleared at the start of every call).
+// Device error word of these calls (cleared at the start of every call), and
+// the arrival counter of the split reduction (re-armed to zero by each call).
 __device__ __align__(256) unsigned g_static_err[64];
+__device__ __align__(256) unsigned g_static_cnt[64];
 
 struct StaticSlot {
     double *part = nullptr;
     unsigned *err = nullptr;
+    unsigned *cnt = nullptr;
     int num_sms = 0;
     bool ready = false;
 };
@@ -55,6 +58,11 @@ int static_slot(int dev, StaticSlot *out)
             return NB_ERR_CUDA;
         }
         s.err = static_cast<unsigned *>(p);
+        if (cudaGetSymbolAddress(&p, g_static_cnt) != cudaSuccess) {
+            cudaGetLastError();
+            return NB_ERR_CUDA;
+        }
+        s.cnt = static_cast<unsigned *>(p);
         if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) !=
             cudaSuccess) {
             cudaGetLastError();
@@ -104,6 +112,7 @@ extern "C" int nb_force_static(int n_j, const double *m, const double *pos, cons
     is.m64 = m;
     is.ld64 = ld;
     is.nj = n_j;
+    is.gathered = false;
 
     // FP64 j-parallel plan whose partial sums fit the static array.
     nb::ForcePlan plan{};
@@ -118,13 +127,14 @@ extern "C" int nb_force_static(int n_j, const double *m, const double *pos, cons
     plan.nsplit = (int)ns;
     plan.jt = 0;
 
-    if (cudaMemsetAsync(slot.err, 0, sizeof(unsigned), st) != cudaSuccess) {
+    if (cudaMemsetAsync(slot.err, 0, sizeof(unsigned), st) != cudaSuccess ||
+        cudaMemsetAsync(slot.cnt, 0, sizeof(unsigned), st) != cudaSuccess) {
         cudaGetLastError();
         return NB_ERR_CUDA;
     }
     nb::Out3 out{acc, jerk, pot, n_i};
-    if (nb::launch_force(NB_F64, plan, js, is, eps * eps, slot.part, out, slot.err, st, nullptr) !=
-        cudaSuccess) {
+    if (nb::launch_force(NB_F64, plan, js, is, eps * eps, slot.part, slot.cnt, out, slot.err, st,
+                         nullptr) != cudaSuccess) {
         cudaGetLastError();
         return NB_ERR_CUDA;
     }

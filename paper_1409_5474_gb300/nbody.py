@@ -56,17 +56,27 @@ class nb_config(ctypes.Structure):
                 ("flags", ctypes.c_int)]
 
 
+class nb_plan(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nwj", ctypes.c_int), ("nsplit", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.kind, self.nwj, self.nsplit)
+
+
 class nb_stats(ctypes.Structure):
     _fields_ = [("block_steps", ctypes.c_longlong), ("force_launches", ctypes.c_longlong),
                 ("interactions", ctypes.c_double), ("force_ms", ctypes.c_double),
                 ("reduce_ms", ctypes.c_double), ("predict_ms", ctypes.c_double),
                 ("correct_ms", ctypes.c_double), ("sched_ms", ctypes.c_double),
                 ("dt_min_hits", ctypes.c_longlong), ("active_hist", ctypes.c_longlong * 32),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong),
+                ("force_ms_hist", ctypes.c_double * 32), ("inter_hist", ctypes.c_double * 32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "active_hist"}
-        d["active_hist"] = list(self.active_hist)
+        hists = ("active_hist", "force_ms_hist", "inter_hist")
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in hists}
+        for k in hists:
+            d[k] = list(getattr(self, k))
         return d
 
 
@@ -100,6 +110,10 @@ _SIGS = [
     ("nb_energy", ctypes.c_int, [_H, _D, _D]),
     ("nb_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_stats)]),
     ("nb_reset_stats", ctypes.c_int, [_H]),
+    ("nb_plan_for", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(nb_plan)]),
+    ("nb_set_plan_table", ctypes.c_int, [_H, ctypes.POINTER(nb_plan), ctypes.c_int]),
+    ("nb_get_plan_table", ctypes.c_int, [_H, ctypes.POINTER(nb_plan)]),
+    ("nb_autotune", ctypes.c_int, [_H, ctypes.c_int]),
     ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -296,6 +310,33 @@ def nb_get_stats(h) -> dict:
 
 def nb_reset_stats(h) -> None:
     _check(load().nb_reset_stats(h), "nb_reset_stats", h)
+
+
+def nb_plan_for(h, n_i):
+    """(kind, nwj, nsplit) of the plan used for n_i i-particles."""
+    pl = nb_plan()
+    _check(load().nb_plan_for(h, int(n_i), ctypes.byref(pl)), "nb_plan_for", h)
+    return pl.as_tuple()
+
+
+def nb_set_plan_table(h, table):
+    """table: list of (kind, nwj, nsplit) per bucket ceil(log2 n_i), or None for the heuristic."""
+    if table is None:
+        _check(load().nb_set_plan_table(h, None, 0), "nb_set_plan_table", h)
+        return
+    arr = (nb_plan * len(table))(*[nb_plan(*t) for t in table])
+    _check(load().nb_set_plan_table(h, arr, len(table)), "nb_set_plan_table", h)
+
+
+def nb_get_plan_table(h):
+    arr = (nb_plan * 32)()
+    _check(load().nb_get_plan_table(h, arr), "nb_get_plan_table", h)
+    return [p.as_tuple() for p in arr]
+
+
+def nb_autotune(h, reps=3):
+    _check(load().nb_autotune(h, int(reps)), "nb_autotune", h)
+    return nb_get_plan_table(h)
 
 
 NB_STATIC_MAX_NI = 1024

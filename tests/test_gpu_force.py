@@ -191,3 +191,42 @@ def test_full_size_sampled_2pow20(nb):
         ea, ej, ep = rel_rms(acc.T, ra), rel_rms(jerk.T, rj), rel_rms(pot, rp)
         print(variant, ea, ej, ep)
         assert ea <= ga and ej <= gj and ep <= gp, (variant, ea, ej, ep)
+
+
+PLANS = [(2, 1, 1), (1, 1, 1), (1, 1, 7), (1, 1, 300), (0, 1, 1), (0, 1, 5), (0, 4, 3), (0, 8, 1),
+         (0, 8, 33)]
+
+
+@pytest.mark.parametrize("variant", ["f32ds", "f64"])
+@pytest.mark.parametrize("plan", PLANS, ids=[str(p) for p in PLANS])
+@pytest.mark.parametrize("n_i", [1, 3, 77, 1000])
+def test_every_plan_gives_the_same_forces(nb, variant, plan, n_i):
+    """A launch plan only reorders the sums: every kind / warp-row count / j-split passes
+    the same gates against the oracle (ragged i-blocks, splits that do not divide the tiles)."""
+    if variant == "f64" and plan[1] != 1:
+        pytest.skip("FP64 tiles have no warp rows")
+    m, pos, vel = _system(4097, 8)
+    idx = np.random.default_rng(n_i).integers(0, 4097, size=n_i).astype(np.int32)
+    with nb.System(m, pos, vel, variant=variant, eps=1e-3, device=0) as s:
+        nb.nb_set_plan_table(s.h, [plan] * 32)
+        s.predict(0.0)
+        acc, jerk, pot = s.force(idx)
+    ra, rj, rp = oracle.force(m, pos, vel, 1e-6, idx=idx)
+    ga, gj, gp = GATES[variant]
+    assert rel_rms(acc.T, ra) <= ga and rel_rms(jerk.T, rj) <= gj and rel_rms(pot, rp) <= gp
+
+
+def test_autotune_table_and_parity(nb):
+    m, pos, vel = _system(5000, 9)
+    with nb.System(m, pos, vel, variant="f32ds", eps=1e-3, device=0) as s:
+        table = nb.nb_autotune(s.h, 2)
+        assert all(t[0] in (0, 1, 2) for t in table[:14])   # buckets up to 2^13 >= 5000 tuned
+        assert all(t[0] == -1 for t in table[14:])
+        assert nb.nb_plan_for(s.h, 700) == table[10]
+        s.predict(0.0)
+        acc, jerk, pot = s.force()
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nb_set_plan_table(s.h, [(0, 3, 1)])
+        assert e.value.status == nb.NB_ERR_ARG
+    ra, rj, rp = oracle.force(m, pos, vel, 1e-6)
+    assert rel_rms(acc.T, ra) <= 1e-6 and rel_rms(jerk.T, rj) <= 1e-5
