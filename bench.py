@@ -22,6 +22,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import math
 import os
 import statistics
@@ -47,6 +49,11 @@ WORKLOADS = {
     "full2p20": dict(n=2 ** 20, eps=1e-4, variant="f32ds", masses="lognormal", kind="force",
                      desc="Plummer N=2^20 log-normal masses (sigma 0.5), eps=1e-4; one bench "
                           "step = one full N^2 acc/jerk/pot evaluation (predict + force)"),
+    "batch4096": dict(n=4096, n_lo=16, n_hi=4096, dt=1.0 / 512, variant="f32ds", kind="batch",
+                      step_t=1.0 / 16, eps=None, masses="equal",
+                      desc="4096 independent Plummer clusters, N log-uniform in [16, 4096], "
+                           "eps = 1/(4 N^(1/3)), shared dt = 1/512, F32-DS; one bench step = "
+                           "1/16 time unit = 32 graph-replayed steps of all clusters"),
     "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
                       variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
                       desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
@@ -206,9 +213,23 @@ ORACLE_BLOCK_STEPS = 64
 def oracle_sample(wl, particles):
     """One bounded oracle sample of the workload; returns (interactions, seconds, desc)."""
     import oracle
+    if wl["kind"] == "batch":
+        # 32 seeded clusters spanning the size range, 64 shared steps each
+        from paper_1409_5474_gb300 import ic
+        sizes = np.rint(np.exp(np.linspace(np.log(wl["n_lo"]), np.log(wl["n_hi"]), 32)))
+        inter = 0.0
+        t0 = time.perf_counter()
+        for c, n in enumerate(sizes.astype(int)):
+            p = ic.plummer(int(n), int(ic.key(ic.MASTER_SEED, 8, c)))
+            st = oracle.State(p.m, p.pos, p.vel)
+            _, it = oracle.hermite_run(st, math.inf, float(ic.cluster_eps(n)) ** 2,
+                                       dt_shared=wl["dt"], max_steps=64)
+            inter += it
+        dt = time.perf_counter() - t0
+        return inter, dt, ("oracle shared-step Hermite on 32 clusters with N log-spaced in "
+                           "[%d, %d]: initial evaluation + 64 steps each" % (wl["n_lo"], wl["n_hi"]))
     eps2 = wl["eps"] ** 2
     if wl["kind"] == "force":
-        import numpy as np
         rng = np.random.default_rng(2014)
         ni = 4096
         idx = rng.choice(particles.n, size=ni, replace=False).astype(np.int32)
@@ -249,6 +270,10 @@ def config_of(wl, name, variant):
     if wl["kind"] == "evolve":
         c.update({"eta": wl["eta"], "dt_max": wl["dt_max"], "shared_dt": wl["shared_dt"],
                   "step_time_units": wl["step_t"]})
+    if wl["kind"] == "batch":
+        c.update({"n_clusters": wl["n"], "n_range": [wl["n_lo"], wl["n_hi"]], "shared_dt": wl["dt"],
+                  "eps": "1/(4 N^(1/3)) per cluster", "step_time_units": wl["step_t"],
+                  "l2": "working set (~1 GB) larger than L2"})
     return c
 
 
@@ -259,7 +284,7 @@ def run_reference(args):
     import oracle
     wl = workload(args)
     variant = args.variant or wl["variant"]
-    p = make_particles(wl)
+    p = make_particles(wl) if wl["kind"] != "batch" else None
     inter_t = secs_t = 0.0
     desc = ""
     for k in range(args.warmup + args.steps):
@@ -282,7 +307,6 @@ def run_reference(args):
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     rank, world, local = dist_env()
@@ -295,6 +319,8 @@ def run_ours(args):
     nbody.load()
     wl = workload(args)
     variant = args.variant or wl["variant"]
+    if wl["kind"] == "batch":
+        return run_batch(args, wl, variant, dist, rank, world, local)
     p = make_particles(wl)
     stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
     torch.cuda.set_stream(stream)
@@ -431,6 +457,90 @@ def run_ours(args):
                                 "seconds": secs_c}
     print(json.dumps(line), flush=True)
     sysm.close()
+    dist.close()
+    return 0
+
+
+def run_batch(args, wl, variant, dist, rank, world, local):
+    """Config 4: many clusters, one graph-replayed shared step of all of them at a time."""
+    import torch
+    from paper_1409_5474_gb300 import ic, nbody
+
+    systems = ic.cluster_batch(wl["n"], wl["n_lo"], wl["n_hi"])
+    sizes = np.array([len(p.m) for p in systems])
+    eps = ic.cluster_eps(sizes)
+    bt = nbody.Batch(systems, eps, wl["dt"], variant=variant, device=local,
+                     flags=nbody.NB_FLAG_TIMING)
+    threads = bt.autotune() if args.autotune else None
+    steps_per = int(round(wl["step_t"] / wl["dt"]))
+    m = np.concatenate([p.m for p in systems])
+    for _ in range(args.warmup):
+        bt.step(steps_per)
+    pos, vel, _ = bt.get()
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    tot_inter = tot_dev = tot_wall = force_ms = 0.0
+    launches = 0
+    for k in range(args.steps):
+        w0 = time.perf_counter()
+        nbody.nb_batch_set(bt.b, m, pos, vel, (args.warmup + k) * wl["step_t"])  # H2D
+        e0 = time.perf_counter()
+        st = bt.step(steps_per)
+        e1 = time.perf_counter()
+        pos, vel, _ = bt.get()                                                    # D2H
+        w1 = time.perf_counter()
+        inter = st["interactions"] - float((sizes.astype(np.float64) ** 2).sum())  # minus init
+        tot_inter += inter
+        tot_dev += e1 - e0
+        tot_wall += w1 - w0
+        force_ms += st["force_ms"]
+        launches += st["kernel_launches"]
+    clocks = sampler.stop()
+    dist.barrier()
+    units, secs = aggregate(dist.gather_pairs(tot_inter, tot_dev, device="cuda"))
+    e2e_units, e2e_secs = aggregate(dist.gather_pairs(tot_inter, tot_wall, device="cuda"))
+    if rank != 0:
+        bt.close()
+        dist.close()
+        return 0
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(measured_peaks().get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    value = units / secs / 1e9
+    achieved = FLOPS_PER_INTERACTION * tot_inter / (force_ms / 1e3) / 1e12 if force_ms else None
+    ntot = int(sizes.sum())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Plummer clusters, N-body units)",
+        "config": dict(config_of(wl, args.workload, variant),
+                       parallelism=("replicas%d" % world) if world > 1 else "single GPU",
+                       cta_threads=threads or "default 128", particles=ntot),
+        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+        "roofline": {"bound": "alu", "kernel": "k_force_batch32 (batched pair force)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived)" % sm_max,
+                     "force_ms": force_ms},
+        "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": ntot * 7 * 8, "d2h_bytes_per_step": ntot * 6 * 8,
+                "note": "host set includes a fresh initial evaluation, not counted as work"},
+        "gpu_launches": launches,
+        "interactions": tot_inter,
+        "clocks": clocks,
+        "timing": "host wall clock around nb_batch_step (synchronous) for value",
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        inter, secs_c, desc = oracle_sample(wl, None)
+        line["cpu_baseline"] = {"value": inter / secs_c / 1e9, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle", "sample": desc,
+                                "seconds": secs_c}
+    print(json.dumps(line), flush=True)
+    bt.close()
     dist.close()
     return 0
 

@@ -249,6 +249,48 @@ int nb_get_plan_table(nb_handle h, nb_plan *table /* 32 entries */);
  * a manual nb_force. */
 int nb_autotune(nb_handle h, int reps);
 
+/* ---- batched systems -------------------------------------------------------
+ * Many independent systems (clusters of uneven N) advanced together with
+ * shared-step 4th-order Hermite (Sect. II/VI), every system with its own
+ * softening; one step of all systems is one CUDA-graph replay of three
+ * kernels: predictor over all particles, one batched force launch (work
+ * items = (system, i-block) pairs in decreasing work, persistent CTAs), and
+ * corrector over all particles. FP32 kinds only (NB_F32DS or NB_F32).
+ * Arrays are concatenated over the systems in order: m[Ntot], pos/vel as 3
+ * rows of Ntot (Ntot = sum of sizes). */
+typedef struct nb_batch_s *nb_batch;
+
+/* cfg supplies variant, device, flags and budget_bytes (its n_max, eps, eta,
+ * dt limits and shared_dt are not used); sizes[n_sys] >= 1; eps[n_sys] >= 0;
+ * dt > 0 the shared step. */
+int nb_batch_create(const nb_config *cfg, int n_sys, const int *sizes, const double *eps,
+                    double dt, nb_batch *out);
+int nb_batch_destroy(nb_batch b);
+
+/* Set every system's particles (concatenated) at time t0; the first step
+ * evaluates the initial acc/jerk. Non-finite values: NB_ERR_NONFINITE. */
+int nb_batch_set(nb_batch b, const double *m, const double *pos, const double *vel, double t0);
+
+/* Advance all systems by n_steps shared steps of dt. st (may be NULL)
+ * receives this call's counters (interactions = sum over systems of N^2 per
+ * step). */
+int nb_batch_step(nb_batch b, int n_steps, nb_stats *st);
+
+/* Current positions and velocities (concatenated; NULL skips) and time. */
+int nb_batch_get(nb_batch b, double *pos, double *vel, double *t);
+
+/* Kinetic and potential energy of every system (kin[n_sys], pot[n_sys]),
+ * with the potential from the batch's pair arithmetic. */
+int nb_batch_energy(nb_batch b, double *kin, double *pot);
+
+/* Autotune the batched kernel's CTA size (64, 128 or 256 threads, i.e.
+ * i-blocks of 128, 256 or 512) on the current particles; returns the choice
+ * in *threads (may be NULL). */
+int nb_batch_autotune(nb_batch b, int *threads);
+
+/* Message of the last failure on a batch. */
+const char *nb_batch_last_error(nb_batch b);
+
 /* ---- allocation-free force evaluation -----------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot call cudaMalloc: a host code that gives all of its device memory to

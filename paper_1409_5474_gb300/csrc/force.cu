@@ -1145,6 +1145,187 @@ __global__ void __launch_bounds__(NT)
 }
 
 // ---------------------------------------------------------------------------
+// Batched force kernel: many independent systems (clusters) in one launch.
+// Every system's particles are contiguous in the concatenated arrays; a work
+// item is one i-block of one system against all j of the same system. The
+// persistent CTAs walk the item list (sorted by decreasing work on the host,
+// so the round-robin assignment is balanced), staging each system's j-tiles
+// through the same bulk-copy ring as the tile kernel; the mbarrier phases run
+// on across items.
+// ---------------------------------------------------------------------------
+
+template <int VAR, int IPT, int NT, int JT, int NS>
+__global__ void __launch_bounds__(NT)
+    k_force_batch32(const float4 *__restrict__ rec, const BatchItem *__restrict__ items,
+                    int nitems, const float *__restrict__ eps2_sys, Out3 out, unsigned *err)
+{
+    extern __shared__ __align__(128) float4 s_tile[];  // NS * JT * DS_REC
+    __shared__ __align__(8) uint64_t s_full[NS];
+    __shared__ int s_abort;
+    constexpr bool DS = (VAR == NB_F32DS);
+    constexpr int IB = NT * IPT;
+    const int tid = threadIdx.x;
+
+    if (tid == 0) {
+        s_abort = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) mbar_init(&s_full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    unsigned seq = 0;  // tiles consumed so far by this CTA (ring position and phase)
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const float eps2f = eps2_sys[w.sys];
+        const int ntiles = (w.nj + JT - 1) / JT;
+
+        float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+        int iid[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = min(p * NT + tid, w.ni - 1);  // idle slots copy the last i
+            const int r = w.i0 + k;
+            const float4 a = __ldg(rec + (size_t)DS_REC * r);
+            const float4 b = __ldg(rec + (size_t)DS_REC * r + 1);
+            const float4 c = __ldg(rec + (size_t)DS_REC * r + 2);
+            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
+            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+            iid[p] = r;
+        }
+        float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A_h[p][c] = A_l[p][c] = J_h[p][c] = J_l[p][c] = 0.f;
+            P_h[p] = P_l[p] = 0.f;
+        }
+
+        auto issue = [&](int kt) {
+            const unsigned sq = seq + (unsigned)kt;
+            const int stage = (int)(sq % NS);
+            const int cnt = min(JT, w.nj - kt * JT);
+            const uint32_t bytes = (uint32_t)cnt * DS_REC * 16u;
+            mbar_expect_tx(&s_full[stage], bytes);
+            bulk_g2s(s_tile + (size_t)stage * JT * DS_REC,
+                     rec + (size_t)(w.j0 + kt * JT) * DS_REC, bytes, &s_full[stage]);
+        };
+        if (tid == 0) {
+            for (int kt = 0; kt < NS && kt < ntiles; ++kt) issue(kt);
+        }
+        for (int kt = 0; kt < ntiles; ++kt) {
+            const unsigned sq = seq + (unsigned)kt;
+            const int stage = (int)(sq % NS);
+            if (!mbar_wait(&s_full[stage], (sq / NS) & 1u)) s_abort = 1;
+            const float4 *T = s_tile + (size_t)stage * JT * DS_REC;
+            const int jbase = w.j0 + kt * JT;
+            const int cnt = min(JT, w.nj - kt * JT);
+            bool own = false;
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) own = own || (iid[p] >= jbase && iid[p] < jbase + cnt);
+            own = __any_sync(0xffffffffu, own);
+            float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
+                tp[p] = 0.f;
+            }
+            auto body = [&](int jj, auto masked_tag) {
+                constexpr bool MASKED = decltype(masked_tag)::value;
+                const float4 a = T[DS_REC * jj];
+                const float4 c = T[DS_REC * jj + 2];
+                float4 b;
+                if (DS) b = T[DS_REC * jj + 1];
+#pragma unroll
+                for (int p = 0; p < IPT; ++p) {
+                    float dx, dy, dz;
+                    if (DS) {
+                        dx = (a.x - xh[p]) + (b.x - xl[p]);
+                        dy = (a.y - yh[p]) + (b.y - yl[p]);
+                        dz = (a.z - zh[p]) + (b.z - zl[p]);
+                    } else {
+                        dx = a.x - xh[p];
+                        dy = a.y - yh[p];
+                        dz = a.z - zh[p];
+                    }
+                    const float dvx = c.x - vx[p], dvy = c.y - vy[p], dvz = c.z - vz[p];
+                    float r2 = fmaf(dx, dx, eps2f);
+                    r2 = fmaf(dy, dy, r2);
+                    r2 = fmaf(dz, dz, r2);
+                    float rv = dx * dvx;
+                    rv = fmaf(dy, dvy, rv);
+                    rv = fmaf(dz, dvz, rv);
+                    float rinv = rsqrtf(r2);
+                    if (MASKED) rinv = (jbase + jj == iid[p]) ? 0.f : rinv;
+                    const float rinv2 = rinv * rinv;
+                    const float mrinv = a.w * rinv;
+                    const float mr3 = mrinv * rinv2;
+                    const float beta = (mr3 * rinv2) * rv;
+                    tp[p] += mrinv;
+                    ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                    ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                    ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                    tja[p][0] = fmaf(mr3, dvx, tja[p][0]);
+                    tja[p][1] = fmaf(mr3, dvy, tja[p][1]);
+                    tja[p][2] = fmaf(mr3, dvz, tja[p][2]);
+                    tjb[p][0] = fmaf(beta, dx, tjb[p][0]);
+                    tjb[p][1] = fmaf(beta, dy, tjb[p][1]);
+                    tjb[p][2] = fmaf(beta, dz, tjb[p][2]);
+                }
+            };
+            if (own) {
+                for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
+            } else if (cnt == JT) {
+#pragma unroll 4
+                for (int jj = 0; jj < JT; ++jj) body(jj, std::false_type{});
+            } else {
+#pragma unroll 2
+                for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
+            }
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float jt = fmaf(-3.f, tjb[p][c], tja[p][c]);
+                    if (DS) {
+                        ds_add(A_h[p][c], A_l[p][c], ta[p][c]);
+                        ds_add(J_h[p][c], J_l[p][c], jt);
+                    } else {
+                        A_h[p][c] += ta[p][c];
+                        J_h[p][c] += jt;
+                    }
+                }
+                if (DS)
+                    ds_add(P_h[p], P_l[p], tp[p]);
+                else
+                    P_h[p] += tp[p];
+            }
+            __syncthreads();
+            if (s_abort) break;
+            if (tid == 0 && kt + NS < ntiles) issue(kt + NS);
+        }
+        if (s_abort) break;
+        seq += (unsigned)ntiles;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int k = p * NT + tid;
+            if (k >= w.ni) continue;
+            double d[7];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                d[c] = ds_to_double(dsf{A_h[p][c], A_l[p][c]});
+                d[3 + c] = ds_to_double(dsf{J_h[p][c], J_l[p][c]});
+            }
+            d[6] = ds_to_double(dsf{P_h[p], P_l[p]});
+            write_final(out, w.i0 + k, d, err);
+        }
+    }
+    if (s_abort && tid == 0) atomicOr(err, DERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
 // Plans and launchers.
 // ---------------------------------------------------------------------------
 
@@ -1375,6 +1556,63 @@ static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is
         return cudaGetLastError();
     }
     return go_tile64<1, 128>(js, is, eps2, p.nsplit, part, cnt, out, err, st);
+}
+
+template <int VAR, int NT>
+static cudaError_t go_batch(const float4 *rec, const BatchItem *items, int nitems,
+                            const float *eps2_sys, Out3 out, unsigned *err, int grid,
+                            cudaStream_t st)
+{
+    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
+    k_force_batch32<VAR, 2, NT, JT32, NS32><<<grid, NT, smem, st>>>(rec, items, nitems, eps2_sys,
+                                                                    out, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_batch(int variant, int threads, const float4 *rec,
+                               const BatchItem *items, int nitems, const float *eps2_sys,
+                               Out3 out, unsigned *err, int grid, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (variant == NB_F32DS) {
+        switch (threads) {
+        case 64: return go_batch<NB_F32DS, 64>(rec, items, nitems, eps2_sys, out, err, grid, st);
+        case 128: return go_batch<NB_F32DS, 128>(rec, items, nitems, eps2_sys, out, err, grid, st);
+        default: return go_batch<NB_F32DS, 256>(rec, items, nitems, eps2_sys, out, err, grid, st);
+        }
+    }
+    switch (threads) {
+    case 64: return go_batch<NB_F32, 64>(rec, items, nitems, eps2_sys, out, err, grid, st);
+    case 128: return go_batch<NB_F32, 128>(rec, items, nitems, eps2_sys, out, err, grid, st);
+    default: return go_batch<NB_F32, 256>(rec, items, nitems, eps2_sys, out, err, grid, st);
+    }
+}
+
+int batch_blocks_per_sm(int variant, int threads)
+{
+    int nb = 0;
+    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
+    cudaError_t e;
+    if (variant == NB_F32DS) {
+        e = threads == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &nb, k_force_batch32<NB_F32DS, 2, 64, JT32, NS32>, 64, smem)
+            : threads == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &nb, k_force_batch32<NB_F32DS, 2, 128, JT32, NS32>, 128, smem)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &nb, k_force_batch32<NB_F32DS, 2, 256, JT32, NS32>, 256, smem);
+    } else {
+        e = threads == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                &nb, k_force_batch32<NB_F32, 2, 64, JT32, NS32>, 64, smem)
+            : threads == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &nb, k_force_batch32<NB_F32, 2, 128, JT32, NS32>, 128, smem)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                   &nb, k_force_batch32<NB_F32, 2, 256, JT32, NS32>, 256, smem);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 size_t plan_counters(const ForcePlan &p, int n_i)

@@ -90,6 +90,26 @@ cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, con
                          double eps2, double *part, unsigned *counters, Out3 out, unsigned *err,
                          cudaStream_t st, cudaEvent_t *ev);
 
+// ---- batched systems -------------------------------------------------------
+
+// One work item of a batched evaluation: particles [i0, i0 + ni) of system
+// sys against all particles [j0, j0 + nj) of the same system (global indices).
+struct BatchItem {
+    int sys, i0, ni, j0, nj;
+};
+
+// CTA sizes the batched kernel is built for (the autotuner picks one).
+constexpr int BATCH_THREADS[3] = {64, 128, 256};
+
+// Batched force (FP32 / double-single): every item's outputs go to out at the
+// global particle index. grid = number of persistent CTAs.
+cudaError_t launch_force_batch(int variant, int threads, const float4 *rec,
+                               const BatchItem *items, int nitems, const float *eps2_sys,
+                               Out3 out, unsigned *err, int grid, cudaStream_t st);
+
+// Resident CTAs per SM of the batched kernel with `threads` threads.
+int batch_blocks_per_sm(int variant, int threads);
+
 // ---- per-particle kernels (K1, K4, K5) -------------------------------------
 
 struct StateDev {
@@ -137,14 +157,26 @@ constexpr int SCHED_TILE = SCHED_THREADS * SCHED_PER_THREAD;
 // K1: predict all particles of s to time t (FP64), writing pos_p, vel_p and,
 // when want_rec, the DS records.
 cudaError_t launch_predict(const StateDev &s, double t, bool want_rec, unsigned *err,
-                           cudaStream_t st);
+                           cudaStream_t st, const double *t_dev = nullptr);
 
 // K4: Hermite corrector + new step for the n_a particles act[k] to time t_new,
 // with the new acc/jerk in f (slot-indexed). dtmin_hits counts clamps. Keeps
 // the level histogram of sd up to date and sets sd->t_cur = t_new.
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new,
                            const Out3 &f, const StepParams &p, SchedDev *sd, unsigned *err,
-                           unsigned long long *dtmin_hits, cudaStream_t st);
+                           unsigned long long *dtmin_hits, cudaStream_t st,
+                           const double *t_dev = nullptr);
+
+// With t_dev != nullptr the two kernels above take their time as *t_dev + t
+// (resp. *t_dev + t_new) from device memory, so a captured graph can be
+// replayed step after step; launch_advance then sets *t_dev += dt.
+cudaError_t launch_advance(double *t_dev, double dt, cudaStream_t st);
+
+// Per-system energies of a batch: kin[s] = sum m v^2/2, pot[s] = sum m pot/2
+// over particles [off[s], off[s] + size[s]) (one CTA per system, fixed order).
+cudaError_t launch_batch_energy(int n_sys, const int *off, const int *size, const double *m,
+                                const double *vel, long long ld, const double *pot,
+                                double *kin_out, double *pot_out, cudaStream_t st);
 
 // K4 at start-up: initial steps from acc/jerk (slot k = particle k), or the
 // shared step; adds every particle to the level histogram (zeroed by the caller).

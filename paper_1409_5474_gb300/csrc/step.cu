@@ -63,10 +63,11 @@ __device__ __forceinline__ float f32_trunc(double x)
 // ---- K1 --------------------------------------------------------------------
 
 template <bool REC>
-__global__ void k_predict(StateDev s, double t, unsigned *err)
+__global__ void k_predict(StateDev s, double t, unsigned *err, const double *t_dev)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
+    if (t_dev) t = *t_dev + t;
     const double d = t - s.t[i];
     const double d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
     if (d < 0.0) atomicOr(err, DERR_BACKWARD);
@@ -94,15 +95,23 @@ __global__ void k_predict(StateDev s, double t, unsigned *err)
 }
 
 cudaError_t launch_predict(const StateDev &s, double t, bool want_rec, unsigned *err,
-                           cudaStream_t st)
+                           cudaStream_t st, const double *t_dev)
 {
     if (s.n <= 0) return cudaSuccess;
     const int bs = 256;
     const int g = (s.n + bs - 1) / bs;
     if (want_rec)
-        k_predict<true><<<g, bs, 0, st>>>(s, t, err);
+        k_predict<true><<<g, bs, 0, st>>>(s, t, err, t_dev);
     else
-        k_predict<false><<<g, bs, 0, st>>>(s, t, err);
+        k_predict<false><<<g, bs, 0, st>>>(s, t, err, t_dev);
+    return cudaGetLastError();
+}
+
+__global__ void k_advance(double *t_dev, double dt) { *t_dev = *t_dev + dt; }
+
+cudaError_t launch_advance(double *t_dev, double dt, cudaStream_t st)
+{
+    k_advance<<<1, 1, 0, st>>>(t_dev, dt);
     return cudaGetLastError();
 }
 
@@ -218,10 +227,13 @@ __device__ double quantize_log2(int e, double dt_old, double t_new, double dt_mi
 
 __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
                           StepParams prm, SchedDev *sd, unsigned *err,
-                          unsigned long long *dtmin_hits)
+                          unsigned long long *dtmin_hits, const double *t_dev)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) sd->t_cur = t_new;
+    if (t_dev)
+        t_new = *t_dev + t_new;
+    else if (k == 0)
+        sd->t_cur = t_new;
     if (k >= na) return;
     const int i = act ? act[k] : k;
     const double dt = t_new - s.t[i];
@@ -313,11 +325,54 @@ __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, doubl
 
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new, const Out3 &f,
                            const StepParams &p, SchedDev *sd, unsigned *err,
-                           unsigned long long *dtmin_hits, cudaStream_t st)
+                           unsigned long long *dtmin_hits, cudaStream_t st, const double *t_dev)
 {
     if (n_a <= 0) return cudaSuccess;
     const int bs = 32;  // FP64-heavy: spread small active sets over many SMs
-    k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits);
+    k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits,
+                                                   t_dev);
+    return cudaGetLastError();
+}
+
+constexpr int BENERGY_T = 256;
+
+__global__ void __launch_bounds__(BENERGY_T)
+    k_batch_energy(const int *__restrict__ off, const int *__restrict__ size,
+                   const double *__restrict__ m, const double *__restrict__ vel, long long ld,
+                   const double *__restrict__ pot, double *kin_out, double *pot_out)
+{
+    __shared__ double sk[BENERGY_T], sw[BENERGY_T];
+    const int sys = blockIdx.x, tid = threadIdx.x;
+    const int o = off[sys], n = size[sys];
+    double k = 0.0, w = 0.0;
+    for (int q = tid; q < n; q += BENERGY_T) {
+        const int i = o + q;
+        const double vx = vel[i], vy = vel[ld + i], vz = vel[2 * ld + i];
+        k += 0.5 * m[i] * (vx * vx + vy * vy + vz * vz);
+        w += 0.5 * m[i] * pot[i];
+    }
+    sk[tid] = k;
+    sw[tid] = w;
+    __syncthreads();
+    for (int h = BENERGY_T / 2; h > 0; h >>= 1) {
+        if (tid < h) {
+            sk[tid] += sk[tid + h];
+            sw[tid] += sw[tid + h];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        kin_out[sys] = sk[0];
+        pot_out[sys] = sw[0];
+    }
+}
+
+cudaError_t launch_batch_energy(int n_sys, const int *off, const int *size, const double *m,
+                                const double *vel, long long ld, const double *pot,
+                                double *kin_out, double *pot_out, cudaStream_t st)
+{
+    if (n_sys <= 0) return cudaSuccess;
+    k_batch_energy<<<n_sys, BENERGY_T, 0, st>>>(off, size, m, vel, ld, pot, kin_out, pot_out);
     return cudaGetLastError();
 }
 

@@ -114,6 +114,15 @@ _SIGS = [
     ("nb_set_plan_table", ctypes.c_int, [_H, ctypes.POINTER(nb_plan), ctypes.c_int]),
     ("nb_get_plan_table", ctypes.c_int, [_H, ctypes.POINTER(nb_plan)]),
     ("nb_autotune", ctypes.c_int, [_H, ctypes.c_int]),
+    ("nb_batch_create", ctypes.c_int, [ctypes.POINTER(nb_config), ctypes.c_int, _I, _D,
+                                       ctypes.c_double, ctypes.POINTER(_H)]),
+    ("nb_batch_destroy", ctypes.c_int, [_H]),
+    ("nb_batch_set", ctypes.c_int, [_H, _D, _D, _D, ctypes.c_double]),
+    ("nb_batch_step", ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(nb_stats)]),
+    ("nb_batch_get", ctypes.c_int, [_H, _D, _D, _D]),
+    ("nb_batch_energy", ctypes.c_int, [_H, _D, _D]),
+    ("nb_batch_autotune", ctypes.c_int, [_H, _I]),
+    ("nb_batch_last_error", ctypes.c_char_p, [_H]),
     ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -337,6 +346,116 @@ def nb_get_plan_table(h):
 def nb_autotune(h, reps=3):
     _check(load().nb_autotune(h, int(reps)), "nb_autotune", h)
     return nb_get_plan_table(h)
+
+
+def _bcheck(rc, func, b):
+    if rc != NB_OK:
+        msg = load().nb_batch_last_error(b) if b else b""
+        raise NBodyError(rc, func, (msg or b"").decode() or nb_status_string(rc))
+
+
+def nb_batch_create(cfg, sizes, eps, dt):
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    b = _H()
+    rc = load().nb_batch_create(ctypes.byref(cfg), int(sizes.shape[0]), sizes.ctypes.data_as(_I),
+                                _dp(eps), float(dt), ctypes.byref(b))
+    if rc != NB_OK:
+        raise NBodyError(rc, "nb_batch_create", nb_status_string(rc))
+    return b.value
+
+
+def nb_batch_destroy(b):
+    load().nb_batch_destroy(b)
+
+
+def nb_batch_set(b, m, pos, vel, t0=0.0):
+    """m (Ntot,), pos and vel (3, Ntot), concatenated over the systems."""
+    m = _f64(m, (-1,))
+    n = m.shape[0]
+    _bcheck(load().nb_batch_set(b, _dp(m), _dp(_f64(pos, (3, n))), _dp(_f64(vel, (3, n))),
+                                float(t0)), "nb_batch_set", b)
+
+
+def nb_batch_step(b, n_steps):
+    st = nb_stats()
+    _bcheck(load().nb_batch_step(b, int(n_steps), ctypes.byref(st)), "nb_batch_step", b)
+    return st.as_dict()
+
+
+def nb_batch_get(b, ntot):
+    pos = np.empty((3, ntot))
+    vel = np.empty((3, ntot))
+    t = ctypes.c_double()
+    _bcheck(load().nb_batch_get(b, _dp(pos), _dp(vel), ctypes.byref(t)), "nb_batch_get", b)
+    return pos, vel, t.value
+
+
+def nb_batch_energy(b, n_sys):
+    k = np.empty(n_sys)
+    w = np.empty(n_sys)
+    _bcheck(load().nb_batch_energy(b, _dp(k), _dp(w)), "nb_batch_energy", b)
+    return k, w
+
+
+def nb_batch_autotune(b):
+    t = ctypes.c_int()
+    _bcheck(load().nb_batch_autotune(b, ctypes.byref(t)), "nb_batch_autotune", b)
+    return t.value
+
+
+class Batch:
+    """Many independent systems advanced with shared-step Hermite on the GPU."""
+
+    def __init__(self, systems, eps, dt, **cfg):
+        """systems: list of ic.Particles (or objects with m, pos (n,3), vel (n,3))."""
+        self.sizes = np.array([len(p.m) for p in systems], dtype=np.int32)
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
+        self.ntot = int(self.sizes.sum())
+        self.cfg = nb_config_default(**cfg)
+        self.b = nb_batch_create(self.cfg, self.sizes, eps, dt)
+        try:
+            m = np.concatenate([np.asarray(p.m, dtype=np.float64) for p in systems])
+            pos = np.concatenate([np.asarray(p.pos, dtype=np.float64) for p in systems]).T
+            vel = np.concatenate([np.asarray(p.vel, dtype=np.float64) for p in systems]).T
+            nb_batch_set(self.b, m, pos, vel)
+        except Exception:
+            self.close()
+            raise
+
+    def close(self):
+        if getattr(self, "b", None):
+            nb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n_steps):
+        return nb_batch_step(self.b, n_steps)
+
+    def get(self):
+        return nb_batch_get(self.b, self.ntot)
+
+    def system(self, s, arr):
+        """Columns of system s in a (3, Ntot) array."""
+        o = self.offsets[s]
+        return arr[:, o:o + self.sizes[s]]
+
+    def energy(self):
+        return nb_batch_energy(self.b, len(self.sizes))
+
+    def autotune(self):
+        return nb_batch_autotune(self.b)
 
 
 NB_STATIC_MAX_NI = 1024
