@@ -291,6 +291,104 @@ int nb_batch_autotune(nb_batch b, int *threads);
 /* Message of the last failure on a batch. */
 const char *nb_batch_last_error(nb_batch b);
 
+/* ---- serving loop ----------------------------------------------------------
+ * A device-resident request loop for subsystems of uneven N such as a hybrid
+ * tree/direct code hands off (Sect. V-VI): each request is one force
+ * evaluation of a subsystem on itself, or an integration of a subsystem with
+ * block-step Hermite over t_span. A server thread admits queued requests in
+ * arrival order while the device-memory budget and the in-flight limit
+ * allow, keeps their particle state on the GPU, and runs ticks: every tick
+ * evaluates, in ONE batched force launch, the new force requests and the
+ * current due set of every integrating request, then corrects and schedules
+ * each integrating request; finished requests are retired and their memory
+ * reused. A request's arithmetic does not depend on what else is in flight.
+ * FP32 kinds only (NB_F32DS or NB_F32). */
+typedef struct nb_server_s *nb_server;
+
+#define NB_REQ_FORCE 0
+#define NB_REQ_EVOLVE 1
+
+#define NB_STATUS_QUEUED 0
+#define NB_STATUS_RUNNING 1
+#define NB_STATUS_DONE 2
+#define NB_STATUS_ERROR 3
+#define NB_STATUS_CANCELLED 4
+
+typedef struct nb_server_cfg {
+    int device;            /* CUDA device */
+    int variant;           /* NB_F32DS or NB_F32 */
+    size_t budget_bytes;   /* device memory for request state; 0 = 4 GiB */
+    int max_inflight;      /* requests on the GPU at once; 0 = 64 */
+    int max_queue;         /* queued requests before nb_submit says NB_ERR_BUSY; 0 = 4096 */
+    double eta;            /* step criterion of EVOLVE requests (0 = 0.01) */
+    double dt_max;         /* largest block step of EVOLVE requests (0 = 1/16) */
+    int flags;             /* NB_FLAG_* */
+} nb_server_cfg;
+
+typedef struct nb_request {
+    int kind;              /* NB_REQ_FORCE or NB_REQ_EVOLVE */
+    int n;                 /* particles, >= 1 */
+    const double *m;       /* m[n] */
+    const double *pos;     /* pos[3n] (x, y, z rows) */
+    const double *vel;     /* vel[3n] */
+    double eps;            /* softening, >= 0 */
+    double t_span;         /* EVOLVE: time to integrate (a multiple of dt_max) */
+} nb_request;
+
+typedef struct nb_result {
+    int status;            /* NB_STATUS_* */
+    int error;             /* NB_OK or the failure's NB_ERR_* code */
+    int n;
+    const double *acc;     /* FORCE: acc[3n], jerk[3n], pot[n]; library-owned until */
+    const double *jerk;    /* nb_result_release */
+    const double *pot;
+    const double *pos;     /* EVOLVE: final pos[3n], vel[3n] (library-owned) */
+    const double *vel;
+    double t_submit;       /* seconds on the server's clock */
+    double t_start;        /* admitted to the GPU */
+    double t_done;
+    double interactions;   /* pair interactions spent on the request */
+    long long block_steps; /* EVOLVE: block steps taken */
+} nb_result;
+
+typedef struct nb_server_stats {
+    long long submitted, completed, cancelled, failed;
+    long long ticks;            /* server ticks that launched work */
+    long long force_launches;   /* batched force launches */
+    double interactions;        /* total pair interactions */
+    double busy_s;              /* time ticks spent on the GPU work */
+    int queued, inflight;       /* right now */
+    size_t bytes_in_use;        /* device bytes held for requests */
+} nb_server_stats;
+
+/* Start a server (one thread). Its device work runs on its own stream. */
+int nb_server_create(const nb_server_cfg *cfg, nb_server *out);
+
+/* Stop the thread (in-flight work finishes first), free everything; results
+ * not yet released are freed too. NULL is a no-op. */
+int nb_server_destroy(nb_server s);
+
+/* Queue a request (its arrays are copied before the call returns); *ticket
+ * identifies it. NB_ERR_BUSY when the queue is full, NB_ERR_BUDGET when the
+ * request alone exceeds the budget, NB_ERR_ARG / NB_ERR_NONFINITE for bad
+ * input. Thread-safe. */
+int nb_submit(nb_server s, const nb_request *req, uint64_t *ticket);
+
+/* Status (and, when done, the results) of a request. Thread-safe.
+ * NB_ERR_NOTFOUND for an unknown or released ticket. */
+int nb_poll(nb_server s, uint64_t ticket, nb_result *out);
+
+/* nb_poll that waits up to timeout_s seconds for the request to finish. */
+int nb_wait(nb_server s, uint64_t ticket, double timeout_s, nb_result *out);
+
+/* Cancel a queued or running request (it ends as NB_STATUS_CANCELLED). */
+int nb_cancel(nb_server s, uint64_t ticket);
+
+/* Free a finished request's results and forget its ticket. */
+int nb_result_release(nb_server s, uint64_t ticket);
+
+int nb_server_get_stats(nb_server s, nb_server_stats *out);
+
 /* ---- allocation-free force evaluation -----------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot call cudaMalloc: a host code that gives all of its device memory to

@@ -39,7 +39,7 @@ struct nb_batch_s {
     double *t = nullptr, *dtv = nullptr, *pos_p = nullptr, *vel_p = nullptr;
     double *f_acc = nullptr, *f_jerk = nullptr, *f_pot = nullptr;
     float4 *rec = nullptr;
-    BatchItem *d_items = nullptr;
+    WorkItem *d_items = nullptr;
     int nitems = 0;
     float *d_eps2 = nullptr;
     int *d_off = nullptr, *d_size = nullptr;
@@ -115,19 +115,35 @@ Out3 bout(nb_batch b) { return Out3{b->f_acc, b->f_jerk, b->f_pot, b->ld}; }
 int build_items(nb_batch b)
 {
     const int ib = 2 * b->threads;
-    std::vector<BatchItem> items;
+    std::vector<WorkItem> items;
     for (int s = 0; s < b->n_sys; ++s) {
         const int n = b->sizes[s], o = b->offs[s];
-        for (int i0 = 0; i0 < n; i0 += ib)
-            items.push_back(BatchItem{s, o + i0, std::min(ib, n - i0), o, n});
+        const float4 *base = b->rec + (size_t)DS_REC * o;  // the system's records
+        const float e2 = (float)(b->eps[s] * b->eps[s]);
+        for (int i0 = 0; i0 < n; i0 += ib) {
+            WorkItem w{};
+            w.jrec = base;
+            w.irec = base;
+            w.acc = b->f_acc + o;
+            w.jerk = b->f_jerk + o;
+            w.pot = b->f_pot + o;
+            w.ld = b->ld;
+            w.i0 = i0;
+            w.ni = std::min(ib, n - i0);
+            w.nj = n;
+            w.gathered = 0;
+            w.eps2 = e2;
+            w.err = b->d_err;
+            items.push_back(w);
+        }
     }
-    std::stable_sort(items.begin(), items.end(), [](const BatchItem &x, const BatchItem &y) {
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem &x, const WorkItem &y) {
         return (long long)x.ni * x.nj > (long long)y.ni * y.nj;
     });
     if (b->d_items) cudaFree(b->d_items);
     b->d_items = nullptr;
-    BCK(b, cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
-    BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(),
+    BCK(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+    BCK(b, cudaMemcpy(b->d_items, items.data(), sizeof(WorkItem) * items.size(),
                       cudaMemcpyHostToDevice));
     b->nitems = (int)items.size();
     b->grid = b->num_sms * batch_blocks_per_sm(b->cfg.variant, b->threads);
@@ -144,8 +160,8 @@ void drop_graph(nb_batch b)
 
 int launch_batch_force(nb_batch b)
 {
-    BCK(b, launch_force_batch(b->cfg.variant, b->threads, b->rec, b->d_items, b->nitems,
-                              b->d_eps2, bout(b), b->d_err, b->grid, b->stream));
+    BCK(b, launch_force_items(b->cfg.variant, b->threads, b->d_items, b->nitems, b->grid,
+                              b->stream));
     return NB_OK;
 }
 
@@ -187,8 +203,8 @@ int capture_step(nb_batch b)
     cudaError_t e = launch_predict(s, b->dt, true, b->d_err, b->stream, b->d_time);
     if (e == cudaSuccess && (b->cfg.flags & NB_FLAG_TIMING)) e = cudaEventRecordWithFlags(b->ev[0], b->stream, cudaEventRecordExternal);
     if (e == cudaSuccess)
-        e = launch_force_batch(b->cfg.variant, b->threads, b->rec, b->d_items, b->nitems,
-                               b->d_eps2, bout(b), b->d_err, b->grid, b->stream);
+        e = launch_force_items(b->cfg.variant, b->threads, b->d_items, b->nitems, b->grid,
+                               b->stream);
     if (e == cudaSuccess && (b->cfg.flags & NB_FLAG_TIMING)) e = cudaEventRecordWithFlags(b->ev[1], b->stream, cudaEventRecordExternal);
     if (e == cudaSuccess)
         e = launch_correct(s, nullptr, (int)b->ntot, b->dt, bout(b), p, b->sd, b->d_err, nullptr,

@@ -538,6 +538,39 @@ cudaError_t d2h_rows(double *dst, const double *src, long long ld, int n, int ro
 
 }  // namespace
 
+namespace nb {
+
+void handle_view(nb_handle h, HandleView *v)
+{
+    v->s = state_of(h);
+    v->irec = h->irec;
+    v->act = h->act;
+    v->f_acc = h->f_acc;
+    v->f_jerk = h->f_jerk;
+    v->f_pot = h->f_pot;
+    v->ld = h->ld;
+    v->sd = h->sd;
+    v->sched_status = h->sched_status;
+    v->mail_h = h->mail_h;
+    v->mail_d = h->mail_d;
+    v->n = h->n;
+    v->cap = h->cap;
+}
+
+size_t handle_bytes(nb_handle h) { return h->bytes; }
+
+unsigned long long handle_take_epoch(nb_handle h) { return h->seq_next++; }
+
+void handle_mark_initialised(nb_handle h, double t0)
+{
+    h->initialised = true;
+    h->sched_valid = true;
+    h->predicted = false;
+    h->t_cur = t0;
+}
+
+}  // namespace nb
+
 extern "C" {
 
 void nb_config_default(nb_config *cfg)

@@ -1145,9 +1145,9 @@ __global__ void __launch_bounds__(NT)
 }
 
 // ---------------------------------------------------------------------------
-// Batched force kernel: many independent systems (clusters) in one launch.
-// Every system's particles are contiguous in the concatenated arrays; a work
-// item is one i-block of one system against all j of the same system. The
+// Batched force kernel: many independent systems in one launch (the batched
+// clusters, and the requests of the serving loop). A work item is one i-block
+// of one system against all j of the same system, with its own pointers. The
 // persistent CTAs walk the item list (sorted by decreasing work on the host,
 // so the round-robin assignment is balanced), staging each system's j-tiles
 // through the same bulk-copy ring as the tile kernel; the mbarrier phases run
@@ -1156,14 +1156,12 @@ __global__ void __launch_bounds__(NT)
 
 template <int VAR, int IPT, int NT, int JT, int NS>
 __global__ void __launch_bounds__(NT)
-    k_force_batch32(const float4 *__restrict__ rec, const BatchItem *__restrict__ items,
-                    int nitems, const float *__restrict__ eps2_sys, Out3 out, unsigned *err)
+    k_force_items32(const WorkItem *__restrict__ items, int nitems)
 {
     extern __shared__ __align__(128) float4 s_tile[];  // NS * JT * DS_REC
     __shared__ __align__(8) uint64_t s_full[NS];
     __shared__ int s_abort;
     constexpr bool DS = (VAR == NB_F32DS);
-    constexpr int IB = NT * IPT;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
@@ -1176,8 +1174,10 @@ __global__ void __launch_bounds__(NT)
 
     unsigned seq = 0;  // tiles consumed so far by this CTA (ring position and phase)
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const BatchItem w = items[it];
-        const float eps2f = eps2_sys[w.sys];
+        const WorkItem w = items[it];
+        unsigned *err = w.err;
+        const float eps2f = w.eps2;
+        const float4 *__restrict__ jrec = w.jrec;
         const int ntiles = (w.nj + JT - 1) / JT;
 
         float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
@@ -1186,13 +1186,13 @@ __global__ void __launch_bounds__(NT)
         for (int p = 0; p < IPT; ++p) {
             const int k = min(p * NT + tid, w.ni - 1);  // idle slots copy the last i
             const int r = w.i0 + k;
-            const float4 a = __ldg(rec + (size_t)DS_REC * r);
-            const float4 b = __ldg(rec + (size_t)DS_REC * r + 1);
-            const float4 c = __ldg(rec + (size_t)DS_REC * r + 2);
+            const float4 a = __ldg(w.irec + (size_t)DS_REC * r);
+            const float4 b = __ldg(w.irec + (size_t)DS_REC * r + 1);
+            const float4 c = __ldg(w.irec + (size_t)DS_REC * r + 2);
             xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
             xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
             vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
-            iid[p] = r;
+            iid[p] = w.gathered ? __float_as_int(b.w) : r;
         }
         float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
 #pragma unroll
@@ -1209,7 +1209,7 @@ __global__ void __launch_bounds__(NT)
             const uint32_t bytes = (uint32_t)cnt * DS_REC * 16u;
             mbar_expect_tx(&s_full[stage], bytes);
             bulk_g2s(s_tile + (size_t)stage * JT * DS_REC,
-                     rec + (size_t)(w.j0 + kt * JT) * DS_REC, bytes, &s_full[stage]);
+                     jrec + (size_t)kt * JT * DS_REC, bytes, &s_full[stage]);
         };
         if (tid == 0) {
             for (int kt = 0; kt < NS && kt < ntiles; ++kt) issue(kt);
@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(NT)
             const int stage = (int)(sq % NS);
             if (!mbar_wait(&s_full[stage], (sq / NS) & 1u)) s_abort = 1;
             const float4 *T = s_tile + (size_t)stage * JT * DS_REC;
-            const int jbase = w.j0 + kt * JT;
+            const int jbase = kt * JT;
             const int cnt = min(JT, w.nj - kt * JT);
             bool own = false;
 #pragma unroll
@@ -1306,7 +1306,10 @@ __global__ void __launch_bounds__(NT)
             if (s_abort) break;
             if (tid == 0 && kt + NS < ntiles) issue(kt + NS);
         }
-        if (s_abort) break;
+        if (s_abort) {
+            if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+            break;
+        }
         seq += (unsigned)ntiles;
 #pragma unroll
         for (int p = 0; p < IPT; ++p) {
@@ -1319,10 +1322,9 @@ __global__ void __launch_bounds__(NT)
                 d[3 + c] = ds_to_double(dsf{J_h[p][c], J_l[p][c]});
             }
             d[6] = ds_to_double(dsf{P_h[p], P_l[p]});
-            write_final(out, w.i0 + k, d, err);
+            write_final(Out3{w.acc, w.jerk, w.pot, w.ld}, w.i0 + k, d, err);
         }
     }
-    if (s_abort && tid == 0) atomicOr(err, DERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -1559,32 +1561,28 @@ static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is
 }
 
 template <int VAR, int NT>
-static cudaError_t go_batch(const float4 *rec, const BatchItem *items, int nitems,
-                            const float *eps2_sys, Out3 out, unsigned *err, int grid,
-                            cudaStream_t st)
+static cudaError_t go_items(const WorkItem *items, int nitems, int grid, cudaStream_t st)
 {
     const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
-    k_force_batch32<VAR, 2, NT, JT32, NS32><<<grid, NT, smem, st>>>(rec, items, nitems, eps2_sys,
-                                                                    out, err);
+    k_force_items32<VAR, 2, NT, JT32, NS32><<<grid, NT, smem, st>>>(items, nitems);
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_batch(int variant, int threads, const float4 *rec,
-                               const BatchItem *items, int nitems, const float *eps2_sys,
-                               Out3 out, unsigned *err, int grid, cudaStream_t st)
+cudaError_t launch_force_items(int variant, int threads, const WorkItem *items, int nitems,
+                               int grid, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (variant == NB_F32DS) {
         switch (threads) {
-        case 64: return go_batch<NB_F32DS, 64>(rec, items, nitems, eps2_sys, out, err, grid, st);
-        case 128: return go_batch<NB_F32DS, 128>(rec, items, nitems, eps2_sys, out, err, grid, st);
-        default: return go_batch<NB_F32DS, 256>(rec, items, nitems, eps2_sys, out, err, grid, st);
+        case 64: return go_items<NB_F32DS, 64>(items, nitems, grid, st);
+        case 128: return go_items<NB_F32DS, 128>(items, nitems, grid, st);
+        default: return go_items<NB_F32DS, 256>(items, nitems, grid, st);
         }
     }
     switch (threads) {
-    case 64: return go_batch<NB_F32, 64>(rec, items, nitems, eps2_sys, out, err, grid, st);
-    case 128: return go_batch<NB_F32, 128>(rec, items, nitems, eps2_sys, out, err, grid, st);
-    default: return go_batch<NB_F32, 256>(rec, items, nitems, eps2_sys, out, err, grid, st);
+    case 64: return go_items<NB_F32, 64>(items, nitems, grid, st);
+    case 128: return go_items<NB_F32, 128>(items, nitems, grid, st);
+    default: return go_items<NB_F32, 256>(items, nitems, grid, st);
     }
 }
 
@@ -1595,18 +1593,18 @@ int batch_blocks_per_sm(int variant, int threads)
     cudaError_t e;
     if (variant == NB_F32DS) {
         e = threads == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &nb, k_force_batch32<NB_F32DS, 2, 64, JT32, NS32>, 64, smem)
+                                &nb, k_force_items32<NB_F32DS, 2, 64, JT32, NS32>, 64, smem)
             : threads == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &nb, k_force_batch32<NB_F32DS, 2, 128, JT32, NS32>, 128, smem)
+                                   &nb, k_force_items32<NB_F32DS, 2, 128, JT32, NS32>, 128, smem)
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &nb, k_force_batch32<NB_F32DS, 2, 256, JT32, NS32>, 256, smem);
+                                   &nb, k_force_items32<NB_F32DS, 2, 256, JT32, NS32>, 256, smem);
     } else {
         e = threads == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                &nb, k_force_batch32<NB_F32, 2, 64, JT32, NS32>, 64, smem)
+                                &nb, k_force_items32<NB_F32, 2, 64, JT32, NS32>, 64, smem)
             : threads == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &nb, k_force_batch32<NB_F32, 2, 128, JT32, NS32>, 128, smem)
+                                   &nb, k_force_items32<NB_F32, 2, 128, JT32, NS32>, 128, smem)
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                   &nb, k_force_batch32<NB_F32, 2, 256, JT32, NS32>, 256, smem);
+                                   &nb, k_force_items32<NB_F32, 2, 256, JT32, NS32>, 256, smem);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

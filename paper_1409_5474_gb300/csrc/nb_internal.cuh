@@ -92,20 +92,29 @@ cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, con
 
 // ---- batched systems -------------------------------------------------------
 
-// One work item of a batched evaluation: particles [i0, i0 + ni) of system
-// sys against all particles [j0, j0 + nj) of the same system (global indices).
-struct BatchItem {
-    int sys, i0, ni, j0, nj;
+// One work item of a batched evaluation: i-rows [i0, i0 + ni) of irec against
+// all nj j-records of jrec (one system; the pair i == j is left out), outputs
+// at slots i0.. of acc/jerk/pot (rows of stride ld). irec is either the
+// system's own records (member rows: the particle index is the row) or a
+// gathered copy of its due set (the index rides in each record).
+struct WorkItem {
+    const float4 *jrec;
+    const float4 *irec;
+    double *acc, *jerk, *pot;
+    long long ld;
+    int i0, ni, nj, gathered;
+    float eps2;
+    int pad;
+    unsigned *err;  // error word of the item's system
 };
 
 // CTA sizes the batched kernel is built for (the autotuner picks one).
 constexpr int BATCH_THREADS[3] = {64, 128, 256};
 
-// Batched force (FP32 / double-single): every item's outputs go to out at the
-// global particle index. grid = number of persistent CTAs.
-cudaError_t launch_force_batch(int variant, int threads, const float4 *rec,
-                               const BatchItem *items, int nitems, const float *eps2_sys,
-                               Out3 out, unsigned *err, int grid, cudaStream_t st);
+// Batched force (FP32 / double-single) over a work list; grid = number of
+// persistent CTAs (items are taken round-robin, so sort them by decreasing work).
+cudaError_t launch_force_items(int variant, int threads, const WorkItem *items, int nitems,
+                               int grid, cudaStream_t st);
 
 // Resident CTAs per SM of the batched kernel with `threads` threads.
 int batch_blocks_per_sm(int variant, int threads);
@@ -206,5 +215,27 @@ cudaError_t launch_make_rec(int n, const double *pos, const double *vel, long lo
 // Check every value of n finite doubles (3 rows of stride ld, or 1 row when rows == 1).
 cudaError_t launch_check_finite(const double *p, int n, int rows, long long ld, unsigned *err,
                                 cudaStream_t st);
+
+// ---- engine handles driven by the serving loop ------------------------------
+
+// Device view of an engine handle (nb_handle) for code that launches the
+// kernels itself.
+struct HandleView {
+    StateDev s;
+    float4 *irec;
+    int *act;
+    double *f_acc, *f_jerk, *f_pot;
+    long long ld;
+    SchedDev *sd;
+    unsigned long long *sched_status;
+    Mailbox *mail_h, *mail_d;
+    int n, cap;
+};
+void handle_view(nb_handle h, HandleView *v);
+size_t handle_bytes(nb_handle h);
+// Epoch of the next scheduler launch on h (advances the handle's mirror).
+unsigned long long handle_take_epoch(nb_handle h);
+// The caller has initialised h's steps and scheduler state at time t0.
+void handle_mark_initialised(nb_handle h, double t0);
 
 }  // namespace nb

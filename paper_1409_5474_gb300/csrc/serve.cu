@@ -1,0 +1,776 @@
+// The serving loop (nbody.h, nb_server_* / nb_submit / nb_poll): continuous
+// batching of force and integration requests on subsystems of uneven N.
+//
+// A server thread owns the GPU work; submit/poll/cancel only touch the
+// request table under a mutex. Each tick the thread
+//   1. retires cancelled requests and admits queued ones (arrival order)
+//      while the in-flight limit and the device-memory budget allow; an
+//      admitted request gets an engine handle from a pool (by capacity
+//      class) and its particles are copied in once - they stay on the GPU;
+//   2. collects work items for ONE batched force launch: new FORCE requests
+//      (every particle against every particle), new EVOLVE requests (their
+//      initial evaluation) and the current due set of every stepping EVOLVE
+//      request (the records its scheduler gathered);
+//   3. launches the batched force, then per request: copy-out of FORCE
+//      results, initial steps, or corrector + next scheduler launch;
+//   4. synchronises once, checks every request's error word and mailbox,
+//      and retires finished requests, returning their handles to the pool.
+// A request's work items and kernels depend only on the request itself, so
+// its results are the same whatever else is in flight.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nb;
+
+namespace {
+
+enum Phase { PH_QUEUED = 0, PH_FORCE, PH_INIT, PH_STEP, PH_FINISHED };
+
+struct Req {
+    uint64_t id = 0;
+    int kind = NB_REQ_FORCE;
+    int n = 0;
+    double eps = 0.0, t_span = 0.0;
+    std::vector<double> m, pos, vel;  // the request's particles (host copy)
+    int status = NB_STATUS_QUEUED;
+    int error = NB_OK;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    double interactions = 0.0;
+    long long block_steps = 0;
+    bool cancel = false;
+    // device side (server thread only)
+    nb_handle h = nullptr;
+    int cap = 0;
+    size_t bytes = 0;
+    int slot = -1;  // error word index
+    int phase = PH_QUEUED;
+    double t_end = 0.0;
+    double t_next = 0.0;
+    int n_active = 0;
+    unsigned long long epoch = 0;
+    bool final_copy = false;  // EVOLVE: t_end reached, results being copied out
+    int pending = NB_OK;      // failure found on the host during the tick
+    // results
+    std::vector<double> acc, jerk, pot, out_pos, out_vel;
+};
+
+using ReqP = std::shared_ptr<Req>;
+
+int capacity_class(int n)
+{
+    int c = 256;
+    while (c < n) c <<= 1;
+    return c;
+}
+
+}  // namespace
+
+struct nb_server_s {
+    nb_server_cfg cfg{};
+    int dev = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    std::chrono::steady_clock::time_point t0;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::map<uint64_t, ReqP> table;
+    std::deque<ReqP> queue;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread thread;
+
+    // server-thread state
+    std::vector<ReqP> inflight;
+    std::map<int, std::vector<nb_handle>> pool;  // idle handles by capacity class
+    size_t bytes_in_use = 0;                      // in-flight + pooled handles
+    std::vector<int> free_slots;
+    unsigned *d_errs = nullptr;                   // one error word per slot
+    unsigned *h_errs = nullptr;                   // their pinned host copy
+    unsigned long long *d_dtmin = nullptr;        // corrector dt_min clamps
+    WorkItem *d_items = nullptr, *h_items = nullptr;
+    size_t items_cap = 0;
+    int threads = 128, grid = 0;
+    nb_server_stats st{};
+    int fatal = NB_OK;
+
+    double now() const
+    {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+size_t estimate_bytes(int cap)
+{
+    // the engine slab for cap particles plus its small buffers (see engine.cu)
+    const size_t ld = ((size_t)cap + 63) / 64 * 64;
+    const size_t vec = ((3 * ld + 64) * 8 + 255) & ~size_t(255);
+    const size_t sca = ((ld + 64) * 8 + 255) & ~size_t(255);
+    const size_t recb = (ld * 48 + 255) & ~size_t(255);
+    const size_t actb = (ld * 4 + 255) & ~size_t(255);
+    return 8 * vec + 4 * sca + 2 * recb + actb + 65536;
+}
+
+// A handle of capacity class cap: from the pool, else created (freeing pooled
+// handles of other classes when the budget needs it). Server thread only.
+nb_handle acquire_handle(nb_server s, int cap, size_t *bytes)
+{
+    auto &v = s->pool[cap];
+    if (!v.empty()) {
+        nb_handle h = v.back();
+        v.pop_back();
+        *bytes = handle_bytes(h);
+        return h;
+    }
+    const size_t need = estimate_bytes(cap);
+    for (auto &kv : s->pool) {
+        while (s->bytes_in_use + need > s->cfg.budget_bytes && !kv.second.empty()) {
+            nb_handle old = kv.second.back();
+            kv.second.pop_back();
+            s->bytes_in_use -= handle_bytes(old);
+            nb_destroy(old);
+        }
+    }
+    nb_config c;
+    nb_config_default(&c);
+    c.n_max = cap;
+    c.variant = s->cfg.variant;
+    c.eta = s->cfg.eta;
+    c.dt_max = s->cfg.dt_max;
+    c.device = s->dev;
+    nb_handle h = nullptr;
+    if (nb_create(&c, &h) != NB_OK) return nullptr;
+    nb_set_stream(h, s->stream);
+    *bytes = handle_bytes(h);
+    s->bytes_in_use += *bytes;
+    return h;
+}
+
+StepParams server_params(nb_server s)
+{
+    StepParams p;
+    p.eta = s->cfg.eta;
+    p.eta_s = s->cfg.eta;
+    p.dt_min = std::ldexp(1.0, -30);
+    p.dt_max = s->cfg.dt_max;
+    p.shared_dt = 0.0;
+    return p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Server thread
+// ---------------------------------------------------------------------------
+
+namespace {
+
+#define CKS(call)                                              \
+    do {                                                       \
+        if ((call) != cudaSuccess) return NB_ERR_CUDA;         \
+    } while (0)
+
+int err_code(unsigned bits)
+{
+    if (bits & DERR_TIMEOUT) return NB_ERR_TIMEOUT;
+    if (bits & DERR_NONFINITE) return NB_ERR_NONFINITE;
+    return NB_ERR_STATE;
+}
+
+// Terminal status of r (lock held): counters, timestamps; frees nothing.
+void finish_locked(nb_server s, Req &r, int status, int error)
+{
+    r.status = status;
+    r.error = error;
+    r.t_done = s->now();
+    r.phase = PH_FINISHED;
+    if (status == NB_STATUS_DONE)
+        s->st.completed++;
+    else if (status == NB_STATUS_CANCELLED)
+        s->st.cancelled++;
+    else
+        s->st.failed++;
+    // the particles are not needed any more
+    std::vector<double>().swap(r.m);
+    if (r.kind == NB_REQ_FORCE) {
+        std::vector<double>().swap(r.pos);
+        std::vector<double>().swap(r.vel);
+    }
+}
+
+// Give r's handle back to the pool (reuse) or free it (after a failure, when
+// its scheduler state may not match the host's epoch mirror).
+void drop_handle(nb_server s, Req &r, bool reuse)
+{
+    if (r.h) {
+        if (reuse) {
+            s->pool[r.cap].push_back(r.h);
+        } else {
+            s->bytes_in_use -= handle_bytes(r.h);
+            nb_destroy(r.h);
+        }
+    }
+    r.h = nullptr;
+    if (r.slot >= 0) s->free_slots.push_back(r.slot);
+    r.slot = -1;
+}
+
+size_t inflight_bytes(nb_server s)
+{
+    size_t b = 0;
+    for (auto &r : s->inflight) b += r->bytes;
+    return b;
+}
+
+bool fits(nb_server s, const Req &r, size_t in_use)
+{
+    auto it = s->pool.find(r.cap);
+    if (it != s->pool.end() && !it->second.empty()) return true;
+    return in_use + estimate_bytes(r.cap) <= s->cfg.budget_bytes;
+}
+
+// Work items of an all-vs-all evaluation of r's records (member rows).
+void member_items(nb_server s, Req &r, const HandleView &v, std::vector<WorkItem> &items)
+{
+    const int ib = s->threads * 2;
+    for (int i0 = 0; i0 < r.n; i0 += ib) {
+        WorkItem w{};
+        w.jrec = v.s.rec;
+        w.irec = v.s.rec;
+        w.acc = v.f_acc;
+        w.jerk = v.f_jerk;
+        w.pot = v.f_pot;
+        w.ld = v.ld;
+        w.i0 = i0;
+        w.ni = std::min(ib, r.n - i0);
+        w.nj = r.n;
+        w.gathered = 0;
+        w.eps2 = (float)(r.eps * r.eps);
+        w.err = s->d_errs + r.slot;
+        items.push_back(w);
+    }
+    r.interactions += (double)r.n * (double)r.n;
+}
+
+// Work items of r's due set: the na records the scheduler gathered into irec.
+void due_items(nb_server s, Req &r, const HandleView &v, int na, std::vector<WorkItem> &items)
+{
+    const int ib = s->threads * 2;
+    for (int i0 = 0; i0 < na; i0 += ib) {
+        WorkItem w{};
+        w.jrec = v.s.rec;
+        w.irec = v.irec;
+        w.acc = v.f_acc;
+        w.jerk = v.f_jerk;
+        w.pot = v.f_pot;
+        w.ld = v.ld;
+        w.i0 = i0;
+        w.ni = std::min(ib, na - i0);
+        w.nj = r.n;
+        w.gathered = 1;
+        w.eps2 = (float)(r.eps * r.eps);
+        w.err = s->d_errs + r.slot;
+        items.push_back(w);
+    }
+    r.interactions += (double)na * (double)r.n;
+}
+
+HandleView view_of(const Req &r)
+{
+    HandleView v;
+    handle_view(r.h, &v);
+    v.s.n = r.n;
+    return v;
+}
+
+// Copy r's particles into its handle (time 0) and predict, which builds the
+// j-records. Queued on the server stream.
+int upload(nb_server s, Req &r)
+{
+    const HandleView v = view_of(r);
+    cudaStream_t st = s->stream;
+    const size_t row = (size_t)r.n * sizeof(double), pitch = (size_t)v.ld * sizeof(double);
+    unsigned *err = s->d_errs + r.slot;
+    CKS(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+    CKS(cudaMemcpyAsync(v.s.m, r.m.data(), row, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpy2DAsync(v.s.pos, pitch, r.pos.data(), row, row, 3, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpy2DAsync(v.s.vel, pitch, r.vel.data(), row, row, 3, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemsetAsync(v.s.t, 0, row, st));
+    CKS(cudaMemsetAsync(v.s.dt, 0, row, st));
+    CKS(launch_predict(v.s, 0.0, true, err, st));
+    return NB_OK;
+}
+
+int grow_items(nb_server s, size_t n)
+{
+    if (n <= s->items_cap) return NB_OK;
+    size_t cap = std::max<size_t>(n, 2 * s->items_cap);
+    if (s->d_items) cudaFree(s->d_items);
+    if (s->h_items) cudaFreeHost(s->h_items);
+    s->d_items = nullptr;
+    s->h_items = nullptr;
+    s->items_cap = 0;
+    CKS(cudaMalloc(&s->d_items, cap * sizeof(WorkItem)));
+    CKS(cudaMallocHost(&s->h_items, cap * sizeof(WorkItem)));
+    s->items_cap = cap;
+    return NB_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// One tick (server thread): cancellations, admission, one batched force
+// launch, the per-request kernels and copies, one synchronisation, and the
+// bookkeeping of what finished. A CUDA failure returns NB_ERR_CUDA.
+int tick(nb_server s)
+{
+    const cudaStream_t st = s->stream;
+    std::vector<ReqP> admitted;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        // running requests that were cancelled (none of their work is on the GPU)
+        for (auto &r : s->inflight)
+            if (r->cancel && r->phase != PH_FINISHED) {
+                finish_locked(s, *r, NB_STATUS_CANCELLED, NB_OK);
+                drop_handle(s, *r, true);
+            }
+        s->inflight.erase(std::remove_if(s->inflight.begin(), s->inflight.end(),
+                                         [](const ReqP &r) { return r->phase == PH_FINISHED; }),
+                          s->inflight.end());
+        // admission in arrival order, while the in-flight limit and the budget allow
+        size_t in_use = inflight_bytes(s);
+        while (!s->queue.empty() && (int)s->inflight.size() < s->cfg.max_inflight) {
+            ReqP r = s->queue.front();
+            if (!s->inflight.empty() && !fits(s, *r, in_use)) break;
+            s->queue.pop_front();
+            r->status = NB_STATUS_RUNNING;
+            r->t_start = s->now();
+            admitted.push_back(r);
+            s->inflight.push_back(r);
+            in_use += estimate_bytes(r->cap);
+        }
+        s->st.queued = (int)s->queue.size();
+        s->st.inflight = (int)s->inflight.size();
+    }
+    if (s->inflight.empty()) return NB_OK;
+    const double t_begin = s->now();
+
+    // handles and uploads of the admitted requests
+    for (auto &r : admitted) {
+        r->h = acquire_handle(s, r->cap, &r->bytes);
+        if (!r->h) {
+            r->pending = NB_ERR_OOM;
+            continue;
+        }
+        r->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        int rc = upload(s, *r);
+        if (rc) return rc;
+    }
+
+    // work items of this tick's force launch
+    std::vector<WorkItem> items;
+    for (auto &r : s->inflight) {
+        if (r->pending) continue;
+        const HandleView v = view_of(*r);
+        if (r->phase == PH_QUEUED) {
+            member_items(s, *r, v, items);
+            r->phase = r->kind == NB_REQ_FORCE ? PH_FORCE : PH_INIT;
+        } else if (r->phase == PH_STEP) {
+            // the last scheduler launch finished before the previous tick ended
+            if (v.mail_h->seq != r->epoch) {
+                r->pending = NB_ERR_STATE;
+                continue;
+            }
+            const double t_next = v.mail_h->t_next;
+            const int na = v.mail_h->n_active;
+            if (!(t_next <= r->t_end)) {
+                r->final_copy = true;
+            } else if (na < 1 || na > r->n) {
+                r->pending = NB_ERR_STATE;
+            } else {
+                r->t_next = t_next;
+                r->n_active = na;
+                due_items(s, *r, v, na, items);
+            }
+        }
+    }
+    if (!items.empty()) {
+        // longest items first: the persistent CTAs take them round-robin
+        std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
+            return (long long)a.ni * a.nj > (long long)b.ni * b.nj;
+        });
+        int rc = grow_items(s, items.size());
+        if (rc) return rc;
+        std::memcpy(s->h_items, items.data(), items.size() * sizeof(WorkItem));
+        CKS(cudaMemcpyAsync(s->d_items, s->h_items, items.size() * sizeof(WorkItem),
+                            cudaMemcpyHostToDevice, st));
+        const int grid = std::min<int>((int)items.size(), s->grid);
+        CKS(launch_force_items(s->cfg.variant, s->threads, s->d_items, (int)items.size(), grid,
+                               st));
+    }
+
+    // per-request kernels and copies after the force
+    const StepParams prm = server_params(s);
+    for (auto &r : s->inflight) {
+        if (r->pending) continue;
+        const HandleView v = view_of(*r);
+        unsigned *err = s->d_errs + r->slot;
+        const Out3 f{v.f_acc, v.f_jerk, v.f_pot, v.ld};
+        const size_t row = (size_t)r->n * sizeof(double), pitch = (size_t)v.ld * sizeof(double);
+        if (r->phase == PH_FORCE) {
+            r->acc.resize(3 * (size_t)r->n);
+            r->jerk.resize(3 * (size_t)r->n);
+            r->pot.resize(r->n);
+            CKS(cudaMemcpy2DAsync(r->acc.data(), row, v.f_acc, pitch, row, 3,
+                                  cudaMemcpyDeviceToHost, st));
+            CKS(cudaMemcpy2DAsync(r->jerk.data(), row, v.f_jerk, pitch, row, 3,
+                                  cudaMemcpyDeviceToHost, st));
+            CKS(cudaMemcpyAsync(r->pot.data(), v.f_pot, row, cudaMemcpyDeviceToHost, st));
+        } else if (r->phase == PH_INIT) {
+            CKS(cudaMemsetAsync(v.sd->hist, 0, NLEVEL * sizeof(int), st));
+            CKS(launch_init_steps(v.s, f, prm, v.sd, err, st));
+            r->epoch = handle_take_epoch(r->h);
+            CKS(launch_sched_predict(v.s, v.sd, v.sched_status, v.act, v.irec, v.mail_d,
+                                     prm.dt_max, true, err, st));
+        } else if (r->phase == PH_STEP && r->final_copy) {
+            r->out_pos.resize(3 * (size_t)r->n);
+            r->out_vel.resize(3 * (size_t)r->n);
+            CKS(cudaMemcpy2DAsync(r->out_pos.data(), row, v.s.pos, pitch, row, 3,
+                                  cudaMemcpyDeviceToHost, st));
+            CKS(cudaMemcpy2DAsync(r->out_vel.data(), row, v.s.vel, pitch, row, 3,
+                                  cudaMemcpyDeviceToHost, st));
+        } else if (r->phase == PH_STEP) {
+            CKS(launch_correct(v.s, v.act, r->n_active, r->t_next, f, prm, v.sd, err,
+                               s->d_dtmin, st));
+            r->block_steps++;
+            r->epoch = handle_take_epoch(r->h);
+            CKS(launch_sched_predict(v.s, v.sd, v.sched_status, v.act, v.irec, v.mail_d,
+                                     prm.dt_max, true, err, st));
+        }
+    }
+    CKS(cudaMemcpyAsync(s->h_errs, s->d_errs, s->cfg.max_inflight * sizeof(unsigned),
+                        cudaMemcpyDeviceToHost, st));
+    CKS(cudaStreamSynchronize(st));
+
+    // bookkeeping
+    double inter = 0.0;
+    for (auto &it : items) inter += (double)it.ni * (double)it.nj;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto &r : s->inflight) {
+            const unsigned bits = r->slot >= 0 ? s->h_errs[r->slot] : 0u;
+            if (r->pending || bits) {
+                finish_locked(s, *r, NB_STATUS_ERROR, r->pending ? r->pending : err_code(bits));
+                drop_handle(s, *r, false);
+            } else if (r->phase == PH_FORCE || r->final_copy) {
+                finish_locked(s, *r, NB_STATUS_DONE, NB_OK);
+                drop_handle(s, *r, true);
+            } else if (r->phase == PH_INIT) {
+                r->phase = PH_STEP;
+            }
+        }
+        s->inflight.erase(std::remove_if(s->inflight.begin(), s->inflight.end(),
+                                         [](const ReqP &r) { return r->phase == PH_FINISHED; }),
+                          s->inflight.end());
+        s->st.ticks++;
+        if (!items.empty()) s->st.force_launches++;
+        s->st.interactions += inter;
+        s->st.busy_s += s->now() - t_begin;
+        s->st.inflight = (int)s->inflight.size();
+        s->st.bytes_in_use = s->bytes_in_use;
+    }
+    s->cv_done.notify_all();
+    return NB_OK;
+}
+
+void fail_all(nb_server s, int error)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fatal = error;
+    for (auto &r : s->inflight) {
+        if (r->phase != PH_FINISHED) finish_locked(s, *r, NB_STATUS_ERROR, error);
+        if (r->h) s->pool[r->cap].push_back(r->h);  // freed at nb_server_destroy
+        r->h = nullptr;
+    }
+    s->inflight.clear();
+    while (!s->queue.empty()) {
+        finish_locked(s, *s->queue.front(), NB_STATUS_ERROR, error);
+        s->queue.pop_front();
+    }
+    s->st.queued = 0;
+    s->st.inflight = 0;
+    s->cv_done.notify_all();
+}
+
+void run(nb_server s)
+{
+    cudaSetDevice(s->dev);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(
+                lk, [&] { return s->stop || !s->queue.empty() || !s->inflight.empty(); });
+            if (s->stop) {
+                // queued requests are cancelled; in-flight ones run to their end
+                while (!s->queue.empty()) {
+                    finish_locked(s, *s->queue.front(), NB_STATUS_CANCELLED, NB_OK);
+                    s->queue.pop_front();
+                }
+                s->st.queued = 0;
+                s->cv_done.notify_all();
+                if (s->inflight.empty()) break;
+            }
+        }
+        if (tick(s) != NB_OK) {
+            cudaGetLastError();
+            fail_all(s, NB_ERR_CUDA);
+            break;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
+{
+    if (!out) return NB_ERR_ARG;
+    *out = nullptr;
+    nb_server_cfg c{};
+    if (cfg) c = *cfg;
+    if (c.budget_bytes == 0) c.budget_bytes = size_t(4) << 30;
+    if (c.max_inflight <= 0) c.max_inflight = 64;
+    if (c.max_queue <= 0) c.max_queue = 4096;
+    if (c.eta == 0.0) c.eta = 0.01;
+    if (c.dt_max == 0.0) c.dt_max = 1.0 / 16;
+    if (c.variant != NB_F32DS && c.variant != NB_F32) return NB_ERR_ARG;
+    if (!(c.eta > 0.0) || !std::isfinite(c.eta)) return NB_ERR_ARG;
+    if (!(c.dt_max > 0.0) || std::ilogb(c.dt_max) < -30 || c.dt_max != std::ldexp(1.0, std::ilogb(c.dt_max)))
+        return NB_ERR_ARG;  // a power of two
+    if (c.max_inflight > 4096) return NB_ERR_ARG;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return NB_ERR_CUDA;
+    }
+    auto s = std::make_unique<nb_server_s>();
+    s->cfg = c;
+    s->dev = c.device;
+    s->t0 = std::chrono::steady_clock::now();
+    if (cudaSetDevice(s->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&s->d_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&s->h_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&s->d_dtmin, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(s->d_errs, 0, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(s->d_dtmin, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->d_errs) cudaFree(s->d_errs);
+        if (s->h_errs) cudaFreeHost(s->h_errs);
+        if (s->d_dtmin) cudaFree(s->d_dtmin);
+        return NB_ERR_CUDA;
+    }
+    s->threads = 128;
+    s->grid = s->num_sms * batch_blocks_per_sm(c.variant, s->threads);
+    for (int k = c.max_inflight - 1; k >= 0; --k) s->free_slots.push_back(k);
+    nb_server raw = s.release();
+    raw->thread = std::thread(run, raw);
+    *out = raw;
+    return NB_OK;
+}
+
+int nb_server_destroy(nb_server s)
+{
+    if (!s) return NB_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->thread.joinable()) s->thread.join();
+    cudaSetDevice(s->dev);
+    cudaStreamSynchronize(s->stream);
+    for (auto &kv : s->pool)
+        for (nb_handle h : kv.second) nb_destroy(h);
+    s->pool.clear();
+    if (s->d_items) cudaFree(s->d_items);
+    if (s->h_items) cudaFreeHost(s->h_items);
+    cudaFree(s->d_errs);
+    cudaFreeHost(s->h_errs);
+    cudaFree(s->d_dtmin);
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return NB_OK;
+}
+
+int nb_submit(nb_server s, const nb_request *req, uint64_t *ticket)
+{
+    if (!s || !req || !ticket) return NB_ERR_ARG;
+    if (req->kind != NB_REQ_FORCE && req->kind != NB_REQ_EVOLVE) return NB_ERR_ARG;
+    const int n = req->n;
+    if (n < 1 || n > (1 << 26)) return NB_ERR_ARG;
+    if (!req->m || !req->pos || !req->vel) return NB_ERR_ARG;
+    if (!(req->eps >= 0.0) || !std::isfinite(req->eps)) return NB_ERR_ARG;
+    if (req->kind == NB_REQ_EVOLVE) {
+        const double q = req->t_span / s->cfg.dt_max;
+        if (!(req->t_span > 0.0) || !std::isfinite(q) || q != std::floor(q) || q > 1e12)
+            return NB_ERR_ARG;  // a positive multiple of dt_max
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(req->m[i]) || req->m[i] < 0.0) return NB_ERR_NONFINITE;
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(req->pos[(size_t)c * n + i]) ||
+                !std::isfinite(req->vel[(size_t)c * n + i]))
+                return NB_ERR_NONFINITE;
+    }
+    auto r = std::make_shared<Req>();
+    r->kind = req->kind;
+    r->n = n;
+    r->eps = req->eps;
+    r->t_span = req->t_span;
+    r->t_end = req->t_span;
+    r->cap = capacity_class(n);
+    if (estimate_bytes(r->cap) > s->cfg.budget_bytes) return NB_ERR_BUDGET;
+    r->m.assign(req->m, req->m + n);
+    r->pos.assign(req->pos, req->pos + 3 * (size_t)n);
+    r->vel.assign(req->vel, req->vel + 3 * (size_t)n);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal) return s->fatal;
+        if (s->stop) return NB_ERR_STATE;
+        if ((int)s->queue.size() >= s->cfg.max_queue) return NB_ERR_BUSY;
+        r->id = s->next_id++;
+        r->t_submit = s->now();
+        s->table[r->id] = r;
+        s->queue.push_back(r);
+        s->st.submitted++;
+        s->st.queued = (int)s->queue.size();
+        *ticket = r->id;
+    }
+    s->cv_work.notify_one();
+    return NB_OK;
+}
+
+namespace {
+
+void fill_result(const Req &r, nb_result *out)
+{
+    std::memset(out, 0, sizeof *out);
+    out->status = r.status;
+    out->error = r.error;
+    out->n = r.n;
+    out->t_submit = r.t_submit;
+    out->t_start = r.t_start;
+    out->t_done = r.t_done;
+    out->interactions = r.interactions;
+    out->block_steps = r.block_steps;
+    if (r.status == NB_STATUS_DONE) {
+        if (r.kind == NB_REQ_FORCE) {
+            out->acc = r.acc.data();
+            out->jerk = r.jerk.data();
+            out->pot = r.pot.data();
+        } else {
+            out->pos = r.out_pos.data();
+            out->vel = r.out_vel.data();
+        }
+    }
+}
+
+bool terminal(int status)
+{
+    return status == NB_STATUS_DONE || status == NB_STATUS_ERROR ||
+           status == NB_STATUS_CANCELLED;
+}
+
+}  // namespace
+
+int nb_poll(nb_server s, uint64_t ticket, nb_result *out)
+{
+    if (!s || !out) return NB_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return NB_ERR_NOTFOUND;
+    fill_result(*it->second, out);
+    return NB_OK;
+}
+
+int nb_wait(nb_server s, uint64_t ticket, double timeout_s, nb_result *out)
+{
+    if (!s || !out) return NB_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return NB_ERR_NOTFOUND;
+    ReqP r = it->second;
+    const auto limit = std::chrono::duration<double>(std::max(0.0, timeout_s));
+    const bool done = s->cv_done.wait_for(lk, limit, [&] { return terminal(r->status); });
+    fill_result(*r, out);
+    return done ? NB_OK : NB_ERR_TIMEOUT;
+}
+
+int nb_cancel(nb_server s, uint64_t ticket)
+{
+    if (!s) return NB_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->table.find(ticket);
+        if (it == s->table.end()) return NB_ERR_NOTFOUND;
+        Req &r = *it->second;
+        if (terminal(r.status)) return NB_ERR_STATE;
+        if (r.status == NB_STATUS_QUEUED) {
+            auto q = std::find(s->queue.begin(), s->queue.end(), it->second);
+            if (q != s->queue.end()) s->queue.erase(q);
+            finish_locked(s, r, NB_STATUS_CANCELLED, NB_OK);
+            s->st.queued = (int)s->queue.size();
+        } else {
+            r.cancel = true;  // the server thread retires it before its next tick
+        }
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
+    return NB_OK;
+}
+
+int nb_result_release(nb_server s, uint64_t ticket)
+{
+    if (!s) return NB_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return NB_ERR_NOTFOUND;
+    if (!terminal(it->second->status)) return NB_ERR_STATE;
+    s->table.erase(it);
+    return NB_OK;
+}
+
+int nb_server_get_stats(nb_server s, nb_server_stats *out)
+{
+    if (!s || !out) return NB_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->st;
+    return NB_OK;
+}
+
+}  // extern "C"

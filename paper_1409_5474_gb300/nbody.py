@@ -80,6 +80,50 @@ class nb_stats(ctypes.Structure):
         return d
 
 
+NB_REQ_FORCE = 0
+NB_REQ_EVOLVE = 1
+NB_STATUS_QUEUED = 0
+NB_STATUS_RUNNING = 1
+NB_STATUS_DONE = 2
+NB_STATUS_ERROR = 3
+NB_STATUS_CANCELLED = 4
+
+
+class nb_server_cfg(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("variant", ctypes.c_int),
+                ("budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("eta", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("flags", ctypes.c_int)]
+
+
+class nb_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int),
+                ("m", ctypes.POINTER(ctypes.c_double)), ("pos", ctypes.POINTER(ctypes.c_double)),
+                ("vel", ctypes.POINTER(ctypes.c_double)), ("eps", ctypes.c_double),
+                ("t_span", ctypes.c_double)]
+
+
+class nb_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("n", ctypes.c_int),
+                ("acc", ctypes.POINTER(ctypes.c_double)), ("jerk", ctypes.POINTER(ctypes.c_double)),
+                ("pot", ctypes.POINTER(ctypes.c_double)), ("pos", ctypes.POINTER(ctypes.c_double)),
+                ("vel", ctypes.POINTER(ctypes.c_double)), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("interactions", ctypes.c_double), ("block_steps", ctypes.c_longlong)]
+
+
+class nb_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("cancelled", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("ticks", ctypes.c_longlong), ("force_launches", ctypes.c_longlong),
+                ("interactions", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("queued", ctypes.c_int), ("inflight", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _H = ctypes.c_void_p
@@ -123,6 +167,14 @@ _SIGS = [
     ("nb_batch_energy", ctypes.c_int, [_H, _D, _D]),
     ("nb_batch_autotune", ctypes.c_int, [_H, _I]),
     ("nb_batch_last_error", ctypes.c_char_p, [_H]),
+    ("nb_server_create", ctypes.c_int, [ctypes.POINTER(nb_server_cfg), ctypes.POINTER(_H)]),
+    ("nb_server_destroy", ctypes.c_int, [_H]),
+    ("nb_submit", ctypes.c_int, [_H, ctypes.POINTER(nb_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("nb_poll", ctypes.c_int, [_H, ctypes.c_uint64, ctypes.POINTER(nb_result)]),
+    ("nb_wait", ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(nb_result)]),
+    ("nb_cancel", ctypes.c_int, [_H, ctypes.c_uint64]),
+    ("nb_result_release", ctypes.c_int, [_H, ctypes.c_uint64]),
+    ("nb_server_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_server_stats)]),
     ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -456,6 +508,123 @@ class Batch:
 
     def autotune(self):
         return nb_batch_autotune(self.b)
+
+
+def _scheck(rc, func):
+    if rc != NB_OK:
+        raise NBodyError(rc, func, nb_status_string(rc))
+
+
+def nb_server_create(device=0, variant=NB_F32DS, budget_bytes=0, max_inflight=0, max_queue=0,
+                     eta=0.0, dt_max=0.0, flags=0):
+    cfg = nb_server_cfg(int(device), int(variant), int(budget_bytes), int(max_inflight),
+                        int(max_queue), float(eta), float(dt_max), int(flags))
+    srv = _H()
+    _scheck(load().nb_server_create(ctypes.byref(cfg), ctypes.byref(srv)), "nb_server_create")
+    return srv.value
+
+
+def nb_server_destroy(srv) -> None:
+    load().nb_server_destroy(srv)
+
+
+def nb_submit(srv, kind, m, pos, vel, eps, t_span=0.0) -> int:
+    """Queue a request; m (n,), pos and vel (3, n). Returns the ticket."""
+    m = _f64(m, (-1,))
+    n = m.shape[0]
+    pos = _f64(pos, (3, n))
+    vel = _f64(vel, (3, n))
+    req = nb_request(int(kind), n, _dp(m), _dp(pos), _dp(vel), float(eps), float(t_span))
+    t = ctypes.c_uint64()
+    _scheck(load().nb_submit(srv, ctypes.byref(req), ctypes.byref(t)), "nb_submit")
+    return t.value
+
+
+def _result_dict(r: nb_result) -> dict:
+    d = {k: getattr(r, k) for k in ("status", "error", "n", "t_submit", "t_start", "t_done",
+                                     "interactions", "block_steps")}
+    n = r.n
+    for k, rows in (("acc", 3), ("jerk", 3), ("pot", 1), ("pos", 3), ("vel", 3)):
+        p = getattr(r, k)
+        if p:
+            a = np.ctypeslib.as_array(p, shape=(rows * n,)).copy()
+            d[k] = a.reshape(3, n) if rows == 3 else a
+    return d
+
+
+def nb_poll(srv, ticket) -> dict:
+    r = nb_result()
+    _scheck(load().nb_poll(srv, int(ticket), ctypes.byref(r)), "nb_poll")
+    return _result_dict(r)
+
+
+def nb_wait(srv, ticket, timeout_s=60.0) -> dict:
+    """Wait for a request; raises NBodyError(NB_ERR_TIMEOUT) if it is not done in time."""
+    r = nb_result()
+    _scheck(load().nb_wait(srv, int(ticket), float(timeout_s), ctypes.byref(r)), "nb_wait")
+    return _result_dict(r)
+
+
+def nb_cancel(srv, ticket) -> None:
+    _scheck(load().nb_cancel(srv, int(ticket)), "nb_cancel")
+
+
+def nb_result_release(srv, ticket) -> None:
+    _scheck(load().nb_result_release(srv, int(ticket)), "nb_result_release")
+
+
+def nb_server_get_stats(srv) -> dict:
+    st = nb_server_stats()
+    _scheck(load().nb_server_get_stats(srv, ctypes.byref(st)), "nb_server_get_stats")
+    return st.as_dict()
+
+
+class Server:
+    """Continuous-batching force / integration service on one GPU."""
+
+    def __init__(self, **cfg):
+        self.s = nb_server_create(**cfg)
+
+    def close(self):
+        if getattr(self, "s", None):
+            nb_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def force(self, m, pos, vel, eps) -> int:
+        return nb_submit(self.s, NB_REQ_FORCE, m, pos, vel, eps)
+
+    def evolve(self, m, pos, vel, eps, t_span) -> int:
+        return nb_submit(self.s, NB_REQ_EVOLVE, m, pos, vel, eps, t_span)
+
+    def poll(self, ticket) -> dict:
+        return nb_poll(self.s, ticket)
+
+    def wait(self, ticket, timeout_s=60.0, release=True) -> dict:
+        d = nb_wait(self.s, ticket, timeout_s)
+        if release:
+            nb_result_release(self.s, ticket)
+        return d
+
+    def cancel(self, ticket) -> None:
+        nb_cancel(self.s, ticket)
+
+    def release(self, ticket) -> None:
+        nb_result_release(self.s, ticket)
+
+    def stats(self) -> dict:
+        return nb_server_get_stats(self.s)
 
 
 NB_STATIC_MAX_NI = 1024
