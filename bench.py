@@ -12,7 +12,7 @@ block steps) per second, in G/s, and its fraction of FP32 peak at 60 flops per
 acc+jerk interaction.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload block65536|full2p20|small1024]
+                  [--workload block65536|full2p20|batch4096|serve|small1024]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (rank 0 only under torchrun). Multi-GPU runs are
@@ -54,6 +54,14 @@ WORKLOADS = {
                       desc="4096 independent Plummer clusters, N log-uniform in [16, 4096], "
                            "eps = 1/(4 N^(1/3)), shared dt = 1/512, F32-DS; one bench step = "
                            "1/16 time unit = 32 graph-replayed steps of all clusters"),
+    "serve": dict(n=64, n_lo=2 ** 8, n_hi=2 ** 18, t_span=0.125, eta=0.01, dt_max=1.0 / 16,
+                  variant="f32ds", kind="serve", eps=None, masses="galaxy",
+                  rates=(8.0, 32.0, 1e6),
+                  desc="Poisson stream of 64 requests on subsystems of 11 Plummer galaxies "
+                       "with a 1% central point mass, N log-uniform in [2^8, 2^18], half one "
+                       "force evaluation, half 1/8 time unit of block steps (eta=0.01, "
+                       "dt_max=1/16), eps = 1/(4 N^(1/3)); one bench step = the whole stream at "
+                       "the saturating rate"),
     "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
                       variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
                       desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
@@ -71,14 +79,26 @@ def parse_args(argv=None):
     ap.add_argument("--variant", choices=["f32", "f32ds", "f64"], default=None)
     ap.add_argument("--n", type=int, default=None,
                     help="override the workload's particle count (profiling of smaller cases)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="run the library's autotuner (nb_autotune) in the untimed set-up")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the library's autotuner (nb_autotune / nb_batch_autotune), which "
+                         "otherwise runs in the untimed set-up; plans are then the built-in "
+                         "heuristic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=None,
+                    help="serve: requests in the stream (default 64)")
+    ap.add_argument("--n-hi", type=int, default=None, help="serve: largest request N")
     return ap.parse_args(argv)
 
 
 def workload(args):
     wl = dict(WORKLOADS[args.workload])
+    if wl["kind"] == "serve":
+        if args.requests:
+            wl["n"] = args.requests
+        if args.n_hi:
+            wl["n_hi"] = args.n_hi
+            wl["desc"] += " [N range overridden to [%d, %d]]" % (wl["n_lo"], args.n_hi)
+        return wl
     if args.n:
         wl["n"] = args.n
         wl["desc"] = wl["desc"] + " [N overridden to %d]" % args.n
@@ -321,6 +341,8 @@ def run_ours(args):
     variant = args.variant or wl["variant"]
     if wl["kind"] == "batch":
         return run_batch(args, wl, variant, dist, rank, world, local)
+    if wl["kind"] == "serve":
+        return run_serve(args, wl, variant, dist, rank, world, local)
     p = make_particles(wl)
     stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
     torch.cuda.set_stream(stream)
@@ -332,7 +354,9 @@ def run_ours(args):
     h = sysm.h
     nbody.nb_set_stream(h, stream.cuda_stream)
     n = p.n
+    t_tune = time.perf_counter()
     plan_table = nbody.nb_autotune(h, 3) if args.autotune else None
+    t_tune = time.perf_counter() - t_tune
 
     def one_step(k, host_state):
         """One bench step; returns (interactions, device_ms, wall_s, launches, stats, state)."""
@@ -445,7 +469,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8,
                 "d2h_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8},
         "gpu_launches": launches,
-        "plans": "autotuned (nb_autotune)" if plan_table else "built-in heuristic",
+        "plans": ("autotuned (nb_autotune, %.1f s untimed set-up)" % t_tune) if plan_table
+                 else "built-in heuristic",
         "interactions": tot_inter,
         "clocks": clocks,
     }
@@ -541,6 +566,200 @@ def run_batch(args, wl, variant, dist, rank, world, local):
                                 "seconds": secs_c}
     print(json.dumps(line), flush=True)
     bt.close()
+    dist.close()
+    return 0
+
+# ---------------------------------------------------------------------------
+# config 5: the request loop
+# ---------------------------------------------------------------------------
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def _lat(xs):
+    return {"p50_s": _pct(xs, 50), "p99_s": _pct(xs, 99), "mean_s": float(np.mean(xs)),
+            "max_s": float(np.max(xs))}
+
+
+def run_serve(args, wl, variant, dist, rank, world, local):
+    """Config 5: a Poisson stream of force / evolve requests through the request loop
+    (nb_submit / nb_wait: continuous batching, one batched force launch per tick), and the
+    same requests served one at a time through the plain engine calls (nb_set_particles +
+    nb_predict + nb_force, or nb_step), in arrival order."""
+    import threading
+    import torch
+    from paper_1409_5474_gb300 import ic, nbody
+
+    base = ic.request_stream(wl["n"], 1.0, n_lo=wl["n_lo"], n_hi=wl["n_hi"], t_span=wl["t_span"])
+    parts = [ic.request_particles(r) for r in base]
+    eps = [float(ic.cluster_eps(r.n)) for r in base]
+    var = nbody.VARIANTS[variant]
+    srv = nbody.Server(variant=var, device=local, budget_bytes=64 << 30, max_inflight=64,
+                       max_queue=4096, eta=wl["eta"], dt_max=wl["dt_max"])
+
+    def submit(r, i, force_only=False):
+        p = parts[i]
+        if force_only or r.kind == "force":
+            return srv.force(p.m, p.pos.T, p.vel.T, eps[i])
+        return srv.evolve(p.m, p.pos.T, p.vel.T, eps[i], r.t_span)
+
+    def run_stream(rate, force_only=False):
+        """Replay the stream at `rate` (a submitter thread sleeps until each arrival);
+        returns the results (server clock) in request order."""
+        reqs = ic.request_stream(wl["n"], rate, n_lo=wl["n_lo"], n_hi=wl["n_hi"],
+                                 t_span=wl["t_span"])
+        tickets = [None] * len(reqs)
+        ready = [threading.Event() for _ in reqs]
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, r in enumerate(reqs):
+                d = t0 + r.arrival - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = submit(r, i, force_only)
+                ready[i].set()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        res = []
+        for i in range(len(reqs)):
+            ready[i].wait()
+            res.append(srv.wait(tickets[i], timeout_s=7200))
+        th.join()
+        bad = [r for r in res if r["status"] != nbody.NB_STATUS_DONE]
+        if bad:
+            raise RuntimeError("request failed: %s" % bad[0])
+        return reqs, res
+
+    def summarise(reqs, res):
+        lat = [r["t_done"] - r["t_submit"] for r in res]
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        inter = sum(r["interactions"] for r in res)
+        out = {"throughput": inter / span / 1e9, "makespan_s": span, "interactions": inter,
+               "latency": _lat(lat)}
+        for kind in ("force", "evolve"):
+            xs = [x for x, q in zip(lat, reqs) if q.kind == kind]
+            if xs:
+                out["latency_" + kind] = _lat(xs)
+        return out
+
+    # warm-up: the stream as force requests only (fills the handle pool, loads the kernels)
+    for _ in range(args.warmup):
+        run_stream(wl["rates"][-1], force_only=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    st0 = srv.stats()
+    timed = []
+    for _ in range(args.steps):
+        timed.append(summarise(*run_stream(wl["rates"][-1])))
+    st1 = srv.stats()
+    clocks = sampler.stop()
+    sweep = []
+    for rate in wl["rates"][:-1]:
+        reqs, res = run_stream(rate)
+        sweep.append({"rate_hz": rate, "server": summarise(reqs, res)})
+
+    # one request per launch: pre-created engine handles, requests served in arrival order
+    systems = [nbody.System(p.m, p.pos, p.vel, variant=variant, eps=e, eta=wl["eta"],
+                            dt_max=wl["dt_max"], device=local) for p, e in zip(parts, eps)]
+    service, b_inter = [], []
+    for r, p, sy in zip(base, parts, systems):
+        t0 = time.perf_counter()
+        nbody.nb_set_particles(sy.h, p.m, p.pos.T, p.vel.T, 0.0)
+        if r.kind == "force":
+            nbody.nb_predict(sy.h, 0.0)
+            nbody.nb_force(sy.h)
+            it = float(r.n) * r.n
+        else:
+            it = nbody.nb_step(sy.h, r.t_span)["interactions"]
+            nbody.nb_get_particles(sy.h)
+        service.append(time.perf_counter() - t0)
+        b_inter.append(it)
+    for sy in systems:
+        sy.close()
+
+    def fifo(rate):
+        reqs = ic.request_stream(wl["n"], rate, n_lo=wl["n_lo"], n_hi=wl["n_hi"],
+                                 t_span=wl["t_span"])
+        fin, lat = 0.0, []
+        for q, sv in zip(reqs, service):
+            fin = max(q.arrival, fin) + sv
+            lat.append(fin - q.arrival)
+        out = {"throughput": sum(b_inter) / (fin - reqs[0].arrival) / 1e9,
+               "makespan_s": fin - reqs[0].arrival, "latency": _lat(lat)}
+        for kind in ("force", "evolve"):
+            xs = [x for x, q in zip(lat, reqs) if q.kind == kind]
+            if xs:
+                out["latency_" + kind] = _lat(xs)
+        return out
+
+    for row in sweep:
+        row["one_request_per_launch"] = fifo(row["rate_hz"])
+    sat = {"rate_hz": wl["rates"][-1], "server": timed[-1],
+           "one_request_per_launch": fifo(wl["rates"][-1])}
+    sweep.append(sat)
+    srv_stats = {k: st1[k] - st0[k] for k in ("ticks", "force_launches", "interactions",
+                                               "busy_s", "completed", "kernel_launches")}
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(measured_peaks().get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    inter = sum(t["interactions"] for t in timed)
+    secs = sum(t["makespan_s"] for t in timed)
+    value = inter / secs / 1e9
+    h2d = sum(8 * 7 * r.n for r in base)
+    d2h = sum(8 * (7 if r.kind == "force" else 6) * r.n for r in base)
+    line = {
+        "metric": METRIC + "; p50/p99 request latency", "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded galaxies with a central point mass, N-body units)",
+        "config": {"workload": args.workload, "requests": wl["n"], "n_range": [wl["n_lo"], wl["n_hi"]],
+                   "t_span": wl["t_span"], "eta": wl["eta"], "dt_max": wl["dt_max"],
+                   "variant": variant, "eps": "1/(4 N^(1/3)) per request", "desc": wl["desc"],
+                   "max_inflight": 64, "budget_bytes": 64 << 30,
+                   "l2": "working set of the stream (GBs) larger than L2",
+                   "parallelism": "single GPU"},
+        "latency": timed[-1]["latency"],
+        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+        "roofline": {"bound": "alu", "kernel": "k_force_items32 (batched pair force)",
+                     "achieved": FLOPS_PER_INTERACTION * value * 1e9 / 1e12, "peak": peak,
+                     "unit": "TFLOP/s", "frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+                     "traffic": None,
+                     "note": "whole-loop throughput (makespan incl. host ticks), not the kernel alone",
+                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived)" % sm_max},
+        "one_request_per_launch": sat["one_request_per_launch"],
+        "sweep": sweep,
+        "server_stats": srv_stats,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "requests carry host arrays in and out: the request loop is end to end"},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    line["gpu_launches"] = int(srv_stats["kernel_launches"])
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        inter_c, used = 0.0, 0
+        for r, p, e in sorted(zip(base, parts, eps), key=lambda x: x[0].n):
+            if r.kind != "force":
+                continue
+            oracle.force(p.m, p.pos, p.vel, e * e)
+            inter_c += float(r.n) * r.n
+            used += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        secs_c = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": inter_c / secs_c / 1e9, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "oracle force on the %d smallest force requests" % used,
+                                "seconds": secs_c}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    srv.close()
     dist.close()
     return 0
 

@@ -359,6 +359,7 @@ typedef struct nb_server_stats {
     double busy_s;              /* time ticks spent on the GPU work */
     int queued, inflight;       /* right now */
     size_t bytes_in_use;        /* device bytes held for requests */
+    long long kernel_launches;  /* kernels the server launched */
 } nb_server_stats;
 
 /* Start a server (one thread). Its device work runs on its own stream. */

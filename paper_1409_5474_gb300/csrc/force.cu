@@ -114,6 +114,18 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     }
 }
 
+// After a wait gave up at tile kt, let the copies already issued (tiles kt ..
+// kt + NS - 1 of n_tiles, ring position seq0 + tile) land before the CTA stops
+// using its shared memory: one more bounded wait on each. Thread 0 only.
+template <int NS>
+__device__ __noinline__ void drain_ring(uint64_t *full, unsigned seq0, int kt, int n_tiles)
+{
+    for (int q = kt; q < n_tiles && q < kt + NS; ++q) {
+        const unsigned sq = seq0 + (unsigned)q;
+        mbar_wait(&full[sq % NS], (sq / NS) & 1u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Double-single accumulation (Knuth/Moller TwoSum + fast renormalisation).
 // ---------------------------------------------------------------------------
@@ -205,7 +217,7 @@ __device__ __forceinline__ void store_component(const Out3 &out, int c, int k, d
 // fixed xor tree, so the result does not depend on which CTA finished last.
 // The same with double-single partials (float2 {hi, lo} in the part buffer)
 // combined in FP32 arithmetic; the final value is converted once.
-template <int NT>
+template <int NT, int U = 8>
 __device__ __forceinline__ void finish_split_ds(int nsplit, int slot0, int nslots, int n_i,
                                                 const float2 *part, long long pld,
                                                 unsigned *counter, const Out3 &out,
@@ -221,7 +233,6 @@ __device__ __forceinline__ void finish_split_ds(int nsplit, int slot0, int nslot
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int valid = min(nslots, n_i - slot0);
     const int total = valid * 7;
-    constexpr int U = 8;
     for (int q0 = warp * U; q0 < total; q0 += (NT / 32) * U) {
         dsf acc[U];
 #pragma unroll
@@ -502,7 +513,10 @@ __global__ void __launch_bounds__(32 * NWI * NWJ)
         }
 
         __syncthreads();  // every warp is done with this stage
-        if (s_abort) break;
+        if (s_abort) {
+            if (tid == 0) drain_ring<NS>(s_full, 0u, kt, my_tiles);
+            break;
+        }
         if (tid == 0 && kt + NS < my_tiles) issue(kt + NS);
     }
     if (s_abort) {
@@ -702,7 +716,10 @@ __global__ void __launch_bounds__(NT)
             P[p] += tp[p];
         }
         __syncthreads();
-        if (s_abort) break;
+        if (s_abort) {
+            if (tid == 0) drain_ring<NS>(s_full, 0u, kt, my_tiles);
+            break;
+        }
         if (tid == 0 && kt + NS < my_tiles) issue(kt + NS);
     }
     if (s_abort) {
@@ -1146,13 +1163,169 @@ __global__ void __launch_bounds__(NT)
 
 // ---------------------------------------------------------------------------
 // Batched force kernel: many independent systems in one launch (the batched
-// clusters, and the requests of the serving loop). A work item is one i-block
-// of one system against all j of the same system, with its own pointers. The
-// persistent CTAs walk the item list (sorted by decreasing work on the host,
-// so the round-robin assignment is balanced), staging each system's j-tiles
-// through the same bulk-copy ring as the tile kernel; the mbarrier phases run
-// on across items.
+// clusters, and the requests of the serving loop). A work item is a block of
+// i-rows of one system against a range of the same system's j-records, with
+// its own pointers (WorkItem). The persistent CTAs walk the item list (sorted
+// by decreasing work on the host, so the round-robin assignment is balanced).
+// i-parallel items stage the j-tiles through the same bulk-copy ring as the
+// tile kernel (the mbarrier phases run on across items); j-parallel items read
+// the j-records straight from L1/L2. Items of a j-split group leave
+// double-single partials that the group's last item sums in split order.
 // ---------------------------------------------------------------------------
+
+// One j-parallel item (kind 1): every thread takes j = j0 + tid, j0 + tid + NT,
+// ... against the same four i-rows at a time. FP32 sums over at most JPAR_RUN
+// j per thread meet in a fixed xor tree per warp (double-single) and a
+// fixed-order sum over the warps, added to double-single totals in shared
+// memory; the totals are the item's outputs, or its partials when its j-range
+// is one split of a group.
+constexpr int JPAR_RUN = 32;
+
+template <bool DS, int NT>
+__device__ __forceinline__ void item_jpar(const WorkItem &w, float2 (*s_red)[28], float2 *s_tot)
+{
+    constexpr int G = 4;
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float eps2f = w.eps2;
+    const int jend = w.j0 + w.nj;
+    for (int g0 = 0; g0 < w.ni; g0 += G) {
+        float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
+        int iid[G];
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+            const int r = w.i0 + min(g0 + p, w.ni - 1);  // idle slots copy the last i
+            const float4 a = __ldg(w.irec + (size_t)DS_REC * r);
+            const float4 b = __ldg(w.irec + (size_t)DS_REC * r + 1);
+            const float4 c = __ldg(w.irec + (size_t)DS_REC * r + 2);
+            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
+            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+            iid[p] = w.gathered ? __float_as_int(b.w) : r;
+        }
+        if (tid < G * 7) s_tot[tid] = make_float2(0.f, 0.f);
+        for (int jb = w.j0; jb < jend; jb += NT * JPAR_RUN) {
+            float ta[G][3], tjv[G][3], tp[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ta[p][c] = tjv[p][c] = 0.f;
+                tp[p] = 0.f;
+            }
+            const int jstop = min(jend, jb + NT * JPAR_RUN);
+#pragma unroll 2
+            for (int j = jb + tid; j < jstop; j += NT) {
+                const float4 a = __ldg(w.jrec + (size_t)DS_REC * j);
+                const float4 c = __ldg(w.jrec + (size_t)DS_REC * j + 2);
+                float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (DS) b = __ldg(w.jrec + (size_t)DS_REC * j + 1);
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    float dx, dy, dz;
+                    if (DS) {
+                        dx = (a.x - xh[p]) + (b.x - xl[p]);
+                        dy = (a.y - yh[p]) + (b.y - yl[p]);
+                        dz = (a.z - zh[p]) + (b.z - zl[p]);
+                    } else {
+                        dx = a.x - xh[p];
+                        dy = a.y - yh[p];
+                        dz = a.z - zh[p];
+                    }
+                    const float dvx = c.x - vx[p], dvy = c.y - vy[p], dvz = c.z - vz[p];
+                    float r2 = fmaf(dx, dx, eps2f);
+                    r2 = fmaf(dy, dy, r2);
+                    r2 = fmaf(dz, dz, r2);
+                    float rv = dx * dvx;
+                    rv = fmaf(dy, dvy, rv);
+                    rv = fmaf(dz, dvz, rv);
+                    float rinv = rsqrtf(r2);
+                    rinv = (j == iid[p]) ? 0.f : rinv;
+                    const float rinv2 = rinv * rinv;
+                    const float mrinv = a.w * rinv;
+                    const float mr3 = mrinv * rinv2;
+                    const float beta = -3.f * ((mr3 * rinv2) * rv);
+                    tp[p] += mrinv;
+                    ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                    ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                    ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                    // per pair: m v / s^3 - 3 m (r.v) r / s^5
+                    tjv[p][0] = fmaf(beta, dx, fmaf(mr3, dvx, tjv[p][0]));
+                    tjv[p][1] = fmaf(beta, dy, fmaf(mr3, dvy, tjv[p][1]));
+                    tjv[p][2] = fmaf(beta, dz, fmaf(mr3, dvz, tjv[p][2]));
+                }
+            }
+            // lanes -> warp (fixed xor tree), warps -> CTA (fixed order) -> totals
+#pragma unroll
+            for (int p = 0; p < G; ++p)
+#pragma unroll
+                for (int c = 0; c < 7; ++c) {
+                    dsf v{c < 3 ? ta[p][c] : (c < 6 ? tjv[p][c - 3] : tp[p]), 0.f};
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) ds_acc(v, ds_shfl_xor(v, o));
+                    if (lane == 0) s_red[warp][p * 7 + c] = make_float2(v.hi, v.lo);
+                }
+            __syncthreads();
+            if (tid < G * 7) {
+                dsf sum{s_tot[tid].x, s_tot[tid].y};
+#pragma unroll
+                for (int q = 0; q < NW; ++q) ds_acc(sum, dsf{s_red[q][tid].x, s_red[q][tid].y});
+                s_tot[tid] = make_float2(sum.hi, sum.lo);
+            }
+            __syncthreads();
+        }
+        if (tid < G * 7) {
+            const int p = tid / 7, c = tid % 7, k = g0 + p;
+            if (k < w.ni) {
+                const float2 t = s_tot[tid];
+                if (w.nsplit <= 1) {
+                    const Out3 out{w.acc, w.jerk, w.pot, w.ld};
+                    store_component(out, c, w.i0 + k, ds_to_double(dsf{t.x, t.y}), w.err);
+                } else {
+                    w.part[((size_t)w.split * 7 + c) * w.ni + k] = t;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The j-parallel items of a batched evaluation (kind 1), in a kernel of their
+// own so that their register needs do not lower the occupancy of the
+// i-parallel kernel; the two run concurrently on two streams.
+template <int VAR, int NT>
+__global__ void __launch_bounds__(NT)
+    k_force_items_jpar32(const WorkItem *__restrict__ items, int nitems)
+{
+    __shared__ float2 s_red[NT / 32][28];
+    __shared__ float2 s_tot[28];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        item_jpar<VAR == NB_F32DS, NT>(w, s_red, s_tot);
+    }
+}
+
+// The j-split groups of a batched evaluation, after the items: each group's
+// outputs are the sums of its nsplit double-single partials in the order
+// split = 0..nsplit-1 (one thread per output, consecutive outputs coalesced).
+__global__ void __launch_bounds__(256)
+    k_split_reduce(const SplitGroup *__restrict__ groups, int ngroups)
+{
+    for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+        const SplitGroup g = groups[gi];
+        const int total = 7 * g.ni;
+        const Out3 out{g.acc, g.jerk, g.pot, g.ld};
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int c = q / g.ni, k = q % g.ni;
+            dsf sum{0.f, 0.f};
+            for (int sp = 0; sp < g.nsplit; ++sp) {
+                const float2 v = __ldcg(g.part + ((size_t)sp * 7 + c) * g.ni + k);
+                ds_acc(sum, dsf{v.x, v.y});
+            }
+            store_component(out, c, g.i0 + k, ds_to_double(sum), g.err);
+        }
+    }
+}
+
 
 template <int VAR, int IPT, int NT, int JT, int NS>
 __global__ void __launch_bounds__(NT)
@@ -1209,7 +1382,7 @@ __global__ void __launch_bounds__(NT)
             const uint32_t bytes = (uint32_t)cnt * DS_REC * 16u;
             mbar_expect_tx(&s_full[stage], bytes);
             bulk_g2s(s_tile + (size_t)stage * JT * DS_REC,
-                     jrec + (size_t)kt * JT * DS_REC, bytes, &s_full[stage]);
+                     jrec + ((size_t)w.j0 + (size_t)kt * JT) * DS_REC, bytes, &s_full[stage]);
         };
         if (tid == 0) {
             for (int kt = 0; kt < NS && kt < ntiles; ++kt) issue(kt);
@@ -1219,7 +1392,7 @@ __global__ void __launch_bounds__(NT)
             const int stage = (int)(sq % NS);
             if (!mbar_wait(&s_full[stage], (sq / NS) & 1u)) s_abort = 1;
             const float4 *T = s_tile + (size_t)stage * JT * DS_REC;
-            const int jbase = kt * JT;
+            const int jbase = w.j0 + kt * JT;
             const int cnt = min(JT, w.nj - kt * JT);
             bool own = false;
 #pragma unroll
@@ -1303,26 +1476,43 @@ __global__ void __launch_bounds__(NT)
                     P_h[p] += tp[p];
             }
             __syncthreads();
-            if (s_abort) break;
+            if (s_abort) {
+                if (tid == 0) {
+                    drain_ring<NS>(s_full, seq, kt, ntiles);
+                    atomicOr(err, DERR_TIMEOUT);
+                }
+                return;
+            }
             if (tid == 0 && kt + NS < ntiles) issue(kt + NS);
         }
-        if (s_abort) {
-            if (tid == 0) atomicOr(err, DERR_TIMEOUT);
-            break;
-        }
         seq += (unsigned)ntiles;
+        if (w.nsplit <= 1) {
 #pragma unroll
-        for (int p = 0; p < IPT; ++p) {
-            const int k = p * NT + tid;
-            if (k >= w.ni) continue;
-            double d[7];
+            for (int p = 0; p < IPT; ++p) {
+                const int k = p * NT + tid;
+                if (k >= w.ni) continue;
+                double d[7];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                d[c] = ds_to_double(dsf{A_h[p][c], A_l[p][c]});
-                d[3 + c] = ds_to_double(dsf{J_h[p][c], J_l[p][c]});
+                for (int c = 0; c < 3; ++c) {
+                    d[c] = ds_to_double(dsf{A_h[p][c], A_l[p][c]});
+                    d[3 + c] = ds_to_double(dsf{J_h[p][c], J_l[p][c]});
+                }
+                d[6] = ds_to_double(dsf{P_h[p], P_l[p]});
+                write_final(Out3{w.acc, w.jerk, w.pot, w.ld}, w.i0 + k, d, err);
             }
-            d[6] = ds_to_double(dsf{P_h[p], P_l[p]});
-            write_final(Out3{w.acc, w.jerk, w.pot, w.ld}, w.i0 + k, d, err);
+        } else {
+            float2 *pp = w.part + (size_t)w.split * 7 * w.ni;
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                const int k = p * NT + tid;
+                if (k >= w.ni) continue;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    pp[(size_t)c * w.ni + k] = make_float2(A_h[p][c], A_l[p][c]);
+                    pp[(size_t)(3 + c) * w.ni + k] = make_float2(J_h[p][c], J_l[p][c]);
+                }
+                pp[(size_t)6 * w.ni + k] = make_float2(P_h[p], P_l[p]);
+            }
         }
     }
 }
@@ -1387,25 +1577,27 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
         tiny_shape(n_i, n_j, p);
         return p;
     }
-    if (n_i <= 4096) {
-        // warp groups: about 16 warps per SM in total, at least 256 j per split
+    if (n_i < 4096) {
+        // warp groups: about 14 warps per SM in total, at least 1024 j per split
+        // (the best plans a sweep over N_i at N = 65536 found on GB300)
         p.kind = 1;
         wgrp_shape(n_i, p);
         const long long groups = (n_i + p.ipt - 1) / p.ipt;
-        const long long cap = n_j / 256 > 1 ? n_j / 256 : 1;
-        p.nsplit = (int)clampll((16LL * num_sms + groups - 1) / groups, 1, cap);
+        const long long cap = n_j / 1024 > 1 ? n_j / 1024 : 1;
+        p.nsplit = (int)clampll((14LL * num_sms + groups - 1) / groups, 1, cap);
         return p;
     }
-    // tiles: 256 threads, 2 i per thread; warp rows share j-tiles below 8192 i
+    // tiles: 256 threads, 2 i per thread; 8 or 4 warp rows share each j-tile
+    // below 65536 i; about 20 CTAs per SM, at least 16 tiles per split
     p.kind = 0;
     p.ipt = 2;
     p.threads = 256;
     p.jt = JT32;
-    p.nwj = n_i >= 8192 ? 1 : 4;
+    p.nwj = n_i >= 65536 ? 1 : (n_i >= 8192 ? 4 : 8);
     const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
     const long long nblk = (n_i + ib - 1) / ib;
     const long long ntiles = (n_j + p.jt - 1) / p.jt;
-    p.nsplit = (int)clampll((4LL * num_sms + nblk - 1) / nblk, 1, ntiles / 2 > 1 ? ntiles / 2 : 1);
+    p.nsplit = (int)clampll((20LL * num_sms + nblk - 1) / nblk, 1, ntiles / 16 > 1 ? ntiles / 16 : 1);
     return p;
 }
 
@@ -1584,6 +1776,41 @@ cudaError_t launch_force_items(int variant, int threads, const WorkItem *items, 
     case 128: return go_items<NB_F32, 128>(items, nitems, grid, st);
     default: return go_items<NB_F32, 256>(items, nitems, grid, st);
     }
+}
+
+cudaError_t launch_force_items_jpar(int variant, const WorkItem *items, int nitems, int grid,
+                                    cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (variant == NB_F32DS)
+        k_force_items_jpar32<NB_F32DS, JPAR_THREADS><<<grid, JPAR_THREADS, 0, st>>>(items, nitems);
+    else
+        k_force_items_jpar32<NB_F32, JPAR_THREADS><<<grid, JPAR_THREADS, 0, st>>>(items, nitems);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_reduce(const SplitGroup *groups, int ngroups, int grid,
+                                cudaStream_t st)
+{
+    if (ngroups <= 0) return cudaSuccess;
+    k_split_reduce<<<grid, 256, 0, st>>>(groups, ngroups);
+    return cudaGetLastError();
+}
+
+int jpar_blocks_per_sm(int variant)
+{
+    int nb = 0;
+    const cudaError_t e =
+        variant == NB_F32DS
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &nb, k_force_items_jpar32<NB_F32DS, JPAR_THREADS>, JPAR_THREADS, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &nb, k_force_items_jpar32<NB_F32, JPAR_THREADS>, JPAR_THREADS, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
 }
 
 int batch_blocks_per_sm(int variant, int threads)

@@ -93,31 +93,66 @@ cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, con
 // ---- batched systems -------------------------------------------------------
 
 // One work item of a batched evaluation: i-rows [i0, i0 + ni) of irec against
-// all nj j-records of jrec (one system; the pair i == j is left out), outputs
-// at slots i0.. of acc/jerk/pot (rows of stride ld). irec is either the
-// system's own records (member rows: the particle index is the row) or a
-// gathered copy of its due set (the index rides in each record).
+// the j-records [j0, j0 + nj) of jrec (one system; jrec points at its record 0,
+// and the pair i == j is left out), outputs at slots i0.. of acc/jerk/pot (rows
+// of stride ld). irec is either the system's own records (member rows: the
+// particle index is the row) or a gathered copy of its due set (the index rides
+// in each record).
+//   kind 0: i-parallel - each thread holds 2 of up to 2 x CTA-size i-rows, the
+//           j-records stream through the bulk-copy ring;
+//   kind 1: j-parallel - for small i-sets (ni <= ITEM_JPAR_MAX_NI): the threads
+//           stride over j, i-rows are taken four at a time.
+// A j-split group (nsplit > 1 items with the same i-rows and consecutive
+// j-ranges) writes double-single partials to part ([nsplit][7][ni] float2);
+// launch_split_reduce, queued after the items, sums them in the order
+// split = 0..nsplit-1 (SplitGroup). nsplit <= 1: the item writes its outputs.
 struct WorkItem {
     const float4 *jrec;
     const float4 *irec;
     double *acc, *jerk, *pot;
     long long ld;
-    int i0, ni, nj, gathered;
+    int i0, ni, j0, nj;
+    int gathered, kind;
+    int split, nsplit;
     float eps2;
     int pad;
+    float2 *part;
     unsigned *err;  // error word of the item's system
 };
+
+// A j-split group: outputs at slots i0 .. i0 + ni - 1 of acc/jerk/pot (rows of
+// stride ld) are the fixed-order sums of the nsplit partials in part.
+struct SplitGroup {
+    const float2 *part;
+    double *acc, *jerk, *pot;
+    long long ld;
+    int i0, ni, nsplit, pad;
+    unsigned *err;
+};
+
+constexpr int ITEM_JPAR_MAX_NI = 64;
 
 // CTA sizes the batched kernel is built for (the autotuner picks one).
 constexpr int BATCH_THREADS[3] = {64, 128, 256};
 
-// Batched force (FP32 / double-single) over a work list; grid = number of
-// persistent CTAs (items are taken round-robin, so sort them by decreasing work).
+// Batched force (FP32 / double-single) over a list of i-parallel items (kind 0);
+// grid = number of persistent CTAs (items are taken round-robin, so sort them
+// by decreasing work).
 cudaError_t launch_force_items(int variant, int threads, const WorkItem *items, int nitems,
                                int grid, cudaStream_t st);
 
 // Resident CTAs per SM of the batched kernel with `threads` threads.
 int batch_blocks_per_sm(int variant, int threads);
+
+// The j-parallel items (kind 1) of a batched evaluation, CTAs of JPAR_THREADS.
+constexpr int JPAR_THREADS = 128;
+cudaError_t launch_force_items_jpar(int variant, const WorkItem *items, int nitems, int grid,
+                                    cudaStream_t st);
+int jpar_blocks_per_sm(int variant);
+
+// The fixed-order sums of j-split groups, after their items (same stream).
+cudaError_t launch_split_reduce(const SplitGroup *groups, int ngroups, int grid,
+                                cudaStream_t st);
 
 // ---- per-particle kernels (K1, K4, K5) -------------------------------------
 
@@ -176,6 +211,22 @@ cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_
                            unsigned long long *dtmin_hits, cudaStream_t st,
                            const double *t_dev = nullptr);
 
+// K4 of many systems in one launch. Job q serves CTAs [block0, block0 +
+// ceil(na / CORRECT_THREADS)) (jobs sorted by block0, nblocks CTAs in all).
+constexpr int CORRECT_THREADS = 32;
+struct CorrectJob {
+    StateDev s;
+    const int *act;
+    int na, block0;
+    double t_new;
+    Out3 f;
+    SchedDev *sd;
+    unsigned *err;
+};
+cudaError_t launch_correct_multi(const CorrectJob *jobs, int njobs, int nblocks,
+                                 const StepParams &p, unsigned long long *dtmin_hits,
+                                 cudaStream_t st);
+
 // With t_dev != nullptr the two kernels above take their time as *t_dev + t
 // (resp. *t_dev + t_new) from device memory, so a captured graph can be
 // replayed step after step; launch_advance then sets *t_dev += dt.
@@ -203,6 +254,21 @@ cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams
 cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long long *status,
                                  int *act, float4 *irec, Mailbox *mail_dev, double dt_max,
                                  bool want_rec, unsigned *err, cudaStream_t st);
+
+// K5 + K1 of many systems in one launch: job q serves CTAs [block0, block0 +
+// ntiles) with ntiles = ceil(n / SCHED_TILE) (jobs sorted by block0).
+struct SchedJob {
+    StateDev s;
+    SchedDev *sd;
+    unsigned long long *status;
+    int *act;
+    float4 *irec;
+    Mailbox *mail;
+    unsigned *err;
+    int block0, ntiles;
+};
+cudaError_t launch_sched_predict_multi(const SchedJob *jobs, int njobs, int nblocks,
+                                       double dt_max, bool want_rec, cudaStream_t st);
 
 // Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
 cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,

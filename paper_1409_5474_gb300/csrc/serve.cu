@@ -7,16 +7,22 @@
 //      while the in-flight limit and the device-memory budget allow; an
 //      admitted request gets an engine handle from a pool (by capacity
 //      class) and its particles are copied in once - they stay on the GPU;
-//   2. collects work items for ONE batched force launch: new FORCE requests
-//      (every particle against every particle), new EVOLVE requests (their
-//      initial evaluation) and the current due set of every stepping EVOLVE
-//      request (the records its scheduler gathered);
-//   3. launches the batched force, then per request: copy-out of FORCE
-//      results, initial steps, or corrector + next scheduler launch;
+//   2. builds the tick's descriptors and uploads them in one copy: force work
+//      items for new FORCE requests (every particle against every particle),
+//      new EVOLVE requests (their initial evaluation) and the due set of every
+//      stepping EVOLVE request (the records its scheduler gathered), with
+//      j-splits for small i-sets; one corrector job and one scheduler job per
+//      integration that goes on;
+//   3. launches the batched force (i-parallel and j-parallel items on two
+//      streams, then the fixed-order sums of the j-split groups), the initial
+//      steps of new integrations, ONE corrector launch and ONE scheduler +
+//      predictor launch over all integrations, and the copies of finished
+//      results;
 //   4. synchronises once, checks every request's error word and mailbox,
 //      and retires finished requests, returning their handles to the pool.
-// A request's work items and kernels depend only on the request itself, so
-// its results are the same whatever else is in flight.
+// A request's items, splits and summation order depend only on the request
+// itself (and the SM count), so its results are the same whatever else is in
+// flight.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,6 +68,8 @@ struct Req {
     int n_active = 0;
     unsigned long long epoch = 0;
     bool final_copy = false;  // EVOLVE: t_end reached, results being copied out
+    double tick_inter = 0.0;  // interactions / block steps of the running tick,
+    long long tick_steps = 0; // published under the lock when it ends
     int pending = NB_OK;      // failure found on the host during the tick
     // results
     std::vector<double> acc, jerk, pot, out_pos, out_vel;
@@ -82,6 +90,8 @@ struct nb_server_s {
     nb_server_cfg cfg{};
     int dev = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;            // the j-parallel items, beside the rest
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::chrono::steady_clock::time_point t0;
 
     std::mutex mu;
@@ -100,9 +110,11 @@ struct nb_server_s {
     unsigned *d_errs = nullptr;                   // one error word per slot
     unsigned *h_errs = nullptr;                   // their pinned host copy
     unsigned long long *d_dtmin = nullptr;        // corrector dt_min clamps
-    WorkItem *d_items = nullptr, *h_items = nullptr;
-    size_t items_cap = 0;
-    int threads = 128, grid = 0;
+    char *d_stage = nullptr, *h_stage = nullptr;  // the tick's descriptors
+    size_t stage_cap = 0;
+    float2 *d_part = nullptr;          // j-split partials of the tick
+    size_t part_cap = 0;               // float2
+    int threads = 128, grid = 0, grid_jpar = 0;
     nb_server_stats st{};
     int fatal = NB_OK;
 
@@ -243,50 +255,91 @@ bool fits(nb_server s, const Req &r, size_t in_use)
     return in_use + estimate_bytes(r.cap) <= s->cfg.budget_bytes;
 }
 
-// Work items of an all-vs-all evaluation of r's records (member rows).
-void member_items(nb_server s, Req &r, const HandleView &v, std::vector<WorkItem> &items)
+// The work items of one tick's batched force launch, with the scratch their
+// j-split groups need (float2 offsets and counter indices until the buffers are
+// sized; -1 = no split).
+struct TickItems {
+    std::vector<WorkItem> items;
+    std::vector<long long> part_off;   // per item
+    std::vector<SplitGroup> groups;
+    std::vector<long long> group_off;  // per group
+    size_t part_total = 0;
+    double interactions = 0.0;
+};
+
+// Smallest j-range of an item in a j-split group (i-parallel, j-parallel).
+constexpr int ITEM_MIN_J_IPAR = 1024;
+constexpr int ITEM_MIN_J_JPAR = 2048;
+
+// Items of n_i i-rows of irec (member rows when !gathered) against all r.n
+// j-records of r. Small i-sets become j-parallel items; the j-range is split
+// so that the request alone yields about four items per SM, as long as every
+// item keeps a minimum j-range. The split depends only on (n_i, r.n) and the
+// SM count, never on the other requests of the tick, so a request's results
+// are the same alone and in any mix.
+void add_group(nb_server s, Req &r, const HandleView &v, const float4 *irec, int n_i,
+               int gathered, TickItems &t)
 {
     const int ib = s->threads * 2;
-    for (int i0 = 0; i0 < r.n; i0 += ib) {
-        WorkItem w{};
-        w.jrec = v.s.rec;
-        w.irec = v.s.rec;
-        w.acc = v.f_acc;
-        w.jerk = v.f_jerk;
-        w.pot = v.f_pot;
-        w.ld = v.ld;
-        w.i0 = i0;
-        w.ni = std::min(ib, r.n - i0);
-        w.nj = r.n;
-        w.gathered = 0;
-        w.eps2 = (float)(r.eps * r.eps);
-        w.err = s->d_errs + r.slot;
-        items.push_back(w);
+    const bool jpar = n_i <= ITEM_JPAR_MAX_NI;
+    const int nblk = jpar ? 1 : (n_i + ib - 1) / ib;
+    const int jmin = jpar ? ITEM_MIN_J_JPAR : ITEM_MIN_J_IPAR;
+    const int target = 4 * s->num_sms;
+    int nsplit = std::max(1, std::min((r.n + jmin - 1) / jmin, (target + nblk - 1) / nblk));
+    int chunk = (r.n + nsplit - 1) / nsplit;
+    chunk = (chunk + 31) / 32 * 32;
+    nsplit = (r.n + chunk - 1) / chunk;
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int i0 = blk * ib;
+        const int ni = jpar ? n_i : std::min(ib, n_i - i0);
+        long long poff = -1;
+        if (nsplit > 1) {
+            poff = (long long)t.part_total;
+            t.part_total += (size_t)nsplit * 7 * ni;
+            SplitGroup g{};
+            g.acc = v.f_acc;
+            g.jerk = v.f_jerk;
+            g.pot = v.f_pot;
+            g.ld = v.ld;
+            g.i0 = i0;
+            g.ni = ni;
+            g.nsplit = nsplit;
+            g.err = s->d_errs + r.slot;
+            t.groups.push_back(g);
+            t.group_off.push_back(poff);
+        }
+        for (int sp = 0; sp < nsplit; ++sp) {
+            WorkItem w{};
+            w.jrec = v.s.rec;
+            w.irec = irec;
+            w.acc = v.f_acc;
+            w.jerk = v.f_jerk;
+            w.pot = v.f_pot;
+            w.ld = v.ld;
+            w.i0 = i0;
+            w.ni = ni;
+            w.j0 = sp * chunk;
+            w.nj = std::min(chunk, r.n - w.j0);
+            w.gathered = gathered;
+            w.kind = jpar ? 1 : 0;
+            w.split = sp;
+            w.nsplit = nsplit;
+            w.eps2 = (float)(r.eps * r.eps);
+            w.err = s->d_errs + r.slot;
+            t.items.push_back(w);
+            t.part_off.push_back(poff);
+        }
     }
-    r.interactions += (double)r.n * (double)r.n;
+    const double inter = (double)n_i * (double)r.n;
+    r.tick_inter += inter;
+    t.interactions += inter;
 }
 
-// Work items of r's due set: the na records the scheduler gathered into irec.
-void due_items(nb_server s, Req &r, const HandleView &v, int na, std::vector<WorkItem> &items)
+// Per-thread work of an item, for ordering the list (longest first).
+double item_cost(const WorkItem &w, int threads)
 {
-    const int ib = s->threads * 2;
-    for (int i0 = 0; i0 < na; i0 += ib) {
-        WorkItem w{};
-        w.jrec = v.s.rec;
-        w.irec = v.irec;
-        w.acc = v.f_acc;
-        w.jerk = v.f_jerk;
-        w.pot = v.f_pot;
-        w.ld = v.ld;
-        w.i0 = i0;
-        w.ni = std::min(ib, na - i0);
-        w.nj = r.n;
-        w.gathered = 1;
-        w.eps2 = (float)(r.eps * r.eps);
-        w.err = s->d_errs + r.slot;
-        items.push_back(w);
-    }
-    r.interactions += (double)na * (double)r.n;
+    if (w.kind == 1) return (double)((w.ni + 3) / 4 * 4) * w.nj / threads;
+    return 2.0 * w.nj;
 }
 
 HandleView view_of(const Req &r)
@@ -315,18 +368,31 @@ int upload(nb_server s, Req &r)
     return NB_OK;
 }
 
-int grow_items(nb_server s, size_t n)
+int grow_stage(nb_server s, size_t bytes)
 {
-    if (n <= s->items_cap) return NB_OK;
-    size_t cap = std::max<size_t>(n, 2 * s->items_cap);
-    if (s->d_items) cudaFree(s->d_items);
-    if (s->h_items) cudaFreeHost(s->h_items);
-    s->d_items = nullptr;
-    s->h_items = nullptr;
-    s->items_cap = 0;
-    CKS(cudaMalloc(&s->d_items, cap * sizeof(WorkItem)));
-    CKS(cudaMallocHost(&s->h_items, cap * sizeof(WorkItem)));
-    s->items_cap = cap;
+    if (bytes <= s->stage_cap) return NB_OK;
+    const size_t cap = std::max<size_t>(bytes, 2 * s->stage_cap);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->d_stage = nullptr;
+    s->h_stage = nullptr;
+    s->stage_cap = 0;
+    CKS(cudaMalloc(&s->d_stage, cap));
+    CKS(cudaMallocHost(&s->h_stage, cap));
+    s->stage_cap = cap;
+    return NB_OK;
+}
+
+int grow_scratch(nb_server s, size_t part, size_t)
+{
+    if (part > s->part_cap) {
+        const size_t cap = std::max(part, 2 * s->part_cap);
+        if (s->d_part) cudaFree(s->d_part);
+        s->d_part = nullptr;
+        s->part_cap = 0;
+        CKS(cudaMalloc(&s->d_part, cap * sizeof(float2)));
+        s->part_cap = cap;
+    }
     return NB_OK;
 }
 
@@ -383,13 +449,19 @@ int tick(nb_server s)
         if (rc) return rc;
     }
 
-    // work items of this tick's force launch
-    std::vector<WorkItem> items;
+    // this tick's descriptors: force items, split groups, corrector jobs and
+    // scheduler jobs (uploaded together)
+    TickItems ti;
+    std::vector<CorrectJob> cjobs;
+    std::vector<SchedJob> sjobs;
+    int c_blocks = 0, s_blocks = 0;
+    const StepParams prm = server_params(s);
     for (auto &r : s->inflight) {
         if (r->pending) continue;
         const HandleView v = view_of(*r);
+        unsigned *err = s->d_errs + r->slot;
         if (r->phase == PH_QUEUED) {
-            member_items(s, *r, v, items);
+            add_group(s, *r, v, v.s.rec, r->n, 0, ti);
             r->phase = r->kind == NB_REQ_FORCE ? PH_FORCE : PH_INIT;
         } else if (r->phase == PH_STEP) {
             // the last scheduler launch finished before the previous tick ended
@@ -401,37 +473,130 @@ int tick(nb_server s)
             const int na = v.mail_h->n_active;
             if (!(t_next <= r->t_end)) {
                 r->final_copy = true;
-            } else if (na < 1 || na > r->n) {
-                r->pending = NB_ERR_STATE;
-            } else {
-                r->t_next = t_next;
-                r->n_active = na;
-                due_items(s, *r, v, na, items);
+                continue;
             }
+            if (na < 1 || na > r->n) {
+                r->pending = NB_ERR_STATE;
+                continue;
+            }
+            r->t_next = t_next;
+            r->n_active = na;
+            add_group(s, *r, v, v.irec, na, 1, ti);
+            CorrectJob j{};
+            j.s = v.s;
+            j.act = v.act;
+            j.na = na;
+            j.block0 = c_blocks;
+            j.t_new = t_next;
+            j.f = Out3{v.f_acc, v.f_jerk, v.f_pot, v.ld};
+            j.sd = v.sd;
+            j.err = err;
+            cjobs.push_back(j);
+            c_blocks += (na + CORRECT_THREADS - 1) / CORRECT_THREADS;
+            r->tick_steps++;
+        }
+        if (r->phase == PH_INIT || r->phase == PH_STEP) {
+            // the integration goes on: its next scheduler launch
+            SchedJob q{};
+            q.s = v.s;
+            q.sd = v.sd;
+            q.status = v.sched_status;
+            q.act = v.act;
+            q.irec = v.irec;
+            q.mail = v.mail_d;
+            q.err = err;
+            q.block0 = s_blocks;
+            q.ntiles = (r->n + SCHED_TILE - 1) / SCHED_TILE;
+            sjobs.push_back(q);
+            s_blocks += q.ntiles;
+            r->epoch = handle_take_epoch(r->h);
         }
     }
+
+    std::vector<WorkItem> &items = ti.items;
+    int n0 = 0, n1 = 0;
     if (!items.empty()) {
-        // longest items first: the persistent CTAs take them round-robin
-        std::stable_sort(items.begin(), items.end(), [](const WorkItem &a, const WorkItem &b) {
-            return (long long)a.ni * a.nj > (long long)b.ni * b.nj;
-        });
-        int rc = grow_items(s, items.size());
+        int rc = grow_scratch(s, ti.part_total, 0);
         if (rc) return rc;
-        std::memcpy(s->h_items, items.data(), items.size() * sizeof(WorkItem));
-        CKS(cudaMemcpyAsync(s->d_items, s->h_items, items.size() * sizeof(WorkItem),
-                            cudaMemcpyHostToDevice, st));
-        const int grid = std::min<int>((int)items.size(), s->grid);
-        CKS(launch_force_items(s->cfg.variant, s->threads, s->d_items, (int)items.size(), grid,
-                               st));
+        for (size_t k = 0; k < items.size(); ++k)
+            if (ti.part_off[k] >= 0) items[k].part = s->d_part + ti.part_off[k];
+        for (size_t g = 0; g < ti.groups.size(); ++g) ti.groups[g].part = s->d_part + ti.group_off[g];
+        // i-parallel items, then j-parallel ones, each longest first (the
+        // persistent CTAs take them round-robin)
+        const int nt = s->threads;
+        std::stable_sort(items.begin(), items.end(), [nt](const WorkItem &x, const WorkItem &y) {
+            if (x.kind != y.kind) return x.kind < y.kind;
+            return item_cost(x, nt) > item_cost(y, nt);
+        });
+        n0 = (int)(std::lower_bound(items.begin(), items.end(), 1,
+                                    [](const WorkItem &w, int k) { return w.kind < k; }) -
+                   items.begin());
+        n1 = (int)items.size() - n0;
+    }
+    // one upload of every descriptor
+    size_t off_items = 0, off_groups, off_c, off_s, total;
+    {
+        auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+        off_groups = up(off_items + items.size() * sizeof(WorkItem));
+        off_c = up(off_groups + ti.groups.size() * sizeof(SplitGroup));
+        off_s = up(off_c + cjobs.size() * sizeof(CorrectJob));
+        total = up(off_s + sjobs.size() * sizeof(SchedJob));
+    }
+    if (total > 0) {
+        int rc = grow_stage(s, total);
+        if (rc) return rc;
+        char *h = s->h_stage;
+        if (!items.empty()) std::memcpy(h + off_items, items.data(), items.size() * sizeof(WorkItem));
+        if (!ti.groups.empty())
+            std::memcpy(h + off_groups, ti.groups.data(), ti.groups.size() * sizeof(SplitGroup));
+        if (!cjobs.empty()) std::memcpy(h + off_c, cjobs.data(), cjobs.size() * sizeof(CorrectJob));
+        if (!sjobs.empty()) std::memcpy(h + off_s, sjobs.data(), sjobs.size() * sizeof(SchedJob));
+        CKS(cudaMemcpyAsync(s->d_stage, h, total, cudaMemcpyHostToDevice, st));
+    }
+    const WorkItem *d_items = reinterpret_cast<const WorkItem *>(s->d_stage + off_items);
+    long long launches = 0;
+
+    // the batched force
+    if (n1 > 0) {
+        CKS(cudaEventRecord(s->ev_fork, st));
+        CKS(cudaStreamWaitEvent(s->stream2, s->ev_fork, 0));
+        CKS(launch_force_items_jpar(s->cfg.variant, d_items + n0, n1, std::min(n1, s->grid_jpar),
+                                    s->stream2));
+        ++launches;
+        CKS(cudaEventRecord(s->ev_join, s->stream2));
+    }
+    if (n0 > 0) {
+        CKS(launch_force_items(s->cfg.variant, s->threads, d_items, n0, std::min(n0, s->grid), st));
+        ++launches;
+    }
+    if (n1 > 0) CKS(cudaStreamWaitEvent(st, s->ev_join, 0));
+    if (!ti.groups.empty()) {
+        const int ng = (int)ti.groups.size();
+        CKS(launch_split_reduce(reinterpret_cast<const SplitGroup *>(s->d_stage + off_groups), ng,
+                                std::min(ng, 4 * s->num_sms), st));
+        ++launches;
     }
 
-    // per-request kernels and copies after the force
-    const StepParams prm = server_params(s);
+    // initial steps of new integrations, then one corrector launch and one
+    // scheduler launch over all integrations
+    for (auto &r : s->inflight) {
+        if (r->pending || r->phase != PH_INIT) continue;
+        const HandleView v = view_of(*r);
+        CKS(cudaMemsetAsync(v.sd->hist, 0, NLEVEL * sizeof(int), st));
+        CKS(launch_init_steps(v.s, Out3{v.f_acc, v.f_jerk, v.f_pot, v.ld}, prm, v.sd,
+                              s->d_errs + r->slot, st));
+        ++launches;
+    }
+    CKS(launch_correct_multi(reinterpret_cast<const CorrectJob *>(s->d_stage + off_c),
+                             (int)cjobs.size(), c_blocks, prm, s->d_dtmin, st));
+    CKS(launch_sched_predict_multi(reinterpret_cast<const SchedJob *>(s->d_stage + off_s),
+                                   (int)sjobs.size(), s_blocks, prm.dt_max, true, st));
+    launches += (cjobs.empty() ? 0 : 1) + (sjobs.empty() ? 0 : 1) + (long long)admitted.size();
+
+    // results leave the GPU
     for (auto &r : s->inflight) {
         if (r->pending) continue;
         const HandleView v = view_of(*r);
-        unsigned *err = s->d_errs + r->slot;
-        const Out3 f{v.f_acc, v.f_jerk, v.f_pot, v.ld};
         const size_t row = (size_t)r->n * sizeof(double), pitch = (size_t)v.ld * sizeof(double);
         if (r->phase == PH_FORCE) {
             r->acc.resize(3 * (size_t)r->n);
@@ -442,12 +607,6 @@ int tick(nb_server s)
             CKS(cudaMemcpy2DAsync(r->jerk.data(), row, v.f_jerk, pitch, row, 3,
                                   cudaMemcpyDeviceToHost, st));
             CKS(cudaMemcpyAsync(r->pot.data(), v.f_pot, row, cudaMemcpyDeviceToHost, st));
-        } else if (r->phase == PH_INIT) {
-            CKS(cudaMemsetAsync(v.sd->hist, 0, NLEVEL * sizeof(int), st));
-            CKS(launch_init_steps(v.s, f, prm, v.sd, err, st));
-            r->epoch = handle_take_epoch(r->h);
-            CKS(launch_sched_predict(v.s, v.sd, v.sched_status, v.act, v.irec, v.mail_d,
-                                     prm.dt_max, true, err, st));
         } else if (r->phase == PH_STEP && r->final_copy) {
             r->out_pos.resize(3 * (size_t)r->n);
             r->out_vel.resize(3 * (size_t)r->n);
@@ -455,13 +614,6 @@ int tick(nb_server s)
                                   cudaMemcpyDeviceToHost, st));
             CKS(cudaMemcpy2DAsync(r->out_vel.data(), row, v.s.vel, pitch, row, 3,
                                   cudaMemcpyDeviceToHost, st));
-        } else if (r->phase == PH_STEP) {
-            CKS(launch_correct(v.s, v.act, r->n_active, r->t_next, f, prm, v.sd, err,
-                               s->d_dtmin, st));
-            r->block_steps++;
-            r->epoch = handle_take_epoch(r->h);
-            CKS(launch_sched_predict(v.s, v.sd, v.sched_status, v.act, v.irec, v.mail_d,
-                                     prm.dt_max, true, err, st));
         }
     }
     CKS(cudaMemcpyAsync(s->h_errs, s->d_errs, s->cfg.max_inflight * sizeof(unsigned),
@@ -469,11 +621,14 @@ int tick(nb_server s)
     CKS(cudaStreamSynchronize(st));
 
     // bookkeeping
-    double inter = 0.0;
-    for (auto &it : items) inter += (double)it.ni * (double)it.nj;
+    const double inter = ti.interactions;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         for (auto &r : s->inflight) {
+            r->interactions += r->tick_inter;
+            r->block_steps += r->tick_steps;
+            r->tick_inter = 0.0;
+            r->tick_steps = 0;
             const unsigned bits = r->slot >= 0 ? s->h_errs[r->slot] : 0u;
             if (r->pending || bits) {
                 finish_locked(s, *r, NB_STATUS_ERROR, r->pending ? r->pending : err_code(bits));
@@ -490,6 +645,7 @@ int tick(nb_server s)
                           s->inflight.end());
         s->st.ticks++;
         if (!items.empty()) s->st.force_launches++;
+        s->st.kernel_launches += launches;
         s->st.interactions += inter;
         s->st.busy_s += s->now() - t_begin;
         s->st.inflight = (int)s->inflight.size();
@@ -582,6 +738,9 @@ int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
     if (cudaSetDevice(s->dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->dev) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&s->d_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&s->h_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&s->d_dtmin, sizeof(unsigned long long)) != cudaSuccess ||
@@ -589,6 +748,9 @@ int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
         cudaMemset(s->d_dtmin, 0, sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->stream2) cudaStreamDestroy(s->stream2);
+        if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+        if (s->ev_join) cudaEventDestroy(s->ev_join);
         if (s->d_errs) cudaFree(s->d_errs);
         if (s->h_errs) cudaFreeHost(s->h_errs);
         if (s->d_dtmin) cudaFree(s->d_dtmin);
@@ -596,6 +758,7 @@ int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
     }
     s->threads = 128;
     s->grid = s->num_sms * batch_blocks_per_sm(c.variant, s->threads);
+    s->grid_jpar = s->num_sms * jpar_blocks_per_sm(c.variant);
     for (int k = c.max_inflight - 1; k >= 0; --k) s->free_slots.push_back(k);
     nb_server raw = s.release();
     raw->thread = std::thread(run, raw);
@@ -617,12 +780,16 @@ int nb_server_destroy(nb_server s)
     for (auto &kv : s->pool)
         for (nb_handle h : kv.second) nb_destroy(h);
     s->pool.clear();
-    if (s->d_items) cudaFree(s->d_items);
-    if (s->h_items) cudaFreeHost(s->h_items);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    if (s->d_part) cudaFree(s->d_part);
     cudaFree(s->d_errs);
     cudaFreeHost(s->h_errs);
     cudaFree(s->d_dtmin);
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->stream2);
+    cudaEventDestroy(s->ev_fork);
+    cudaEventDestroy(s->ev_join);
     delete s;
     return NB_OK;
 }

@@ -225,11 +225,13 @@ __device__ double quantize_log2(int e, double dt_old, double t_new, double dt_mi
 
 // ---- K4 --------------------------------------------------------------------
 
-__global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
-                          StepParams prm, SchedDev *sd, unsigned *err,
-                          unsigned long long *dtmin_hits, const double *t_dev)
+// K4 for active slot k (thread k of the corrector's grid).
+__device__ __forceinline__ void correct_body(const StateDev &s, const int *__restrict__ act, int na,
+                                             double t_new, const Out3 &f, const StepParams &prm,
+                                             SchedDev *sd, unsigned *err,
+                                             unsigned long long *dtmin_hits, const double *t_dev,
+                                             int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (t_dev)
         t_new = *t_dev + t_new;
     else if (k == 0)
@@ -323,14 +325,56 @@ __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, doubl
     s.dt[i] = dt_new;
 }
 
+__global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
+                          StepParams prm, SchedDev *sd, unsigned *err,
+                          unsigned long long *dtmin_hits, const double *t_dev)
+{
+    correct_body(s, act, na, t_new, f, prm, sd, err, dtmin_hits, t_dev,
+                 blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The job of CTA b in a list sorted by first CTA (block0 ascending).
+template <class Job>
+__device__ __forceinline__ int job_of(const Job *jobs, int njobs, int b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// K4 of many systems in one launch: CTA b serves the job whose CTA range holds b.
+__global__ void k_correct_multi(const CorrectJob *__restrict__ jobs, int njobs, StepParams prm,
+                                unsigned long long *dtmin_hits)
+{
+    const int q = job_of(jobs, njobs, blockIdx.x);
+    const CorrectJob &jb = jobs[q];
+    correct_body(jb.s, jb.act, jb.na, jb.t_new, jb.f, prm, jb.sd, jb.err, dtmin_hits, nullptr,
+                 (blockIdx.x - jb.block0) * blockDim.x + threadIdx.x);
+}
+
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new, const Out3 &f,
                            const StepParams &p, SchedDev *sd, unsigned *err,
                            unsigned long long *dtmin_hits, cudaStream_t st, const double *t_dev)
 {
     if (n_a <= 0) return cudaSuccess;
-    const int bs = 32;  // FP64-heavy: spread small active sets over many SMs
+    const int bs = CORRECT_THREADS;  // FP64-heavy: spread small active sets over many SMs
     k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits,
                                                    t_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct_multi(const CorrectJob *jobs, int njobs, int nblocks,
+                                 const StepParams &p, unsigned long long *dtmin_hits,
+                                 cudaStream_t st)
+{
+    if (njobs <= 0 || nblocks <= 0) return cudaSuccess;
+    k_correct_multi<<<nblocks, CORRECT_THREADS, 0, st>>>(jobs, njobs, p, dtmin_hits);
     return cudaGetLastError();
 }
 
@@ -441,10 +485,13 @@ __device__ __forceinline__ unsigned long long st_word(unsigned epoch, unsigned f
     return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | v;
 }
 
+// K5 + K1 for one tile of one system (ntiles CTAs serve the system; each takes
+// its tile number from a ticket, so tiles start in order).
 template <bool REC>
-__global__ void __launch_bounds__(SCHED_THREADS)
-    k_sched_predict(StateDev s, SchedDev *sd, unsigned long long *status, int *act,
-                    float4 *irec, Mailbox *mail, double dt_max, unsigned *err)
+__device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
+                                           unsigned long long *status, int *act, float4 *irec,
+                                           Mailbox *mail, double dt_max, unsigned *err,
+                                           int ntiles)
 {
     constexpr int NWORD = SCHED_TILE / 32;
     __shared__ unsigned s_flags[NWORD];
@@ -455,7 +502,6 @@ __global__ void __launch_bounds__(SCHED_THREADS)
     __shared__ unsigned s_occ[NLEVEL / 32];
     __shared__ double s_tnext, s_tcur;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ntiles = gridDim.x;
 
     // occupied step levels -> t_next
     static_assert(NLEVEL % 32 == 0 && NLEVEL / 32 <= SCHED_THREADS / 32, "levels");
@@ -649,6 +695,25 @@ __global__ void __launch_bounds__(SCHED_THREADS)
     }
 }
 
+template <bool REC>
+__global__ void __launch_bounds__(SCHED_THREADS)
+    k_sched_predict(StateDev s, SchedDev *sd, unsigned long long *status, int *act,
+                    float4 *irec, Mailbox *mail, double dt_max, unsigned *err)
+{
+    sched_body<REC>(s, sd, status, act, irec, mail, dt_max, err, gridDim.x);
+}
+
+// K5 + K1 of many systems in one launch (each system's tiles as above).
+template <bool REC>
+__global__ void __launch_bounds__(SCHED_THREADS)
+    k_sched_predict_multi(const SchedJob *__restrict__ jobs, int njobs, double dt_max)
+{
+    const int q = job_of(jobs, njobs, blockIdx.x);
+    const SchedJob &jb = jobs[q];
+    sched_body<REC>(jb.s, jb.sd, jb.status, jb.act, jb.irec, jb.mail, dt_max, jb.err,
+                    jb.ntiles);
+}
+
 cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long long *status,
                                  int *act, float4 *irec, Mailbox *mail_dev, double dt_max,
                                  bool want_rec, unsigned *err, cudaStream_t st)
@@ -660,6 +725,17 @@ cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long 
     else
         k_sched_predict<false><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, irec, mail_dev,
                                                             dt_max, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sched_predict_multi(const SchedJob *jobs, int njobs, int nblocks,
+                                       double dt_max, bool want_rec, cudaStream_t st)
+{
+    if (njobs <= 0 || nblocks <= 0) return cudaSuccess;
+    if (want_rec)
+        k_sched_predict_multi<true><<<nblocks, SCHED_THREADS, 0, st>>>(jobs, njobs, dt_max);
+    else
+        k_sched_predict_multi<false><<<nblocks, SCHED_THREADS, 0, st>>>(jobs, njobs, dt_max);
     return cudaGetLastError();
 }
 

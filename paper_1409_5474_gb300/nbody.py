@@ -118,7 +118,7 @@ class nb_server_stats(ctypes.Structure):
                 ("ticks", ctypes.c_longlong), ("force_launches", ctypes.c_longlong),
                 ("interactions", ctypes.c_double), ("busy_s", ctypes.c_double),
                 ("queued", ctypes.c_int), ("inflight", ctypes.c_int),
-                ("bytes_in_use", ctypes.c_size_t)]
+                ("bytes_in_use", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
