@@ -561,6 +561,31 @@ size_t handle_bytes(nb_handle h) { return h->bytes; }
 
 unsigned long long handle_take_epoch(nb_handle h) { return h->seq_next++; }
 
+void handle_attach(nb_handle h, int n)
+{
+    h->n = n;
+    h->have_particles = true;
+    h->initialised = false;
+    h->predicted = false;
+    h->sched_valid = false;
+    h->last_force_n = -1;
+}
+
+int handle_force(nb_handle h, int n_i, bool due, double eps2, unsigned *err, cudaStream_t st)
+{
+    if (n_i <= 0) return NB_OK;
+    const int variant = h->cfg.variant;
+    const ISet is = due ? due_set(h, n_i) : members_of(h, nullptr, n_i);
+    const ForcePlan p = plan_for(h, variant, n_i);
+    int rc = ensure_part(h, p, n_i);
+    if (rc) return rc;
+    const Out3 out{h->f_acc, h->f_jerk, h->f_pot, h->ld};
+    if (launch_force(variant, p, jset_of(h), is, eps2, h->part, h->split_cnt, out, err, st,
+                     nullptr) != cudaSuccess)
+        return NB_ERR_CUDA;
+    return NB_OK;
+}
+
 void handle_mark_initialised(nb_handle h, double t0)
 {
     h->initialised = true;

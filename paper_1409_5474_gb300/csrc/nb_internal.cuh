@@ -303,5 +303,12 @@ size_t handle_bytes(nb_handle h);
 unsigned long long handle_take_epoch(nb_handle h);
 // The caller has initialised h's steps and scheduler state at time t0.
 void handle_mark_initialised(nb_handle h, double t0);
+// The caller has written n particles into h's state (not yet initialised).
+void handle_attach(nb_handle h, int n);
+// The engine's planned force (K2 + folded K3) on h: all n members (due == false)
+// or the first n_i gathered records of its due set, softening eps2, into h's
+// f_acc / f_jerk / f_pot (slot-indexed); errors OR-ed into *err; queued on st.
+// May grow h's split scratch (synchronising h's stream). NB_OK or NB_ERR_*.
+int handle_force(nb_handle h, int n_i, bool due, double eps2, unsigned *err, cudaStream_t st);
 
 }  // namespace nb

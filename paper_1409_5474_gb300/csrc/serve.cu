@@ -77,6 +77,8 @@ struct Req {
 
 using ReqP = std::shared_ptr<Req>;
 
+constexpr int NSIDE = 4;  // side streams of the engine-planned force launches
+
 int capacity_class(int n)
 {
     int c = 256;
@@ -92,6 +94,8 @@ struct nb_server_s {
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;            // the j-parallel items, beside the rest
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side[NSIDE] = {};             // engine-planned force launches
+    cudaEvent_t ev_side[NSIDE] = {};
     std::chrono::steady_clock::time_point t0;
 
     std::mutex mu;
@@ -258,7 +262,15 @@ bool fits(nb_server s, const Req &r, size_t in_use)
 // The work items of one tick's batched force launch, with the scratch their
 // j-split groups need (float2 offsets and counter indices until the buffers are
 // sized; -1 = no split).
+// A group large enough for the engine's own planned kernels (one launch).
+struct EngineGroup {
+    Req *r;
+    int n_i;
+    bool due;
+};
+
 struct TickItems {
+    std::vector<EngineGroup> engine;
     std::vector<WorkItem> items;
     std::vector<long long> part_off;   // per item
     std::vector<SplitGroup> groups;
@@ -270,6 +282,11 @@ struct TickItems {
 // Smallest j-range of an item in a j-split group (i-parallel, j-parallel).
 constexpr int ITEM_MIN_J_IPAR = 1024;
 constexpr int ITEM_MIN_J_JPAR = 2048;
+// Groups of more i-rows than the j-parallel items take and at least this many
+// interactions run on the engine's planned kernels (tile / warp-group kernels
+// with their tuned j-splits) in a launch of their own, on one of the side
+// streams; smaller work shares the batched item launch.
+constexpr double ENGINE_MIN_INTERACTIONS = 4194304.0;
 
 // Items of n_i i-rows of irec (member rows when !gathered) against all r.n
 // j-records of r. Small i-sets become j-parallel items; the j-range is split
@@ -280,6 +297,13 @@ constexpr int ITEM_MIN_J_JPAR = 2048;
 void add_group(nb_server s, Req &r, const HandleView &v, const float4 *irec, int n_i,
                int gathered, TickItems &t)
 {
+    const double inter = (double)n_i * (double)r.n;
+    r.tick_inter += inter;
+    t.interactions += inter;
+    if (n_i > ITEM_JPAR_MAX_NI && inter >= ENGINE_MIN_INTERACTIONS) {
+        t.engine.push_back(EngineGroup{&r, n_i, gathered != 0});
+        return;
+    }
     const int ib = s->threads * 2;
     const bool jpar = n_i <= ITEM_JPAR_MAX_NI;
     const int nblk = jpar ? 1 : (n_i + ib - 1) / ib;
@@ -330,9 +354,6 @@ void add_group(nb_server s, Req &r, const HandleView &v, const float4 *irec, int
             t.part_off.push_back(poff);
         }
     }
-    const double inter = (double)n_i * (double)r.n;
-    r.tick_inter += inter;
-    t.interactions += inter;
 }
 
 // Per-thread work of an item, for ordering the list (longest first).
@@ -358,6 +379,7 @@ int upload(nb_server s, Req &r)
     cudaStream_t st = s->stream;
     const size_t row = (size_t)r.n * sizeof(double), pitch = (size_t)v.ld * sizeof(double);
     unsigned *err = s->d_errs + r.slot;
+    handle_attach(r.h, r.n);
     CKS(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
     CKS(cudaMemcpyAsync(v.s.m, r.m.data(), row, cudaMemcpyHostToDevice, st));
     CKS(cudaMemcpy2DAsync(v.s.pos, pitch, r.pos.data(), row, row, 3, cudaMemcpyHostToDevice, st));
@@ -557,8 +579,8 @@ int tick(nb_server s)
     long long launches = 0;
 
     // the batched force
+    if (n1 > 0 || !ti.engine.empty()) CKS(cudaEventRecord(s->ev_fork, st));
     if (n1 > 0) {
-        CKS(cudaEventRecord(s->ev_fork, st));
         CKS(cudaStreamWaitEvent(s->stream2, s->ev_fork, 0));
         CKS(launch_force_items_jpar(s->cfg.variant, d_items + n0, n1, std::min(n1, s->grid_jpar),
                                     s->stream2));
@@ -568,6 +590,24 @@ int tick(nb_server s)
     if (n0 > 0) {
         CKS(launch_force_items(s->cfg.variant, s->threads, d_items, n0, std::min(n0, s->grid), st));
         ++launches;
+    }
+    if (!ti.engine.empty()) {
+        // the large groups: the engine's planned kernels, spread over the side streams
+        const int nside = std::min<int>(NSIDE, (int)ti.engine.size());
+        for (int k = 0; k < nside; ++k) CKS(cudaStreamWaitEvent(s->side[k], s->ev_fork, 0));
+        for (size_t g = 0; g < ti.engine.size(); ++g) {
+            const EngineGroup &eg = ti.engine[g];
+            Req &r = *eg.r;
+            const int rc = handle_force(r.h, eg.n_i, eg.due, r.eps * r.eps, s->d_errs + r.slot,
+                                        s->side[g % NSIDE]);
+            if (rc == NB_ERR_CUDA) return rc;
+            if (rc) r.pending = rc;
+            ++launches;
+        }
+        for (int k = 0; k < nside; ++k) {
+            CKS(cudaEventRecord(s->ev_side[k], s->side[k]));
+            CKS(cudaStreamWaitEvent(st, s->ev_side[k], 0));
+        }
     }
     if (n1 > 0) CKS(cudaStreamWaitEvent(st, s->ev_join, 0));
     if (!ti.groups.empty()) {
@@ -644,7 +684,7 @@ int tick(nb_server s)
                                          [](const ReqP &r) { return r->phase == PH_FINISHED; }),
                           s->inflight.end());
         s->st.ticks++;
-        if (!items.empty()) s->st.force_launches++;
+        if (!items.empty() || !ti.engine.empty()) s->st.force_launches++;
         s->st.kernel_launches += launches;
         s->st.interactions += inter;
         s->st.busy_s += s->now() - t_begin;
@@ -703,6 +743,29 @@ void run(nb_server s)
 
 }  // namespace
 
+namespace {
+
+bool make_side_streams(nb_server s)
+{
+    for (int k = 0; k < NSIDE; ++k)
+        if (cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->ev_side[k], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+    return true;
+}
+
+void free_side_streams(nb_server s)
+{
+    for (int k = 0; k < NSIDE; ++k) {
+        if (s->side[k]) cudaStreamDestroy(s->side[k]);
+        if (s->ev_side[k]) cudaEventDestroy(s->ev_side[k]);
+        s->side[k] = nullptr;
+        s->ev_side[k] = nullptr;
+    }
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -741,6 +804,7 @@ int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
         cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        !make_side_streams(s.get()) ||
         cudaMalloc(&s->d_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&s->h_errs, c.max_inflight * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&s->d_dtmin, sizeof(unsigned long long)) != cudaSuccess ||
@@ -751,6 +815,7 @@ int nb_server_create(const nb_server_cfg *cfg, nb_server *out)
         if (s->stream2) cudaStreamDestroy(s->stream2);
         if (s->ev_fork) cudaEventDestroy(s->ev_fork);
         if (s->ev_join) cudaEventDestroy(s->ev_join);
+        free_side_streams(s.get());
         if (s->d_errs) cudaFree(s->d_errs);
         if (s->h_errs) cudaFreeHost(s->h_errs);
         if (s->d_dtmin) cudaFree(s->d_dtmin);
@@ -790,6 +855,7 @@ int nb_server_destroy(nb_server s)
     cudaStreamDestroy(s->stream2);
     cudaEventDestroy(s->ev_fork);
     cudaEventDestroy(s->ev_join);
+    free_side_streams(s);
     delete s;
     return NB_OK;
 }
