@@ -15,50 +15,9 @@
 #include <math.h>
 
 #include "nb_internal.cuh"
+#include "step_body.cuh"
 
 namespace nb {
-
-// ---- double -> double-single split without FP64 instructions ------------
-//
-// GB300's FP64 pipe is narrow (a warp-wide FP64 instruction occupies it for
-// ~64 cycles), so the records are split with integer operations: hi keeps the
-// leading 24 significant bits of x (truncated), lo is the remaining 29 bits,
-// converted to FP32 (rounded to 24 bits); x = hi + lo to ~48 bits. Values
-// below 2^-74 in magnitude keep hi only (their lo is < 2^-98); zero gives 0.
-
-__device__ __forceinline__ void split_ds(double x, float &hi, float &lo)
-{
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(u >> 63) << 31;
-    const int e = (int)((u >> 52) & 0x7ff) - 1023;  // unbiased exponent
-    if (e < -126) {                                 // zero or below the float range
-        hi = __uint_as_float(sign);
-        lo = __uint_as_float(sign);
-        return;
-    }
-    if (e > 127) {                                  // beyond the float range
-        hi = __uint_as_float(sign | 0x7f800000u);
-        lo = 0.f;
-        return;
-    }
-    const unsigned mant_hi = (unsigned)((u >> 29) & 0x7fffffu);
-    hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | mant_hi);
-    const unsigned rem = (unsigned)(u & ((1ull << 29) - 1ull));  // weight 2^(e-52)
-    if (e - 52 + 127 < 1 || rem == 0u) {             // 2^(e-52) not a normal float
-        lo = __uint_as_float(sign);
-        return;
-    }
-    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);
-    lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn(rem) * scale));
-}
-
-// FP32 value of x truncated to 24 significant bits (integer operations only).
-__device__ __forceinline__ float f32_trunc(double x)
-{
-    float hi, lo;
-    split_ds(x, hi, lo);
-    return hi;
-}
 
 // ---- K1 --------------------------------------------------------------------
 
@@ -113,216 +72,6 @@ cudaError_t launch_advance(double *t_dev, double dt, cudaStream_t st)
 {
     k_advance<<<1, 1, 0, st>>>(t_dev, dt);
     return cudaGetLastError();
-}
-
-// ---- step criterion and block quantization ---------------------------------
-
-__device__ __forceinline__ double norm3(double x, double y, double z)
-{
-    return sqrt(x * x + y * y + z * z);
-}
-
-// t is a whole multiple of the power of two d: t / d is exact, so test it for an
-// integer (equivalent to fmod(t, d) == 0 for power-of-two d, and cheaper).
-__device__ __forceinline__ bool divides(double t, double d)
-{
-    const double q = t * ldexp(1.0, -ilogb(d));
-    return q == trunc(q);
-}
-
-// Largest power of two <= raw (dt_max for raw >= dt_max or +inf), at most twice
-// dt_old, clamped to [dt_min, dt_max], halved until it divides t_new.
-__device__ double quantize(double raw, double dt_old, double t_new, double dt_min, double dt_max,
-                           bool *clamped)
-{
-    double d;
-    if (!(raw < dt_max)) {
-        d = dt_max;
-    } else {
-        int e;
-        frexp(raw, &e);
-        d = ldexp(1.0, e - 1);
-    }
-    if (dt_old > 0.0 && d > 2.0 * dt_old) d = 2.0 * dt_old;
-    if (d > dt_max) d = dt_max;
-    *clamped = false;
-    if (d < dt_min) {
-        d = dt_min;
-        *clamped = true;
-    }
-    while (d > dt_min && !divides(t_new, d)) d = 0.5 * d;
-    return d;
-}
-
-// Level of a power-of-two step: dt = dt_max * 2^-k.
-__device__ __forceinline__ int step_level(double dt, double dt_max)
-{
-    int k = ilogb(dt_max) - ilogb(dt);
-    return k < 0 ? 0 : (k >= NLEVEL ? NLEVEL - 1 : k);
-}
-
-// hist[level] += delta, one atomic per group of lanes with the same level.
-__device__ __forceinline__ void hist_add(int *hist, int level, int delta)
-{
-    const unsigned act = __activemask();
-    const unsigned same = __match_any_sync(act, level);
-    const int lane = threadIdx.x & 31;
-    if (lane == __ffs(same) - 1) atomicAdd(hist + level, delta * __popc(same));
-}
-
-__device__ __forceinline__ double dot3(const double *u, const double *v)
-{
-    return u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
-}
-
-// quantize() for raw = sqrt(num / den) without forming the ratio: the largest
-// power of two <= raw is 2^floor(floor(log2(num / den)) / 2), and
-// floor(log2(num / den)) comes from the exponents and the significands of num
-// and den. den == 0 means raw = +inf (dt_max); num == 0 means raw = 0 (dt_min).
-__device__ double quantize_sq(double num, double den, double dt_old, double t_new,
-                              double dt_min, double dt_max, bool *clamped)
-{
-    double d;
-    if (!(den > 0.0) || !(num == num)) {
-        d = dt_max;
-    } else if (!(num > 0.0)) {
-        d = 0.0;
-    } else {
-        const int en = ilogb(num), ed = ilogb(den);
-        const double mn = scalbn(num, -en), md = scalbn(den, -ed);  // in [1, 2)
-        const int e = en - ed - (mn < md ? 1 : 0);                   // floor(log2(num/den))
-        const int half = e >= 0 ? e / 2 : -((1 - e) / 2);            // floor(e / 2)
-        d = (half >= ilogb(dt_max)) ? dt_max : ldexp(1.0, half);
-    }
-    if (dt_old > 0.0 && d > 2.0 * dt_old) d = 2.0 * dt_old;
-    if (d > dt_max) d = dt_max;
-    *clamped = false;
-    if (d < dt_min) {
-        d = dt_min;
-        *clamped = true;
-    }
-    while (d > dt_min && !divides(t_new, d)) d = 0.5 * d;
-    return d;
-}
-
-// quantize() given e = floor(log2(raw^2)) (raw > 0 finite): the largest power of
-// two <= raw is 2^floor(e / 2).
-__device__ double quantize_log2(int e, double dt_old, double t_new, double dt_min, double dt_max,
-                                bool *clamped)
-{
-    const int half = e >= 0 ? e / 2 : -((1 - e) / 2);  // floor(e / 2)
-    double d = (half >= ilogb(dt_max)) ? dt_max : ldexp(1.0, half);
-    if (dt_old > 0.0 && d > 2.0 * dt_old) d = 2.0 * dt_old;
-    if (d > dt_max) d = dt_max;
-    *clamped = false;
-    if (d < dt_min) {
-        d = dt_min;
-        *clamped = true;
-    }
-    while (d > dt_min && !divides(t_new, d)) d = 0.5 * d;
-    return d;
-}
-
-// ---- K4 --------------------------------------------------------------------
-
-// K4 for active slot k (thread k of the corrector's grid).
-__device__ __forceinline__ void correct_body(const StateDev &s, const int *__restrict__ act, int na,
-                                             double t_new, const Out3 &f, const StepParams &prm,
-                                             SchedDev *sd, unsigned *err,
-                                             unsigned long long *dtmin_hits, const double *t_dev,
-                                             int k)
-{
-    if (t_dev)
-        t_new = *t_dev + t_new;
-    else if (k == 0)
-        sd->t_cur = t_new;
-    if (k >= na) return;
-    const int i = act ? act[k] : k;
-    const double dt = t_new - s.t[i];
-    const double dt_old = s.dt[i];
-    // block steps are powers of two, whose reciprocal is exact by exponent
-    // arithmetic; a shared step may be any number
-    const double idt = prm.shared_dt > 0.0 ? 1.0 / dt : ldexp(1.0, -ilogb(dt));
-    const double idt2 = idt * idt, idt3 = idt2 * idt;
-    const double dt2 = dt * dt;
-    double a1v[3], j1v[3], a2e[3], a3e[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long q = c * s.ld + i;
-        const double a0 = s.acc[q], j0 = s.jerk[q];
-        const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
-        // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
-        // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
-        // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
-        // v1 = vp + dt (A2/6 + A3/24) - the same corrector in fewer FP64 steps
-        const double da = a0 - a1;
-        const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
-        const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
-        const double x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), s.pos_p[q]);
-        const double v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), s.vel_p[q]);
-        const double a2 = A2 * idt2, a3 = A3 * idt3;
-        s.pos[q] = x1;
-        s.vel[q] = v1;
-        s.acc[q] = a1;
-        s.jerk[q] = j1;
-        a1v[c] = a1;
-        j1v[c] = j1;
-        a2e[c] = a2 + dt * a3;
-        a3e[c] = a3;
-        finite = finite && isfinite(x1) && isfinite(v1);
-    }
-    if (!finite) atomicOr(err, DERR_NONFINITE);
-    double dt_new;
-    if (prm.shared_dt > 0.0) {
-        dt_new = prm.shared_dt;
-    } else {
-        // Aarseth: dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2). Only the
-        // power-of-two floor of dt is needed: estimate floor(log2(dt^2)) in
-        // FP32 (relative error ~1e-6) and redo it exactly in FP64 only when the
-        // estimate lies within 1e-5 of a power of two, where the two could differ.
-        float af[3], jf[3], a2f[3], a3f[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            af[c] = f32_trunc(a1v[c]);
-            jf[c] = f32_trunc(j1v[c]);
-            a2f[c] = f32_trunc(a2e[c]);
-            a3f[c] = f32_trunc(a3e[c]);
-        }
-        const float Af = af[0] * af[0] + af[1] * af[1] + af[2] * af[2];
-        const float Jf = jf[0] * jf[0] + jf[1] * jf[1] + jf[2] * jf[2];
-        const float A2f = a2f[0] * a2f[0] + a2f[1] * a2f[1] + a2f[2] * a2f[2];
-        const float A3f = a3f[0] * a3f[0] + a3f[1] * a3f[1] + a3f[2] * a3f[2];
-        const float numf = (float)prm.eta * (sqrtf(Af * A2f) + Jf);
-        const float denf = sqrtf(Jf * A3f) + A2f;
-        const float qf = numf / denf;
-        int e2 = 0;
-        bool exact_needed = !(qf > 1e-30f && qf < 1e30f) || !(denf > 0.f);
-        if (!exact_needed) {
-            const int eb = (int)((__float_as_uint(qf) >> 23) & 0xffu) - 127;
-            const float mant = __uint_as_float((__float_as_uint(qf) & 0x007fffffu) | 0x3f800000u);
-            e2 = eb;
-            exact_needed = mant < 1.00001f || mant > 1.99998f;
-        }
-        bool clamped;
-        if (exact_needed) {
-            const double A = dot3(a1v, a1v), J = dot3(j1v, j1v);
-            const double A2 = dot3(a2e, a2e), A3 = dot3(a3e, a3e);
-            const double num = prm.eta * (sqrt(A * A2) + J);
-            const double den = sqrt(J * A3) + A2;
-            dt_new = quantize_sq(num, den, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
-        } else {
-            dt_new = quantize_log2(e2, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
-        }
-        if (clamped && dtmin_hits) atomicAdd(dtmin_hits, 1ull);
-        const int lo = step_level(dt_old, prm.dt_max), ln = step_level(dt_new, prm.dt_max);
-        if (lo != ln) {
-            hist_add(sd->hist, lo, -1);
-            hist_add(sd->hist, ln, +1);
-        }
-    }
-    s.t[i] = t_new;
-    s.dt[i] = dt_new;
 }
 
 __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
@@ -458,33 +207,6 @@ cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams
 
 // ---- K5 + K1: fused block scheduler and predictor -----------------------
 
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-constexpr unsigned long long LOOKBACK_LIMIT_NS = 4000000000ull;  // 4 s
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-constexpr unsigned ST_AGG = 1u, ST_PREFIX = 2u;
-
-__device__ __forceinline__ unsigned long long st_word(unsigned epoch, unsigned flag, unsigned v)
-{
-    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | v;
-}
-
 // K5 + K1 for one tile of one system (ntiles CTAs serve the system; each takes
 // its tile number from a ticket, so tiles start in order).
 template <bool REC>
@@ -537,37 +259,7 @@ __device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
     for (int r = 0; r < SCHED_PER_THREAD; ++r) {
         const int i = base + r * SCHED_THREADS + tid;
         bool due = false;
-        if (i < s.n) {
-            const double ti = s.t[i];
-            const double d = tn - ti;
-            const double d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
-            due = (ti + s.dt[i] == tn);
-            double xp[3], vp[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const long long q = c * s.ld + i;
-                const double x = s.pos[q], v = s.vel[q], a = s.acc[q], j = s.jerk[q];
-                xp[c] = fma(fma(fma(j, d6, 0.5 * a), d, v), d, x);
-                vp[c] = fma(fma(j, d2h, a), d, v);
-                s.pos_p[q] = xp[c];
-                s.vel_p[q] = vp[c];
-            }
-            if (REC) {
-                float hi[3], lo[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    split_ds(xp[c], hi[c], lo[c]);
-                }
-                float4 *rr = s.rec + (size_t)DS_REC * i;
-                keep[r][0] = make_float4(hi[0], hi[1], hi[2], f32_trunc(s.m[i]));
-                keep[r][1] = make_float4(lo[0], lo[1], lo[2], __int_as_float(i));
-                keep[r][2] =
-                    make_float4(f32_trunc(vp[0]), f32_trunc(vp[1]), f32_trunc(vp[2]), 0.f);
-                rr[0] = keep[r][0];
-                rr[1] = keep[r][1];
-                rr[2] = keep[r][2];
-            }
-        }
+        if (i < s.n) due = predict_one<REC>(s, i, tn, keep[r]);
         const unsigned b = __ballot_sync(0xffffffffu, due);
         if (lane == 0) s_flags[r * (SCHED_THREADS / 32) + warp] = b;
     }
