@@ -408,9 +408,12 @@ def run_ours(args):
     launches = 0
     force_ms = reduce_ms = 0.0
     force_launches = 0
-    other_ms = {"sched_ms": 0.0, "predict_ms": 0.0, "correct_ms": 0.0}
+    other_ms = {"sched_ms": 0.0, "predict_ms": 0.0, "correct_ms": 0.0, "fused_ms": 0.0}
+    fused_steps = 0
     block_steps = 0
-    hist = {"active_hist": [0] * 32, "force_ms_hist": [0.0] * 32, "inter_hist": [0.0] * 32}
+    hist = {"active_hist": [0] * 32, "force_ms_hist": [0.0] * 32, "inter_hist": [0.0] * 32,
+            "fused_step_ms_hist": [0.0] * 32}
+    fused_stage_ms = [0.0] * 4
     for k in range(args.warmup, args.warmup + args.steps):
         flush.fill_(float(k))                              # L2 flush between timed steps
         inter, ms, wall, nl, st, host_state = one_step(k, host_state)
@@ -424,6 +427,9 @@ def run_ours(args):
         for key in other_ms:
             other_ms[key] += st.get(key, 0.0)
         block_steps += st.get("block_steps", 0)
+        fused_steps += st.get("fused_steps", 0)
+        for q, x in enumerate(st.get("fused_stage_ms", [0.0] * 4)):
+            fused_stage_ms[q] += x
         for key in hist:
             for b, x in enumerate(st.get(key, [0] * 32)):
                 hist[key][b] += x
@@ -443,7 +449,11 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0)
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     value = units / secs / 1e9
-    achieved = FLOPS_PER_INTERACTION * tot_inter / (force_ms / 1e3) / 1e12 if force_ms else None
+    # the planned force launches' own interactions (the fused kernel's steps are
+    # timed as a whole and reported apart)
+    planned_inter = float(sum(hist["inter_hist"])) if wl["kind"] == "evolve" else tot_inter
+    achieved = (FLOPS_PER_INTERACTION * planned_inter / (force_ms / 1e3) / 1e12
+                if force_ms else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -453,16 +463,20 @@ def run_ours(args):
         "config": dict(config_of(wl, args.workload, variant),
                        parallelism=("replicas%d" % world) if world > 1 else "single GPU"),
         "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
-        "roofline": {"bound": "alu", "kernel": "k_force_tile32/k_force_jmode32 (pair force)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_force_tile32/k_force_wgrp32/k_force_tiny32 (planned pair force)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived; "
                                     "FP32 is not in MEASURED_PEAKS.json)" % sm_max,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "force_ms": force_ms, "reduce_ms": reduce_ms,
-                     "force_launches": force_launches},
+                     "force_launches": force_launches, "interactions": planned_inter},
         "kernel_ms": dict(other_ms, force_ms=force_ms, reduce_ms=reduce_ms),
         "block_steps": block_steps,
+        "fused_steps": fused_steps,
+        "fused_stage_ms": {"predict_flags": fused_stage_ms[0], "gather": fused_stage_ms[1],
+                           "force": fused_stage_ms[2], "reduce_correct": fused_stage_ms[3]},
         "by_log2_active": {k: [round(x, 3) if isinstance(x, float) else x for x in v]
                            for k, v in hist.items()},
         "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,

@@ -63,6 +63,14 @@ extern "C" {
 
 /* ---- configuration ------------------------------------------------------ */
 #define NB_FLAG_TIMING 1 /* time every kernel launch with CUDA events (nb_stats) */
+/* Block steps of NB_F32 / NB_F32DS handles normally run in the fused
+ * persistent kernel: one cooperative launch takes block steps (scheduler +
+ * predictor, force, reduction, corrector, with grid-wide barriers between
+ * the stages) until a due set larger than NB_FUSED_MAX_NA or t_end, so small
+ * steps need no host round trip; larger due sets go to the planned force
+ * kernels. NB_FLAG_NO_FUSED takes every block step with separate launches. */
+#define NB_FLAG_NO_FUSED 2
+#define NB_FUSED_MAX_NA 1024
 
 typedef struct nb_config {
     int n_max;           /* particle capacity of the handle, >= 1 */
@@ -98,6 +106,11 @@ typedef struct nb_stats {
     long long kernel_launches;  /* CUDA kernels this library launched */
     double force_ms_hist[32];   /* force kernel time by floor(log2(N_i)) (NB_FLAG_TIMING) */
     double inter_hist[32];      /* interactions by floor(log2(N_i)) */
+    long long fused_steps;      /* block steps taken inside the fused kernel */
+    long long fused_launches;   /* fused-kernel launches */
+    double fused_ms;            /* fused-kernel time (NB_FLAG_TIMING) */
+    double fused_stage_ms[4];   /* fused kernel: predict + flags, gather, force, reduce + correct */
+    double fused_step_ms_hist[32]; /* fused kernel: step time by floor(log2(N_active)) */
 } nb_stats;
 
 typedef struct nb_handle_s *nb_handle;

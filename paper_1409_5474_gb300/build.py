@@ -23,6 +23,11 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"
                      "-I", INCLUDE, "-Xptxas", "-warn-spills"]
 
 
+# Per-file flags: the fused persistent kernel reads data that other CTAs of the
+# same launch wrote, so its plain global loads are cached in L2 only.
+FILE_FLAGS = {"persist.cu": ["-Xptxas", "-dlcm=cg"]}
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
         if cand and (os.path.isabs(cand) and os.path.exists(cand) or not os.path.isabs(cand)):
@@ -47,7 +52,8 @@ def up_to_date() -> bool:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    cmd = ([nvcc()] + NVCC_FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + list(extra)
+           + ["-c", src, "-o", obj])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

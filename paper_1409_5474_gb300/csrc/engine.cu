@@ -40,7 +40,7 @@ bool is_pow2(double x)
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Timing: pairs of events recorded around launches, harvested at sync points.
-enum TimerKind { T_FORCE = 0, T_REDUCE, T_PREDICT, T_CORRECT, T_SCHED, T_NKIND };
+enum TimerKind { T_FORCE = 0, T_REDUCE, T_PREDICT, T_CORRECT, T_SCHED, T_FUSED, T_NKIND };
 
 struct Timer {
     std::vector<cudaEvent_t> free_ev;
@@ -50,7 +50,7 @@ struct Timer {
         int bucket;  // floor(log2 n_i) for force launches, else -1
     };
     std::vector<Pending> pending;
-    double ms[T_NKIND] = {0, 0, 0, 0, 0};
+    double ms[T_NKIND] = {0, 0, 0, 0, 0, 0};
     double force_hist[32] = {0};
 
     cudaEvent_t get()
@@ -135,6 +135,14 @@ struct nb_handle_s {
     bool sched_valid = false;              // sd->t_cur / hist match the particles
     double t_cur = 0.0;                    // host mirror of the last block time
     cudaEvent_t ev_sched = nullptr;
+
+    // fused persistent block steps (allocated at first use)
+    int fused_grid = -1;                  // CTAs per launch; 0 = not available
+    float2 *fused_part = nullptr;
+    size_t fused_part_cap = 0;            // float2
+    int *fused_cnt = nullptr;
+    unsigned *fused_bar = nullptr;
+    FusedStats *fused_stats = nullptr;
 
     size_t bytes = 0;  // device bytes held
 
@@ -490,6 +498,63 @@ int do_init(nb_handle h)
     return NB_OK;
 }
 
+// Whether nb_step takes small block steps in the fused persistent kernel;
+// allocates its scratch at first use.
+bool fused_ready(nb_handle h)
+{
+    if (h->cfg.variant == NB_F64 || (h->cfg.flags & NB_FLAG_NO_FUSED) ||
+        h->cfg.shared_dt > 0.0)
+        return false;
+    if (h->fused_grid < 0) h->fused_grid = fused_grid(h->dev);
+    const int g = h->fused_grid;
+    if (g <= 0) return false;
+    if ((h->n + g - 1) / g > FUSED_MAX_WORDS * 32) return false;
+    if (!h->fused_cnt) {
+        const size_t part = fused_part_float2s(g, NB_FUSED_MAX_NA);
+        const size_t add = part * sizeof(float2) + g * sizeof(int) + 256 + sizeof(FusedStats);
+        if (h->cfg.budget_bytes && h->bytes + add > h->cfg.budget_bytes) return false;
+        if (cudaMalloc(&h->fused_part, part * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&h->fused_cnt, g * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->fused_bar, 256) != cudaSuccess ||
+            cudaMalloc(&h->fused_stats, sizeof(FusedStats)) != cudaSuccess ||
+            cudaMemset(h->fused_stats, 0, sizeof(FusedStats)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(h->fused_part);
+            cudaFree(h->fused_cnt);
+            cudaFree(h->fused_bar);
+            cudaFree(h->fused_stats);
+            h->fused_part = nullptr;
+            h->fused_cnt = nullptr;
+            h->fused_bar = nullptr;
+            h->fused_stats = nullptr;
+            h->fused_grid = 0;
+            return false;
+        }
+        h->fused_part_cap = part;
+        h->bytes += add;
+    }
+    return true;
+}
+
+// Add the steps the fused kernel took to the handle's counters (and clear them).
+int fold_fused_stats(nb_handle h)
+{
+    if (!h->fused_stats) return NB_OK;
+    FusedStats f{};
+    CK(h, cudaMemcpyAsync(&f, h->fused_stats, sizeof f, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemsetAsync(h->fused_stats, 0, sizeof f, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->stats.block_steps += (long long)f.steps;
+    h->stats.fused_steps += (long long)f.steps;
+    h->stats.interactions += f.interactions;
+    for (int k = 0; k < 32; ++k) {
+        h->stats.active_hist[k] += (long long)f.active_hist[k];
+        h->stats.fused_step_ms_hist[k] += 1e-6 * (double)f.step_ns_hist[k];
+    }
+    for (int k = 0; k < 4; ++k) h->stats.fused_stage_ms[k] += 1e-6 * (double)f.phase_ns[k];
+    return NB_OK;
+}
+
 void sync_stats_counters(nb_handle h)
 {
     unsigned long long hits = 0;
@@ -504,6 +569,7 @@ void sync_stats_counters(nb_handle h)
         h->stats.predict_ms = h->timer.ms[T_PREDICT];
         h->stats.correct_ms = h->timer.ms[T_CORRECT];
         h->stats.sched_ms = h->timer.ms[T_SCHED];
+        h->stats.fused_ms = h->timer.ms[T_FUSED];
         for (int k = 0; k < 32; ++k) h->stats.force_ms_hist[k] = h->timer.force_hist[k];
     }
 }
@@ -788,6 +854,10 @@ int nb_destroy(nb_handle h)
     cudaFree(h->d_energy);
     cudaFree(h->sd);
     cudaFree(h->sched_status);
+    cudaFree(h->fused_part);
+    cudaFree(h->fused_cnt);
+    cudaFree(h->fused_bar);
+    cudaFree(h->fused_stats);
     if (h->ev_sched) cudaEventDestroy(h->ev_sched);
     if (h->mail_h) cudaFreeHost(h->mail_h);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -1122,12 +1192,41 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         // block steps: the fused scheduler + predictor publishes (t_next, N_active)
         // to the mailbox; the force, corrector and the next scheduler launch are
         // queued as soon as it is read
+        const bool fused = fused_ready(h);
+        FusedArgs fa{};
+        if (fused) {
+            fa.s = s;
+            fa.sd = h->sd;
+            fa.act = h->act;
+            fa.irec = h->irec;
+            fa.mail = h->mail_d;
+            fa.f = f;
+            fa.prm = prm;
+            fa.eps2f = (float)(h->cfg.eps * h->cfg.eps);
+            fa.na_max = NB_FUSED_MAX_NA;
+            fa.t_end = t_end;
+            fa.part = h->fused_part;
+            fa.cnt = h->fused_cnt;
+            fa.bar = h->fused_bar;
+            fa.err = h->d_err;
+            fa.dtmin_hits = h->d_dtmin;
+            fa.stats = h->fused_stats;
+        }
         auto launch_sched = [&]() -> int {
             const unsigned long long ep = h->seq_next++;
-            int r = timed(h, T_SCHED, [&] {
-                return launch_sched_predict(s, h->sd, h->sched_status, h->act, h->irec,
-                                            h->mail_d, prm.dt_max, rec, h->d_err, h->stream);
-            });
+            int r;
+            if (fused) {
+                r = timed(h, T_FUSED, [&] {
+                    return launch_fused_steps(fa, h->fused_grid, h->cfg.variant == NB_F32DS,
+                                              h->stream);
+                });
+                h->stats.fused_launches++;
+            } else {
+                r = timed(h, T_SCHED, [&] {
+                    return launch_sched_predict(s, h->sd, h->sched_status, h->act, h->irec,
+                                                h->mail_d, prm.dt_max, rec, h->d_err, h->stream);
+                });
+            }
             if (r) return r;
             CK(h, cudaEventRecord(h->ev_sched, h->stream));
             (void)ep;
@@ -1159,6 +1258,10 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
     h->predicted = false;
     h->last_force_n = -1;
     rc = check_err(h);
+    {
+        const int rc2 = fold_fused_stats(h);
+        if (!rc) rc = rc2;
+    }
     sync_stats_counters(h);
     if (st) {
         nb_stats d = h->stats;
@@ -1177,6 +1280,11 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             d.inter_hist[k] -= before.inter_hist[k];
         }
         d.kernel_launches -= before.kernel_launches;
+        d.fused_steps -= before.fused_steps;
+        d.fused_launches -= before.fused_launches;
+        d.fused_ms -= before.fused_ms;
+        for (int k = 0; k < 4; ++k) d.fused_stage_ms[k] -= before.fused_stage_ms[k];
+        for (int k = 0; k < 32; ++k) d.fused_step_ms_hist[k] -= before.fused_step_ms_hist[k];
         *st = d;
     }
     return rc;

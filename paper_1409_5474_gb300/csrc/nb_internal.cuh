@@ -270,6 +270,54 @@ struct SchedJob {
 cudaError_t launch_sched_predict_multi(const SchedJob *jobs, int njobs, int nblocks,
                                        double dt_max, bool want_rec, cudaStream_t st);
 
+// ---- fused persistent block steps (persist.cu) ------------------------------
+
+// Counters of the steps a fused launch took itself (added, not reset, by the kernel).
+struct FusedStats {
+    unsigned long long steps;
+    double interactions;
+    unsigned long long active_hist[32];
+    unsigned long long phase_ns[4];     // CTA 0's time in stages A, B, C, D (globaltimer)
+    unsigned long long step_ns_hist[32];  // step time by floor(log2 N_active)
+};
+
+// One cooperative launch of the fused block-step kernel on a system whose
+// state is corrected at sd->t_cur with a valid level histogram (as after K4):
+// it takes block steps while the due set has at most na_max members and
+// t_next <= t_end; at the first step that fails either test it has predicted
+// every particle to that t_next and gathered the due set (act, irec), then
+// publishes (epoch, t_next, N_active) to the mailbox exactly as K5 + K1 do,
+// so the caller continues with the planned kernels. part: j-chunk partials
+// (fused_part_floats2(grid, na_max) float2); cnt: grid ints; bar: 3 words,
+// zero at launch (the launcher clears them).
+struct FusedArgs {
+    StateDev s;
+    SchedDev *sd;
+    int *act;
+    float4 *irec;
+    Mailbox *mail;
+    Out3 f;
+    StepParams prm;
+    float eps2f;
+    int na_max;
+    double t_end;
+    float2 *part;
+    int *cnt;
+    unsigned *bar;
+    unsigned *err;
+    unsigned long long *dtmin_hits;
+    FusedStats *stats;
+};
+
+constexpr int FUSED_THREADS = 256;
+constexpr int FUSED_MAX_WORDS = 256;  // due-flag words per CTA: n <= 8192 x grid
+
+// CTAs of the fused launch on this device (one per SM); 0 if the kernel cannot
+// be launched cooperatively.
+int fused_grid(int device);
+size_t fused_part_float2s(int grid, int na_max);
+cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st);
+
 // Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
 cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,
                           const double *pot, double *out2, cudaStream_t st);

@@ -1,0 +1,459 @@
+// Fused persistent block steps: one cooperative launch takes block step after
+// block step of one system with grid-wide barriers between the stages, so a
+// step with a small due set (the common case of block time steps, Sect. III:
+// most block times have only a few particles due) costs no host round trip
+// and no launch gaps:
+//   A  t_next from the level histogram; every CTA predicts its contiguous
+//      range of particles (K1, FP64 + double-single records) and flags the
+//      due ones;                                            -- barrier
+//   B  the due set is compacted in ascending index (CTA counts, prefix over
+//      the CTAs) with its records gathered; if t_next > t_end or the due set
+//      is larger than na_max the kernel publishes (epoch, t_next, N_active)
+//      to the mailbox like K5 + K1 and returns;             -- barrier
+//   C  pair force (K2): warp items of four due particles against a j-chunk,
+//      lanes over j, double-single partials per chunk;      -- barrier
+//   D  one warp per due particle sums its chunk partials in chunk order (K3)
+//      and corrects it (K4: Hermite corrector, Aarseth step, histogram);
+//                                                            -- barrier
+// Every inter-CTA wait is bounded; a CTA that gives up raises the abort flag
+// and all CTAs leave at their next barrier (the host then reports a timeout).
+// This file is compiled with global loads cached in L2 only (-dlcm=cg): data
+// written by other CTAs in the same launch must not be served from a stale L1.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ds.cuh"
+#include "nb_internal.cuh"
+#include "step_body.cuh"
+
+namespace nb {
+
+constexpr unsigned long long BARRIER_LIMIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1]
+// is the generation, bar[2] the abort flag (all zero at launch). The last CTA
+// to arrive resets the count and releases the next generation; the others
+// wait for it, bounded by BARRIER_LIMIT_NS or until another CTA gave up.
+// Returns false once any CTA has given up. gen: thread 0's generation.
+__device__ bool grid_barrier(unsigned *bar, unsigned &gen)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gen + 1u;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            st_release_u32(&bar[1], target);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar[1]) != target) {
+                if (ld_acquire_u32(&bar[2]) != 0u) {
+                    ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
+                    atomicExch(&bar[2], 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        gen = target;
+        s_ok = ok && ld_acquire_u32(&bar[2]) == 0u;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// K2 for one warp item: due slots k0 .. k0 + 3 (gathered records in irec)
+// against j-records [j0, j1) of the system; the lanes take j = j0 + lane,
+// j0 + lane + 32, ...; FP32 sums over at most 32 j per lane are folded into
+// double-single totals, which meet in a fixed xor tree; lane q < 28 stores
+// total q = (slot q / 7, component q % 7) to the chunk's partials.
+template <bool DS>
+__device__ __forceinline__ void warp_item(const FusedArgs &a, int na, int k0, int j0, int j1,
+                                          int chunk)
+{
+    constexpr int G = 4;
+    const int lane = threadIdx.x & 31;
+    const float eps2f = a.eps2f;
+    float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
+    int iid[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const int slot = min(k0 + p, na - 1);  // idle slots copy the last one
+        const float4 *r = a.irec + (size_t)DS_REC * slot;
+        const float4 A = __ldcg(r), B = __ldcg(r + 1), C = __ldcg(r + 2);
+        xh[p] = A.x; yh[p] = A.y; zh[p] = A.z;
+        xl[p] = B.x; yl[p] = B.y; zl[p] = B.z;
+        vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
+        iid[p] = __float_as_int(B.w);
+    }
+    dsf S[G][7];
+#pragma unroll
+    for (int p = 0; p < G; ++p)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) S[p][c] = dsf{0.f, 0.f};
+    const float4 *jr = a.s.rec;
+    for (int jb = j0; jb < j1; jb += 32 * 32) {
+        const int je = min(j1, jb + 32 * 32);
+        float ta[G][3], tjv[G][3], tp[G];
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ta[p][c] = tjv[p][c] = 0.f;
+            tp[p] = 0.f;
+        }
+#pragma unroll 2
+        for (int j = jb + lane; j < je; j += 32) {
+            const float4 A = __ldcg(jr + (size_t)DS_REC * j);
+            const float4 C = __ldcg(jr + (size_t)DS_REC * j + 2);
+            float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (DS) B = __ldcg(jr + (size_t)DS_REC * j + 1);
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (A.x - xh[p]) + (B.x - xl[p]);
+                    dy = (A.y - yh[p]) + (B.y - yl[p]);
+                    dz = (A.z - zh[p]) + (B.z - zl[p]);
+                } else {
+                    dx = A.x - xh[p];
+                    dy = A.y - yh[p];
+                    dz = A.z - zh[p];
+                }
+                const float dvx = C.x - vx[p], dvy = C.y - vy[p], dvz = C.z - vz[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float rinv = rsqrtf(r2);
+                rinv = (j == iid[p]) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = A.w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float beta = -3.f * ((mr3 * rinv2) * rv);
+                tp[p] += mrinv;
+                ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                tjv[p][0] = fmaf(beta, dx, fmaf(mr3, dvx, tjv[p][0]));
+                tjv[p][1] = fmaf(beta, dy, fmaf(mr3, dvy, tjv[p][1]));
+                tjv[p][2] = fmaf(beta, dz, fmaf(mr3, dvz, tjv[p][2]));
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ds_acc(S[p][c], dsf{ta[p][c], 0.f});
+                ds_acc(S[p][3 + c], dsf{tjv[p][c], 0.f});
+            }
+            ds_acc(S[p][6], dsf{tp[p], 0.f});
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < G; ++p)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ds_acc(S[p][c], ds_shfl_xor(S[p][c], o));
+        }
+#pragma unroll
+    for (int q = 0; q < G * 7; ++q) {
+        const int p = q / 7, c = q % 7;
+        if (lane == q && k0 + p < na)
+            a.part[((size_t)chunk * 7 + c) * na + k0 + p] = make_float2(S[p][c].hi, S[p][c].lo);
+    }
+}
+
+// The j-chunks of a step with na due particles on n: about two warp items per
+// warp of the grid, at least 256 j per chunk (a function of (na, n, grid) only).
+__device__ __forceinline__ void chunking(int na, int n, int total_warps, int &nchunk, int &jc)
+{
+    const int ng = (na + 3) / 4;
+    int nc = (2 * total_warps + ng - 1) / ng;
+    nc = max(1, min(nc, (n + 255) / 256));
+    jc = (n + nc - 1) / nc;
+    jc = (jc + 31) & ~31;
+    nchunk = (n + jc - 1) / jc;
+}
+
+template <bool DS>
+__global__ void __launch_bounds__(FUSED_THREADS)
+    k_fused_steps(FusedArgs a)
+{
+    constexpr int NT = FUSED_THREADS, NW = NT / 32;
+    __shared__ unsigned s_flags[FUSED_MAX_WORDS];
+    __shared__ int s_woff[FUSED_MAX_WORDS];
+    __shared__ int s_wsum[NW];
+    __shared__ int s_total, s_base, s_na;
+    __shared__ double s_tn;
+    __shared__ unsigned long long s_hist[32], s_step_ns[32], s_phase[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, bid = blockIdx.x;
+    const StateDev &s = a.s;
+    const int n = s.n;
+    const int per = (n + G - 1) / G;
+    const int p0 = min(n, bid * per), p1 = min(n, p0 + per);
+    const int nwords = (p1 - p0 + 31) / 32;
+    const int total_warps = G * NW;
+    const int gw = bid * NW + warp;
+    unsigned gen = 0;
+    bool ok = true;
+    double t_cur = __ldcg(&a.sd->t_cur);
+    const unsigned long long epoch = __ldcg(&a.sd->seq);
+    unsigned long long steps = 0;
+    double inter = 0.0;
+    if (tid < 32) s_hist[tid] = s_step_ns[tid] = 0ull;
+    if (tid < 4) s_phase[tid] = 0ull;
+    unsigned long long t_mark = 0;  // CTA 0, thread 0: stage boundaries
+    if (bid == 0 && tid == 0) t_mark = globaltimer_ns();
+    unsigned long long t_step = t_mark;
+
+    for (;;) {
+        // A: t_next = next multiple after t_cur of the smallest occupied step
+        if (warp == 0) {
+            static_assert(NLEVEL == 64, "two ballot words of levels");
+            const bool o0 = __ldcg(a.sd->hist + lane) > 0;
+            const bool o1 = __ldcg(a.sd->hist + 32 + lane) > 0;
+            const unsigned b0 = __ballot_sync(0xffffffffu, o0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, o1);
+            if (lane == 0) {
+                const int kmax = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : 0);
+                const double dm = ldexp(a.prm.dt_max, -kmax);
+                s_tn = (floor(t_cur * (1.0 / dm)) + 1.0) * dm;
+            }
+        }
+        __syncthreads();
+        const double tn = s_tn;
+        for (int w0 = 0; w0 < nwords; w0 += NW) {
+            const int i = p0 + w0 * 32 + tid;
+            float4 rec[DS_REC];
+            bool due = false;
+            if (i < p1) due = predict_one<true>(s, i, tn, rec);
+            const unsigned b = __ballot_sync(0xffffffffu, due);
+            if (lane == 0 && w0 + warp < nwords) s_flags[w0 + warp] = b;
+        }
+        __syncthreads();
+        // word offsets inside the CTA (exclusive scan of the popcounts)
+        for (int w0 = 0; w0 < nwords; w0 += NT) {
+            const int w = w0 + tid;
+            const int v = w < nwords ? __popc(s_flags[w]) : 0;
+            const int incl = warp_incl_scan(v);
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                const int x = lane < NW ? s_wsum[lane] : 0;
+                const int xi = warp_incl_scan(x);
+                if (lane < NW) s_wsum[lane] = xi - x;
+                if (lane == NW - 1) s_total = xi;
+            }
+            __syncthreads();
+            const int carry = (w0 == 0) ? 0 : s_base;  // total of the previous rounds
+            if (w < nwords) s_woff[w] = carry + s_wsum[warp] + incl - v;
+            __syncthreads();
+            if (tid == 0) s_base = carry + s_total;
+            __syncthreads();
+        }
+        if (tid == 0) a.cnt[bid] = nwords > 0 ? s_base : 0;
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[0] += t - t_mark;
+            t_mark = t;
+        }
+
+        // B: this CTA's offset and the due count; gather the due set
+        if (warp == 0) {
+            int before = 0, all = 0;
+            for (int q = lane; q < G; q += 32) {
+                const int c = __ldcg(a.cnt + q);
+                all += c;
+                if (q < bid) before += c;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                before += __shfl_xor_sync(0xffffffffu, before, o);
+                all += __shfl_xor_sync(0xffffffffu, all, o);
+            }
+            if (lane == 0) {
+                s_base = before;
+                s_na = all;
+            }
+        }
+        __syncthreads();
+        const int na = s_na, base = s_base;
+        for (int w = warp; w < nwords; w += NW) {
+            const unsigned b = s_flags[w];
+            if (b & (1u << lane)) {
+                const int i = p0 + w * 32 + lane;
+                const int slot = base + s_woff[w] + __popc(b & ((1u << lane) - 1u));
+                a.act[slot] = i;
+                const float4 *r = s.rec + (size_t)DS_REC * i;
+                float4 *g = a.irec + (size_t)DS_REC * slot;
+                g[0] = __ldcg(r);
+                g[1] = __ldcg(r + 1);
+                g[2] = __ldcg(r + 2);
+            }
+        }
+        const bool stop = !(tn <= a.t_end) || na < 1 || na > a.na_max;
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[1] += t - t_mark;
+            t_mark = t;
+        }
+        if (stop) {
+            // hand the step to the caller exactly as the scheduler kernel would
+            if (bid == 0 && tid == 0) {
+                a.sd->t_cur = t_cur;
+                a.sd->n_active = na;
+                a.mail->t_next = tn;
+                a.mail->n_active = na;
+                __threadfence_system();
+                a.mail->seq = epoch;
+                a.sd->seq = epoch + 1ull;
+            }
+            break;
+        }
+
+        // C: pair force, warp items (4 due slots x one j-chunk)
+        int nchunk, jc;
+        chunking(na, n, total_warps, nchunk, jc);
+        const int ng = (na + 3) / 4;
+        for (int it = gw; it < ng * nchunk; it += total_warps) {
+            const int g = it / nchunk, c = it - g * nchunk;
+            const int j0 = c * jc;
+            warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
+        }
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[2] += t - t_mark;
+            t_mark = t;
+        }
+
+        // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
+        for (int k = gw; k < na; k += total_warps) {
+            dsf v[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] = dsf{0.f, 0.f};
+            for (int c = lane; c < nchunk; c += 32) {
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    const float2 x = __ldcg(a.part + ((size_t)c * 7 + q) * na + k);
+                    ds_acc(v[q], dsf{x.x, x.y});
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ds_acc(v[q], ds_shfl_xor(v[q], o));
+            if (lane == 0) {
+                const Out3 &f = a.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    f.acc[q * f.ld + k] = ds_to_double(v[q]);
+                    f.jerk[q * f.ld + k] = ds_to_double(v[3 + q]);
+                }
+                f.pot[k] = -ds_to_double(v[6]);
+                correct_body(s, a.act, na, tn, f, a.prm, a.sd, a.err, a.dtmin_hits, nullptr, k);
+            }
+        }
+        if (bid == 0 && tid == 0) {
+            ++steps;
+            inter += (double)na * (double)n;
+            int lg = 0;
+            while ((2LL << lg) <= na && lg < 31) ++lg;
+            s_hist[lg] += 1ull;
+        }
+        t_cur = tn;
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[3] += t - t_mark;
+            t_mark = t;
+            int lg = 0;
+            while ((2LL << lg) <= na && lg < 31) ++lg;
+            s_step_ns[lg] += t - t_step;
+            t_step = t;
+        }
+    }
+    if (!ok && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+    if (bid == 0) {
+        __syncthreads();
+        if (tid == 0) {
+            a.stats->steps += steps;
+            a.stats->interactions += inter;
+        }
+        if (tid < 32) {
+            a.stats->active_hist[tid] += s_hist[tid];
+            a.stats->step_ns_hist[tid] += s_step_ns[tid];
+        }
+        if (tid < 4) a.stats->phase_ns[tid] += s_phase[tid];
+    }
+}
+
+int fused_grid(int device)
+{
+    int coop = 0, sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_steps<true>, FUSED_THREADS,
+                                                      0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (!coop || per < 1) return 0;
+    return sms * (per >= 2 ? 2 : 1);
+}
+
+size_t fused_part_float2s(int grid, int na_max)
+{
+    // nchunk * na <= (2 W / ceil(na/4) + 1) * na <= 8 W + na for W warps
+    const size_t w = (size_t)grid * (FUSED_THREADS / 32);
+    return 7 * (8 * w + (size_t)na_max + 64);
+}
+
+cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    FusedArgs copy = a;
+    void *args[] = {&copy};
+    const void *fn = ds ? (const void *)k_fused_steps<true> : (const void *)k_fused_steps<false>;
+    return cudaLaunchCooperativeKernel(fn, grid, FUSED_THREADS, args, 0, st);
+}
+
+}  // namespace nb

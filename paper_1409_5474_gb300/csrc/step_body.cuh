@@ -202,7 +202,7 @@ static __device__ double quantize_log2(int e, double dt_old, double t_new, doubl
 // ---- K4 --------------------------------------------------------------------
 
 // K4 for active slot k (thread k of the corrector's grid).
-__device__ __forceinline__ void correct_body(const StateDev &s, const int *__restrict__ act, int na,
+__device__ __forceinline__ void correct_body(const StateDev &s, const int *act, int na,
                                              double t_new, const Out3 &f, const StepParams &prm,
                                              SchedDev *sd, unsigned *err,
                                              unsigned long long *dtmin_hits, const double *t_dev,

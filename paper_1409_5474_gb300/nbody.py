@@ -39,6 +39,8 @@ NB_F64 = 2
 VARIANTS = {"f32": NB_F32, "f32ds": NB_F32DS, "f64": NB_F64}
 
 NB_FLAG_TIMING = 1
+NB_FLAG_NO_FUSED = 2
+NB_FUSED_MAX_NA = 1024
 
 
 class NBodyError(RuntimeError):
@@ -70,10 +72,14 @@ class nb_stats(ctypes.Structure):
                 ("correct_ms", ctypes.c_double), ("sched_ms", ctypes.c_double),
                 ("dt_min_hits", ctypes.c_longlong), ("active_hist", ctypes.c_longlong * 32),
                 ("kernel_launches", ctypes.c_longlong),
-                ("force_ms_hist", ctypes.c_double * 32), ("inter_hist", ctypes.c_double * 32)]
+                ("force_ms_hist", ctypes.c_double * 32), ("inter_hist", ctypes.c_double * 32),
+                ("fused_steps", ctypes.c_longlong), ("fused_launches", ctypes.c_longlong),
+                ("fused_ms", ctypes.c_double), ("fused_stage_ms", ctypes.c_double * 4),
+                ("fused_step_ms_hist", ctypes.c_double * 32)]
 
     def as_dict(self):
-        hists = ("active_hist", "force_ms_hist", "inter_hist")
+        hists = ("active_hist", "force_ms_hist", "inter_hist", "fused_stage_ms",
+                 "fused_step_ms_hist")
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in hists}
         for k in hists:
             d[k] = list(getattr(self, k))
