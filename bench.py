@@ -84,6 +84,8 @@ def parse_args(argv=None):
                          "otherwise runs in the untimed set-up; plans are then the built-in "
                          "heuristic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fused-max-na", type=int, default=0,
+                    help="largest due set the fused block-step kernel takes (0: library default)")
     ap.add_argument("--requests", type=int, default=None,
                     help="serve: requests in the stream (default 64)")
     ap.add_argument("--n-hi", type=int, default=None, help="serve: largest request N")
@@ -347,7 +349,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    cfg = dict(variant=variant, eps=wl["eps"], device=local, flags=nbody.NB_FLAG_TIMING)
+    cfg = dict(variant=variant, eps=wl["eps"], device=local, flags=nbody.NB_FLAG_TIMING,
+               fused_max_na=args.fused_max_na)
     if wl["kind"] == "evolve":
         cfg.update(eta=wl["eta"], dt_max=wl["dt_max"], shared_dt=wl["shared_dt"])
     sysm = nbody.System(p.m, p.pos, p.vel, **cfg)

@@ -84,10 +84,12 @@ typedef struct nb_config {
     size_t budget_bytes; /* device-memory cap for the handle; 0 = none */
     int device;          /* CUDA device ordinal */
     int flags;           /* NB_FLAG_* */
+    int fused_max_na;    /* largest due set the fused kernel takes itself; 0 = NB_FUSED_MAX_NA */
 } nb_config;
 
 /* Fills cfg with: n_max 1024, NB_F32DS, eps 0, eta 0.01, eta_s 0 (= eta),
- * dt_max 1/16, dt_min 2^-30, shared_dt 0, budget 0, device 0, flags 0. */
+ * dt_max 1/16, dt_min 2^-30, shared_dt 0, budget 0, device 0, flags 0,
+ * fused_max_na 0. */
 void nb_config_default(nb_config *cfg);
 
 /* Counters of a handle since creation or nb_reset_stats. Kernel times are

@@ -724,6 +724,7 @@ int nb_create(const nb_config *cfg, nb_handle *out)
         return fail(nullptr, NB_ERR_ARG, "dt_min must be a power of two <= dt_max");
     if (!(cfg->shared_dt >= 0.0) || !std::isfinite(cfg->shared_dt))
         return fail(nullptr, NB_ERR_ARG, "shared_dt must be finite and >= 0");
+    if (cfg->fused_max_na < 0) return fail(nullptr, NB_ERR_ARG, "fused_max_na must be >= 0");
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1203,7 +1204,9 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             fa.f = f;
             fa.prm = prm;
             fa.eps2f = (float)(h->cfg.eps * h->cfg.eps);
-            fa.na_max = NB_FUSED_MAX_NA;
+            fa.na_max = h->cfg.fused_max_na > 0
+                            ? std::min(h->cfg.fused_max_na, NB_FUSED_MAX_NA)
+                            : NB_FUSED_MAX_NA;
             fa.t_end = t_end;
             fa.part = h->fused_part;
             fa.cnt = h->fused_cnt;

@@ -13,7 +13,8 @@
 //   C  pair force (K2): warp items of four due particles against a j-chunk,
 //      lanes over j, double-single partials per chunk;      -- barrier
 //   D  one warp per due particle sums its chunk partials in chunk order (K3)
-//      and corrects it (K4: Hermite corrector, Aarseth step, histogram);
+//      and corrects it, three lanes for the three components (K4: Hermite
+//      corrector, Aarseth step, histogram);
 //                                                            -- barrier
 // Every inter-CTA wait is bounded; a CTA that gives up raises the abort flag
 // and all CTAs leave at their next barrier (the host then reports a timeout).
@@ -198,12 +199,15 @@ __device__ __forceinline__ void warp_item(const FusedArgs &a, int na, int k0, in
 }
 
 // The j-chunks of a step with na due particles on n: about two warp items per
-// warp of the grid, at least 256 j per chunk (a function of (na, n, grid) only).
+// warp of the grid, at least 256 j per chunk, at most FUSED_MAX_CHUNKS chunks
+// (a function of (na, n, grid) only).
+constexpr int FUSED_MAX_CHUNKS = 128;
+
 __device__ __forceinline__ void chunking(int na, int n, int total_warps, int &nchunk, int &jc)
 {
     const int ng = (na + 3) / 4;
     int nc = (2 * total_warps + ng - 1) / ng;
-    nc = max(1, min(nc, (n + 255) / 256));
+    nc = max(1, min(min(nc, (n + 255) / 256), FUSED_MAX_CHUNKS));
     jc = (n + nc - 1) / nc;
     jc = (jc + 31) & ~31;
     nchunk = (n + jc - 1) / jc;
@@ -366,15 +370,23 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 
         // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
         for (int k = gw; k < na; k += total_warps) {
-            dsf v[7];
+            // lane l holds chunks l, l + 32, l + 64, l + 96, all loaded at once
+            constexpr int CPL = FUSED_MAX_CHUNKS / 32;
+            float2 x[CPL][7];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[q] = dsf{0.f, 0.f};
-            for (int c = lane; c < nchunk; c += 32) {
+            for (int u = 0; u < CPL; ++u)
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
-                    const float2 x = __ldcg(a.part + ((size_t)c * 7 + q) * na + k);
-                    ds_acc(v[q], dsf{x.x, x.y});
+                    const int c = lane + 32 * u;
+                    x[u][q] = c < nchunk ? __ldcg(a.part + ((size_t)c * 7 + q) * na + k)
+                                         : make_float2(0.f, 0.f);
                 }
+            dsf v[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                v[q] = dsf{x[0][q].x, x[0][q].y};
+#pragma unroll
+                for (int u = 1; u < CPL; ++u) ds_acc(v[q], dsf{x[u][q].x, x[u][q].y});
             }
 #pragma unroll
             for (int q = 0; q < 7; ++q)
@@ -388,8 +400,9 @@ __global__ void __launch_bounds__(FUSED_THREADS)
                     f.jerk[q * f.ld + k] = ds_to_double(v[3 + q]);
                 }
                 f.pot[k] = -ds_to_double(v[6]);
-                correct_body(s, a.act, na, tn, f, a.prm, a.sd, a.err, a.dtmin_hits, nullptr, k);
             }
+            __syncwarp();
+            correct_lanes(s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, k, 0, true);
         }
         if (bid == 0 && tid == 0) {
             ++steps;

@@ -201,54 +201,47 @@ static __device__ double quantize_log2(int e, double dt_old, double t_new, doubl
 
 // ---- K4 --------------------------------------------------------------------
 
-// K4 for active slot k (thread k of the corrector's grid).
-__device__ __forceinline__ void correct_body(const StateDev &s, const int *act, int na,
-                                             double t_new, const Out3 &f, const StepParams &prm,
-                                             SchedDev *sd, unsigned *err,
-                                             unsigned long long *dtmin_hits, const double *t_dev,
-                                             int k)
+// K4, component c of active slot k (particle i): Hermite corrector of x, v with
+// the new acc/jerk f (slot-indexed); writes pos, vel, acc, jerk of i and
+// returns the new acc, jerk and the end-of-step a2 (a2 + dt a3) and a3
+// components for the step criterion. Whether x and v stayed finite.
+__device__ __forceinline__ bool correct_component(const StateDev &s, const Out3 &f, int i, int k,
+                                                  int c, double dt, double dt2, double idt2,
+                                                  double idt3, double &a1o, double &j1o,
+                                                  double &a2eo, double &a3eo)
 {
-    if (t_dev)
-        t_new = *t_dev + t_new;
-    else if (k == 0)
-        sd->t_cur = t_new;
-    if (k >= na) return;
-    const int i = act ? act[k] : k;
-    const double dt = t_new - s.t[i];
-    const double dt_old = s.dt[i];
-    // block steps are powers of two, whose reciprocal is exact by exponent
-    // arithmetic; a shared step may be any number
-    const double idt = prm.shared_dt > 0.0 ? 1.0 / dt : ldexp(1.0, -ilogb(dt));
-    const double idt2 = idt * idt, idt3 = idt2 * idt;
-    const double dt2 = dt * dt;
-    double a1v[3], j1v[3], a2e[3], a3e[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long q = c * s.ld + i;
-        const double a0 = s.acc[q], j0 = s.jerk[q];
-        const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
-        // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
-        // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
-        // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
-        // v1 = vp + dt (A2/6 + A3/24) - the same corrector in fewer FP64 steps
-        const double da = a0 - a1;
-        const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
-        const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
-        const double x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), s.pos_p[q]);
-        const double v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), s.vel_p[q]);
-        const double a2 = A2 * idt2, a3 = A3 * idt3;
-        s.pos[q] = x1;
-        s.vel[q] = v1;
-        s.acc[q] = a1;
-        s.jerk[q] = j1;
-        a1v[c] = a1;
-        j1v[c] = j1;
-        a2e[c] = a2 + dt * a3;
-        a3e[c] = a3;
-        finite = finite && isfinite(x1) && isfinite(v1);
-    }
-    if (!finite) atomicOr(err, DERR_NONFINITE);
+    const long long q = c * s.ld + i;
+    const double a0 = s.acc[q], j0 = s.jerk[q];
+    const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
+    // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
+    // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
+    // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
+    // v1 = vp + dt (A2/6 + A3/24) - the same corrector in fewer FP64 steps
+    const double da = a0 - a1;
+    const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
+    const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
+    const double x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), s.pos_p[q]);
+    const double v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), s.vel_p[q]);
+    const double a2 = A2 * idt2, a3 = A3 * idt3;
+    s.pos[q] = x1;
+    s.vel[q] = v1;
+    s.acc[q] = a1;
+    s.jerk[q] = j1;
+    a1o = a1;
+    j1o = j1;
+    a2eo = a2 + dt * a3;
+    a3eo = a3;
+    return isfinite(x1) && isfinite(v1);
+}
+
+// K4, the new step of particle i from its new acc, jerk, a2 and a3 (Aarseth's
+// criterion, block quantization, level histogram), and its new time.
+__device__ __forceinline__ void correct_step(const StateDev &s, int i, double t_new, double dt,
+                                             double dt_old, const double a1v[3],
+                                             const double j1v[3], const double a2e[3],
+                                             const double a3e[3], const StepParams &prm,
+                                             SchedDev *sd, unsigned long long *dtmin_hits)
+{
     double dt_new;
     if (prm.shared_dt > 0.0) {
         dt_new = prm.shared_dt;
@@ -299,6 +292,86 @@ __device__ __forceinline__ void correct_body(const StateDev &s, const int *act, 
     }
     s.t[i] = t_new;
     s.dt[i] = dt_new;
+}
+
+// The step of a particle whose time is t_i (block steps: a power of two, whose
+// reciprocal is exact by exponent arithmetic; a shared step may be any number).
+__device__ __forceinline__ void step_factors(double dt, const StepParams &prm, double &dt2,
+                                             double &idt2, double &idt3)
+{
+    const double idt = prm.shared_dt > 0.0 ? 1.0 / dt : ldexp(1.0, -ilogb(dt));
+    idt2 = idt * idt;
+    idt3 = idt2 * idt;
+    dt2 = dt * dt;
+}
+
+// K4 for active slot k (thread k of the corrector's grid).
+__device__ __forceinline__ void correct_body(const StateDev &s, const int *act, int na,
+                                             double t_new, const Out3 &f, const StepParams &prm,
+                                             SchedDev *sd, unsigned *err,
+                                             unsigned long long *dtmin_hits, const double *t_dev,
+                                             int k)
+{
+    if (t_dev)
+        t_new = *t_dev + t_new;
+    else if (k == 0)
+        sd->t_cur = t_new;
+    if (k >= na) return;
+    const int i = act ? act[k] : k;
+    const double dt = t_new - s.t[i];
+    const double dt_old = s.dt[i];
+    double dt2, idt2, idt3;
+    step_factors(dt, prm, dt2, idt2, idt3);
+    double a1v[3], j1v[3], a2e[3], a3e[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        finite = correct_component(s, f, i, k, c, dt, dt2, idt2, idt3, a1v[c], j1v[c], a2e[c],
+                                   a3e[c]) &&
+                 finite;
+    if (!finite) atomicOr(err, DERR_NONFINITE);
+    correct_step(s, i, t_new, dt, dt_old, a1v, j1v, a2e, a3e, prm, sd, dtmin_hits);
+}
+
+// K4 for active slot k by three lanes of a warp (component c = lane - lane0 on
+// lanes lane0 .. lane0 + 2; every lane of the warp calls this, valid marks the
+// three that hold a slot): the same arithmetic as correct_body, the FP64
+// dependency chain split over the components.
+__device__ __forceinline__ void correct_lanes(const StateDev &s, const int *act, int na,
+                                              double t_new, const Out3 &f, const StepParams &prm,
+                                              SchedDev *sd, unsigned *err,
+                                              unsigned long long *dtmin_hits, int k, int lane0,
+                                              bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = lane - lane0;
+    const bool mine = valid && k < na && c >= 0 && c < 3;
+    double a1 = 0.0, j1 = 0.0, a2e = 0.0, a3e = 0.0, dt = 1.0, dt_old = 0.0;
+    int i = 0;
+    bool fin = true;
+    if (mine) {
+        if (k == 0 && c == 0) sd->t_cur = t_new;
+        i = act ? act[k] : k;
+        dt = t_new - s.t[i];
+        dt_old = s.dt[i];
+        double dt2, idt2, idt3;
+        step_factors(dt, prm, dt2, idt2, idt3);
+        fin = correct_component(s, f, i, k, c, dt, dt2, idt2, idt3, a1, j1, a2e, a3e);
+    }
+    double a1v[3], j1v[3], a2v[3], a3v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int src = min(31, lane0 + q);
+        a1v[q] = __shfl_sync(0xffffffffu, a1, src);
+        j1v[q] = __shfl_sync(0xffffffffu, j1, src);
+        a2v[q] = __shfl_sync(0xffffffffu, a2e, src);
+        a3v[q] = __shfl_sync(0xffffffffu, a3e, src);
+    }
+    const unsigned bad = __ballot_sync(0xffffffffu, mine && !fin);
+    if (mine && c == 0) {
+        if (bad & (7u << lane0)) atomicOr(err, DERR_NONFINITE);
+        correct_step(s, i, t_new, dt, dt_old, a1v, j1v, a2v, a3v, prm, sd, dtmin_hits);
+    }
 }
 
 // ---- bounded waits and ordered status words ---------------------------------

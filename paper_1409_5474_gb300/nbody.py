@@ -55,7 +55,7 @@ class nb_config(ctypes.Structure):
                 ("eta", ctypes.c_double), ("eta_s", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("dt_min", ctypes.c_double), ("shared_dt", ctypes.c_double),
                 ("budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-                ("flags", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("fused_max_na", ctypes.c_int)]
 
 
 class nb_plan(ctypes.Structure):
