@@ -397,10 +397,10 @@ __global__ void __launch_bounds__(32 * NWI * NWJ)
 
         auto body = [&](int jj, auto masked_tag) {
             constexpr bool MASKED = decltype(masked_tag)::value;
-            const float4 a = T[DS_REC * jj];
-            const float4 c = T[DS_REC * jj + 2];
+            const float4 a = lds4(T + DS_REC * jj);
+            const float4 c = lds4(T + DS_REC * jj + 2);
             float4 b;
-            if (DS) b = T[DS_REC * jj + 1];
+            if (DS) b = lds4(T + DS_REC * jj + 1);
 #pragma unroll
             for (int p = 0; p < IPT; ++p) {
                 float dx, dy, dz;
@@ -1368,10 +1368,10 @@ __global__ void __launch_bounds__(NT)
             }
             auto body = [&](int jj, auto masked_tag) {
                 constexpr bool MASKED = decltype(masked_tag)::value;
-                const float4 a = T[DS_REC * jj];
-                const float4 c = T[DS_REC * jj + 2];
+                const float4 a = lds4(T + DS_REC * jj);
+                const float4 c = lds4(T + DS_REC * jj + 2);
                 float4 b;
-                if (DS) b = T[DS_REC * jj + 1];
+                if (DS) b = lds4(T + DS_REC * jj + 1);
 #pragma unroll
                 for (int p = 0; p < IPT; ++p) {
                     float dx, dy, dz;
@@ -1549,7 +1549,7 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
         return p;
     }
     // tiles: 256 threads, 2 i per thread; 8 or 4 warp rows share each j-tile
-    // below 65536 i; about 20 CTAs per SM, at least 16 tiles per split
+    // below 65536 i; about 40 CTAs per SM, at least 16 tiles per split
     p.kind = 0;
     p.ipt = 2;
     p.threads = 256;
@@ -1558,7 +1558,7 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
     const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
     const long long nblk = (n_i + ib - 1) / ib;
     const long long ntiles = (n_j + p.jt - 1) / p.jt;
-    p.nsplit = (int)clampll((20LL * num_sms + nblk - 1) / nblk, 1, ntiles / 16 > 1 ? ntiles / 16 : 1);
+    p.nsplit = (int)clampll((40LL * num_sms + nblk - 1) / nblk, 1, ntiles / 16 > 1 ? ntiles / 16 : 1);
     return p;
 }
 

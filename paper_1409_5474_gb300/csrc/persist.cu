@@ -10,8 +10,10 @@
 //      the CTAs) with its records gathered; if t_next > t_end or the due set
 //      is larger than na_max the kernel publishes (epoch, t_next, N_active)
 //      to the mailbox like K5 + K1 and returns;             -- barrier
-//   C  pair force (K2): warp items of four due particles against a j-chunk,
-//      lanes over j, double-single partials per chunk;      -- barrier
+//   C  pair force (K2): warp items of four due particles against a j-chunk
+//      (lanes over j), or, for larger due sets, CTA items of 32 due particles
+//      whose j-chunk is staged through shared memory; double-single partials
+//      per chunk;                                           -- barrier
 //   D  one warp per due particle sums its chunk partials in chunk order (K3)
 //      and corrects it, three lanes for the three components (K4: Hermite
 //      corrector, Aarseth step, histogram);
@@ -198,15 +200,168 @@ __device__ __forceinline__ void warp_item(const FusedArgs &a, int na, int k0, in
     }
 }
 
-// The j-chunks of a step with na due particles on n: about two warp items per
-// warp of the grid, at least 256 j per chunk, at most FUSED_MAX_CHUNKS chunks
-// (a function of (na, n, grid) only).
-constexpr int FUSED_MAX_CHUNKS = 128;
+// K2 for one CTA item (steps with at least 29 due particles): the CTA's
+// eight warps take four due slots each (slots k0 .. k0 + 31) against the
+// j-records [j0, j1), staged through shared memory in tiles of FUSED_TILE
+// records (double-buffered, the next tile's loads in flight during the
+// arithmetic); lanes take the tile's records l, l + 32, ...; double-single
+// totals per warp as in warp_item.
+constexpr int FUSED_TILE = 256;
 
-__device__ __forceinline__ void chunking(int na, int n, int total_warps, int &nchunk, int &jc)
+template <bool DS>
+__device__ __forceinline__ void cta_item(const FusedArgs &a, int na, int k0, int j0, int j1,
+                                         int chunk, float4 (*s_tile)[DS_REC * FUSED_TILE])
+{
+    constexpr int G = 4, NT = FUSED_THREADS, PF = (DS_REC * FUSED_TILE + NT - 1) / NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kw = k0 + G * warp;
+    const bool active = kw < na;  // warp-uniform
+    const float eps2f = a.eps2f;
+    float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
+    int iid[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const int slot = min(kw + p, na - 1);
+        const float4 *r = a.irec + (size_t)DS_REC * slot;
+        const float4 A = __ldcg(r), B = __ldcg(r + 1), C = __ldcg(r + 2);
+        xh[p] = A.x; yh[p] = A.y; zh[p] = A.z;
+        xl[p] = B.x; yl[p] = B.y; zl[p] = B.z;
+        vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
+        iid[p] = __float_as_int(B.w);
+    }
+    dsf S[G][7];
+#pragma unroll
+    for (int p = 0; p < G; ++p)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) S[p][c] = dsf{0.f, 0.f};
+    const float4 *jr = a.s.rec;
+    const int ntile = (j1 - j0 + FUSED_TILE - 1) / FUSED_TILE;
+    float4 pf[PF];
+    auto fetch = [&](int t) {
+        const int tb = j0 + t * FUSED_TILE;
+        const int m = DS_REC * min(FUSED_TILE, j1 - tb);
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int q = tid + u * NT;
+            pf[u] = q < m ? __ldcg(jr + (size_t)DS_REC * tb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int q = tid + u * NT;
+            if (q < DS_REC * FUSED_TILE) s_tile[buf][q] = pf[u];
+        }
+    };
+    __syncthreads();  // the buffers are free (a previous item may still read them)
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int t = 0; t < ntile; ++t) {
+        const int tb = j0 + t * FUSED_TILE;
+        const int cnt = min(FUSED_TILE, j1 - tb);
+        if (t + 1 < ntile) fetch(t + 1);
+        if (active) {
+            const float4 *T = s_tile[t & 1];
+            float ta[G][3], tjv[G][3], tp[G];
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ta[p][c] = tjv[p][c] = 0.f;
+                tp[p] = 0.f;
+            }
+#pragma unroll 2
+            for (int jj = lane; jj < cnt; jj += 32) {
+                const int j = tb + jj;
+                const float4 A = lds4(T + DS_REC * jj);
+                const float4 C = lds4(T + DS_REC * jj + 2);
+                float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (DS) B = lds4(T + DS_REC * jj + 1);
+#pragma unroll
+                for (int p = 0; p < G; ++p) {
+                    float dx, dy, dz;
+                    if (DS) {
+                        dx = (A.x - xh[p]) + (B.x - xl[p]);
+                        dy = (A.y - yh[p]) + (B.y - yl[p]);
+                        dz = (A.z - zh[p]) + (B.z - zl[p]);
+                    } else {
+                        dx = A.x - xh[p];
+                        dy = A.y - yh[p];
+                        dz = A.z - zh[p];
+                    }
+                    const float dvx = C.x - vx[p], dvy = C.y - vy[p], dvz = C.z - vz[p];
+                    float r2 = fmaf(dx, dx, eps2f);
+                    r2 = fmaf(dy, dy, r2);
+                    r2 = fmaf(dz, dz, r2);
+                    float rv = dx * dvx;
+                    rv = fmaf(dy, dvy, rv);
+                    rv = fmaf(dz, dvz, rv);
+                    float rinv = rsqrtf(r2);
+                    rinv = (j == iid[p]) ? 0.f : rinv;
+                    const float rinv2 = rinv * rinv;
+                    const float mrinv = A.w * rinv;
+                    const float mr3 = mrinv * rinv2;
+                    const float beta = -3.f * ((mr3 * rinv2) * rv);
+                    tp[p] += mrinv;
+                    ta[p][0] = fmaf(mr3, dx, ta[p][0]);
+                    ta[p][1] = fmaf(mr3, dy, ta[p][1]);
+                    ta[p][2] = fmaf(mr3, dz, ta[p][2]);
+                    tjv[p][0] = fmaf(beta, dx, fmaf(mr3, dvx, tjv[p][0]));
+                    tjv[p][1] = fmaf(beta, dy, fmaf(mr3, dvy, tjv[p][1]));
+                    tjv[p][2] = fmaf(beta, dz, fmaf(mr3, dvz, tjv[p][2]));
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < G; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ds_acc(S[p][c], dsf{ta[p][c], 0.f});
+                    ds_acc(S[p][3 + c], dsf{tjv[p][c], 0.f});
+                }
+                ds_acc(S[p][6], dsf{tp[p], 0.f});
+            }
+        }
+        if (t + 1 < ntile) stash((t + 1) & 1);
+        __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+        for (int p = 0; p < G; ++p)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ds_acc(S[p][c], ds_shfl_xor(S[p][c], o));
+            }
+#pragma unroll
+        for (int q = 0; q < G * 7; ++q) {
+            const int p = q / 7, c = q % 7;
+            if (lane == q && kw + p < na)
+                a.part[((size_t)chunk * 7 + c) * na + kw + p] =
+                    make_float2(S[p][c].hi, S[p][c].lo);
+        }
+    }
+}
+
+// The j-chunks of a step with na due particles on n (a function of (na, n,
+// grid) only): with at least eight groups of four due slots the CTAs take
+// items of 32 slots (cta mode), about two per CTA; otherwise warps take items of
+// four slots, about two per warp. At least 256 j per chunk, at most
+// FUSED_MAX_CHUNKS chunks.
+constexpr int FUSED_MAX_CHUNKS = 128;
+constexpr int FUSED_CTA_SLOTS = 4 * (FUSED_THREADS / 32);
+
+__device__ __forceinline__ void chunking(int na, int n, int grid, int total_warps, int &nchunk,
+                                         int &jc, bool &cta_mode)
 {
     const int ng = (na + 3) / 4;
-    int nc = (2 * total_warps + ng - 1) / ng;
+    cta_mode = ng >= FUSED_THREADS / 32;
+    int nc;
+    if (cta_mode) {
+        const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
+        nc = (2 * grid + nsb - 1) / nsb;
+    } else {
+        nc = (2 * total_warps + ng - 1) / ng;
+    }
     nc = max(1, min(min(nc, (n + 255) / 256), FUSED_MAX_CHUNKS));
     jc = (n + nc - 1) / nc;
     jc = (jc + 31) & ~31;
@@ -224,6 +379,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     __shared__ int s_total, s_base, s_na;
     __shared__ double s_tn;
     __shared__ unsigned long long s_hist[32], s_step_ns[32], s_phase[4];
+    __shared__ __align__(16) float4 s_tile[2][DS_REC * FUSED_TILE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, bid = blockIdx.x;
     const StateDev &s = a.s;
@@ -354,12 +510,22 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 
         // C: pair force, warp items (4 due slots x one j-chunk)
         int nchunk, jc;
-        chunking(na, n, total_warps, nchunk, jc);
-        const int ng = (na + 3) / 4;
-        for (int it = gw; it < ng * nchunk; it += total_warps) {
-            const int g = it / nchunk, c = it - g * nchunk;
-            const int j0 = c * jc;
-            warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
+        bool cta_mode;
+        chunking(na, n, G, total_warps, nchunk, jc, cta_mode);
+        if (cta_mode) {
+            const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
+            for (int it = bid; it < nsb * nchunk; it += G) {
+                const int sb = it / nchunk, c = it - sb * nchunk;
+                const int j0 = c * jc;
+                cta_item<DS>(a, na, FUSED_CTA_SLOTS * sb, j0, min(n, j0 + jc), c, s_tile);
+            }
+        } else {
+            const int ng = (na + 3) / 4;
+            for (int it = gw; it < ng * nchunk; it += total_warps) {
+                const int g = it / nchunk, c = it - g * nchunk;
+                const int j0 = c * jc;
+                warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
+            }
         }
         if (!(ok = grid_barrier(a.bar, gen))) break;
         if (bid == 0 && tid == 0) {
