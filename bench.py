@@ -39,6 +39,12 @@ if ROOT not in sys.path:
 METRIC = "G pair-interactions/s (acc+jerk)"
 UNIT = "G interactions/s"
 FLOPS_PER_INTERACTION = 60
+FP64_NOMINAL_TFLOPS = 1.25
+# algorithmic bytes per particle of the per-particle stages (FP64 SoA state):
+# predictor: t, dt, m, x, v, a, j read (120 B) + x_p, v_p and the 48-B j-record written (96 B)
+# corrector: index, t, dt, x_p, v_p, a, j, new a, j read (164 B) + x, v, a, j, t, dt written (112 B)
+PREDICT_BYTES = 216
+CORRECT_BYTES = 276
 L2_FLUSH_BYTES = 256 << 20
 
 WORKLOADS = {
@@ -62,6 +68,11 @@ WORKLOADS = {
                        "force evaluation, half 1/8 time unit of block steps (eta=0.01, "
                        "dt_max=1/16), eps = 1/(4 N^(1/3)); one bench step = the whole stream at "
                        "the saturating rate"),
+    "ext65536": dict(n=65536, n_ext=65536, eps=1e-3, variant="f32ds", masses="equal", kind="ext",
+                     desc="field-particle service (nb_force_ext): the force of a Plummer j-set of "
+                          "N=65536 (eps=1e-3) on 65536 external particles of a second Plummer "
+                          "sphere offset by (0.5, 0, 0); one bench step = one call with host "
+                          "arrays in and out"),
     "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
                       variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
                       desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
@@ -225,6 +236,29 @@ def fp32_peak_tflops(sm_count, sm_mhz):
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms, planned_inter, peaks):
+    """HBM-side rates of the O(N) stages: the fused kernel's predict stage (all N
+    particles per fused step) and the planned-path corrector (the due particles of the
+    planned steps), in GB/s of algorithmic bytes against the measured copy bandwidth."""
+    if wl["kind"] != "evolve":
+        return None
+    hbm = float(peaks.get("hbm_gbs") or 0.0) or None
+    out = {"hbm_peak_gbs": hbm, "predict_bytes_per_particle": PREDICT_BYTES,
+           "correct_bytes_per_particle": CORRECT_BYTES}
+    if fused_steps and fused_stage_ms[0] > 0:
+        g = PREDICT_BYTES * n * fused_steps / (fused_stage_ms[0] / 1e3) / 1e9
+        out["fused_predict_stage_gbs"] = g
+        out["fused_predict_stage_us_per_step"] = 1e3 * fused_stage_ms[0] / fused_steps
+    if other_ms.get("correct_ms"):
+        g = CORRECT_BYTES * (planned_inter / n) / (other_ms["correct_ms"] / 1e3) / 1e9
+        out["planned_correct_gbs"] = g
+    if hbm:
+        for k in ("fused_predict_stage_gbs", "planned_correct_gbs"):
+            if k in out:
+                out[k.replace("_gbs", "_frac")] = out[k] / hbm
+    return out
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -251,6 +285,16 @@ def oracle_sample(wl, particles):
         return inter, dt, ("oracle shared-step Hermite on 32 clusters with N log-spaced in "
                            "[%d, %d]: initial evaluation + 64 steps each" % (wl["n_lo"], wl["n_hi"]))
     eps2 = wl["eps"] ** 2
+    if wl["kind"] == "ext":
+        from paper_1409_5474_gb300 import ic
+        q = ic.plummer(wl["n_ext"], ic.MASTER_SEED + 7)
+        ni = 2048
+        t0 = time.perf_counter()
+        oracle.force_ext(particles.m, particles.pos, particles.vel, eps2,
+                         q.pos[:ni] + np.array([0.5, 0.0, 0.0]), q.vel[:ni])
+        dt = time.perf_counter() - t0
+        return float(ni) * particles.n, dt, (
+            "oracle force_ext of the j-set on the first %d external particles" % ni)
     if wl["kind"] == "force":
         rng = np.random.default_rng(2014)
         ni = 4096
@@ -345,6 +389,8 @@ def run_ours(args):
         return run_batch(args, wl, variant, dist, rank, world, local)
     if wl["kind"] == "serve":
         return run_serve(args, wl, variant, dist, rank, world, local)
+    if wl["kind"] == "ext":
+        return run_ext(args, wl, variant, dist, rank, world, local)
     p = make_particles(wl)
     stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
     torch.cuda.set_stream(stream)
@@ -398,8 +444,10 @@ def run_ours(args):
     host_state = None
     for k in range(args.warmup):
         one_step(k, None)
+    energy0 = None
     if wl["kind"] == "evolve":
         host_state = nbody.nb_get_state(h)
+        energy0 = sum(nbody.nb_energy(h))          # untimed: softened E at a synchronised time
     else:
         host_state = True
     nbody.nb_reset_stats(h)
@@ -438,6 +486,7 @@ def run_ours(args):
                 hist[key][b] += x
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    energy1 = sum(nbody.nb_energy(h)) if energy0 is not None else None  # untimed
     dist.barrier()
     pairs = dist.gather_pairs(tot_inter, tot_ms / 1e3, device="cuda")
     units, secs = aggregate(pairs)
@@ -451,6 +500,12 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0)
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    peak_source = ("SMs x 128 x 2 x max SM clock %.0f MHz (derived; FP32 is not in "
+                   "MEASURED_PEAKS.json)" % sm_max)
+    if variant == "f64":
+        # the FP64 pair path is bound by GB300's FP64 rate
+        peak = FP64_NOMINAL_TFLOPS
+        peak_source = "GB300 nominal dense FP64 rate (not measured)"
     value = units / secs / 1e9
     # the planned force launches' own interactions (the fused kernel's steps are
     # timed as a whole and reported apart)
@@ -467,17 +522,24 @@ def run_ours(args):
                        parallelism=("replicas%d" % world) if world > 1 else "single GPU"),
         "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
         "roofline": {"bound": "alu",
-                     "kernel": "k_force_tile32/k_force_wgrp32/k_force_tiny32 (planned pair force)",
+                     "kernel": ("k_force_tile64/k_force_jmode64 (planned FP64 pair force)"
+                                if variant == "f64" else
+                                "k_force_tile32/k_force_wgrp32/k_force_tiny32 (planned pair force)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived; "
-                                    "FP32 is not in MEASURED_PEAKS.json)" % sm_max,
+                     "peak_source": peak_source,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "force_ms": force_ms, "reduce_ms": reduce_ms,
                      "force_launches": force_launches, "interactions": planned_inter},
         "kernel_ms": dict(other_ms, force_ms=force_ms, reduce_ms=reduce_ms),
         "block_steps": block_steps,
         "fused_steps": fused_steps,
+        "stage_bandwidth": stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms,
+                                           float(sum(hist["inter_hist"])), peaks),
+        "energy": ({"E0": energy0, "E1": energy1,
+                    "rel_drift": abs(energy1 - energy0) / abs(energy0),
+                    "over_time_units": args.steps * wl["step_t"]}
+                   if energy0 is not None else None),
         "fused_stage_ms": {"predict_flags": fused_stage_ms[0], "gather": fused_stage_ms[1],
                            "force": fused_stage_ms[2], "reduce_correct": fused_stage_ms[3]},
         "by_log2_active": {k: [round(x, 3) if isinstance(x, float) else x for x in v]
@@ -585,6 +647,88 @@ def run_batch(args, wl, variant, dist, rank, world, local):
     bt.close()
     dist.close()
     return 0
+
+# ---------------------------------------------------------------------------
+# the field-particle service (nb_force_ext): an i-set disjoint from the j-set
+# ---------------------------------------------------------------------------
+
+def run_ext(args, wl, variant, dist, rank, world, local):
+    """The force of the predicted j-set on an external i-set, as a hybrid code would call
+    it every bridge kick (host arrays in and out: the call is end to end by design)."""
+    import torch
+    from paper_1409_5474_gb300 import ic, nbody
+
+    p = make_particles(wl)
+    q = ic.plummer(wl["n_ext"], ic.MASTER_SEED + 7)
+    ipos = (q.pos + np.array([0.5, 0.0, 0.0])).T.copy()
+    ivel = q.vel.T.copy()
+    sysm = nbody.System(p.m, p.pos, p.vel, variant=variant, eps=wl["eps"], device=local,
+                        flags=nbody.NB_FLAG_TIMING)
+    h = sysm.h
+    nbody.nb_predict(h, 0.0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        nbody.nb_force_ext(h, ipos, ivel)
+    nbody.nb_reset_stats(h)
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    wall = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nbody.nb_force_ext(h, ipos, ivel)
+        wall += time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = nbody.nb_get_stats(h)
+    inter = float(wl["n_ext"]) * p.n * args.steps
+    units, secs = aggregate(dist.gather_pairs(inter, wall, device="cuda"))
+    if rank != 0:
+        sysm.close()
+        dist.close()
+        return 0
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(measured_peaks().get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    value = units / secs / 1e9
+    force_ms = st["force_ms"]
+    achieved = FLOPS_PER_INTERACTION * inter / (force_ms / 1e3) / 1e12 if force_ms else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Plummer spheres, N-body units)",
+        "config": dict(config_of(wl, args.workload, variant), n_ext=wl["n_ext"],
+                       parallelism="single GPU", timing="host wall clock around the call"),
+        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+        "roofline": {"bound": "alu", "kernel": "k_force_tile32 (planned pair force, external i)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "force_ms": force_ms,
+                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived)" % sm_max},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 48 * wl["n_ext"],
+                "d2h_bytes_per_step": 56 * wl["n_ext"],
+                "note": "the call takes and returns host arrays: value is end to end"},
+        "gpu_launches": int(st["kernel_launches"]),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ni = 2048
+        t0 = time.perf_counter()
+        oracle.force_ext(p.m, p.pos, p.vel, wl["eps"] ** 2, ipos[:, :ni].T, ivel[:, :ni].T)
+        secs_c = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ni * p.n / secs_c / 1e9, "unit": UNIT,
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "oracle force_ext of the j-set on the first %d "
+                                          "external particles" % ni, "seconds": secs_c}
+    print(json.dumps(line), flush=True)
+    sysm.close()
+    dist.close()
+    return 0
+
 
 # ---------------------------------------------------------------------------
 # config 5: the request loop

@@ -97,7 +97,7 @@ def _bind(lib):
     lib.orc_quantize.restype = ctypes.c_double
     lib.orc_hermite_run.argtypes = ([ctypes.c_int, _D, _D, _D, _D, _D, _D, _D]
                                     + [ctypes.c_double] * 7
-                                    + [ctypes.c_long, ctypes.c_int,
+                                    + [ctypes.c_long, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_long), _D])
     lib.orc_hermite_run.restype = ctypes.c_int
     lib.orc_energy.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D, _D]
@@ -216,8 +216,9 @@ class State:
 
 
 def hermite_run(state: State, t_end, eps2, eta=0.01, eta_s=None, dt_min=2.0 ** -30,
-                dt_max=1.0 / 16, dt_shared=0.0, max_steps=0):
-    """Advance ``state`` in place with block (or shared, dt_shared > 0) steps to t_end.
+                dt_max=1.0 / 16, dt_shared=0.0, max_steps=0, n_corr=1):
+    """Advance ``state`` in place with block (or shared, dt_shared > 0) steps to t_end;
+    n_corr force evaluations and corrections per step (1: PEC, 2: P(EC)^2, ...).
 
     Returns (n_block_steps, n_interactions)."""
     lib = _load()
@@ -229,8 +230,8 @@ def hermite_run(state: State, t_end, eps2, eta=0.01, eta_s=None, dt_min=2.0 ** -
     rc = lib.orc_hermite_run(state.n, _p(state.m), _p(state.pos), _p(state.vel), _p(state.acc),
                              _p(state.jerk), _p(state.t), _p(state.dt), float(eps2), float(eta),
                              float(eta_s), float(dt_min), float(dt_max), float(dt_shared),
-                             float(t_end), int(max_steps), init, ctypes.byref(steps),
-                             ctypes.byref(inter))
+                             float(t_end), int(max_steps), init, int(n_corr),
+                             ctypes.byref(steps), ctypes.byref(inter))
     if rc != 0:
         raise MemoryError("oracle scratch allocation failed")
     state.initialised = True

@@ -317,12 +317,19 @@ static void initialise(orc_state *s, double eta_s, double dt_min,
  *      ascending index order;
  *   2. predict every particle to t_next;
  *   3. evaluate acc/jerk on the active particles from the predicted set;
- *   4. correct the active particles and give them a new step.
+ *   4. correct the active particles; with n_corr > 1 (the iterated Hermite
+ *      corrector, P(EC)^n) the corrected positions and velocities of the
+ *      active particles replace their predicted ones in the j-set, their
+ *      acc/jerk are evaluated again and the corrector is applied again to the
+ *      same predicted values and start-of-step acc/jerk, n_corr times in all;
+ *   5. give the active particles a new step from the last evaluation.
  * Returns the number of active particles, sets *t_out = t_next.
+ * Scratch: pp, vp (n,3); a1, j1, p1, xs, vs, x1, v1 (n,3) for the active set.
  */
 static int block_step(orc_state *s, double eta, double dt_min, double dt_max,
-                      double dt_shared, int *active, double *pp, double *vp,
-                      double *a1, double *j1, double *p1, double *t_out)
+                      double dt_shared, int n_corr, int *active, double *pp,
+                      double *vp, double *a1, double *j1, double *p1, double *xs,
+                      double *vs, double *x1, double *v1, double *t_out)
 {
     int n = s->n;
     double t_next = INFINITY;
@@ -335,15 +342,39 @@ static int block_step(orc_state *s, double eta, double dt_min, double dt_max,
             active[na++] = i;
 
     orc_predict(n, t_next, s->t, s->pos, s->vel, s->acc, s->jerk, pp, vp);
+    for (int k = 0; k < na; k++) {
+        size_t q = 3 * (size_t)active[k], r = 3 * (size_t)k;
+        for (int c = 0; c < 3; c++) {
+            xs[r + c] = pp[q + c];
+            vs[r + c] = vp[q + c];
+        }
+    }
     orc_force_idx(n, s->m, pp, vp, s->eps2, na, active, a1, j1, p1);
+    for (int it = 1; it < n_corr; it++) {
+        for (int k = 0; k < na; k++) {
+            int i = active[k];
+            size_t q = 3 * (size_t)i, r = 3 * (size_t)k;
+            double a2[3], a3[3];
+            orc_correct_one(t_next - s->t[i], xs + r, vs + r, s->acc + q,
+                            s->jerk + q, a1 + r, j1 + r, x1 + r, v1 + r, a2, a3);
+        }
+        for (int k = 0; k < na; k++) {
+            size_t q = 3 * (size_t)active[k], r = 3 * (size_t)k;
+            for (int c = 0; c < 3; c++) {
+                pp[q + c] = x1[r + c];
+                vp[q + c] = v1[r + c];
+            }
+        }
+        orc_force_idx(n, s->m, pp, vp, s->eps2, na, active, a1, j1, p1);
+    }
 
     for (int k = 0; k < na; k++) {
         int i = active[k];
         size_t q = 3 * (size_t)i, r = 3 * (size_t)k;
         double dt = t_next - s->t[i];
-        double x1[3], v1[3], a2[3], a3[3];
-        orc_correct_one(dt, pp + q, vp + q, s->acc + q, s->jerk + q, a1 + r,
-                        j1 + r, x1, v1, a2, a3);
+        double xn[3], vn[3], a2[3], a3[3];
+        orc_correct_one(dt, xs + r, vs + r, s->acc + q, s->jerk + q, a1 + r,
+                        j1 + r, xn, vn, a2, a3);
         double dt_new;
         if (dt_shared > 0.0) {
             dt_new = dt_shared;
@@ -352,8 +383,8 @@ static int block_step(orc_state *s, double eta, double dt_min, double dt_max,
             dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
         }
         for (int c = 0; c < 3; c++) {
-            s->pos[q + c] = x1[c];
-            s->vel[q + c] = v1[c];
+            s->pos[q + c] = xn[c];
+            s->vel[q + c] = vn[c];
             s->acc[q + c] = a1[r + c];
             s->jerk[q + c] = j1[r + c];
         }
@@ -373,28 +404,33 @@ static int block_step(orc_state *s, double eta, double dt_min, double dt_max,
  * the acc/jerk are evaluated at the start and dt is assigned (t must then be
  * the same for all particles); otherwise acc, jerk, t and dt are taken as
  * given (a resumed run).
- * dt_shared > 0 selects shared-step mode with that step.
- * Counters: *n_block_steps, *n_interactions (sum over steps of N_active * N,
- * the initial evaluation included when init != 0).
+ * dt_shared > 0 selects shared-step mode with that step; n_corr >= 1 is the
+ * number of force evaluations and corrections per step (1: PEC).
+ * Counters: *n_block_steps, *n_interactions (sum over steps of
+ * n_corr * N_active * N, the initial evaluation included when init != 0).
  * Returns 0, or -1 if a scratch allocation failed.
  */
 int orc_hermite_run(int n, const double *m, double *pos, double *vel,
                     double *acc, double *jerk, double *t, double *dt,
                     double eps2, double eta, double eta_s, double dt_min,
                     double dt_max, double dt_shared, double t_end,
-                    long max_steps, int init, long *n_block_steps,
+                    long max_steps, int init, int n_corr, long *n_block_steps,
                     double *n_interactions)
 {
     orc_state s = {n, eps2, (double *)m, pos, vel, acc, jerk, t, dt};
     int *active = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
-    double *buf = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 15);
+    double *buf = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 27);
     if (!active || !buf) {
         free(active);
         free(buf);
         return -1;
     }
+    if (n_corr < 1)
+        n_corr = 1;
     double *pp = buf, *vp = buf + 3 * (size_t)n, *a1 = buf + 6 * (size_t)n;
     double *j1 = buf + 9 * (size_t)n, *p1 = buf + 12 * (size_t)n;
+    double *xs = buf + 15 * (size_t)n, *vs = buf + 18 * (size_t)n;
+    double *x1 = buf + 21 * (size_t)n, *v1 = buf + 24 * (size_t)n;
     long steps = 0;
     double inter = 0.0;
     if (init && n > 0) {
@@ -409,9 +445,9 @@ int orc_hermite_run(int n, const double *m, double *pos, double *vel,
         if (t_next > t_end)
             break;
         double tn;
-        int na = block_step(&s, eta, dt_min, dt_max, dt_shared, active, pp, vp,
-                            a1, j1, p1, &tn);
-        inter += (double)na * (double)n;
+        int na = block_step(&s, eta, dt_min, dt_max, dt_shared, n_corr, active,
+                            pp, vp, a1, j1, p1, xs, vs, x1, v1, &tn);
+        inter += (double)n_corr * (double)na * (double)n;
         steps++;
     }
     *n_block_steps = steps;

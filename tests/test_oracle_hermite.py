@@ -268,3 +268,74 @@ def test_block_schedule_counts_two_binaries():
     np.testing.assert_array_equal(st.dt, [2.0 ** -13] * 2 + [2.0 ** -10] * 2)
     assert steps == 128
     assert inter == 16 + 4 * (2 * 128 + 2 * 16)
+
+
+# ---- the iterated corrector P(EC)^n -------------------------------------------
+
+def _kepler_setup(nper):
+    e, d = 0.5, 0.5
+    a = d / (1 - e)
+    m, pos, vel = _two_body(d, e_frac=e)
+    return m, pos, vel, 2 * math.pi * a ** 1.5 / nper, a, e
+
+
+def _kepler_error_corr(nper, n_corr):
+    m, pos, vel, dt, a, e = _kepler_setup(nper)
+    n = nper // 3
+    st = oracle.State(m, pos, vel)
+    steps, inter = oracle.hermite_run(st, math.inf, 0.0, dt_shared=dt, max_steps=n,
+                                      n_corr=n_corr)
+    assert inter == n_corr * n * 4 + 4      # every iteration is a full evaluation, plus init
+    rel = st.pos[1] - st.pos[0]
+    return np.abs(rel - _kepler_position(n * dt, a, e)).max()
+
+
+def test_iterated_corrector_order_and_accuracy():
+    """P(EC)^2 stays 4th order (error / 16 when dt halves) and is about twice as accurate
+    as PEC on the e = 0.5 Kepler orbit; one iteration is PEC."""
+    pec = _kepler_error_corr(768, 1)
+    assert pec == _kepler_error(768)
+    e1 = _kepler_error_corr(768, 2)
+    e2 = _kepler_error_corr(1536, 2)
+    assert 14.0 < e1 / e2 < 18.0
+    assert e1 < 0.7 * pec
+
+
+def _reversal_error(n_corr, nper=256, periods=3):
+    """Integrate forward, reverse the velocities, integrate back: the distance to the start."""
+    m, pos, vel, dt, _, _ = _kepler_setup(nper)
+    n = nper * periods
+    st = oracle.State(m, pos, vel)
+    oracle.hermite_run(st, math.inf, 0.0, dt_shared=dt, max_steps=n, n_corr=n_corr)
+    back = oracle.State(m, st.pos.copy(), -st.vel.copy())
+    oracle.hermite_run(back, math.inf, 0.0, dt_shared=dt, max_steps=n, n_corr=n_corr)
+    return np.abs(back.pos - pos).max()
+
+
+def test_iterated_corrector_approaches_time_symmetry():
+    """The iterations converge to the time-symmetric (implicit) Hermite scheme: every
+    iteration shrinks the forward-backward return error by orders of magnitude."""
+    r1, r2, r3 = (_reversal_error(k) for k in (1, 2, 3))
+    assert r1 > 1e-5
+    assert r2 < 1e-3 * r1
+    assert r3 < 1e-2 * r2
+
+
+def test_iterated_corrector_block_steps_energy():
+    """Block steps with P(EC)^2 on a 256-particle Plummer sphere: synchronised at the end,
+    and a smaller energy drift than PEC over the same 1/8 time unit."""
+    p = ic.plummer(256, 5)
+    eps2 = (1.0 / 64) ** 2
+    e0 = _energy_of(p.m, p.pos, p.vel, eps2)
+    drifts = []
+    for nc in (1, 2):
+        st = oracle.State(p.m, p.pos, p.vel)
+        oracle.hermite_run(st, 0.125, eps2, eta=0.02, dt_max=1.0 / 16, n_corr=nc)
+        np.testing.assert_array_equal(st.t, 0.125)
+        drifts.append(abs(_energy_of(p.m, st.pos, st.vel, eps2) - e0) / abs(e0))
+    assert drifts[1] < drifts[0]
+
+
+def _energy_of(m, pos, vel, eps2):
+    k, w = oracle.energy(m, pos, vel, eps2)
+    return k + w

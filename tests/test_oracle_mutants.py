@@ -39,6 +39,10 @@ MUTANTS = [
     ("scheduler takes a particle early", "if (s->t[i] + s->dt[i] == t_next)\n            active[na++] = i;",
      "if (s->t[i] + s->dt[i] <= t_next + s->dt[i] / 2)\n            active[na++] = i;"),
     ("kinetic energy factor", "0.5 * m[i] * (v[0]", "m[i] * (v[0]"),
+    ("iterated corrector from corrected positions", "orc_correct_one(dt, xs + r, vs + r,",
+     "orc_correct_one(dt, pp + q, vp + q,"),
+    ("iterated corrector keeps predicted velocities", "vp[q + c] = v1[r + c];", "(void)v1;"),
+    ("one iteration too few", "for (int it = 1; it < n_corr; it++)", "for (int it = 2; it < n_corr; it++)"),
 ]
 
 
@@ -67,6 +71,9 @@ def _pins():
         ("equal_block_shared", H.test_equal_block_steps_equal_shared_steps),
         ("schedule_counts", H.test_block_schedule_counts_two_binaries),
         ("energy_order", H.test_energy_convergence_order),
+        ("pec_order", H.test_iterated_corrector_order_and_accuracy),
+        ("pec_symmetry", H.test_iterated_corrector_approaches_time_symmetry),
+        ("pec_block", H.test_iterated_corrector_block_steps_energy),
     ]
     return out
 
