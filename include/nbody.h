@@ -66,11 +66,13 @@ extern "C" {
 /* Block steps of NB_F32 / NB_F32DS handles normally run in the fused
  * persistent kernel: one cooperative launch takes block steps (scheduler +
  * predictor, force, reduction, corrector, with grid-wide barriers between
- * the stages) until a due set larger than NB_FUSED_MAX_NA or t_end, so small
+ * the stages) until a due set larger than nb_config.fused_max_na (default
+ * NB_FUSED_DEFAULT_NA) or t_end, so small
  * steps need no host round trip; larger due sets go to the planned force
  * kernels. NB_FLAG_NO_FUSED takes every block step with separate launches. */
 #define NB_FLAG_NO_FUSED 2
-#define NB_FUSED_MAX_NA 1024
+#define NB_FUSED_MAX_NA 4096      /* upper bound of nb_config.fused_max_na */
+#define NB_FUSED_DEFAULT_NA 1024  /* fused_max_na = 0 */
 
 typedef struct nb_config {
     int n_max;           /* particle capacity of the handle, >= 1 */
@@ -84,12 +86,18 @@ typedef struct nb_config {
     size_t budget_bytes; /* device-memory cap for the handle; 0 = none */
     int device;          /* CUDA device ordinal */
     int flags;           /* NB_FLAG_* */
-    int fused_max_na;    /* largest due set the fused kernel takes itself; 0 = NB_FUSED_MAX_NA */
+    int fused_max_na;    /* largest due set the fused kernel takes itself (<= NB_FUSED_MAX_NA);
+                          * 0 = NB_FUSED_DEFAULT_NA */
+    int n_corr;          /* force evaluations + corrections per step in nb_step: 0 or 1 = PEC,
+                          * n > 1 = the iterated corrector P(EC)^n (Hermite iteration: the
+                          * corrected active particles are evaluated and corrected again);
+                          * at most NB_MAX_CORR. Steps with n > 1 use separate launches. */
 } nb_config;
+#define NB_MAX_CORR 8
 
 /* Fills cfg with: n_max 1024, NB_F32DS, eps 0, eta 0.01, eta_s 0 (= eta),
  * dt_max 1/16, dt_min 2^-30, shared_dt 0, budget 0, device 0, flags 0,
- * fused_max_na 0. */
+ * fused_max_na 0, n_corr 0. */
 void nb_config_default(nb_config *cfg);
 
 /* Counters of a handle since creation or nb_reset_stats. Kernel times are

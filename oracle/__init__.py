@@ -16,6 +16,9 @@ Every routine follows a passage of the paper (Portegies Zwart & Bedorf,
   4th-order Hermite predictor-corrector with individual block steps
   (Sect. II, III, VI);
 - ``hermite_run``: the block-step (or shared-step) integration loop;
+- ``kick``, ``bridge_run``: the 2nd-order kick-drift-kick coupling of two
+  systems (Sect. V, the Hamiltonian split behind the hybrid codes), composed
+  of ``force_ext``, ``force`` and ``hermite_run``;
 - ``energy``: kinetic plus softened potential energy.
 
 Parity pins live in ``tests/test_oracle_*.py``; none is unpinned.
@@ -236,6 +239,36 @@ def hermite_run(state: State, t_end, eps2, eta=0.01, eta_s=None, dt_min=2.0 ** -
         raise MemoryError("oracle scratch allocation failed")
     state.initialised = True
     return int(steps.value), float(inter.value)
+
+
+def kick(state: State, field: State, eps2_field, eps2_self, dt_kick):
+    """Bridge kick (Sect. V): the velocities of ``state`` (synchronised) change by dt_kick
+    times the acceleration of the ``field`` system at their positions (softening of the
+    field), then acc and jerk of ``state``'s own particles are evaluated again at the new
+    velocities; the particles' steps are kept."""
+    acc, _, _ = force_ext(field.m, field.pos, field.vel, eps2_field, state.pos, state.vel)
+    state.vel += dt_kick * acc
+    a, j, _ = force(state.m, state.pos, state.vel, eps2_self)
+    state.acc[:] = a
+    state.jerk[:] = j
+
+
+def bridge_run(sa: State, sb: State, eps2_a, eps2_b, dt, n_steps, **hermite_kw):
+    """n_steps kick-drift-kick bridge steps of two systems (Sect. V, 2nd order): each
+    system is kicked by the other's field for dt/2, evolves with its own Hermite
+    integrator (``hermite_run`` keywords) for dt, and is kicked again. Both systems start
+    synchronised at the same time; uninitialised ones are initialised first."""
+    for st, e2 in ((sa, eps2_a), (sb, eps2_b)):
+        if not st.initialised:
+            hermite_run(st, float(st.t[0]), e2, **hermite_kw)
+    for _ in range(n_steps):
+        t = float(sa.t[0])
+        kick(sa, sb, eps2_b, eps2_a, 0.5 * dt)
+        kick(sb, sa, eps2_a, eps2_b, 0.5 * dt)
+        hermite_run(sa, t + dt, eps2_a, **hermite_kw)
+        hermite_run(sb, t + dt, eps2_b, **hermite_kw)
+        kick(sa, sb, eps2_b, eps2_a, 0.5 * dt)
+        kick(sb, sa, eps2_a, eps2_b, 0.5 * dt)
 
 
 def energy(m, pos, vel, eps2):

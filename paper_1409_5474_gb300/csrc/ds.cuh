@@ -46,17 +46,4 @@ __device__ __forceinline__ dsf ds_shfl_xor(dsf a, int o)
 
 __device__ __forceinline__ double ds_to_double(dsf a) { return (double)a.hi + (double)a.lo; }
 
-// A 16-byte shared-memory load kept as one vector load (LDS.128) even when some
-// of the four components are unused, where the compiler would otherwise split
-// it into narrower loads: a j-record costs three load instructions per warp.
-__device__ __forceinline__ float4 lds4(const float4 *p)
-{
-    float4 v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(a));
-    return v;
-}
-
 }  // namespace nb

@@ -498,12 +498,34 @@ int do_init(nb_handle h)
     return NB_OK;
 }
 
+// The iterations of P(EC)^n (n = cfg.n_corr > 1) after a step's first force
+// evaluation on the i-set `is` (n_a active particles act, or all when act is
+// null): n - 1 times a trial correction that puts the corrected active
+// particles into the j-set, and a new evaluation. The caller's final corrector
+// then recomputes the predicted values.
+int iterate_corrector(nb_handle h, const StateDev &s, const int *act, int n_a, double t_next,
+                      const StepParams &prm, const ISet &is, const Out3 &f)
+{
+    const bool rec = h->cfg.variant != NB_F64;
+    for (int it = 1; it < h->cfg.n_corr; ++it) {
+        int rc = timed(h, T_CORRECT, [&] {
+            return launch_correct_trial(s, act, n_a, t_next, f, prm, rec,
+                                        (rec && is.gathered) ? h->irec : nullptr, h->d_err,
+                                        h->stream);
+        });
+        if (rc) return rc;
+        rc = run_force(h, h->cfg.variant, is, f);
+        if (rc) return rc;
+    }
+    return NB_OK;
+}
+
 // Whether nb_step takes small block steps in the fused persistent kernel;
 // allocates its scratch at first use.
 bool fused_ready(nb_handle h)
 {
     if (h->cfg.variant == NB_F64 || (h->cfg.flags & NB_FLAG_NO_FUSED) ||
-        h->cfg.shared_dt > 0.0)
+        h->cfg.shared_dt > 0.0 || h->cfg.n_corr > 1)
         return false;
     if (h->fused_grid < 0) h->fused_grid = fused_grid(h->dev);
     const int g = h->fused_grid;
@@ -725,6 +747,8 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     if (!(cfg->shared_dt >= 0.0) || !std::isfinite(cfg->shared_dt))
         return fail(nullptr, NB_ERR_ARG, "shared_dt must be finite and >= 0");
     if (cfg->fused_max_na < 0) return fail(nullptr, NB_ERR_ARG, "fused_max_na must be >= 0");
+    if (cfg->n_corr < 0 || cfg->n_corr > NB_MAX_CORR)
+        return fail(nullptr, NB_ERR_ARG, "n_corr must be in [0, %d]", NB_MAX_CORR);
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1181,9 +1205,11 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             if (rc) return rc;
             rc = run_force(h, h->cfg.variant, all, f);
             if (rc) return rc;
+            rc = iterate_corrector(h, s, nullptr, h->n, t_next, prm, all, f);
+            if (rc) return rc;
             rc = timed(h, T_CORRECT, [&] {
                 return launch_correct(s, nullptr, h->n, t_next, f, prm, h->sd, h->d_err,
-                                      h->d_dtmin, h->stream);
+                                      h->d_dtmin, h->stream, nullptr, h->cfg.n_corr > 1);
             });
             if (rc) return rc;
             h->t_cur = t_next;
@@ -1206,7 +1232,7 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             fa.eps2f = (float)(h->cfg.eps * h->cfg.eps);
             fa.na_max = h->cfg.fused_max_na > 0
                             ? std::min(h->cfg.fused_max_na, NB_FUSED_MAX_NA)
-                            : NB_FUSED_MAX_NA;
+                            : NB_FUSED_DEFAULT_NA;
             fa.t_end = t_end;
             fa.part = h->fused_part;
             fa.cnt = h->fused_cnt;
@@ -1247,9 +1273,11 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
                 return fail(h, NB_ERR_STATE, "scheduler returned %d due particles", na);
             rc = run_force(h, h->cfg.variant, due_set(h, na), f);
             if (rc) return rc;
+            rc = iterate_corrector(h, s, h->act, na, t_next, prm, due_set(h, na), f);
+            if (rc) return rc;
             rc = timed(h, T_CORRECT, [&] {
                 return launch_correct(s, h->act, na, t_next, f, prm, h->sd, h->d_err, h->d_dtmin,
-                                      h->stream);
+                                      h->stream, nullptr, h->cfg.n_corr > 1);
             });
             if (rc) return rc;
             h->t_cur = t_next;

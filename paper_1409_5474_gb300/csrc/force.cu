@@ -397,10 +397,10 @@ __global__ void __launch_bounds__(32 * NWI * NWJ)
 
         auto body = [&](int jj, auto masked_tag) {
             constexpr bool MASKED = decltype(masked_tag)::value;
-            const float4 a = lds4(T + DS_REC * jj);
-            const float4 c = lds4(T + DS_REC * jj + 2);
+            const float4 a = T[DS_REC * jj];
+            const float4 c = T[DS_REC * jj + 2];
             float4 b;
-            if (DS) b = lds4(T + DS_REC * jj + 1);
+            if (DS) b = T[DS_REC * jj + 1];
 #pragma unroll
             for (int p = 0; p < IPT; ++p) {
                 float dx, dy, dz;
@@ -1368,10 +1368,10 @@ __global__ void __launch_bounds__(NT)
             }
             auto body = [&](int jj, auto masked_tag) {
                 constexpr bool MASKED = decltype(masked_tag)::value;
-                const float4 a = lds4(T + DS_REC * jj);
-                const float4 c = lds4(T + DS_REC * jj + 2);
+                const float4 a = T[DS_REC * jj];
+                const float4 c = T[DS_REC * jj + 2];
                 float4 b;
-                if (DS) b = lds4(T + DS_REC * jj + 1);
+                if (DS) b = T[DS_REC * jj + 1];
 #pragma unroll
                 for (int p = 0; p < IPT; ++p) {
                     float dx, dy, dz;

@@ -209,7 +209,17 @@ cudaError_t launch_predict(const StateDev &s, double t, bool want_rec, unsigned 
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new,
                            const Out3 &f, const StepParams &p, SchedDev *sd, unsigned *err,
                            unsigned long long *dtmin_hits, cudaStream_t st,
-                           const double *t_dev = nullptr);
+                           const double *t_dev = nullptr, bool xp_from_state = false);
+
+// The iterated corrector P(EC)^n: a trial correction of the n_a active
+// particles writes their corrected x, v over their predicted ones (pos_p,
+// vel_p, and with want_rec their j-records and, when irec is given, the
+// gathered due-set records in slot order), keeping the start-of-step state;
+// the next force evaluation then sees them. The final launch_correct of the
+// step passes xp_from_state = true (its predicted values are recomputed).
+cudaError_t launch_correct_trial(const StateDev &s, const int *act, int n_a, double t_new,
+                                 const Out3 &f, const StepParams &p, bool want_rec, float4 *irec,
+                                 unsigned *err, cudaStream_t st);
 
 // K4 of many systems in one launch. Job q serves CTAs [block0, block0 +
 // ceil(na / CORRECT_THREADS)) (jobs sorted by block0, nblocks CTAs in all).

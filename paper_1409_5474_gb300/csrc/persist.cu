@@ -273,10 +273,10 @@ __device__ __forceinline__ void cta_item(const FusedArgs &a, int na, int k0, int
 #pragma unroll 2
             for (int jj = lane; jj < cnt; jj += 32) {
                 const int j = tb + jj;
-                const float4 A = lds4(T + DS_REC * jj);
-                const float4 C = lds4(T + DS_REC * jj + 2);
+                const float4 A = T[DS_REC * jj];
+                const float4 C = T[DS_REC * jj + 2];
                 float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (DS) B = lds4(T + DS_REC * jj + 1);
+                if (DS) B = T[DS_REC * jj + 1];
 #pragma unroll
                 for (int p = 0; p < G; ++p) {
                     float dx, dy, dz;
@@ -344,7 +344,7 @@ __device__ __forceinline__ void cta_item(const FusedArgs &a, int na, int k0, int
 
 // The j-chunks of a step with na due particles on n (a function of (na, n,
 // grid) only): with at least eight groups of four due slots the CTAs take
-// items of 32 slots (cta mode), about two per CTA; otherwise warps take items of
+// items of 32 slots (cta mode), about four per CTA; otherwise warps take items of
 // four slots, about two per warp. At least 256 j per chunk, at most
 // FUSED_MAX_CHUNKS chunks.
 constexpr int FUSED_MAX_CHUNKS = 128;
@@ -358,7 +358,7 @@ __device__ __forceinline__ void chunking(int na, int n, int grid, int total_warp
     int nc;
     if (cta_mode) {
         const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
-        nc = (2 * grid + nsb - 1) / nsb;
+        nc = (4 * grid + nsb - 1) / nsb;
     } else {
         nc = (2 * total_warps + ng - 1) / ng;
     }
@@ -620,9 +620,10 @@ int fused_grid(int device)
 
 size_t fused_part_float2s(int grid, int na_max)
 {
-    // nchunk * na <= (2 W / ceil(na/4) + 1) * na <= 8 W + na for W warps
+    // warp items: nchunk * na <= (2 W / ceil(na/4) + 1) * na <= 8 W + na for W warps;
+    // CTA items: nchunk * na <= (4 G / ceil(na/32) + 1) * na <= 128 G + na = 16 W + na
     const size_t w = (size_t)grid * (FUSED_THREADS / 32);
-    return 7 * (8 * w + (size_t)na_max + 64);
+    return 7 * (16 * w + (size_t)na_max + 64);
 }
 
 cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st)

@@ -41,15 +41,12 @@ __global__ void k_predict(StateDev s, double t, unsigned *err, const double *t_d
         s.vel_p[q] = vp[c];
     }
     if (REC) {
-        float hi[3], lo[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            split_ds(xp[c], hi[c], lo[c]);
-        }
+        float4 rec[DS_REC];
+        make_record(xp, vp, s.m[i], i, rec);
         float4 *r = s.rec + (size_t)DS_REC * i;
-        r[0] = make_float4(hi[0], hi[1], hi[2], f32_trunc(s.m[i]));
-        r[1] = make_float4(lo[0], lo[1], lo[2], __int_as_float(i));
-        r[2] = make_float4(f32_trunc(vp[0]), f32_trunc(vp[1]), f32_trunc(vp[2]), 0.f);
+        r[0] = rec[0];
+        r[1] = rec[1];
+        r[2] = rec[2];
     }
 }
 
@@ -76,10 +73,51 @@ cudaError_t launch_advance(double *t_dev, double dt, cudaStream_t st)
 
 __global__ void k_correct(StateDev s, const int *__restrict__ act, int na, double t_new, Out3 f,
                           StepParams prm, SchedDev *sd, unsigned *err,
-                          unsigned long long *dtmin_hits, const double *t_dev)
+                          unsigned long long *dtmin_hits, const double *t_dev, bool xp_from_state)
 {
     correct_body(s, act, na, t_new, f, prm, sd, err, dtmin_hits, t_dev,
-                 blockIdx.x * blockDim.x + threadIdx.x);
+                 blockIdx.x * blockDim.x + threadIdx.x, xp_from_state);
+}
+
+// A trial correction of the iterated corrector P(EC)^n: the corrected x, v of
+// each active particle replace its predicted ones (pos_p, vel_p and, for the
+// FP32 kinds, its j-record and the gathered copy of its due-set record), so
+// that the next evaluation sees them; the start-of-step state is kept.
+template <bool REC>
+__global__ void k_correct_trial(StateDev s, const int *act, int na, double t_new, Out3 f,
+                                StepParams prm, float4 *irec, unsigned *err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    const int i = act ? act[k] : k;
+    const double dt = t_new - s.t[i];
+    double dt2, idt2, idt3;
+    step_factors(dt, prm, dt2, idt2, idt3);
+    double x1[3], v1[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double a1, j1, a2e, a3e;
+        correct_values(s, f, i, k, c, dt, dt2, idt2, idt3, true, x1[c], v1[c], a1, j1, a2e, a3e);
+        s.pos_p[c * s.ld + i] = x1[c];
+        s.vel_p[c * s.ld + i] = v1[c];
+        finite = finite && isfinite(x1[c]) && isfinite(v1[c]);
+    }
+    if (!finite) atomicOr(err, DERR_NONFINITE);
+    if (REC) {
+        float4 rec[DS_REC];
+        make_record(x1, v1, s.m[i], i, rec);
+        float4 *r = s.rec + (size_t)DS_REC * i;
+        r[0] = rec[0];
+        r[1] = rec[1];
+        r[2] = rec[2];
+        if (irec) {
+            float4 *g = irec + (size_t)DS_REC * k;
+            g[0] = rec[0];
+            g[1] = rec[1];
+            g[2] = rec[2];
+        }
+    }
 }
 
 // The job of CTA b in a list sorted by first CTA (block0 ascending).
@@ -109,12 +147,28 @@ __global__ void k_correct_multi(const CorrectJob *__restrict__ jobs, int njobs, 
 
 cudaError_t launch_correct(const StateDev &s, const int *act, int n_a, double t_new, const Out3 &f,
                            const StepParams &p, SchedDev *sd, unsigned *err,
-                           unsigned long long *dtmin_hits, cudaStream_t st, const double *t_dev)
+                           unsigned long long *dtmin_hits, cudaStream_t st, const double *t_dev,
+                           bool xp_from_state)
 {
     if (n_a <= 0) return cudaSuccess;
     const int bs = CORRECT_THREADS;  // FP64-heavy: spread small active sets over many SMs
     k_correct<<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits,
-                                                   t_dev);
+                                                   t_dev, xp_from_state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct_trial(const StateDev &s, const int *act, int n_a, double t_new,
+                                 const Out3 &f, const StepParams &p, bool want_rec, float4 *irec,
+                                 unsigned *err, cudaStream_t st)
+{
+    if (n_a <= 0) return cudaSuccess;
+    const int bs = CORRECT_THREADS;
+    if (want_rec)
+        k_correct_trial<true><<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p, irec,
+                                                                   err);
+    else
+        k_correct_trial<false><<<(n_a + bs - 1) / bs, bs, 0, st>>>(s, act, n_a, t_new, f, p,
+                                                                    irec, err);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,19 @@ __device__ __forceinline__ float f32_trunc(double x)
 
 // ---- K1 for one particle ------------------------------------------------------
 
+// The double-single j-record of particle i at position x, velocity v:
+// {x_hi, y_hi, z_hi, m}, {x_lo, y_lo, z_lo, index bits}, {vx, vy, vz, 0}.
+__device__ __forceinline__ void make_record(const double x[3], const double v[3], double m, int i,
+                                            float4 rec[3])
+{
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) split_ds(x[c], hi[c], lo[c]);
+    rec[0] = make_float4(hi[0], hi[1], hi[2], f32_trunc(m));
+    rec[1] = make_float4(lo[0], lo[1], lo[2], __int_as_float(i));
+    rec[2] = make_float4(f32_trunc(v[0]), f32_trunc(v[1]), f32_trunc(v[2]), 0.f);
+}
+
 // Predict particle i to time tn (FP64 Taylor series to the jerk term), write
 // pos_p / vel_p and, when REC, its double-single j-record (also left in rec[]);
 // returns whether the particle is due at tn (t_i + dt_i == tn).
@@ -77,13 +90,8 @@ __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn,
         s.vel_p[q] = vp[c];
     }
     if (REC) {
-        float hi[3], lo[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) split_ds(xp[c], hi[c], lo[c]);
+        make_record(xp, vp, s.m[i], i, rec);
         float4 *rr = s.rec + (size_t)DS_REC * i;
-        rec[0] = make_float4(hi[0], hi[1], hi[2], f32_trunc(s.m[i]));
-        rec[1] = make_float4(lo[0], lo[1], lo[2], __int_as_float(i));
-        rec[2] = make_float4(f32_trunc(vp[0]), f32_trunc(vp[1]), f32_trunc(vp[2]), 0.f);
         rr[0] = rec[0];
         rr[1] = rec[1];
         rr[2] = rec[2];
@@ -201,18 +209,31 @@ static __device__ double quantize_log2(int e, double dt_old, double t_new, doubl
 
 // ---- K4 --------------------------------------------------------------------
 
-// K4, component c of active slot k (particle i): Hermite corrector of x, v with
-// the new acc/jerk f (slot-indexed); writes pos, vel, acc, jerk of i and
-// returns the new acc, jerk and the end-of-step a2 (a2 + dt a3) and a3
-// components for the step criterion. Whether x and v stayed finite.
-__device__ __forceinline__ bool correct_component(const StateDev &s, const Out3 &f, int i, int k,
-                                                  int c, double dt, double dt2, double idt2,
-                                                  double idt3, double &a1o, double &j1o,
-                                                  double &a2eo, double &a3eo)
+// K4, component c of active slot k (particle i): the Hermite corrector of x, v
+// with the new acc/jerk f (slot-indexed). The predicted x_p, v_p are read from
+// pos_p / vel_p, or, with xp_from_state (the iterated corrector, which has
+// overwritten them), recomputed from the start-of-step state with the K1
+// formula, which gives the same bits. Returns x1, v1, the new acc/jerk and the
+// end-of-step a2 (a2 + dt a3) and a3 for the step criterion.
+__device__ __forceinline__ void correct_values(const StateDev &s, const Out3 &f, int i, int k,
+                                               int c, double dt, double dt2, double idt2,
+                                               double idt3, bool xp_from_state, double &x1,
+                                               double &v1, double &a1o, double &j1o,
+                                               double &a2eo, double &a3eo)
 {
     const long long q = c * s.ld + i;
     const double a0 = s.acc[q], j0 = s.jerk[q];
     const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
+    double xp, vp;
+    if (xp_from_state) {
+        const double x = s.pos[q], v = s.vel[q];
+        const double d = dt, d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
+        xp = fma(fma(fma(j0, d6, 0.5 * a0), d, v), d, x);
+        vp = fma(fma(j0, d2h, a0), d, v);
+    } else {
+        xp = s.pos_p[q];
+        vp = s.vel_p[q];
+    }
     // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
     // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
     // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
@@ -220,17 +241,31 @@ __device__ __forceinline__ bool correct_component(const StateDev &s, const Out3 
     const double da = a0 - a1;
     const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
     const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
-    const double x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), s.pos_p[q]);
-    const double v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), s.vel_p[q]);
+    x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), xp);
+    v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), vp);
     const double a2 = A2 * idt2, a3 = A3 * idt3;
-    s.pos[q] = x1;
-    s.vel[q] = v1;
-    s.acc[q] = a1;
-    s.jerk[q] = j1;
     a1o = a1;
     j1o = j1;
     a2eo = a2 + dt * a3;
     a3eo = a3;
+}
+
+// K4, component c of active slot k: correct_values, then the new pos, vel,
+// acc, jerk of particle i are stored. Whether x and v stayed finite.
+__device__ __forceinline__ bool correct_component(const StateDev &s, const Out3 &f, int i, int k,
+                                                  int c, double dt, double dt2, double idt2,
+                                                  double idt3, double &a1o, double &j1o,
+                                                  double &a2eo, double &a3eo,
+                                                  bool xp_from_state = false)
+{
+    const long long q = c * s.ld + i;
+    double x1, v1;
+    correct_values(s, f, i, k, c, dt, dt2, idt2, idt3, xp_from_state, x1, v1, a1o, j1o, a2eo,
+                   a3eo);
+    s.pos[q] = x1;
+    s.vel[q] = v1;
+    s.acc[q] = a1o;
+    s.jerk[q] = j1o;
     return isfinite(x1) && isfinite(v1);
 }
 
@@ -310,7 +345,7 @@ __device__ __forceinline__ void correct_body(const StateDev &s, const int *act, 
                                              double t_new, const Out3 &f, const StepParams &prm,
                                              SchedDev *sd, unsigned *err,
                                              unsigned long long *dtmin_hits, const double *t_dev,
-                                             int k)
+                                             int k, bool xp_from_state = false)
 {
     if (t_dev)
         t_new = *t_dev + t_new;
@@ -327,7 +362,7 @@ __device__ __forceinline__ void correct_body(const StateDev &s, const int *act, 
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         finite = correct_component(s, f, i, k, c, dt, dt2, idt2, idt3, a1v[c], j1v[c], a2e[c],
-                                   a3e[c]) &&
+                                   a3e[c], xp_from_state) &&
                  finite;
     if (!finite) atomicOr(err, DERR_NONFINITE);
     correct_step(s, i, t_new, dt, dt_old, a1v, j1v, a2e, a3e, prm, sd, dtmin_hits);

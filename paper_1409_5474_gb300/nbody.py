@@ -40,7 +40,9 @@ VARIANTS = {"f32": NB_F32, "f32ds": NB_F32DS, "f64": NB_F64}
 
 NB_FLAG_TIMING = 1
 NB_FLAG_NO_FUSED = 2
-NB_FUSED_MAX_NA = 1024
+NB_FUSED_MAX_NA = 4096
+NB_FUSED_DEFAULT_NA = 1024
+NB_MAX_CORR = 8
 
 
 class NBodyError(RuntimeError):
@@ -55,7 +57,8 @@ class nb_config(ctypes.Structure):
                 ("eta", ctypes.c_double), ("eta_s", ctypes.c_double), ("dt_max", ctypes.c_double),
                 ("dt_min", ctypes.c_double), ("shared_dt", ctypes.c_double),
                 ("budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
-                ("flags", ctypes.c_int), ("fused_max_na", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("fused_max_na", ctypes.c_int),
+                ("n_corr", ctypes.c_int)]
 
 
 class nb_plan(ctypes.Structure):

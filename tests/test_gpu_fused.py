@@ -27,7 +27,7 @@ def test_fused_first_step_force_vs_oracle(nb, n):
         s0 = s.state()
         t_next = float((s0["t"] + s0["dt"]).min())
         due = np.nonzero(s0["t"] + s0["dt"] == t_next)[0].astype(np.int32)
-        assert 1 <= len(due) <= nb.NB_FUSED_MAX_NA
+        assert 1 <= len(due) <= nb.NB_FUSED_DEFAULT_NA
         st = s.step(t_next)
         s1 = s.state()
     assert st["block_steps"] == 1 and st["fused_steps"] == 1 and st["fused_launches"] >= 1
@@ -44,7 +44,7 @@ def test_fused_first_step_force_vs_oracle(nb, n):
 def test_fused_matches_separate_launches(nb):
     """1/16 time unit of block steps, with and without the fused kernel: the same schedule
     (block steps, final steps), states equal to the double-single force error, and the
-    hand-over to the planned kernels (steps with more than NB_FUSED_MAX_NA due) used."""
+    hand-over to the planned kernels (steps with more than NB_FUSED_DEFAULT_NA due) used."""
     p = ic.plummer(5000, 61)
     kw = dict(variant="f32ds", eps=1e-2, eta=0.02, dt_max=1.0 / 16, device=0)
     with nb.System(p.m, p.pos, p.vel, **kw) as a:
@@ -74,7 +74,7 @@ def test_fused_block_steps_vs_oracle(nb):
                    device=0) as s:
         stats = s.step(1.0 / 16)
         g = s.state()
-    assert stats["fused_steps"] == stats["block_steps"]      # N < NB_FUSED_MAX_NA
+    assert stats["fused_steps"] == stats["block_steps"]      # N < NB_FUSED_DEFAULT_NA
     assert abs(stats["block_steps"] - o_steps) <= 0.05 * o_steps
     np.testing.assert_array_equal(g["t"], 1.0 / 16)
     assert np.abs(g["pos"].T - st.pos).max() < 1e-5
