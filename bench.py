@@ -73,6 +73,12 @@ WORKLOADS = {
                           "N=65536 (eps=1e-3) on 65536 external particles of a second Plummer "
                           "sphere offset by (0.5, 0, 0); one bench step = one call with host "
                           "arrays in and out"),
+    "bridge32768": dict(n=32768, eps=1e-3, eta=0.01, dt_max=1.0 / 16, variant="f32ds",
+                        masses="equal", kind="bridge", step_t=1.0 / 16,
+                        desc="bridge (Sect. V): two Plummer clusters of N=32768 (half mass, "
+                             "radius x0.25) 2 length units apart, each advanced with its own "
+                             "block-step Hermite (eta=0.01, dt_max=1/16), kicked by the other "
+                             "every 1/16 time unit; one bench step = one nb_bridge_step"),
     "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
                       variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
                       desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
@@ -393,6 +399,8 @@ def run_ours(args):
         return run_serve(args, wl, variant, dist, rank, world, local)
     if wl["kind"] == "ext":
         return run_ext(args, wl, variant, dist, rank, world, local)
+    if wl["kind"] == "bridge":
+        return run_bridge(args, wl, variant, dist, rank, world, local)
     p = make_particles(wl)
     stream = torch.cuda.Stream()          # the stream every kernel of the step runs on
     torch.cuda.set_stream(stream)
@@ -732,6 +740,76 @@ def run_ext(args, wl, variant, dist, rank, world, local):
                                           "external particles" % ni, "seconds": secs_c}
     print(json.dumps(line), flush=True)
     sysm.close()
+    dist.close()
+    return 0
+
+
+def run_bridge(args, wl, variant, dist, rank, world, local):
+    """Two systems coupled by the bridge; interactions = both systems' own block-step
+    evaluations plus the four cross evaluations (kicks) per step."""
+    import torch
+    from paper_1409_5474_gb300 import ic, nbody
+
+    n = wl["n"]
+    a = ic.plummer(n, ic.MASTER_SEED + 11)
+    b = ic.plummer(n, ic.MASTER_SEED + 12)
+    off = np.array([1.0, 0.0, 0.0])
+    vorb = np.array([0.0, 0.5 * math.sqrt(1.0 / 2.0), 0.0])   # mutual orbit of two halves
+    kw = dict(variant=variant, eps=wl["eps"], eta=wl["eta"], dt_max=wl["dt_max"], device=local,
+              flags=nbody.NB_FLAG_TIMING)
+    A = nbody.System(a.m * 0.5, a.pos * 0.25 - off, a.vel * math.sqrt(2.0) - vorb, **kw)
+    B = nbody.System(b.m * 0.5, b.pos * 0.25 + off, b.vel * math.sqrt(2.0) + vorb, **kw)
+    for _ in range(args.warmup):
+        nbody.nb_bridge_step(A.h, B.h, wl["step_t"])
+    nbody.nb_reset_stats(A.h)
+    nbody.nb_reset_stats(B.h)
+    torch.cuda.synchronize()
+    dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        nbody.nb_bridge_step(A.h, B.h, wl["step_t"])
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    sa, sb = nbody.nb_get_stats(A.h), nbody.nb_get_stats(B.h)
+    inter = sa["interactions"] + sb["interactions"]
+    units, secs = aggregate(dist.gather_pairs(inter, wall, device="cuda"))
+    if rank != 0:
+        A.close()
+        B.close()
+        dist.close()
+        return 0
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(measured_peaks().get("sm_max_mhz") or 2070.0)
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    value = units / secs / 1e9
+    force_ms = sa["force_ms"] + sb["force_ms"]
+    planned = float(sum(sa["inter_hist"]) + sum(sb["inter_hist"]))
+    achieved = FLOPS_PER_INTERACTION * planned / (force_ms / 1e3) / 1e12 if force_ms else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Plummer spheres, N-body units)",
+        "config": dict(config_of(wl, args.workload, variant), systems=2,
+                       parallelism="single GPU", timing="host wall clock around the call"),
+        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+        "roofline": {"bound": "alu", "kernel": "planned pair force kernels (both systems)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "force_ms": force_ms,
+                     "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived)" % sm_max},
+        "block_steps": sa["block_steps"] + sb["block_steps"],
+        "fused_steps": sa["fused_steps"] + sb["fused_steps"],
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "the state stays on the device; value is the call's wall clock"},
+        "gpu_launches": int(sa["kernel_launches"] + sb["kernel_launches"]),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    A.close()
+    B.close()
     dist.close()
     return 0
 

@@ -413,6 +413,30 @@ int nb_result_release(nb_server s, uint64_t ticket);
 
 int nb_server_get_stats(nb_server s, nb_server_stats *out);
 
+/* ---- bridge coupling of two systems (Sect. V) ------------------------------
+ * The paper's multi-scale method splits the Hamiltonian of two systems into
+ * their own parts and the interaction, and advances them with a 2nd-order
+ * kick-drift-kick "bridge": each system is kicked by the other's field, evolves
+ * with its own integrator, and is kicked again. Here both systems are handles
+ * of this library on the same device (for example a star cluster and the
+ * field particles of its host galaxy).
+ *
+ * nb_kick_ext: the velocities of target change by dt_kick times the
+ * acceleration of field's particles at target's positions (field's softening
+ * and precision variant); then target's own acc and jerk are evaluated again
+ * at the new velocities (the jerk depends on them); the steps dt_i stay. Both
+ * systems must be synchronised at the same time (every particle's own time
+ * equal to it), else NB_ERR_STATE; uninitialised systems are initialised
+ * first. The field's force counts in field's statistics.
+ *
+ * nb_bridge_step: one bridge step of length dt: kick both systems by each
+ * other for dt/2, advance each with nb_step to t + dt, kick both again for
+ * dt/2. dt must be a multiple of both systems' dt_max (block steps) or shared
+ * step, so both end synchronised; NB_ERR_ARG otherwise. Messages of a failure
+ * of b are reported on a. */
+int nb_kick_ext(nb_handle target, nb_handle field, double dt_kick);
+int nb_bridge_step(nb_handle a, nb_handle b, double dt);
+
 /* ---- allocation-free force evaluation -----------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot call cudaMalloc: a host code that gives all of its device memory to

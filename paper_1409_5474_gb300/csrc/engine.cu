@@ -301,6 +301,8 @@ int check_err(nb_handle h)
     if (e & DERR_BADINDEX) return fail(h, NB_ERR_ARG, "an i-set index is outside [0, n)");
     if (e & DERR_BACKWARD)
         return fail(h, NB_ERR_ARG, "prediction time is before some particle's own time");
+    if (e & DERR_UNSYNC)
+        return fail(h, NB_ERR_STATE, "the particles are not synchronised at the system time");
     return fail(h, NB_ERR_NONFINITE,
                 "non-finite force or state (coincident particles with eps = 0?)");
 }
@@ -496,6 +498,67 @@ int do_init(nb_handle h)
     h->t_cur = t0;
     h->sched_valid = true;
     return NB_OK;
+}
+
+// Bridge kick (Sect. V): the velocities of tgt change by dt_kick times the
+// acceleration of fld's particles at tgt's positions (fld's softening and
+// precision variant), then tgt's own acc and jerk are evaluated again at the new
+// velocities (jerk depends on them); the steps stay. Both systems must be
+// initialised and synchronised at the same time.
+int kick_by(nb_handle tgt, nb_handle fld, double dt_kick)
+{
+    const double t = tgt->t_cur;
+    if (fld->t_cur != t)
+        return fail(tgt, NB_ERR_STATE, "the two systems are at different times (%.17g, %.17g)",
+                    t, fld->t_cur);
+    // both synchronised at t (checked on the device)
+    CK(tgt, launch_check_sync(tgt->n, tgt->t, t, tgt->d_err, tgt->stream));
+    CK(fld, launch_check_sync(fld->n, fld->t, t, fld->d_err, fld->stream));
+    int rc = check_err(tgt);
+    if (rc) return rc;
+    rc = check_err(fld);
+    if (rc) return fail(tgt, rc, "field system: %s", fld->msg.c_str());
+    // the field's force on tgt's particles (an external i-set of fld)
+    rc = predict_to(fld, t);
+    if (rc) return rc;
+    const int n = tgt->n;
+    rc = grow(fld, &fld->io, &fld->io_cap, 7 * (size_t)n);
+    if (rc) return rc;
+    ISet ext;
+    ext.n = n;
+    ext.idx = nullptr;
+    ext.member = false;
+    ext.rec32 = nullptr;
+    ext.pos64 = tgt->pos;
+    ext.vel64 = tgt->vel;
+    ext.m64 = nullptr;
+    ext.ld64 = tgt->ld;
+    ext.nj = fld->n;
+    ext.gathered = false;
+    if (fld->cfg.variant != NB_F64) {
+        rc = grow(fld, &fld->ext_rec, &fld->ext_rec_cap, (size_t)DS_REC * n);
+        if (rc) return rc;
+        CK(fld, launch_make_rec(n, tgt->pos, tgt->vel, tgt->ld, fld->ext_rec, fld->stream));
+        ext.rec32 = fld->ext_rec;
+    }
+    const Out3 out{fld->io, fld->io + 3 * (size_t)n, fld->io + 6 * (size_t)n, n};
+    rc = run_force(fld, fld->cfg.variant, ext, out);
+    if (rc) return rc;
+    CK(fld, launch_kick(n, tgt->vel, tgt->ld, out.acc, n, dt_kick, fld->stream));
+    fld->stats.kernel_launches += 2;
+    rc = check_err(fld);  // synchronises fld's stream: tgt's velocities are final
+    if (rc) return fail(tgt, rc, "field system: %s", fld->msg.c_str());
+    // tgt's own acc and jerk at the kicked velocities
+    rc = predict_to(tgt, t);
+    if (rc) return rc;
+    const Out3 f{tgt->f_acc, tgt->f_jerk, tgt->f_pot, tgt->ld};
+    rc = run_force(tgt, tgt->cfg.variant, members_of(tgt, nullptr, tgt->n), f);
+    if (rc) return rc;
+    CK(tgt, launch_set_derivs(state_of(tgt), f, tgt->stream));
+    tgt->stats.kernel_launches++;
+    tgt->predicted = false;
+    tgt->last_force_n = -1;
+    return check_err(tgt);
 }
 
 // The iterations of P(EC)^n (n = cfg.n_corr > 1) after a step's first force
@@ -1285,6 +1348,11 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
             rc = launch_sched();
             if (rc) return rc;
         }
+        if (fused) {
+            // the fused kernel took steps of its own: the last block time is on the device
+            CK(h, cudaMemcpyAsync(&h->t_cur, &h->sd->t_cur, sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream));
+        }
     }
     h->predicted = false;
     h->last_force_n = -1;
@@ -1515,6 +1583,57 @@ int nb_autotune(nb_handle h, int reps)
     h->last_force_n = -1;
     if (rc) return rc;
     return check_err(h);
+}
+
+int nb_kick_ext(nb_handle target, nb_handle field, double dt_kick)
+{
+    if (!target || !field || target == field) return NB_ERR_ARG;
+    if (!std::isfinite(dt_kick)) return fail(target, NB_ERR_ARG, "dt_kick is not finite");
+    if (target->dev != field->dev)
+        return fail(target, NB_ERR_ARG, "the two systems are on different devices");
+    if (!target->have_particles || !field->have_particles)
+        return fail(target, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(target->dev);
+    for (nb_handle h : {target, field})
+        if (!h->initialised) {
+            int rc = do_init(h);
+            if (rc) return h == target ? rc : fail(target, rc, "field: %s", h->msg.c_str());
+        }
+    return kick_by(target, field, dt_kick);
+}
+
+// A step length that keeps a system synchronised: a multiple of its shared
+// step, or of dt_max with block steps.
+static bool keeps_sync(nb_handle h, double dt)
+{
+    const double unit = h->cfg.shared_dt > 0.0 ? h->cfg.shared_dt : h->cfg.dt_max;
+    const double q = dt / unit;
+    return q >= 1.0 && q == std::floor(q) && q < 1e15;
+}
+
+int nb_bridge_step(nb_handle a, nb_handle b, double dt)
+{
+    if (!a || !b || a == b) return NB_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(a, NB_ERR_ARG, "dt must be > 0");
+    if (a->dev != b->dev) return fail(a, NB_ERR_ARG, "the two systems are on different devices");
+    if (!a->have_particles || !b->have_particles) return fail(a, NB_ERR_STATE, "no particles set");
+    if (!keeps_sync(a, dt) || !keeps_sync(b, dt))
+        return fail(a, NB_ERR_ARG, "dt must be a multiple of both systems' dt_max (or shared step)");
+    cudaSetDevice(a->dev);
+    for (nb_handle h : {a, b})
+        if (!h->initialised) {
+            int rc = do_init(h);
+            if (rc) return h == a ? rc : fail(a, rc, "second system: %s", h->msg.c_str());
+        }
+    const double t = a->t_cur;
+    int rc;
+    if ((rc = kick_by(a, b, 0.5 * dt))) return rc;
+    if ((rc = kick_by(b, a, 0.5 * dt))) return fail(a, rc, "second system: %s", b->msg.c_str());
+    if ((rc = nb_step(a, t + dt, nullptr))) return rc;
+    if ((rc = nb_step(b, t + dt, nullptr))) return fail(a, rc, "second system: %s", b->msg.c_str());
+    if ((rc = kick_by(a, b, 0.5 * dt))) return rc;
+    if ((rc = kick_by(b, a, 0.5 * dt))) return fail(a, rc, "second system: %s", b->msg.c_str());
+    return NB_OK;
 }
 
 }  // extern "C"

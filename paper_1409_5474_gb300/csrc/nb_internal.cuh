@@ -15,6 +15,7 @@ enum : unsigned {
     DERR_TIMEOUT = 2u,    // a bounded mbarrier wait gave up
     DERR_BACKWARD = 4u,   // prediction to a time before a particle's own time
     DERR_BADINDEX = 8u,   // an i-set index outside [0, n_j) (replaced by 0)
+    DERR_UNSYNC = 16u,    // a particle's own time differs from the system time
 };
 
 // Double-single j-record, 48 bytes per particle (see DS_REC):
@@ -327,6 +328,14 @@ constexpr int FUSED_MAX_WORDS = 256;  // due-flag words per CTA: n <= 8192 x gri
 int fused_grid(int device);
 size_t fused_part_float2s(int grid, int na_max);
 cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st);
+
+// Bridge kicks (Sect. V): vel += dt * acc (SoA rows of strides ld, lda);
+// acc, jerk := a slot-indexed evaluation f for all particles; DERR_UNSYNC when
+// some t[i] != tc.
+cudaError_t launch_kick(int n, double *vel, long long ld, const double *acc, long long lda,
+                        double dt, cudaStream_t st);
+cudaError_t launch_set_derivs(const StateDev &s, const Out3 &f, cudaStream_t st);
+cudaError_t launch_check_sync(int n, const double *t, double tc, unsigned *err, cudaStream_t st);
 
 // Energy: K = sum m v^2 / 2 and W = sum m pot / 2 (single-CTA, fixed order).
 cudaError_t launch_energy(int n, const double *m, const double *vel, long long ld,

@@ -485,6 +485,59 @@ cudaError_t launch_sched_predict_multi(const SchedJob *jobs, int njobs, int nblo
     return cudaGetLastError();
 }
 
+// ---- bridge kicks (Sect. V) ---------------------------------------------------
+
+// vel[c][i] += dt * acc[c][i] for the n particles (SoA rows of stride ld / lda).
+__global__ void k_kick(int n, double *__restrict__ vel, long long ld,
+                       const double *__restrict__ acc, long long lda, double dt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vel[c * ld + i] = fma(dt, acc[c * lda + i], vel[c * ld + i]);
+}
+
+cudaError_t launch_kick(int n, double *vel, long long ld, const double *acc, long long lda,
+                        double dt, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_kick<<<(n + 255) / 256, 256, 0, st>>>(n, vel, ld, acc, lda, dt);
+    return cudaGetLastError();
+}
+
+// acc, jerk of every particle from a slot-indexed evaluation f (the steps stay).
+__global__ void k_set_derivs(StateDev s, Out3 f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s.acc[c * s.ld + i] = f.acc[c * f.ld + i];
+        s.jerk[c * s.ld + i] = f.jerk[c * f.ld + i];
+    }
+}
+
+cudaError_t launch_set_derivs(const StateDev &s, const Out3 &f, cudaStream_t st)
+{
+    if (s.n <= 0) return cudaSuccess;
+    k_set_derivs<<<(s.n + 255) / 256, 256, 0, st>>>(s, f);
+    return cudaGetLastError();
+}
+
+// Flags DERR_UNSYNC when some particle's own time is not tc.
+__global__ void k_check_sync(int n, const double *__restrict__ t, double tc, unsigned *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && t[i] != tc) atomicOr(err, DERR_UNSYNC);
+}
+
+cudaError_t launch_check_sync(int n, const double *t, double tc, unsigned *err, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_check_sync<<<(n + 255) / 256, 256, 0, st>>>(n, t, tc, err);
+    return cudaGetLastError();
+}
+
 // ---- energy ----------------------------------------------------------------
 
 constexpr int ENERGY_T = 512;

@@ -184,6 +184,8 @@ _SIGS = [
     ("nb_cancel", ctypes.c_int, [_H, ctypes.c_uint64]),
     ("nb_result_release", ctypes.c_int, [_H, ctypes.c_uint64]),
     ("nb_server_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_server_stats)]),
+    ("nb_kick_ext", ctypes.c_int, [_H, _H, ctypes.c_double]),
+    ("nb_bridge_step", ctypes.c_int, [_H, _H, ctypes.c_double]),
     ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -463,6 +465,14 @@ def nb_batch_autotune(b):
     t = ctypes.c_int()
     _bcheck(load().nb_batch_autotune(b, ctypes.byref(t)), "nb_batch_autotune", b)
     return t.value
+
+
+def nb_kick_ext(target, field, dt_kick) -> None:
+    _check(load().nb_kick_ext(target, field, float(dt_kick)), "nb_kick_ext", target)
+
+
+def nb_bridge_step(a, b, dt) -> None:
+    _check(load().nb_bridge_step(a, b, float(dt)), "nb_bridge_step", a)
 
 
 class Batch:
