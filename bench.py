@@ -257,6 +257,10 @@ def stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms, planned_inter,
         g = PREDICT_BYTES * n * fused_steps / (fused_stage_ms[0] / 1e3) / 1e9
         out["fused_predict_stage_gbs"] = g
         out["fused_predict_stage_us_per_step"] = 1e3 * fused_stage_ms[0] / fused_steps
+    if fused_steps and fused_stage_ms[2] > 0:
+        # the j-records every fused step's force stage reads (48 B per particle, from L2)
+        out["fused_force_stage_record_gbs"] = 48.0 * n * fused_steps / (fused_stage_ms[2] / 1e3) / 1e9
+        out["fused_force_stage_us_per_step"] = 1e3 * fused_stage_ms[2] / fused_steps
     if other_ms.get("correct_ms"):
         g = CORRECT_BYTES * (planned_inter / n) / (other_ms["correct_ms"] / 1e3) / 1e9
         out["planned_correct_gbs"] = g

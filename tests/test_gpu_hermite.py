@@ -191,3 +191,24 @@ def test_set_state_rejects_broken_block_invariant(nb):
         assert e.value.status == nb.NB_ERR_ARG
         s.set_state(ck)                     # the genuine checkpoint is accepted
         s.step(1.0 / 16)
+
+
+def test_double_single_against_fp64_pairs_block_steps(nb):
+    """The config-2 cross-check at N = 16384 (the oracle cannot run it in seconds): the
+    F32-DS path (fused small steps, planned large ones) against the FP64-pair path over
+    1/16 time unit of block steps: the same schedule to a few steps, states and energy
+    agreeing to the double-single level."""
+    p = ic.plummer(16384, 90)
+    kw = dict(eps=1e-3, eta=0.01, dt_max=1.0 / 16, device=0)
+    runs = {}
+    for variant in ("f32ds", "f64"):
+        with nb.System(p.m, p.pos, p.vel, variant=variant, **kw) as s:
+            st = s.step(1.0 / 16)
+            k, w = s.energy()
+            runs[variant] = (st, s.state(), k + w)
+    (sd, gd, ed), (s64, g64, e64) = runs["f32ds"], runs["f64"]
+    assert sd["fused_steps"] > 0
+    assert abs(sd["block_steps"] - s64["block_steps"]) <= 0.02 * s64["block_steps"]
+    np.testing.assert_array_equal(gd["t"], g64["t"])
+    assert np.abs(gd["pos"] - g64["pos"]).max() < 1e-5
+    assert abs(ed - e64) < 1e-6 * abs(e64)

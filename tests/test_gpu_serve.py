@@ -187,3 +187,29 @@ def test_many_small_requests_share_ticks(nb):
     eps = 0.25 / np.cbrt(sizes[i])
     ra, _, _ = oracle.force(m, pos.T, vel.T, eps * eps)
     assert _rel_rms(res[i]["acc"].T, ra) < 1e-6
+
+
+def test_sixty_four_stream_requests_alone_equal_mix(nb):
+    """64 requests drawn from the serving stream (galaxy subsystems with a central point
+    mass, N log-uniform in [2^8, 2^12], half force, half 1/16 time unit of block steps):
+    every result of the concurrent run is bitwise the result of the request served alone."""
+    reqs = ic.request_stream(64, 1e6, n_lo=2 ** 8, n_hi=2 ** 12, t_span=1.0 / 16)
+    parts = [ic.request_particles(r) for r in reqs]
+    kw = dict(variant=nb.NB_F32DS, eta=0.02, dt_max=1.0 / 16, device=0)
+
+    def submit(srv, r, p):
+        eps = 0.25 / np.cbrt(r.n)
+        if r.kind == "force":
+            return srv.force(p.m, p.pos.T, p.vel.T, eps)
+        return srv.evolve(p.m, p.pos.T, p.vel.T, eps, r.t_span)
+
+    with nb.Server(**kw) as srv:
+        mix = [srv.wait(t, timeout_s=300) for t in [submit(srv, r, p) for r, p in zip(reqs, parts)]]
+    with nb.Server(**kw) as srv:
+        alone = [srv.wait(submit(srv, r, p), timeout_s=300) for r, p in zip(reqs, parts)]
+    for r, a, b in zip(reqs, alone, mix):
+        assert a["status"] == b["status"] == nb.NB_STATUS_DONE
+        keys = ("acc", "jerk", "pot") if r.kind == "force" else ("pos", "vel")
+        for k in keys:
+            np.testing.assert_array_equal(a[k], b[k])
+        assert a["interactions"] == b["interactions"]
