@@ -437,6 +437,20 @@ int nb_server_get_stats(nb_server s, nb_server_stats *out);
 int nb_kick_ext(nb_handle target, nb_handle field, double dt_kick);
 int nb_bridge_step(nb_handle a, nb_handle b, double dt);
 
+/* ---- self-check of the bounded device waits ---------------------------------
+ * Every device-side wait of the library (a bulk copy's mbarrier, the
+ * scheduler's look-back, the fused kernel's grid barriers) gives up after a
+ * time limit, sets an error bit and returns, so the host reports NB_ERR_TIMEOUT
+ * and the device stays usable. nb_selftest_wait runs one such wait that
+ * nothing can complete, on device `device`, with a limit of limit_s seconds
+ * (0 < limit_s <= 2): which = 0, an mbarrier phase that no copy or arrival
+ * completes; which = 1, a grid barrier of a cooperative launch that one CTA
+ * never reaches. It returns NB_ERR_TIMEOUT when the wait gave up and reported
+ * it (the expected outcome), NB_ERR_STATE if the wait completed, NB_ERR_ARG /
+ * NB_ERR_CUDA / NB_ERR_OOM otherwise. For tests of failure detection; the paper
+ * has no counterpart. */
+int nb_selftest_wait(int which, double limit_s, int device);
+
 /* ---- allocation-free force evaluation -----------------------------------
  * The paper has no counterpart of this call; it exists for callers that
  * cannot call cudaMalloc: a host code that gives all of its device memory to

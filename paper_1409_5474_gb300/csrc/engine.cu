@@ -1636,4 +1636,38 @@ int nb_bridge_step(nb_handle a, nb_handle b, double dt)
     return NB_OK;
 }
 
+int nb_selftest_wait(int which, double limit_s, int device)
+{
+    if (which < 0 || which > 1 || !(limit_s > 0.0) || limit_s > 2.0) return NB_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return NB_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return NB_ERR_CUDA;
+    unsigned *d = nullptr;  // [0..2] barrier words, [3] error word
+    if (cudaMalloc(&d, 4 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return NB_ERR_OOM;
+    }
+    cudaStream_t st = nullptr;
+    unsigned e = 0;
+    const unsigned long long limit_ns = (unsigned long long)(limit_s * 1e9);
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), st);
+    if (ce == cudaSuccess)
+        ce = which == 0 ? launch_selftest_mbar(d + 3, limit_ns, st)
+                        : launch_selftest_barrier(d, d + 3, limit_ns, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(&e, d + 3, sizeof e, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(d);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return NB_ERR_CUDA;
+    }
+    return (e & DERR_TIMEOUT) ? NB_ERR_TIMEOUT : NB_ERR_STATE;
+}
+
 }  // extern "C"

@@ -103,15 +103,16 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Wait for phase `parity` of bar; gives up after WAIT_LIMIT_NS.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of bar; gives up after limit_ns (WAIT_LIMIT_NS).
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                       unsigned long long limit_ns = WAIT_LIMIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         for (int k = 0; k < 32; ++k)
             if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 
@@ -1772,6 +1773,25 @@ int jpar_blocks_per_sm(int variant)
         return 1;
     }
     return nb > 0 ? nb : 1;
+}
+
+// Self-check of the bounded copy wait: an mbarrier that no copy or arrival
+// completes; the wait gives up after limit_ns and reports DERR_TIMEOUT.
+__global__ void k_selftest_mbar(unsigned *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit_ns)) atomicOr(err, DERR_TIMEOUT);
+}
+
+cudaError_t launch_selftest_mbar(unsigned *err, unsigned long long limit_ns, cudaStream_t st)
+{
+    k_selftest_mbar<<<1, 32, 0, st>>>(err, limit_ns);
+    return cudaGetLastError();
 }
 
 int batch_blocks_per_sm(int variant, int threads)

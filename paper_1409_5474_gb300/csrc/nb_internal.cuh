@@ -327,6 +327,13 @@ constexpr int FUSED_MAX_WORDS = 256;  // due-flag words per CTA: n <= 8192 x gri
 // be launched cooperatively.
 int fused_grid(int device);
 size_t fused_part_float2s(int grid, int na_max);
+
+// Self-checks of the bounded device waits: a wait that nothing completes (an
+// mbarrier without arrivals; a grid barrier one CTA never reaches) gives up
+// after limit_ns and sets DERR_TIMEOUT in *err. bar: 3 words (cleared here).
+cudaError_t launch_selftest_mbar(unsigned *err, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t launch_selftest_barrier(unsigned *bar, unsigned *err, unsigned long long limit_ns,
+                                    cudaStream_t st);
 cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st);
 
 // Bridge kicks (Sect. V): vel += dt * acc (SoA rows of strides ld, lda);

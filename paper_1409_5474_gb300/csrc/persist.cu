@@ -50,7 +50,8 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 // to arrive resets the count and releases the next generation; the others
 // wait for it, bounded by BARRIER_LIMIT_NS or until another CTA gave up.
 // Returns false once any CTA has given up. gen: thread 0's generation.
-__device__ bool grid_barrier(unsigned *bar, unsigned &gen)
+__device__ bool grid_barrier(unsigned *bar, unsigned &gen,
+                             unsigned long long limit_ns = BARRIER_LIMIT_NS)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -70,7 +71,7 @@ __device__ bool grid_barrier(unsigned *bar, unsigned &gen)
                     ok = 0;
                     break;
                 }
-                if (globaltimer_ns() - t0 > BARRIER_LIMIT_NS) {
+                if (globaltimer_ns() - t0 > limit_ns) {
                     atomicExch(&bar[2], 1u);
                     ok = 0;
                     break;
@@ -602,6 +603,24 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         }
         if (tid < 4) a.stats->phase_ns[tid] += s_phase[tid];
     }
+}
+
+// Self-check of the bounded grid barrier: CTA 0 never arrives, the others give
+// up after limit_ns, raise the abort flag and report DERR_TIMEOUT.
+__global__ void k_selftest_barrier(unsigned *bar, unsigned *err, unsigned long long limit_ns)
+{
+    unsigned gen = 0;
+    if (blockIdx.x == 0) return;
+    if (!grid_barrier(bar, gen, limit_ns) && threadIdx.x == 0) atomicOr(err, DERR_TIMEOUT);
+}
+
+cudaError_t launch_selftest_barrier(unsigned *bar, unsigned *err, unsigned long long limit_ns,
+                                    cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&bar, &err, &limit_ns};
+    return cudaLaunchCooperativeKernel((const void *)k_selftest_barrier, 4, 64, args, 0, st);
 }
 
 int fused_grid(int device)

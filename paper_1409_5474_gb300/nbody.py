@@ -186,6 +186,7 @@ _SIGS = [
     ("nb_server_get_stats", ctypes.c_int, [_H, ctypes.POINTER(nb_server_stats)]),
     ("nb_kick_ext", ctypes.c_int, [_H, _H, ctypes.c_double]),
     ("nb_bridge_step", ctypes.c_int, [_H, _H, ctypes.c_double]),
+    ("nb_selftest_wait", ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int]),
     ("nb_force_static", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
@@ -465,6 +466,12 @@ def nb_batch_autotune(b):
     t = ctypes.c_int()
     _bcheck(load().nb_batch_autotune(b, ctypes.byref(t)), "nb_batch_autotune", b)
     return t.value
+
+
+def nb_selftest_wait(which, limit_s, device=0) -> int:
+    """Run one bounded device wait that nothing completes; returns the status
+    (NB_ERR_TIMEOUT is the expected one)."""
+    return load().nb_selftest_wait(int(which), float(limit_s), int(device))
 
 
 def nb_kick_ext(target, field, dt_kick) -> None:

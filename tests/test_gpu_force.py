@@ -230,3 +230,21 @@ def test_autotune_table_and_parity(nb):
         assert e.value.status == nb.NB_ERR_ARG
     ra, rj, rp = oracle.force(m, pos, vel, 1e-6)
     assert rel_rms(acc.T, ra) <= 1e-6 and rel_rms(jerk.T, rj) <= 1e-5
+
+
+@pytest.mark.parametrize("which", [0, 1], ids=["mbarrier", "grid_barrier"])
+def test_bounded_waits_time_out_and_leave_the_device_usable(nb, which):
+    """A device wait that nothing completes gives up after its limit and reports
+    NB_ERR_TIMEOUT; the next evaluation on the same device works."""
+    import time
+    t0 = time.perf_counter()
+    rc = nb.nb_selftest_wait(which, 0.05, 0)
+    dt = time.perf_counter() - t0
+    assert rc == nb.NB_ERR_TIMEOUT
+    assert 0.04 < dt < 5.0
+    m, pos, vel = _system(300, 9)
+    with nb.System(m, pos, vel, variant="f32ds", eps=1e-2, device=0) as s:
+        s.predict(0.0)
+        acc, _, _ = s.force()
+    ra, _, _ = oracle.force(m, pos, vel, 1e-4)
+    assert rel_rms(acc.T, ra) < 1e-6
