@@ -43,6 +43,10 @@ FP64_NOMINAL_TFLOPS = 1.25
 # algorithmic bytes per particle of the per-particle stages (FP64 SoA state):
 # predictor: t, dt, m, x, v, a, j read (120 B) + x_p, v_p and the 48-B j-record written (96 B)
 # corrector: index, t, dt, x_p, v_p, a, j, new a, j read (164 B) + x, v, a, j, t, dt written (112 B)
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+# one-pass ncu capture of the same launch): full N = 2^20 F32-DS evaluation with the
+# built-in plan (2048 i-blocks x 3 j-splits of k_force_tile32)
+MEASURED_TRAFFIC = {("full2p20", "f32ds", 1 << 20): 453.3e6}
 PREDICT_BYTES = 216
 CORRECT_BYTES = 276
 L2_FLUSH_BYTES = 256 << 20
@@ -544,7 +548,9 @@ def run_ours(args):
                                 if variant == "f64" else
                                 "k_force_tile32/k_force_wgrp32/k_force_tiny32 (planned pair force)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": (MEASURED_TRAFFIC.get((args.workload, variant, n))
+                                 if not args.autotune or wl["kind"] != "evolve" else None),
                      "peak_source": peak_source,
                      "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "force_ms": force_ms, "reduce_ms": reduce_ms,
