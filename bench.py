@@ -300,6 +300,25 @@ def oracle_sample(wl, particles):
         dt = time.perf_counter() - t0
         return inter, dt, ("oracle shared-step Hermite on 32 clusters with N log-spaced in "
                            "[%d, %d]: initial evaluation + 64 steps each" % (wl["n_lo"], wl["n_hi"]))
+    if wl["kind"] == "serve":
+        # the force requests of the stream, smallest first, for about 10 s
+        from paper_1409_5474_gb300 import ic
+        reqs = ic.request_stream(wl["n"], 1.0, n_lo=wl["n_lo"], n_hi=wl["n_hi"],
+                                 t_span=wl["t_span"])
+        inter, used = 0.0, 0
+        t0 = time.perf_counter()
+        for r in sorted(reqs, key=lambda q: q.n):
+            if r.kind != "force":
+                continue
+            q = ic.request_particles(r)
+            e = float(ic.cluster_eps(r.n))
+            oracle.force(q.m, q.pos, q.vel, e * e)
+            inter += float(r.n) * r.n
+            used += 1
+            if time.perf_counter() - t0 > 10.0:
+                break
+        return inter, time.perf_counter() - t0, (
+            "oracle force on the %d smallest force requests of the stream" % used)
     eps2 = wl["eps"] ** 2
     if wl["kind"] == "ext":
         from paper_1409_5474_gb300 import ic
@@ -366,7 +385,7 @@ def run_reference(args):
     import oracle
     wl = workload(args)
     variant = args.variant or wl["variant"]
-    p = make_particles(wl) if wl["kind"] != "batch" else None
+    p = make_particles(wl) if wl["kind"] not in ("batch", "serve") else None
     inter_t = secs_t = 0.0
     desc = ""
     for k in range(args.warmup + args.steps):

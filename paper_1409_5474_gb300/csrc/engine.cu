@@ -1546,6 +1546,19 @@ int nb_autotune(nb_handle h, int reps)
                     entries.push_back(nb_plan{kind, nwj, (int)ns});
                 }
             }
+            if (kind == 0 && variant != NB_F64) {
+                // splits that fill whole waves of resident CTAs (no ragged last wave)
+                const long long ib = (long long)(one.threads / one.nwj) * one.ipt;
+                const long long nblk = (n_i + ib - 1) / ib;
+                const long long slots = (long long)h->num_sms * tile_blocks_per_sm(variant, nwj);
+                long long last = 0;
+                for (long long k = 1; k <= 8; ++k) {
+                    const long long ns = (k * slots + nblk / 2) / nblk;  // nearest
+                    if (ns >= 1 && ns != last && ns <= 256)
+                        entries.push_back(nb_plan{kind, nwj, (int)ns});
+                    last = ns;
+                }
+            }
         }
         entries.push_back(entry_of(base));
         double best = 1e30;

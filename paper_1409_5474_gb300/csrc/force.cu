@@ -1794,6 +1794,32 @@ cudaError_t launch_selftest_mbar(unsigned *err, unsigned long long limit_ns, cud
     return cudaGetLastError();
 }
 
+template <int VAR, int NWI, int NWJ>
+static int tile_occ()
+{
+    constexpr int NT = 32 * NWI * NWJ;
+    constexpr int IB = 32 * NWI * 2;
+    const size_t ring = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
+    const size_t red = NWJ > 1 ? (size_t)NWJ * 7 * IB * sizeof(double) : 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, k_force_tile32<VAR, 2, NWI, NWJ, JT32, NS32>, NT, ring > red ? ring : red) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+int tile_blocks_per_sm(int variant, int nwj)
+{
+    if (variant == NB_F32DS)
+        return nwj == 1 ? tile_occ<NB_F32DS, 8, 1>()
+                        : (nwj == 4 ? tile_occ<NB_F32DS, 2, 4>() : tile_occ<NB_F32DS, 1, 8>());
+    return nwj == 1 ? tile_occ<NB_F32, 8, 1>()
+                    : (nwj == 4 ? tile_occ<NB_F32, 2, 4>() : tile_occ<NB_F32, 1, 8>());
+}
+
 int batch_blocks_per_sm(int variant, int threads)
 {
     int nb = 0;

@@ -75,6 +75,9 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms);
 // A plan from a plan-table entry (kind 0 or 1; sizes clamped to the sets).
 ForcePlan plan_from_entry(const nb_plan &e, int variant, int n_i, int n_j);
 
+// Resident CTAs per SM of the FP32 / double-single tile kernel with nwj warp rows.
+int tile_blocks_per_sm(int variant, int nwj);
+
 // Scratch doubles the plan needs for partial sums (0 when nsplit == 1).
 size_t plan_partial_doubles(const ForcePlan &p, int n_i);
 
