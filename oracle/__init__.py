@@ -16,6 +16,9 @@ Every routine follows a passage of the paper (Portegies Zwart & Bedorf,
   4th-order Hermite predictor-corrector with individual block steps
   (Sect. II, III, VI);
 - ``hermite_run``: the block-step (or shared-step) integration loop;
+- ``force6``, ``predict6``, ``correct6_one``, ``aarseth6_dt``, ``hermite6_run``: the
+  6th-order Hermite scheme (acc, jerk and snap per pair; Sect. II, the >= 4th-order
+  integrators with individual steps that direct codes use);
 - ``kick``, ``bridge_run``: the 2nd-order kick-drift-kick coupling of two
   systems (Sect. V, the Hamiltonian split behind the hybrid codes), composed
   of ``force_ext``, ``force`` and ``hermite_run``;
@@ -104,6 +107,17 @@ def _bind(lib):
                                        ctypes.POINTER(ctypes.c_long), _D])
     lib.orc_hermite_run.restype = ctypes.c_int
     lib.orc_energy.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double, _D, _D]
+    lib.orc_force6_idx.argtypes = [ctypes.c_int, _D, _D, _D, _D, ctypes.c_double,
+                                   ctypes.c_int, _I, _D, _D, _D, _D]
+    lib.orc_predict6.argtypes = [ctypes.c_int, ctypes.c_double] + [_D] * 10
+    lib.orc_correct6_one.argtypes = [ctypes.c_double] + [_D] * 13
+    lib.orc_aarseth6_dt.argtypes = [_D] * 6 + [ctypes.c_double]
+    lib.orc_aarseth6_dt.restype = ctypes.c_double
+    lib.orc_hermite6_run.argtypes = ([ctypes.c_int] + [_D] * 9
+                                     + [ctypes.c_double] * 7
+                                     + [ctypes.c_long, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_long), _D])
+    lib.orc_hermite6_run.restype = ctypes.c_int
     lib.orc_num_threads.restype = ctypes.c_int
     return lib
 
@@ -269,6 +283,84 @@ def bridge_run(sa: State, sb: State, eps2_a, eps2_b, dt, n_steps, **hermite_kw):
         hermite_run(sb, t + dt, eps2_b, **hermite_kw)
         kick(sa, sb, eps2_b, eps2_a, 0.5 * dt)
         kick(sb, sa, eps2_a, eps2_b, 0.5 * dt)
+
+
+def force6(m, pos, vel, acc_j, eps2, idx=None):
+    """acc, jerk, snap (ni,3) and pot (ni,) on i = idx[k] (all if None) from every j != i,
+    with acc_j (n,3) the particles' accelerations (the snap differentiates along them)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    pos, vel, acc_j = (_f64(a, (n, 3)) for a in (pos, vel, acc_j))
+    if idx is None:
+        ni, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.size and (idx.min() < 0 or idx.max() >= n):
+            raise IndexError("idx out of range")
+        ni, ip = idx.shape[0], idx.ctypes.data_as(_I)
+    acc, jerk, snap = (np.zeros((ni, 3)) for _ in range(3))
+    pot = np.zeros(ni)
+    lib.orc_force6_idx(n, _p(m), _p(pos), _p(vel), _p(acc_j), float(eps2), ni, ip, _p(acc),
+                       _p(jerk), _p(snap), _p(pot))
+    return acc, jerk, snap, pot
+
+
+def predict6(t, tj, pos, vel, acc, jerk, snap, crackle):
+    """Predicted (pos, vel, acc) at time t through the crackle term."""
+    lib = _load()
+    tj = _f64(tj)
+    n = tj.shape[0]
+    ins = [_f64(a, (n, 3)) for a in (pos, vel, acc, jerk, snap, crackle)]
+    outs = [np.zeros((n, 3)) for _ in range(3)]
+    lib.orc_predict6(n, float(t), _p(tj), *[_p(a) for a in ins], *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def correct6_one(dt, x0, v0, a0, j0, s0, a1, j1, s1):
+    """6th-order Hermite corrector for one particle: (x1, v1, a3_end, a4_end, a5_end)."""
+    lib = _load()
+    args = [_f64(a, (3,)) for a in (x0, v0, a0, j0, s0, a1, j1, s1)]
+    outs = [np.zeros(3) for _ in range(5)]
+    lib.orc_correct6_one(float(dt), *[_p(a) for a in args], *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def aarseth6_dt(a, a1, a2, a3, a4, a5, eta):
+    lib = _load()
+    return float(lib.orc_aarseth6_dt(*[_p(_f64(v, (3,))) for v in (a, a1, a2, a3, a4, a5)],
+                                     float(eta)))
+
+
+class State6(State):
+    """State of the 6th-order scheme: State plus snap and crackle per particle."""
+
+    def __init__(self, m, pos, vel, t0=0.0, acc=None, jerk=None, snap=None, crackle=None,
+                 t=None, dt=None):
+        super().__init__(m, pos, vel, t0, acc, jerk, t, dt)
+        n = self.n
+        self.snap = np.zeros((n, 3)) if snap is None else _f64(snap, (n, 3)).copy()
+        self.crackle = np.zeros((n, 3)) if crackle is None else _f64(crackle, (n, 3)).copy()
+
+
+def hermite6_run(state: State6, t_end, eps2, eta=0.1, eta_s=0.01, dt_min=2.0 ** -30,
+                 dt_max=1.0 / 16, dt_shared=0.0, max_steps=0):
+    """Advance ``state`` in place with the 6th-order Hermite scheme and block (or shared)
+    steps to t_end. Returns (n_block_steps, n_interactions)."""
+    lib = _load()
+    steps = ctypes.c_long(0)
+    inter = ctypes.c_double(0.0)
+    init = 0 if state.initialised else 1
+    rc = lib.orc_hermite6_run(state.n, _p(state.m), _p(state.pos), _p(state.vel),
+                              _p(state.acc), _p(state.jerk), _p(state.snap),
+                              _p(state.crackle), _p(state.t), _p(state.dt), float(eps2),
+                              float(eta), float(eta_s), float(dt_min), float(dt_max),
+                              float(dt_shared), float(t_end), int(max_steps), init,
+                              ctypes.byref(steps), ctypes.byref(inter))
+    if rc != 0:
+        raise MemoryError("oracle scratch allocation failed")
+    state.initialised = True
+    return int(steps.value), float(inter.value)
 
 
 def energy(m, pos, vel, eps2):

@@ -503,3 +503,325 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ---- 6th-order Hermite (Sect. II: direct codes pair with >= 4th-order
+ * integrators and individual steps; the reference cited there is Nitadori &
+ * Makino's 6th- and 8th-order Hermite schemes) ----------------------------- */
+
+/*
+ * Contribution of particle j to particle i with the second time derivative of
+ * the acceleration (the snap). With dx = xj - xi, dv = vj - vi, da = aj - ai
+ * (the particles' own accelerations) and q2 = |dx|^2 + eps2, differentiate
+ * A = mj dx q2^(-3/2) twice along the motion:
+ *   alpha = (dx.dv) / q2,   beta = (|dv|^2 + dx.da) / q2 + alpha^2
+ *   A = mj dx / q2^(3/2)
+ *   J = mj dv / q2^(3/2) - 3 alpha A                        (dA/dt)
+ *   S = mj da / q2^(3/2) - 6 alpha J - 3 beta A             (d^2A/dt^2)
+ *   pot = -mj / q2^(1/2)
+ */
+static void pair_terms6(double mj, const double *xj, const double *vj,
+                        const double *aj, const double *xi, const double *vi,
+                        const double *ai, double eps2, double acc[3],
+                        double jerk[3], double snap[3], double *pot)
+{
+    double dx[3], dv[3], da[3];
+    for (int c = 0; c < 3; c++) {
+        dx[c] = xj[c] - xi[c];
+        dv[c] = vj[c] - vi[c];
+        da[c] = aj[c] - ai[c];
+    }
+    double q2 = eps2 + dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    double q = sqrt(q2);
+    double inv_q3 = 1.0 / (q * q2);
+    double alpha = (dx[0] * dv[0] + dx[1] * dv[1] + dx[2] * dv[2]) / q2;
+    double beta = (dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] + dx[0] * da[0] +
+                   dx[1] * da[1] + dx[2] * da[2]) / q2 + alpha * alpha;
+    for (int c = 0; c < 3; c++) {
+        acc[c] = mj * dx[c] * inv_q3;
+        jerk[c] = mj * dv[c] * inv_q3 - 3.0 * alpha * acc[c];
+        snap[c] = mj * da[c] * inv_q3 - 6.0 * alpha * jerk[c] - 3.0 * beta * acc[c];
+    }
+    *pot = -mj / q;
+}
+
+static void sum_over_j6(int nj, const double *m, const double *pos,
+                        const double *vel, const double *acc_j,
+                        const double *xi, const double *vi, const double *ai,
+                        double eps2, int skip, double acc[3], double jerk[3],
+                        double snap[3], double *pot)
+{
+    ksum ka[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum kj[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum ks[3] = {{0, 0}, {0, 0}, {0, 0}};
+    ksum kp = {0, 0};
+    for (int j = 0; j < nj; j++) {
+        if (skip == j)
+            continue;
+        double a[3], jk[3], sn[3], p;
+        pair_terms6(m[j], pos + 3 * (size_t)j, vel + 3 * (size_t)j,
+                    acc_j + 3 * (size_t)j, xi, vi, ai, eps2, a, jk, sn, &p);
+        for (int c = 0; c < 3; c++) {
+            ks_add(&ka[c], a[c]);
+            ks_add(&kj[c], jk[c]);
+            ks_add(&ks[c], sn[c]);
+        }
+        ks_add(&kp, p);
+    }
+    for (int c = 0; c < 3; c++) {
+        acc[c] = ks_val(&ka[c]);
+        jerk[c] = ks_val(&kj[c]);
+        snap[c] = ks_val(&ks[c]);
+    }
+    *pot = ks_val(&kp);
+}
+
+/*
+ * acc, jerk, snap and pot of the members i = idx[k] (idx == NULL: i = k) from
+ * every j != i, given each particle's position, velocity and acceleration
+ * (acc_j: the accelerations the snap term differentiates along).
+ */
+void orc_force6_idx(int nj, const double *m, const double *pos,
+                    const double *vel, const double *acc_j, double eps2,
+                    int ni, const int *idx, double *acc, double *jerk,
+                    double *snap, double *pot)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int k = 0; k < ni; k++) {
+        int i = idx ? idx[k] : k;
+        sum_over_j6(nj, m, pos, vel, acc_j, pos + 3 * (size_t)i,
+                    vel + 3 * (size_t)i, acc_j + 3 * (size_t)i, eps2, i,
+                    acc + 3 * (size_t)k, jerk + 3 * (size_t)k,
+                    snap + 3 * (size_t)k, pot + k);
+    }
+}
+
+/*
+ * Taylor prediction to time t through the crackle term, d = t - tj[i]:
+ *   xp = x + v d + a d^2/2 + j d^3/6 + s d^4/24 + c d^5/120
+ *   vp = v + a d + j d^2/2 + s d^3/6 + c d^4/24
+ *   ap = a + j d + s d^2/2 + c d^3/6
+ */
+void orc_predict6(int n, double t, const double *tj, const double *pos,
+                  const double *vel, const double *acc, const double *jerk,
+                  const double *snap, const double *crackle, double *pos_p,
+                  double *vel_p, double *acc_p)
+{
+    for (int i = 0; i < n; i++) {
+        double d = t - tj[i];
+        double d2 = d * d, d3 = d2 * d, d4 = d3 * d, d5 = d4 * d;
+        for (int c = 0; c < 3; c++) {
+            size_t q = 3 * (size_t)i + c;
+            pos_p[q] = pos[q] + vel[q] * d + acc[q] * d2 / 2.0 + jerk[q] * d3 / 6.0 +
+                       snap[q] * d4 / 24.0 + crackle[q] * d5 / 120.0;
+            vel_p[q] = vel[q] + acc[q] * d + jerk[q] * d2 / 2.0 + snap[q] * d3 / 6.0 +
+                       crackle[q] * d4 / 24.0;
+            acc_p[q] = acc[q] + jerk[q] * d + snap[q] * d2 / 2.0 + crackle[q] * d3 / 6.0;
+        }
+    }
+}
+
+/*
+ * 6th-order Hermite corrector of one particle over a step dt, from the
+ * start-of-step x0, v0, a0, j0, s0 and the end-of-step a1, j1, s1 (evaluated
+ * at the predicted state). The two-point Hermite quadrature that is exact
+ * when the acceleration is a polynomial of degree <= 5 in time:
+ *   v1 = v0 + dt/2 (a0 + a1) - dt^2/10 (j1 - j0) + dt^3/120 (s0 + s1)
+ *   x1 = x0 + dt/2 (v0 + v1) - dt^2/10 (a1 - a0) + dt^3/120 (j0 + j1)
+ * The 3rd, 4th and 5th derivatives of the acceleration at the end of the
+ * step (for the step criterion and the next prediction) come from that
+ * quintic. Expanding it about the mid-point with T = dt/2, c_k its k-th
+ * derivative there, and the half sums / half differences
+ *   Am = (a1 - a0)/2, Jp = (j1 + j0)/2, Jm = (j1 - j0)/2,
+ *   Sp = (s1 + s0)/2, Sm = (s1 - s0)/2,
+ * the odd and even parts give
+ *   c5 = (45 Am - 45 T Jp + 15 T^2 Sm) / T^5
+ *   c3 = (15 (T Jp - Am) - 3 T^2 Sm) / (2 T^3)
+ *   c4 = 3 (T Sp - Jm) / T^3
+ * and at t1 = mid + T: a3 = c3 + c4 T + c5 T^2/2, a4 = c4 + c5 T, a5 = c5.
+ */
+void orc_correct6_one(double dt, const double x0[3], const double v0[3],
+                      const double a0[3], const double j0[3],
+                      const double s0[3], const double a1[3],
+                      const double j1[3], const double s1[3], double x1[3],
+                      double v1[3], double a3_end[3], double a4_end[3],
+                      double a5_end[3])
+{
+    double T = dt / 2.0;
+    for (int c = 0; c < 3; c++) {
+        v1[c] = v0[c] + dt / 2.0 * (a0[c] + a1[c]) - dt * dt / 10.0 * (j1[c] - j0[c]) +
+                dt * dt * dt / 120.0 * (s0[c] + s1[c]);
+        x1[c] = x0[c] + dt / 2.0 * (v0[c] + v1[c]) - dt * dt / 10.0 * (a1[c] - a0[c]) +
+                dt * dt * dt / 120.0 * (j0[c] + j1[c]);
+        double Am = (a1[c] - a0[c]) / 2.0;
+        double Jp = (j1[c] + j0[c]) / 2.0, Jm = (j1[c] - j0[c]) / 2.0;
+        double Sp = (s1[c] + s0[c]) / 2.0, Sm = (s1[c] - s0[c]) / 2.0;
+        double c5 = (45.0 * Am - 45.0 * T * Jp + 15.0 * T * T * Sm) / (T * T * T * T * T);
+        double c3 = (15.0 * (T * Jp - Am) - 3.0 * T * T * Sm) / (2.0 * T * T * T);
+        double c4 = 3.0 * (T * Sp - Jm) / (T * T * T);
+        a3_end[c] = c3 + c4 * T + c5 * T * T / 2.0;
+        a4_end[c] = c4 + c5 * T;
+        a5_end[c] = c5;
+    }
+}
+
+/*
+ * Step criterion of the 6th-order scheme (Aarseth's form generalised to
+ * order p = 6: the ratio of low to high derivatives to the power 1/(p - 3)):
+ *   dt = eta ( (sqrt(|a| |a2|) + |a1|) / (sqrt(|a3| |a5|) + |a4|) )^(1/3)
+ * with a1 = jerk, a2 = snap, a3 = crackle. A zero denominator gives +inf.
+ */
+double orc_aarseth6_dt(const double a[3], const double a1[3],
+                       const double a2[3], const double a3[3],
+                       const double a4[3], const double a5[3], double eta)
+{
+    double num = sqrt(norm3(a) * norm3(a2)) + norm3(a1);
+    double den = sqrt(norm3(a3) * norm3(a5)) + norm3(a4);
+    if (den == 0.0)
+        return INFINITY;
+    return eta * cbrt(num / den);
+}
+
+typedef struct {
+    int n;
+    double eps2;
+    double *m, *pos, *vel, *acc, *jerk, *snap, *crk, *t, *dt;
+} orc_state6;
+
+/* acc, jerk and snap of all particles at their common time: a first pass
+ * gives acc and jerk (which do not depend on the accelerations), a second
+ * pass with those accelerations gives the snap; crackle starts at zero and
+ * the initial step is eta_s |a| / |jerk| (quantized). Scratch: 4n doubles. */
+static void initialise6(orc_state6 *s, double eta_s, double dt_min,
+                        double dt_max, double dt_shared, double *scratch)
+{
+    int n = s->n;
+    double *aj = scratch, *pot = scratch + 3 * (size_t)n;
+    memset(aj, 0, sizeof(double) * 3 * (size_t)n);
+    orc_force6_idx(n, s->m, s->pos, s->vel, aj, s->eps2, n, NULL, s->acc,
+                   s->jerk, s->snap, pot);
+    memcpy(aj, s->acc, sizeof(double) * 3 * (size_t)n);
+    orc_force6_idx(n, s->m, s->pos, s->vel, aj, s->eps2, n, NULL, s->acc,
+                   s->jerk, s->snap, pot);
+    memset(s->crk, 0, sizeof(double) * 3 * (size_t)n);
+    for (int i = 0; i < n; i++) {
+        if (dt_shared > 0.0) {
+            s->dt[i] = dt_shared;
+        } else {
+            double raw = orc_initial_dt(s->acc + 3 * (size_t)i,
+                                        s->jerk + 3 * (size_t)i, eta_s);
+            s->dt[i] = orc_quantize(raw, 0.0, s->t[i], dt_min, dt_max);
+        }
+    }
+}
+
+/*
+ * One block step of the 6th-order scheme (PEC):
+ *   1. t_next = min_i (t_i + dt_i); active = {i : t_i + dt_i == t_next};
+ *   2. predict every particle's x, v, a to t_next (orc_predict6);
+ *   3. evaluate acc, jerk, snap of the active particles from the predicted
+ *      positions, velocities and accelerations;
+ *   4. correct them (orc_correct6_one) and give each a new step from the
+ *      end-of-step derivatives (orc_aarseth6_dt, quantized), or dt_shared.
+ * Scratch: pp, vp, ap (n,3); a1, j1, s1 (n,3) and p1 (n) for the active set.
+ */
+static int block_step6(orc_state6 *s, double eta, double dt_min, double dt_max,
+                       double dt_shared, int *active, double *pp, double *vp,
+                       double *ap, double *a1, double *j1, double *s1,
+                       double *p1, double *t_out)
+{
+    int n = s->n;
+    double t_next = INFINITY;
+    for (int i = 0; i < n; i++)
+        t_next = fmin(t_next, s->t[i] + s->dt[i]);
+    int na = 0;
+    for (int i = 0; i < n; i++) {
+        double due = s->t[i] + s->dt[i];
+        if (due == t_next)
+            active[na++] = i;
+    }
+
+    orc_predict6(n, t_next, s->t, s->pos, s->vel, s->acc, s->jerk, s->snap,
+                 s->crk, pp, vp, ap);
+    orc_force6_idx(n, s->m, pp, vp, ap, s->eps2, na, active, a1, j1, s1, p1);
+    for (int k = 0; k < na; k++) {
+        int i = active[k];
+        size_t q = 3 * (size_t)i, r = 3 * (size_t)k;
+        double dt = t_next - s->t[i];
+        double xn[3], vn[3], a3[3], a4[3], a5[3];
+        orc_correct6_one(dt, s->pos + q, s->vel + q, s->acc + q, s->jerk + q,
+                         s->snap + q, a1 + r, j1 + r, s1 + r, xn, vn, a3, a4, a5);
+        double dt_new;
+        if (dt_shared > 0.0) {
+            dt_new = dt_shared;
+        } else {
+            double raw = orc_aarseth6_dt(a1 + r, j1 + r, s1 + r, a3, a4, a5, eta);
+            dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
+        }
+        for (int c = 0; c < 3; c++) {
+            s->pos[q + c] = xn[c];
+            s->vel[q + c] = vn[c];
+            s->acc[q + c] = a1[r + c];
+            s->jerk[q + c] = j1[r + c];
+            s->snap[q + c] = s1[r + c];
+            s->crk[q + c] = a3[c];
+        }
+        s->t[i] = t_next;
+        s->dt[i] = dt_new;
+    }
+    *t_out = t_next;
+    return na;
+}
+
+/*
+ * Integrate with the 6th-order Hermite scheme and block (or shared) steps
+ * until every particle reaches t_end or max_steps block steps were taken
+ * (max_steps <= 0: no limit). In/out (n,3) arrays: pos, vel, acc, jerk, snap,
+ * crackle; (n) arrays t, dt. init != 0 evaluates acc, jerk, snap at the
+ * common start time, zeroes the crackle and assigns the steps; otherwise the
+ * given derivatives, times and steps are used (a resumed run).
+ * Counters as orc_hermite_run (the initial evaluation counts twice: it takes
+ * two passes). Returns 0, or -1 if a scratch allocation failed.
+ */
+int orc_hermite6_run(int n, const double *m, double *pos, double *vel,
+                     double *acc, double *jerk, double *snap, double *crackle,
+                     double *t, double *dt, double eps2, double eta,
+                     double eta_s, double dt_min, double dt_max,
+                     double dt_shared, double t_end, long max_steps, int init,
+                     long *n_block_steps, double *n_interactions)
+{
+    orc_state6 s = {n, eps2, (double *)m, pos, vel, acc, jerk, snap, crackle, t, dt};
+    int *active = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *buf = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 19);
+    if (!active || !buf) {
+        free(active);
+        free(buf);
+        return -1;
+    }
+    double *pp = buf, *vp = buf + 3 * (size_t)n, *ap = buf + 6 * (size_t)n;
+    double *a1 = buf + 9 * (size_t)n, *j1 = buf + 12 * (size_t)n;
+    double *s1 = buf + 15 * (size_t)n, *p1 = buf + 18 * (size_t)n;
+    long steps = 0;
+    double inter = 0.0;
+    if (init && n > 0) {
+        initialise6(&s, eta_s, dt_min, dt_max, dt_shared, buf);
+        inter += 2.0 * (double)n * (double)n;
+    }
+    while (n > 0 && (max_steps <= 0 || steps < max_steps)) {
+        double t_next = INFINITY;
+        for (int i = 0; i < n; i++)
+            if (t[i] + dt[i] < t_next)
+                t_next = t[i] + dt[i];
+        if (!(t_next <= t_end)) /* also ends a run whose times became NaN */
+            break;
+        double tn;
+        int na = block_step6(&s, eta, dt_min, dt_max, dt_shared, active, pp, vp,
+                             ap, a1, j1, s1, p1, &tn);
+        inter += (double)na * (double)n;
+        steps++;
+    }
+    *n_block_steps = steps;
+    *n_interactions = inter;
+    free(active);
+    free(buf);
+    return 0;
+}

@@ -2,8 +2,9 @@
 
 Each case copies ``oracle/oracle.c``, plants one plausible slip (a wrong factor,
 sign, power, operand order, dropped term), compiles the copy on the CPU, points
-the oracle wrapper at it and runs the pin tests of ``test_oracle_force.py`` and
-``test_oracle_hermite.py``; at least one pin must fail for every mutant. The
+the oracle wrapper at it and runs the pin tests of ``test_oracle_force.py``,
+``test_oracle_hermite.py`` and ``test_oracle_hermite6.py``; at least one pin must fail
+for every mutant. The
 unmodified source must pass them all.
 """
 import os
@@ -14,6 +15,7 @@ import oracle
 
 from . import test_oracle_force as F
 from . import test_oracle_hermite as H
+from . import test_oracle_hermite6 as H6
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -22,7 +24,7 @@ MUTANTS = [
     ("jerk radial term sign", "v[c] * inv_s3 - 3.0", "v[c] * inv_s3 + 3.0"),
     ("acc power of distance", "inv_s3 = 1.0 / (s2 * s);", "inv_s3 = 1.0 / (s2);"),
     ("separation transposed", "r[c] = xj[c] - xi[c];", "r[c] = xi[c] - xj[c];"),
-    ("relative velocity transposed", "v[c] = vj[c] - vi[c];", "v[c] = vi[c] - vj[c];"),
+    ("relative velocity transposed", " v[c] = vj[c] - vi[c];", " v[c] = vi[c] - vj[c];"),
     ("pot sign", "*pot = -mj / s;", "*pot = mj / s;"),
     ("softening dropped", "r[2] * r[2] + eps2;", "r[2] * r[2];"),
     ("self pair kept", "if (j == skip)", "if (j == skip && j < 0)"),
@@ -43,6 +45,28 @@ MUTANTS = [
      "orc_correct_one(dt, pp + q, vp + q,"),
     ("iterated corrector keeps predicted velocities", "vp[q + c] = v1[r + c];", "(void)v1;"),
     ("one iteration too few", "for (int it = 1; it < n_corr; it++)", "for (int it = 2; it < n_corr; it++)"),
+    ("snap: beta without alpha^2", "/ q2 + alpha * alpha;", "/ q2;"),
+    ("snap: alpha factor 6 -> 3", "- 6.0 * alpha * jerk[c]", "- 3.0 * alpha * jerk[c]"),
+    ("snap: relative acceleration transposed", "da[c] = aj[c] - ai[c];", "da[c] = ai[c] - aj[c];"),
+    ("snap: r.a term partly dropped", "dv[2] * dv[2] + dx[0] * da[0] +", "dv[2] * dv[2] + 0.0 * da[0] +"),
+    ("snap kernel: self pair kept", "if (skip == j)", "if (skip == j && j < 0)"),
+    ("snap kernel: softening dropped", "double q2 = eps2 + dx[0]", "double q2 = 0.0 + dx[0]"),
+    ("snap kernel: velocity transposed", "dv[c] = vj[c] - vi[c];", "dv[c] = vi[c] - vj[c];"),
+    ("predictor6 crackle term 1/120 -> 1/24", "crackle[q] * d5 / 120.0", "crackle[q] * d5 / 24.0"),
+    ("predictor6 acceleration truncated",
+     "acc_p[q] = acc[q] + jerk[q] * d + snap[q] * d2 / 2.0 + crackle[q] * d3 / 6.0;",
+     "acc_p[q] = acc[q] + jerk[q] * d;"),
+    ("corrector6 jerk coefficient 1/10 -> 1/12", "dt * dt / 10.0 * (j1[c] - j0[c])",
+     "dt * dt / 12.0 * (j1[c] - j0[c])"),
+    ("corrector6 position from v0 only", "dt / 2.0 * (v0[c] + v1[c])", "dt * v0[c]"),
+    ("crackle coefficient 15 -> 12", "(15.0 * (T * Jp - Am)", "(12.0 * (T * Jp - Am)"),
+    ("crackle left at the mid-point", "a3_end[c] = c3 + c4 * T + c5 * T * T / 2.0;", "a3_end[c] = c3;"),
+    ("pop sign", "a4_end[c] = c4 + c5 * T;", "a4_end[c] = c4 - c5 * T;"),
+    ("criterion6 exponent 1/3 -> 1/2", "eta * cbrt(num / den)", "eta * sqrt(num / den)"),
+    ("crackle not kept", "s->crk[q + c] = a3[c];", "s->crk[q + c] = 0.0;"),
+    ("scheduler6 takes a particle early", "if (due == t_next)", "if (due <= t_next + s->dt[i] / 2)"),
+    ("initial snap without accelerations", "memcpy(aj, s->acc, sizeof(double) * 3 * (size_t)n);",
+     "(void)0;"),
 ]
 
 
@@ -75,6 +99,7 @@ def _pins():
         ("pec_symmetry", H.test_iterated_corrector_approaches_time_symmetry),
         ("pec_block", H.test_iterated_corrector_block_steps_energy),
     ]
+    out += [("h6_" + k[5:], getattr(H6, k)) for k in sorted(dir(H6)) if k.startswith("test_")]
     return out
 
 
