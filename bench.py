@@ -12,7 +12,7 @@ block steps) per second, in G/s, and its fraction of FP32 peak at 60 flops per
 acc+jerk interaction.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload block65536|full2p20|batch4096|serve|small1024]
+                  [--workload block65536|h6block65536|full2p20|batch4096|serve|ext65536|bridge32768|small1024]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (rank 0 only under torchrun). Multi-GPU runs are
@@ -39,6 +39,9 @@ if ROOT not in sys.path:
 METRIC = "G pair-interactions/s (acc+jerk)"
 UNIT = "G interactions/s"
 FLOPS_PER_INTERACTION = 60
+# the 6th-order pair adds the snap: a_ij (3), |v|^2 + r.a (6), beta (3), the three
+# scale factors (3) and S = m a r^-3 - 6 alpha J - 3 beta A with its sum (3 x 6 + 3)
+FLOPS_PER_INTERACTION6 = 97
 FP64_NOMINAL_TFLOPS = 1.25
 # algorithmic bytes per particle of the per-particle stages (FP64 SoA state):
 # predictor: t, dt, m, x, v, a, j read (120 B) + x_p, v_p and the 48-B j-record written (96 B)
@@ -83,6 +86,13 @@ WORKLOADS = {
                              "radius x0.25) 2 length units apart, each advanced with its own "
                              "block-step Hermite (eta=0.01, dt_max=1/16), kicked by the other "
                              "every 1/16 time unit; one bench step = one nb_bridge_step"),
+    "h6block65536": dict(n=65536, eps=1e-3, eta=0.02, eta_s=0.01, dt_max=1.0 / 16, shared_dt=0.0,
+                         variant="f32ds", masses="equal", step_t=1.0 / 16, kind="evolve",
+                         order=6,
+                         desc="Plummer N=65536 equal masses, eps=1e-3, block steps of the "
+                              "6th-order Hermite scheme (acc, jerk, snap per pair; Aarseth "
+                              "criterion on a, jerk, snap, crackle with eta=0.02, eta_s=0.01, "
+                              "dt_max=1/16); one bench step = 1/16 time unit"),
     "small1024": dict(n=1024, eps=1.0 / 64, eta=0.01, dt_max=1.0 / 16, shared_dt=1.0 / 256,
                       variant="f64", masses="equal", step_t=1.0 / 16, kind="evolve",
                       desc="Plummer N=1024, eps=1/64, shared dt=1/256, FP64 pairs; one bench "
@@ -339,6 +349,14 @@ def oracle_sample(wl, particles):
         dt = time.perf_counter() - t0
         return float(ni) * particles.n, dt, (
             f"oracle force on a seeded {ni}-particle i-subset against all {particles.n} j")
+    if wl.get("order", 4) == 6:
+        st = oracle.State6(particles.m, particles.pos, particles.vel)
+        t0 = time.perf_counter()
+        steps, inter = oracle.hermite6_run(st, math.inf, eps2, eta=wl["eta"], eta_s=wl["eta_s"],
+                                           dt_max=wl["dt_max"], max_steps=ORACLE_BLOCK_STEPS)
+        return inter, time.perf_counter() - t0, (
+            f"oracle 6th-order block-step Hermite of the same system from t=0: two-pass "
+            f"start-up + first {ORACLE_BLOCK_STEPS} block steps")
     st = oracle.State(particles.m, particles.pos, particles.vel)
     t0 = time.perf_counter()
     if wl.get("shared_dt", 0.0) > 0:
@@ -370,7 +388,9 @@ def config_of(wl, name, variant):
          "l2": "flushed between timed steps (256 MB write)"}
     if wl["kind"] == "evolve":
         c.update({"eta": wl["eta"], "dt_max": wl["dt_max"], "shared_dt": wl["shared_dt"],
-                  "step_time_units": wl["step_t"]})
+                  "step_time_units": wl["step_t"], "order": wl.get("order", 4)})
+        if wl.get("order", 4) == 6:
+            c["eta_s"] = wl["eta_s"]
     if wl["kind"] == "batch":
         c.update({"n_clusters": wl["n"], "n_range": [wl["n_lo"], wl["n_hi"]], "shared_dt": wl["dt"],
                   "eps": "1/(4 N^(1/3)) per cluster", "step_time_units": wl["step_t"],
@@ -434,8 +454,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     cfg = dict(variant=variant, eps=wl["eps"], device=local, flags=nbody.NB_FLAG_TIMING,
                fused_max_na=args.fused_max_na, n_corr=args.n_corr)
+    order = wl.get("order", 4)
+    fpi = FLOPS_PER_INTERACTION6 if order == 6 else FLOPS_PER_INTERACTION
     if wl["kind"] == "evolve":
         cfg.update(eta=wl["eta"], dt_max=wl["dt_max"], shared_dt=wl["shared_dt"])
+    if order == 6:
+        cfg.update(order=6, eta_s=wl["eta_s"])
     sysm = nbody.System(p.m, p.pos, p.vel, **cfg)
     h = sysm.h
     nbody.nb_set_stream(h, stream.cuda_stream)
@@ -443,8 +467,8 @@ def run_ours(args):
     t_tune = time.perf_counter()
     # block steps use every N_active bucket: tune them all; a full evaluation uses one
     # plan, which the built-in heuristic already takes from a sweep
-    plan_table = (nbody.nb_autotune(h, 3) if args.autotune and wl["kind"] == "evolve"
-                  else None)
+    plan_table = (nbody.nb_autotune(h, 3)
+                  if args.autotune and wl["kind"] == "evolve" and order == 4 else None)
     t_tune = time.perf_counter() - t_tune
 
     def one_step(k, host_state):
@@ -455,10 +479,14 @@ def run_ours(args):
             w0 = time.perf_counter()
             if host_state is not None:
                 nbody.nb_set_state(h, host_state)          # H2D of the whole state
+                if order == 6:
+                    nbody.nb_set_snap(h, host_state["snap"], host_state["crackle"])
             e0.record(stream)
             st = nbody.nb_step(h, (k + 1) * wl["step_t"])
             e1.record(stream)
             out = nbody.nb_get_state(h)                    # D2H of the whole state
+            if order == 6:
+                out["snap"], out["crackle"] = nbody.nb_get_snap(h)
             w1 = time.perf_counter()
             stream.synchronize()
             return st["interactions"], e0.elapsed_time(e1), w1 - w0, st["kernel_launches"], st, out
@@ -487,6 +515,8 @@ def run_ours(args):
     energy0 = None
     if wl["kind"] == "evolve":
         host_state = nbody.nb_get_state(h)
+        if order == 6:
+            host_state["snap"], host_state["crackle"] = nbody.nb_get_snap(h)
         energy0 = sum(nbody.nb_energy(h))          # untimed: softened E at a synchronised time
     else:
         host_state = True
@@ -550,8 +580,7 @@ def run_ours(args):
     # the planned force launches' own interactions (the fused kernel's steps are
     # timed as a whole and reported apart)
     planned_inter = float(sum(hist["inter_hist"])) if wl["kind"] == "evolve" else tot_inter
-    achieved = (FLOPS_PER_INTERACTION * planned_inter / (force_ms / 1e3) / 1e12
-                if force_ms else None)
+    achieved = fpi * planned_inter / (force_ms / 1e3) / 1e12 if force_ms else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -560,10 +589,13 @@ def run_ours(args):
         "data": "synthetic (seeded Plummer sphere, N-body units)",
         "config": dict(config_of(wl, args.workload, variant),
                        parallelism=("replicas%d" % world) if world > 1 else "single GPU",
-                       corrector=("P(EC)^%d" % args.n_corr) if args.n_corr > 1 else "PEC"),
-        "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
+                       corrector=("P(EC)^%d" % args.n_corr) if args.n_corr > 1 else "PEC",
+                       integrator="Hermite order %d" % order),
+        "fp32_peak_frac": fpi * value * 1e9 / (peak * 1e12),
         "roofline": {"bound": "alu",
-                     "kernel": ("k_force_tile64/k_force_jmode64 (planned FP64 pair force)"
+                     "kernel": ("k_force6_tile32 / k_force6_tile64 (6th-order pair force)"
+                                if order == 6 else
+                                "k_force_tile64/k_force_jmode64 (planned FP64 pair force)"
                                 if variant == "f64" else
                                 "k_force_tile32/k_force_wgrp32/k_force_tiny32 (planned pair force)"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -571,14 +603,15 @@ def run_ours(args):
                      "traffic": (MEASURED_TRAFFIC.get((args.workload, variant, n))
                                  if not args.autotune or wl["kind"] != "evolve" else None),
                      "peak_source": peak_source,
-                     "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "flops_per_interaction": fpi,
                      "force_ms": force_ms, "reduce_ms": reduce_ms,
                      "force_launches": force_launches, "interactions": planned_inter},
         "kernel_ms": dict(other_ms, force_ms=force_ms, reduce_ms=reduce_ms),
         "block_steps": block_steps,
         "fused_steps": fused_steps,
-        "stage_bandwidth": stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms,
-                                           float(sum(hist["inter_hist"])), peaks),
+        "stage_bandwidth": (stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms,
+                                            float(sum(hist["inter_hist"])), peaks)
+                            if order == 4 else None),
         "energy": ({"E0": energy0, "E1": energy1,
                     "rel_drift": abs(energy1 - energy0) / abs(energy0),
                     "over_time_units": args.steps * wl["step_t"]}
@@ -588,8 +621,10 @@ def run_ours(args):
         "by_log2_active": {k: [round(x, 3) if isinstance(x, float) else x for x in v]
                            for k, v in hist.items()},
         "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8,
-                "d2h_bytes_per_step": (n * 15 * 8) if wl["kind"] == "evolve" else n * 7 * 8},
+                "h2d_bytes_per_step": (n * (15 if order == 4 else 21) * 8)
+                if wl["kind"] == "evolve" else n * 7 * 8,
+                "d2h_bytes_per_step": (n * (15 if order == 4 else 21) * 8)
+                if wl["kind"] == "evolve" else n * 7 * 8},
         "gpu_launches": launches,
         "plans": ("autotuned (nb_autotune, %.1f s untimed set-up)" % t_tune) if plan_table
                  else "built-in heuristic",

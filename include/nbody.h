@@ -92,12 +92,22 @@ typedef struct nb_config {
                           * n > 1 = the iterated corrector P(EC)^n (Hermite iteration: the
                           * corrected active particles are evaluated and corrected again);
                           * at most NB_MAX_CORR. Steps with n > 1 use separate launches. */
+    int order;           /* integrator order: 4 (0 = 4), the Hermite scheme with acc and jerk,
+                          * or 6, the 6th-order Hermite scheme that also evaluates the snap
+                          * (the second time derivative of the acceleration) of every pair
+                          * and predicts through the crackle (Sect. II: >= 4th-order
+                          * integrators with individual steps; the cited 6th-order Hermite
+                          * scheme of Nitadori & Makino). Order 6 needs NB_F32DS or NB_F64
+                          * pairs and n_corr <= 1, and has
+                          * no fused steps, plan table, external i-sets or bridge calls. Its
+                          * steps follow Aarseth's criterion with the evaluated snap as a2
+                          * and the end-of-step crackle as a3 (eta ~ 0.01-0.04). */
 } nb_config;
 #define NB_MAX_CORR 8
 
 /* Fills cfg with: n_max 1024, NB_F32DS, eps 0, eta 0.01, eta_s 0 (= eta),
  * dt_max 1/16, dt_min 2^-30, shared_dt 0, budget 0, device 0, flags 0,
- * fused_max_na 0, n_corr 0. */
+ * fused_max_na 0, n_corr 0, order 4. */
 void nb_config_default(nb_config *cfg);
 
 /* Counters of a handle since creation or nb_reset_stats. Kernel times are
@@ -203,6 +213,29 @@ int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk,
  * the next synchronous call. */
 int nb_force_dev(nb_handle h, const int *idx_dev, int n_i, double *acc_dev,
                  double *jerk_dev, double *pot_dev);
+
+/* nb_force on a handle of order 6 (NB_ERR_ARG otherwise), with the snap:
+ * acc, jerk, snap[3 n_i] (structure of arrays, any may be NULL) and pot of the members idx
+ * from every other particle at the state predicted by nb_predict (positions,
+ * velocities and accelerations through the crackle term). The pair snap is
+ * the second time derivative of the pair acceleration along the motion:
+ * with r, v, a the j-minus-i position, velocity and acceleration,
+ * r2 = |r|^2 + eps^2, alpha = r.v / r2, beta = (|v|^2 + r.a) / r2 + alpha^2:
+ * S = m a / r2^(3/2) - 6 alpha J - 3 beta A (A, J as in nb_force). nb_correct
+ * may follow (the 6th-order corrector). Errors as nb_force. */
+int nb_force_snap(nb_handle h, const int *idx, int n_i, double *acc, double *jerk,
+                  double *snap, double *pot);
+
+/* The 6th-order state beyond nb_get_state: snap and crackle (the 2nd and 3rd
+ * time derivatives of the acceleration) of the n particles, [3 n] structure of
+ * arrays each, either may be NULL. Order-6 handles only (NB_ERR_ARG otherwise). */
+int nb_get_snap(nb_handle h, double *snap, double *crackle);
+
+/* Completes a checkpoint restored by nb_set_state on an order-6 handle (both
+ * arrays [3 n], required, finite: else NB_ERR_ARG / NB_ERR_NONFINITE). Until it
+ * is called after nb_set_state, nb_step on that handle returns NB_ERR_STATE.
+ * With it the run resumes bit-identically. */
+int nb_set_snap(nb_handle h, const double *snap, const double *crackle);
 
 /* nb_force_ext (Sect. III.A, disjoint i-set): the force of the predicted
  * j-set on n_i external particles (pos[3 n_i], vel[3 n_i]); no pair is left

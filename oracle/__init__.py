@@ -16,7 +16,7 @@ Every routine follows a passage of the paper (Portegies Zwart & Bedorf,
   4th-order Hermite predictor-corrector with individual block steps
   (Sect. II, III, VI);
 - ``hermite_run``: the block-step (or shared-step) integration loop;
-- ``force6``, ``predict6``, ``correct6_one``, ``aarseth6_dt``, ``hermite6_run``: the
+- ``force6``, ``predict6``, ``correct6_one``, ``hermite6_run``: the
   6th-order Hermite scheme (acc, jerk and snap per pair; Sect. II, the >= 4th-order
   integrators with individual steps that direct codes use);
 - ``kick``, ``bridge_run``: the 2nd-order kick-drift-kick coupling of two
@@ -111,10 +111,8 @@ def _bind(lib):
                                    ctypes.c_int, _I, _D, _D, _D, _D]
     lib.orc_predict6.argtypes = [ctypes.c_int, ctypes.c_double] + [_D] * 10
     lib.orc_correct6_one.argtypes = [ctypes.c_double] + [_D] * 13
-    lib.orc_aarseth6_dt.argtypes = [_D] * 6 + [ctypes.c_double]
-    lib.orc_aarseth6_dt.restype = ctypes.c_double
     lib.orc_hermite6_run.argtypes = ([ctypes.c_int] + [_D] * 9
-                                     + [ctypes.c_double] * 7
+                                     + [ctypes.c_double] * 8
                                      + [ctypes.c_long, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_long), _D])
     lib.orc_hermite6_run.restype = ctypes.c_int
@@ -326,12 +324,6 @@ def correct6_one(dt, x0, v0, a0, j0, s0, a1, j1, s1):
     return tuple(outs)
 
 
-def aarseth6_dt(a, a1, a2, a3, a4, a5, eta):
-    lib = _load()
-    return float(lib.orc_aarseth6_dt(*[_p(_f64(v, (3,))) for v in (a, a1, a2, a3, a4, a5)],
-                                     float(eta)))
-
-
 class State6(State):
     """State of the 6th-order scheme: State plus snap and crackle per particle."""
 
@@ -343,10 +335,12 @@ class State6(State):
         self.crackle = np.zeros((n, 3)) if crackle is None else _f64(crackle, (n, 3)).copy()
 
 
-def hermite6_run(state: State6, t_end, eps2, eta=0.1, eta_s=0.01, dt_min=2.0 ** -30,
-                 dt_max=1.0 / 16, dt_shared=0.0, max_steps=0):
+def hermite6_run(state: State6, t_end, eps2, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30,
+                 dt_max=1.0 / 16, dt_shared=0.0, max_steps=0, noise=0.0):
     """Advance ``state`` in place with the 6th-order Hermite scheme and block (or shared)
-    steps to t_end. Returns (n_block_steps, n_interactions)."""
+    steps to t_end; ``noise``: the forces' relative rounding noise, which sets the floor
+    under the crackle in the step criterion (0: exact forces, no floor).
+    Returns (n_block_steps, n_interactions)."""
     lib = _load()
     steps = ctypes.c_long(0)
     inter = ctypes.c_double(0.0)
@@ -355,7 +349,7 @@ def hermite6_run(state: State6, t_end, eps2, eta=0.1, eta_s=0.01, dt_min=2.0 ** 
                               _p(state.acc), _p(state.jerk), _p(state.snap),
                               _p(state.crackle), _p(state.t), _p(state.dt), float(eps2),
                               float(eta), float(eta_s), float(dt_min), float(dt_max),
-                              float(dt_shared), float(t_end), int(max_steps), init,
+                              float(dt_shared), float(noise), float(t_end), int(max_steps), init,
                               ctypes.byref(steps), ctypes.byref(inter))
     if rc != 0:
         raise MemoryError("oracle scratch allocation failed")

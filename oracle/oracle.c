@@ -638,6 +638,11 @@ void orc_predict6(int n, double t, const double *tj, const double *pos,
  *   c3 = (15 (T Jp - Am) - 3 T^2 Sm) / (2 T^3)
  *   c4 = 3 (T Sp - Jm) / T^3
  * and at t1 = mid + T: a3 = c3 + c4 T + c5 T^2/2, a4 = c4 + c5 T, a5 = c5.
+ * The k-th derivative carries the force's rounding error divided by T^k; the
+ * step criterion of the block steps takes a, jerk, snap (evaluated) and the
+ * crackle a3 only (Aarseth's form, orc_aarseth_dt with a2 = snap, a3 =
+ * crackle): with FP32 pair arithmetic (rounding ~1e-7 of |a|), a criterion on
+ * a4 and a5 sees mostly noise at small T and drives the steps down to dt_min.
  */
 void orc_correct6_one(double dt, const double x0[3], const double v0[3],
                       const double a0[3], const double j0[3],
@@ -662,23 +667,6 @@ void orc_correct6_one(double dt, const double x0[3], const double v0[3],
         a4_end[c] = c4 + c5 * T;
         a5_end[c] = c5;
     }
-}
-
-/*
- * Step criterion of the 6th-order scheme (Aarseth's form generalised to
- * order p = 6: the ratio of low to high derivatives to the power 1/(p - 3)):
- *   dt = eta ( (sqrt(|a| |a2|) + |a1|) / (sqrt(|a3| |a5|) + |a4|) )^(1/3)
- * with a1 = jerk, a2 = snap, a3 = crackle. A zero denominator gives +inf.
- */
-double orc_aarseth6_dt(const double a[3], const double a1[3],
-                       const double a2[3], const double a3[3],
-                       const double a4[3], const double a5[3], double eta)
-{
-    double num = sqrt(norm3(a) * norm3(a2)) + norm3(a1);
-    double den = sqrt(norm3(a3) * norm3(a5)) + norm3(a4);
-    if (den == 0.0)
-        return INFINITY;
-    return eta * cbrt(num / den);
 }
 
 typedef struct {
@@ -721,12 +709,13 @@ static void initialise6(orc_state6 *s, double eta_s, double dt_min,
  *   3. evaluate acc, jerk, snap of the active particles from the predicted
  *      positions, velocities and accelerations;
  *   4. correct them (orc_correct6_one) and give each a new step from the
- *      end-of-step derivatives (orc_aarseth6_dt, quantized), or dt_shared.
+ *      end-of-step a, jerk, snap and crackle (orc_aarseth_dt, quantized), or
+ *      dt_shared.
  * Scratch: pp, vp, ap (n,3); a1, j1, s1 (n,3) and p1 (n) for the active set.
  */
-static int block_step6(orc_state6 *s, double eta, double dt_min, double dt_max,
-                       double dt_shared, int *active, double *pp, double *vp,
-                       double *ap, double *a1, double *j1, double *s1,
+static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
+                       double dt_max, double dt_shared, int *active, double *pp,
+                       double *vp, double *ap, double *a1, double *j1, double *s1,
                        double *p1, double *t_out)
 {
     int n = s->n;
@@ -754,9 +743,24 @@ static int block_step6(orc_state6 *s, double eta, double dt_min, double dt_max,
         if (dt_shared > 0.0) {
             dt_new = dt_shared;
         } else {
-            double raw = orc_aarseth6_dt(a1 + r, j1 + r, s1 + r, a3, a4, a5, eta);
+            /* Aarseth's criterion with the evaluated snap as a2 and the
+             * interpolated crackle as a3 (the 5th and 4th derivatives stay
+             * out: see orc_correct6_one). The crackle's magnitude is reduced
+             * by its rounding floor 30 noise |a| / T^3 (T = dt/2; the force's
+             * relative rounding noise enters a3 through (a1 - a0) / T^3 with
+             * coefficients 7.5 + 22.5): a crackle below the floor carries no
+             * information and counts as zero. noise = 0: no floor. */
+            double T = dt / 2.0;
+            double cfl = 30.0 * noise * norm3(a1 + r) / (T * T * T);
+            double cn = norm3(a3), ce[3] = {0.0, 0.0, 0.0};
+            if (cn > cfl)
+                for (int c = 0; c < 3; c++)
+                    ce[c] = a3[c] * ((cn - cfl) / cn);
+            double raw = orc_aarseth_dt(a1 + r, j1 + r, s1 + r, ce, eta);
             dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
         }
+        (void)a4;
+        (void)a5;
         for (int c = 0; c < 3; c++) {
             s->pos[q + c] = xn[c];
             s->vel[q + c] = vn[c];
@@ -779,6 +783,8 @@ static int block_step6(orc_state6 *s, double eta, double dt_min, double dt_max,
  * crackle; (n) arrays t, dt. init != 0 evaluates acc, jerk, snap at the
  * common start time, zeroes the crackle and assigns the steps; otherwise the
  * given derivatives, times and steps are used (a resumed run).
+ * noise >= 0 is the relative rounding noise of the forces for the crackle's
+ * floor in the step criterion (block_step6); 0 for exact forces.
  * Counters as orc_hermite_run (the initial evaluation counts twice: it takes
  * two passes). Returns 0, or -1 if a scratch allocation failed.
  */
@@ -786,8 +792,8 @@ int orc_hermite6_run(int n, const double *m, double *pos, double *vel,
                      double *acc, double *jerk, double *snap, double *crackle,
                      double *t, double *dt, double eps2, double eta,
                      double eta_s, double dt_min, double dt_max,
-                     double dt_shared, double t_end, long max_steps, int init,
-                     long *n_block_steps, double *n_interactions)
+                     double dt_shared, double noise, double t_end, long max_steps,
+                     int init, long *n_block_steps, double *n_interactions)
 {
     orc_state6 s = {n, eps2, (double *)m, pos, vel, acc, jerk, snap, crackle, t, dt};
     int *active = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
@@ -814,8 +820,8 @@ int orc_hermite6_run(int n, const double *m, double *pos, double *vel,
         if (!(t_next <= t_end)) /* also ends a run whose times became NaN */
             break;
         double tn;
-        int na = block_step6(&s, eta, dt_min, dt_max, dt_shared, active, pp, vp,
-                             ap, a1, j1, s1, p1, &tn);
+        int na = block_step6(&s, eta, noise, dt_min, dt_max, dt_shared, active, pp,
+                             vp, ap, a1, j1, s1, p1, &tn);
         inter += (double)na * (double)n;
         steps++;
     }

@@ -99,7 +99,7 @@ StateDev bstate(nb_batch b)
 
 StepParams bparams(nb_batch b)
 {
-    StepParams p;
+    StepParams p{};
     p.eta = 0.01;
     p.eta_s = 0.01;
     p.dt_min = b->dt;

@@ -5,7 +5,9 @@
 // stride ld = capacity rounded up to 64 (plus 64 doubles of padding, so that
 // bulk copies rounded up to 16 bytes stay inside the slab):
 //   m[ld], pos/vel/acc/jerk[3][ld], t[ld], dt[ld], pos_p/vel_p[3][ld],
-//   f_acc/f_jerk[3][ld], f_pot[ld], DS j-records rec[ld][3] (float4), act[ld].
+//   f_acc/f_jerk[3][ld], f_pot[ld], DS j-records rec[ld][3] (float4), act[ld],
+//   and for the 6th-order scheme snap/crackle/acc_p/f_snap[3][ld] and the
+//   64-byte j-records rec6[ld][4].
 // The block-step loop (paper Sect. III, III.A) runs one scheduler kernel per
 // block step, reads t_next and N_active from a mapped-memory mailbox, and
 // launches predictor, force (+ reduction) and corrector for that N_active.
@@ -16,6 +18,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -112,6 +115,11 @@ struct nb_handle_s {
     float4 *rec = nullptr;
     float4 *irec = nullptr;  // records of the due set, gathered by the scheduler
     int *act = nullptr;
+    // 6th-order scheme (order 6 only): snap, crackle, predicted acceleration,
+    // the snap output of a force evaluation, and the 64-byte j-records
+    double *snap = nullptr, *crk = nullptr, *acc_p = nullptr, *f_snap = nullptr;
+    float4 *rec6 = nullptr;
+    bool snap_valid = false;  // snap / crackle belong to the current state
 
     // growable scratch
     double *part = nullptr;
@@ -198,17 +206,25 @@ StateDev state_of(nb_handle h)
     s.pos_p = h->pos_p;
     s.vel_p = h->vel_p;
     s.rec = h->rec;
+    s.snap = h->snap;
+    s.crk = h->crk;
+    s.acc_p = h->acc_p;
+    s.rec6 = h->rec6;
     return s;
 }
 
+bool order6(nb_handle h) { return h->cfg.order == 6; }
+
 StepParams params_of(nb_handle h)
 {
-    StepParams p;
+    StepParams p{};
     p.eta = h->cfg.eta;
     p.eta_s = h->cfg.eta_s > 0.0 ? h->cfg.eta_s : h->cfg.eta;
     p.dt_min = h->cfg.dt_min;
     p.dt_max = h->cfg.dt_max;
     p.shared_dt = h->cfg.shared_dt;
+    // double-single pairs round at 2^-23 relative (FP32 pair arithmetic); FP64: none
+    p.noise = (h->cfg.order == 6 && h->cfg.variant == NB_F32DS) ? std::ldexp(1.0, -23) : 0.0;
     return p;
 }
 
@@ -404,7 +420,10 @@ int predict_to(nb_handle h, double t)
 {
     const bool rec = h->cfg.variant != NB_F64;
     StateDev s = state_of(h);
-    int rc = timed(h, T_PREDICT, [&] { return launch_predict(s, t, rec, h->d_err, h->stream); });
+    int rc = timed(h, T_PREDICT, [&] {
+        return order6(h) ? launch_predict6(s, t, rec, h->d_err, h->stream)
+                         : launch_predict(s, t, rec, h->d_err, h->stream);
+    });
     if (rc) return rc;
     h->predicted = true;
     h->t_pred = t;
@@ -475,12 +494,15 @@ int wait_mail(nb_handle h, unsigned long long epoch)
     return NB_OK;
 }
 
+int do_init6(nb_handle h, double t0);
+
 int do_init(nb_handle h)
 {
     // all own times are equal at set-up: predict with d = 0 builds the records
     double t0 = 0.0;
     CK(h, cudaMemcpyAsync(&t0, h->t, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (order6(h)) return do_init6(h, t0);
     int rc = predict_to(h, t0);
     if (rc) return rc;
     Out3 f{h->f_acc, h->f_jerk, h->f_pot, h->ld};
@@ -497,6 +519,140 @@ int do_init(nb_handle h)
     h->predicted = false;
     h->t_cur = t0;
     h->sched_valid = true;
+    return NB_OK;
+}
+
+// ---- 6th-order scheme ---------------------------------------------------------
+
+// acc, jerk, snap and pot of the members idx_dev[k] (null: k) at the predicted
+// state into out; plans, grows scratch, records timers and counters.
+int run_force6(nb_handle h, int variant, const int *idx_dev, int n_i, const Out6 &out)
+{
+    if (n_i <= 0) return NB_OK;
+    const ForcePlan p = plan_force6(variant, n_i, h->n, h->num_sms);
+    int rc = grow(h, &h->part, &h->part_cap, std::max<size_t>(plan6_partial_doubles(p, n_i), 1));
+    if (rc) return rc;
+    cudaEvent_t ev[4];
+    cudaEvent_t *evp = nullptr;
+    if (timing(h)) {
+        for (auto &e : ev) e = h->timer.get();
+        evp = ev;
+    }
+    const double eps2 = h->cfg.eps * h->cfg.eps;
+    CK(h, launch_force6(variant, p, state_of(h), idx_dev, n_i, eps2, h->part, out, h->d_err,
+                        h->stream, evp));
+    h->stats.kernel_launches += p.nsplit > 1 ? 2 : 1;
+    int lg = 0;
+    while ((2LL << lg) <= n_i && lg < 31) ++lg;
+    if (evp) {
+        h->timer.add(T_FORCE, ev[0], ev[1], lg);
+        h->timer.add(T_REDUCE, ev[2], ev[3]);
+    }
+    h->stats.force_launches++;
+    h->stats.interactions += (double)n_i * (double)h->n;
+    h->stats.inter_hist[lg] += (double)n_i * (double)h->n;
+    return NB_OK;
+}
+
+Out6 out6_of(nb_handle h) { return Out6{h->f_acc, h->f_jerk, h->f_snap, h->f_pot, h->ld}; }
+
+// Start-up of the 6th-order scheme at the common time t0: a first evaluation
+// gives acc and jerk (they do not depend on the accelerations), a second one
+// with those accelerations in the records gives the snap; crackle starts at
+// zero; the initial steps come from acc and jerk as in the 4th-order path.
+int do_init6(nb_handle h, double t0)
+{
+    const int n = h->n;
+    CK(h, cudaMemsetAsync(h->acc, 0, 3 * h->ld * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->jerk, 0, 3 * h->ld * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->snap, 0, 3 * h->ld * sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->crk, 0, 3 * h->ld * sizeof(double), h->stream));
+    const Out6 f = out6_of(h);
+    const Out3 f3{h->f_acc, h->f_jerk, h->f_pot, h->ld};
+    for (int pass = 0; pass < 2; ++pass) {
+        int rc = predict_to(h, t0);
+        if (rc) return rc;
+        rc = run_force6(h, h->cfg.variant, nullptr, n, f);
+        if (rc) return rc;
+        if (pass == 0) CK(h, launch_set_derivs(state_of(h), f3, h->stream));
+    }
+    StateDev s = state_of(h);
+    CK(h, cudaMemsetAsync(h->sd->hist, 0, NLEVEL * sizeof(int), h->stream));
+    CK(h, launch_init_steps(s, f3, params_of(h), h->sd, h->d_err, h->stream));
+    CK(h, cudaMemcpyAsync(h->snap, h->f_snap, 3 * h->ld * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->stream));
+    h->stats.kernel_launches += 2;
+    int rc = check_err(h);
+    if (rc) return rc;
+    h->initialised = true;
+    h->snap_valid = true;
+    h->predicted = false;
+    h->t_cur = t0;
+    h->sched_valid = true;
+    return NB_OK;
+}
+
+// Block (or shared) steps of the 6th-order scheme to t_end: the order-6
+// scheduler + predictor publishes (t_next, N_active), then the force on the
+// due set and the corrector are queued; shared steps need no scheduler.
+int step6_loop(nb_handle h, double t_end, const std::function<void(int)> &count_step)
+{
+    StateDev s = state_of(h);
+    const StepParams prm = params_of(h);
+    const bool rec = h->cfg.variant != NB_F64;
+    const Out6 f = out6_of(h);
+    int rc;
+    if (prm.shared_dt > 0.0) {
+        for (;;) {
+            const double t_next = h->t_cur + prm.shared_dt;
+            if (!(t_next <= t_end)) break;
+            rc = timed(h, T_PREDICT,
+                       [&] { return launch_predict6(s, t_next, rec, h->d_err, h->stream); });
+            if (rc) return rc;
+            rc = run_force6(h, h->cfg.variant, nullptr, h->n, f);
+            if (rc) return rc;
+            rc = timed(h, T_CORRECT, [&] {
+                return launch_correct6(s, nullptr, h->n, t_next, f, prm, h->sd, h->d_err,
+                                       h->d_dtmin, h->stream);
+            });
+            if (rc) return rc;
+            h->t_cur = t_next;
+            count_step(h->n);
+        }
+        return NB_OK;
+    }
+    auto launch_sched = [&]() -> int {
+        h->seq_next++;
+        int r = timed(h, T_SCHED, [&] {
+            return launch_sched_predict6(s, h->sd, h->sched_status, h->act, h->mail_d,
+                                         prm.dt_max, rec, h->d_err, h->stream);
+        });
+        if (r) return r;
+        CK(h, cudaEventRecord(h->ev_sched, h->stream));
+        return NB_OK;
+    };
+    rc = launch_sched();
+    if (rc) return rc;
+    for (;;) {
+        rc = wait_mail(h, h->seq_next - 1);
+        if (rc) return rc;
+        const double t_next = h->mail_h->t_next;
+        const int na = h->mail_h->n_active;
+        if (!(t_next <= t_end)) break;
+        if (na < 1 || na > h->n)
+            return fail(h, NB_ERR_STATE, "scheduler returned %d due particles", na);
+        rc = run_force6(h, h->cfg.variant, h->act, na, f);
+        if (rc) return rc;
+        rc = timed(h, T_CORRECT, [&] {
+            return launch_correct6(s, h->act, na, t_next, f, prm, h->sd, h->d_err, h->d_dtmin,
+                                   h->stream);
+        });
+        if (rc) return rc;
+        h->t_cur = t_next;
+        count_step(na);
+        rc = launch_sched();
+        if (rc) return rc;
+    }
     return NB_OK;
 }
 
@@ -588,7 +744,7 @@ int iterate_corrector(nb_handle h, const StateDev &s, const int *act, int n_a, d
 bool fused_ready(nb_handle h)
 {
     if (h->cfg.variant == NB_F64 || (h->cfg.flags & NB_FLAG_NO_FUSED) ||
-        h->cfg.shared_dt > 0.0 || h->cfg.n_corr > 1)
+        h->cfg.shared_dt > 0.0 || h->cfg.n_corr > 1 || order6(h))
         return false;
     if (h->fused_grid < 0) h->fused_grid = fused_grid(h->dev);
     const int g = h->fused_grid;
@@ -764,6 +920,7 @@ void nb_config_default(nb_config *cfg)
     cfg->budget_bytes = 0;
     cfg->device = 0;
     cfg->flags = 0;
+    cfg->order = 4;
 }
 
 const char *nb_status_string(int status)
@@ -812,6 +969,14 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     if (cfg->fused_max_na < 0) return fail(nullptr, NB_ERR_ARG, "fused_max_na must be >= 0");
     if (cfg->n_corr < 0 || cfg->n_corr > NB_MAX_CORR)
         return fail(nullptr, NB_ERR_ARG, "n_corr must be in [0, %d]", NB_MAX_CORR);
+    if (cfg->order != 0 && cfg->order != 4 && cfg->order != 6)
+        return fail(nullptr, NB_ERR_ARG, "order must be 4 or 6 (0 = 4)");
+    if (cfg->order == 6 && cfg->n_corr > 1)
+        return fail(nullptr, NB_ERR_ARG, "the 6th-order scheme takes one evaluation per step");
+    if (cfg->order == 6 && cfg->variant == NB_F32)
+        return fail(nullptr, NB_ERR_ARG,
+                    "the 6th-order scheme needs double-single or FP64 pairs (its end-of-step "
+                    "derivatives amplify the FP32 position rounding)");
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -823,6 +988,7 @@ int nb_create(const nb_config *cfg, nb_handle *out)
 
     nb_handle h = new nb_handle_s();
     h->cfg = *cfg;
+    if (h->cfg.order == 0) h->cfg.order = 4;
     for (auto &e : h->plans) e = nb_plan{-1, 1, 1};
     h->dev = cfg->device;
     h->cap = cfg->n_max;
@@ -844,7 +1010,9 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     const size_t sca = align256((row + 64) * sizeof(double));
     const size_t recb = align256(row * DS_REC * sizeof(float4));
     const size_t actb = align256(row * sizeof(int));
+    const size_t rec6b = align256(row * DS6_REC * sizeof(float4));
     h->slab_bytes = 6 * vec + 4 * sca + 2 * vec + 2 * recb + actb;  // see the file header
+    if (h->cfg.order == 6) h->slab_bytes += 4 * vec + rec6b;
     const size_t small = 256 * 3;
     if (cfg->budget_bytes && h->slab_bytes + small > cfg->budget_bytes) {
         char msg[160];
@@ -887,6 +1055,13 @@ int nb_create(const nb_config *cfg, nb_handle *out)
     h->rec = (float4 *)take(recb);
     h->irec = (float4 *)take(recb);
     h->act = (int *)take(actb);
+    if (h->cfg.order == 6) {
+        h->snap = (double *)take(vec);
+        h->crk = (double *)take(vec);
+        h->acc_p = (double *)take(vec);
+        h->f_snap = (double *)take(vec);
+        h->rec6 = (float4 *)take(rec6b);
+    }
     if (cudaMemsetAsync(h->slab, 0, h->slab_bytes, h->stream) != cudaSuccess ||
         cudaMalloc(&h->d_err, 256) != cudaSuccess || cudaMalloc(&h->d_dtmin, 256) != cudaSuccess ||
         cudaMalloc(&h->d_energy, 256) != cudaSuccess ||
@@ -983,8 +1158,13 @@ int nb_set_particles(nb_handle h, int n, const double *m, const double *pos, con
     CK(h, cudaMemsetAsync(h->dt, 0, n * sizeof(double), h->stream));
     CK(h, cudaMemsetAsync(h->acc, 0, 3 * h->ld * sizeof(double), h->stream));
     CK(h, cudaMemsetAsync(h->jerk, 0, 3 * h->ld * sizeof(double), h->stream));
+    if (order6(h)) {
+        CK(h, cudaMemsetAsync(h->snap, 0, 3 * h->ld * sizeof(double), h->stream));
+        CK(h, cudaMemsetAsync(h->crk, 0, 3 * h->ld * sizeof(double), h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     h->have_particles = true;
+    h->snap_valid = false;
     h->initialised = false;
     h->predicted = false;
     h->sched_valid = false;
@@ -1065,8 +1245,13 @@ int nb_set_state(nb_handle h, int n, const double *m, const double *pos, const d
     CK(h, h2d_rows(h->jerk, h->ld, jerk, n, 3, h->stream));
     CK(h, cudaMemcpyAsync(h->t, t, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->dt, dt, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (order6(h)) {
+        CK(h, cudaMemsetAsync(h->snap, 0, 3 * h->ld * sizeof(double), h->stream));
+        CK(h, cudaMemsetAsync(h->crk, 0, 3 * h->ld * sizeof(double), h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     h->have_particles = true;
+    h->snap_valid = false;  // order 6: nb_set_snap completes the state
     h->initialised = true;
     h->predicted = false;
     h->last_force_n = -1;
@@ -1097,12 +1282,23 @@ int nb_force_dev(nb_handle h, const int *idx_dev, int n_i, double *acc_dev, doub
     cudaSetDevice(h->dev);
     Out3 out{acc_dev, jerk_dev, pot_dev, n_i};
     h->last_force_n = -1;  // device buffers: nb_correct cannot use them
+    if (order6(h)) {
+        int rc = grow(h, &h->io, &h->io_cap, 3 * (size_t)n_i);  // the snap, not returned
+        if (rc) return rc;
+        return run_force6(h, h->cfg.variant, idx_dev, n_i,
+                          Out6{acc_dev, jerk_dev, h->io, pot_dev, n_i});
+    }
     return run_force(h, h->cfg.variant, members_of(h, idx_dev, n_i), out);
 }
 
-int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, double *pot)
+namespace {
+
+// nb_force / nb_force_snap: the outputs go through the io staging buffer, rows
+// acc 0-2, jerk 3-5, pot 6 and (order 6) snap 7-9 of stride n_i, where
+// nb_correct finds them.
+int host_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, double *snap,
+               double *pot)
 {
-    if (!h) return NB_ERR_ARG;
     if (!h->predicted) return fail(h, NB_ERR_STATE, "nb_force needs a preceding nb_predict");
     if (n_i < 0) return fail(h, NB_ERR_ARG, "n_i < 0");
     if (!idx && n_i > h->n) return fail(h, NB_ERR_ARG, "n_i > n with idx == NULL");
@@ -1114,7 +1310,8 @@ int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, do
     h->last_force_n = -1;
     if (n_i == 0) return NB_OK;
     cudaSetDevice(h->dev);
-    int rc = grow(h, &h->io, &h->io_cap, 7 * (size_t)n_i);
+    const int rows = order6(h) ? 10 : 7;
+    int rc = grow(h, &h->io, &h->io_cap, rows * (size_t)n_i);
     if (rc) return rc;
     const int *idx_dev = nullptr;
     if (idx) {
@@ -1124,9 +1321,13 @@ int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, do
         idx_dev = h->d_idx;
     }
     Out3 out{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i, n_i};
-    rc = run_force(h, h->cfg.variant, members_of(h, idx_dev, n_i), out);
+    if (order6(h))
+        rc = run_force6(h, h->cfg.variant, idx_dev, n_i,
+                        Out6{out.acc, out.jerk, h->io + 7 * (size_t)n_i, out.pot, n_i});
+    else
+        rc = run_force(h, h->cfg.variant, members_of(h, idx_dev, n_i), out);
     if (rc) return rc;
-    std::vector<double> buf(7 * (size_t)n_i);
+    std::vector<double> buf(rows * (size_t)n_i);
     CK(h, cudaMemcpyAsync(buf.data(), h->io, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
                           h->stream));
     rc = check_err(h);
@@ -1134,6 +1335,7 @@ int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, do
     if (acc) std::memcpy(acc, buf.data(), 3 * n_i * sizeof(double));
     if (jerk) std::memcpy(jerk, buf.data() + 3 * (size_t)n_i, 3 * n_i * sizeof(double));
     if (pot) std::memcpy(pot, buf.data() + 6 * (size_t)n_i, n_i * sizeof(double));
+    if (snap) std::memcpy(snap, buf.data() + 7 * (size_t)n_i, 3 * n_i * sizeof(double));
     h->last_force_n = n_i;
     h->last_force_all = (idx == nullptr);
     if (idx)
@@ -1143,10 +1345,58 @@ int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, do
     return NB_OK;
 }
 
+}  // namespace
+
+int nb_force(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, double *pot)
+{
+    if (!h) return NB_ERR_ARG;
+    return host_force(h, idx, n_i, acc, jerk, nullptr, pot);
+}
+
+int nb_force_snap(nb_handle h, const int *idx, int n_i, double *acc, double *jerk, double *snap,
+                  double *pot)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!order6(h)) return fail(h, NB_ERR_ARG, "nb_force_snap needs a handle of order 6");
+    return host_force(h, idx, n_i, acc, jerk, snap, pot);
+}
+
+int nb_get_snap(nb_handle h, double *snap, double *crackle)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!order6(h)) return fail(h, NB_ERR_ARG, "nb_get_snap needs a handle of order 6");
+    if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    cudaSetDevice(h->dev);
+    if (snap) CK(h, d2h_rows(snap, h->snap, h->ld, h->n, 3, h->stream));
+    if (crackle) CK(h, d2h_rows(crackle, h->crk, h->ld, h->n, 3, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return NB_OK;
+}
+
+int nb_set_snap(nb_handle h, const double *snap, const double *crackle)
+{
+    if (!h) return NB_ERR_ARG;
+    if (!order6(h)) return fail(h, NB_ERR_ARG, "nb_set_snap needs a handle of order 6");
+    if (!h->have_particles || !h->initialised)
+        return fail(h, NB_ERR_STATE, "nb_set_snap completes a state set by nb_set_state");
+    if (!snap || !crackle) return fail(h, NB_ERR_ARG, "snap and crackle must not be NULL");
+    for (long long q = 0; q < 3LL * h->n; ++q)
+        if (!std::isfinite(snap[q]) || !std::isfinite(crackle[q]))
+            return fail(h, NB_ERR_NONFINITE, "snap / crackle value %lld is not finite", q);
+    cudaSetDevice(h->dev);
+    CK(h, h2d_rows(h->snap, h->ld, snap, h->n, 3, h->stream));
+    CK(h, h2d_rows(h->crk, h->ld, crackle, h->n, 3, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->snap_valid = true;
+    h->predicted = false;
+    return NB_OK;
+}
+
 int nb_force_ext(nb_handle h, int n_i, const double *pos, const double *vel, double *acc,
                  double *jerk, double *pot)
 {
     if (!h) return NB_ERR_ARG;
+    if (order6(h)) return fail(h, NB_ERR_ARG, "nb_force_ext is not available at order 6");
     if (!h->predicted) return fail(h, NB_ERR_STATE, "nb_force_ext needs a preceding nb_predict");
     if (n_i < 0 || (n_i > 0 && (!pos || !vel)))
         return fail(h, NB_ERR_ARG, "n_i < 0 or NULL pos/vel");
@@ -1218,6 +1468,10 @@ int nb_correct(nb_handle h, const int *idx, int n_i, double t)
     StateDev s = state_of(h);
     StepParams p = params_of(h);
     int rc = timed(h, T_CORRECT, [&] {
+        if (order6(h))
+            return launch_correct6(s, idx ? h->d_idx : nullptr, n_i, t,
+                                   Out6{f.acc, f.jerk, h->io + 7 * (size_t)n_i, f.pot, n_i}, p,
+                                   h->sd, h->d_err, h->d_dtmin, h->stream);
         return launch_correct(s, idx ? h->d_idx : nullptr, n_i, t, f, p, h->sd, h->d_err,
                               h->d_dtmin, h->stream);
     });
@@ -1256,7 +1510,13 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         while ((2LL << lg) <= na && lg < 31) ++lg;
         h->stats.active_hist[lg]++;
     };
-    if (prm.shared_dt > 0.0) {
+    if (order6(h)) {
+        if (!h->snap_valid)
+            return fail(h, NB_ERR_STATE,
+                        "6th-order state without snap and crackle (restore them with nb_set_snap)");
+        rc = step6_loop(h, t_end, count_step);
+        if (rc) return rc;
+    } else if (prm.shared_dt > 0.0) {
         // shared steps: every particle is due at t_cur + dt; the host knows the
         // schedule, so the launches are queued without waiting on the device
         const ISet all = members_of(h, nullptr, h->n);
@@ -1484,6 +1744,7 @@ int nb_get_plan_table(nb_handle h, nb_plan *table)
 int nb_autotune(nb_handle h, int reps)
 {
     if (!h) return NB_ERR_ARG;
+    if (order6(h)) return fail(h, NB_ERR_ARG, "the plan table serves the 4th-order kernels");
     if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
     if (reps < 1) reps = 1;
     cudaSetDevice(h->dev);
@@ -1601,6 +1862,8 @@ int nb_autotune(nb_handle h, int reps)
 int nb_kick_ext(nb_handle target, nb_handle field, double dt_kick)
 {
     if (!target || !field || target == field) return NB_ERR_ARG;
+    if (order6(target) || order6(field))
+        return fail(target, NB_ERR_ARG, "bridge kicks take 4th-order systems");
     if (!std::isfinite(dt_kick)) return fail(target, NB_ERR_ARG, "dt_kick is not finite");
     if (target->dev != field->dev)
         return fail(target, NB_ERR_ARG, "the two systems are on different devices");
@@ -1627,6 +1890,7 @@ static bool keeps_sync(nb_handle h, double dt)
 int nb_bridge_step(nb_handle a, nb_handle b, double dt)
 {
     if (!a || !b || a == b) return NB_ERR_ARG;
+    if (order6(a) || order6(b)) return fail(a, NB_ERR_ARG, "bridge steps take 4th-order systems");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(a, NB_ERR_ARG, "dt must be > 0");
     if (a->dev != b->dev) return fail(a, NB_ERR_ARG, "the two systems are on different devices");
     if (!a->have_particles || !b->have_particles) return fail(a, NB_ERR_STATE, "no particles set");

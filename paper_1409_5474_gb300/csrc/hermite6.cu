@@ -1,0 +1,575 @@
+// The 6th-order Hermite scheme on the GPU (Sect. II: direct-summation codes
+// pair with integrators of 4th or higher order and individual time steps; the
+// scheme is the two-point Hermite one of Nitadori & Makino's 6th-order paper,
+// which the same passage cites).
+//
+// What differs from the 4th-order path: every pair also yields the snap, the
+// second time derivative of its acceleration,
+//   alpha = (r.v) / r2,   beta = (|v|^2 + r.a) / r2 + alpha^2,
+//   A = m r / r2^(3/2),   J = m v / r2^(3/2) - 3 alpha A,
+//   S = m a / r2^(3/2) - 6 alpha J - 3 beta A,
+// with r, v, a the j-minus-i position, velocity and predicted acceleration and
+// r2 = |r|^2 + eps^2. So the j-records carry the predicted acceleration (64
+// bytes instead of 48), the prediction runs through the crackle term, and the
+// corrector is the order-6 two-point quadrature with the crackle, pop and 5th
+// derivative of the acceleration taken from the quintic through (a, jerk,
+// snap) at both ends of the step.
+//
+// Kernels:
+//   k_predict6           K1 for all particles (the block scheduler has its own
+//                        order-6 instantiation in step.cu)
+//   k_force6_tile32<DS>  K2, FP32 / double-single pairs: a CTA of 8 warps owns
+//                        256 i-particles (one per thread), j-tiles of 128
+//                        records stream through a 3-stage ring of bulk copies
+//                        (TMA engine, mbarrier completion, bounded waits);
+//                        FP32 sums per tile are folded into double-single
+//                        totals; grid.y splits the j-range
+//   k_force6_tile64      K2, FP64 pairs (the correctness variant)
+//   k_force6_reduce<DS>  K3: the splits of each output added in fixed order
+//   k_correct6           K4: corrector, end-of-step crackle, step criterion,
+//                        block quantization
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "ds.cuh"
+#include "nb_internal.cuh"
+#include "step_body.cuh"
+#include "tma.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int H6_VALS = 10;     // acc 3, jerk 3, snap 3, pot 1 per i-particle
+constexpr int H6_JT = 128;      // j-records per tile
+constexpr int H6_NS = 3;        // ring stages
+constexpr int H6_NWARP = 8;     // warps per FP32 CTA (one i-particle per thread)
+constexpr int H6_T64 = 128;     // threads per FP64 CTA
+constexpr int H6_JT64 = 128;    // j per FP64 shared tile
+
+// ---- K1 ----------------------------------------------------------------------
+
+template <bool REC>
+__global__ void k_predict6(StateDev s, double t, unsigned *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    if (t < s.t[i]) atomicOr(err, DERR_BACKWARD);
+    predict6_one<REC>(s, i, t);
+}
+
+// Member index of slot k; an index outside [0, n) is flagged and replaced by 0.
+__device__ __forceinline__ int member6(const int *idx, int k, int n, unsigned *err)
+{
+    const int r = idx ? __ldg(idx + k) : k;
+    if ((unsigned)r >= (unsigned)n) {
+        atomicOr(err, DERR_BADINDEX);
+        return 0;
+    }
+    return r;
+}
+
+// Store the 10 totals of slot k (v[9] is the positive potential sum P; pot = -P).
+__device__ __forceinline__ void store6(const Out6 &out, int k, double v[H6_VALS], unsigned *err)
+{
+    v[9] = -v[9];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < H6_VALS; ++c) ok = ok && isfinite(v[c]);
+    if (!ok) atomicOr(err, DERR_NONFINITE);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (out.acc) out.acc[c * out.ld + k] = v[c];
+        if (out.jerk) out.jerk[c * out.ld + k] = v[3 + c];
+        if (out.snap) out.snap[c * out.ld + k] = v[6 + c];
+    }
+    if (out.pot) out.pot[k] = v[9];
+}
+
+// ---- K2, FP32 / double-single ---------------------------------------------------
+
+// IPT i-particles per thread share each j-record loaded from shared memory.
+template <bool DS, int IPT>
+__global__ void __launch_bounds__(32 * H6_NWARP, 1)
+    k_force6_tile32(const float4 *__restrict__ jrec, int nj, const int *__restrict__ idx,
+                    int n_i, float eps2f, int ntiles, float2 *__restrict__ part, long long pld,
+                    Out6 out, unsigned *err)
+{
+    extern __shared__ __align__(128) float4 s_tile6[];  // H6_NS * H6_JT * DS6_REC
+    __shared__ __align__(8) uint64_t s_full[H6_NS];
+    __shared__ int s_abort;
+
+    constexpr int NT = 32 * H6_NWARP;
+    constexpr int IB = NT * IPT;
+    const int tid = threadIdx.x;
+    const int nsplit = gridDim.y, split = blockIdx.y;
+    const int tile0 = (int)((long long)ntiles * split / nsplit);
+    const int tile1 = (int)((long long)ntiles * (split + 1) / nsplit);
+    const int my_tiles = tile1 - tile0;
+
+    // this thread's i-particles (idle slots past n_i compute a copy of the last one)
+    int ii[IPT];
+    float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT];
+    float vx[IPT], vy[IPT], vz[IPT], ax[IPT], ay[IPT], az[IPT];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        const int k = min(blockIdx.x * IB + p * NT + tid, n_i - 1);
+        ii[p] = member6(idx, k, nj, err);
+        const float4 *r = jrec + (size_t)DS6_REC * ii[p];
+        const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+        xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
+        xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
+        vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+        ax[p] = d.x; ay[p] = d.y; az[p] = d.z;
+    }
+
+    // double-single totals (hi, lo) and the FP32 sums of the current tile (folded
+    // after every tile: 128 pairs per sum)
+    float H[IPT][H6_VALS], L[IPT][H6_VALS], t[IPT][H6_VALS];
+#pragma unroll
+    for (int p = 0; p < IPT; ++p)
+#pragma unroll
+        for (int c = 0; c < H6_VALS; ++c) H[p][c] = L[p][c] = t[p][c] = 0.f;
+
+    if (tid == 0) {
+        s_abort = 0;
+#pragma unroll
+        for (int q = 0; q < H6_NS; ++q) mbar_init(&s_full[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int kt) {
+        const int stage = kt % H6_NS;
+        const int tt = tile0 + kt;
+        const int cnt = min(H6_JT, nj - tt * H6_JT);
+        const uint32_t bytes = (uint32_t)cnt * DS6_REC * 16u;
+        mbar_expect_tx(&s_full[stage], bytes);
+        bulk_g2s(s_tile6 + (size_t)stage * H6_JT * DS6_REC, jrec + (size_t)tt * H6_JT * DS6_REC,
+                 bytes, &s_full[stage]);
+    };
+    if (tid == 0)
+        for (int kt = 0; kt < H6_NS && kt < my_tiles; ++kt) issue(kt);
+
+    for (int kt = 0; kt < my_tiles; ++kt) {
+        const int stage = kt % H6_NS;
+        if (!mbar_wait(&s_full[stage], (uint32_t)((kt / H6_NS) & 1))) s_abort = 1;
+        const float4 *T = s_tile6 + (size_t)stage * H6_JT * DS6_REC;
+        const int jbase = (tile0 + kt) * H6_JT;
+        const int cnt = min(H6_JT, nj - jbase);
+        bool mine = false;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) mine = mine || (ii[p] >= jbase && ii[p] < jbase + cnt);
+        const bool own = __any_sync(0xffffffffu, mine);
+
+        auto body = [&](int jj, auto masked_tag) {
+            constexpr bool MASKED = decltype(masked_tag)::value;
+            const float4 P = T[DS6_REC * jj];
+            const float4 V = T[DS6_REC * jj + 2];
+            const float4 W = T[DS6_REC * jj + 3];
+            float4 Q;
+            if (DS) Q = T[DS6_REC * jj + 1];
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (P.x - xh[p]) + (Q.x - xl[p]);
+                    dy = (P.y - yh[p]) + (Q.y - yl[p]);
+                    dz = (P.z - zh[p]) + (Q.z - zl[p]);
+                } else {
+                    dx = P.x - xh[p];
+                    dy = P.y - yh[p];
+                    dz = P.z - zh[p];
+                }
+                const float dvx = V.x - vx[p], dvy = V.y - vy[p], dvz = V.z - vz[p];
+                const float dax = W.x - ax[p], day = W.y - ay[p], daz = W.z - az[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float w2 = dvx * dvx;  // |v|^2 + r.a
+                w2 = fmaf(dvy, dvy, w2);
+                w2 = fmaf(dvz, dvz, w2);
+                w2 = fmaf(dx, dax, w2);
+                w2 = fmaf(dy, day, w2);
+                w2 = fmaf(dz, daz, w2);
+                float rinv = rsqrtf(r2);
+                if (MASKED) rinv = (jbase + jj == ii[p]) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = P.w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float alpha = rv * rinv2;
+                const float beta = fmaf(alpha, alpha, w2 * rinv2);
+                const float m3a = -3.f * alpha, m6a = -6.f * alpha, m3b = -3.f * beta;
+                const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+                const float Jx = fmaf(m3a, Ax, mr3 * dvx);
+                const float Jy = fmaf(m3a, Ay, mr3 * dvy);
+                const float Jz = fmaf(m3a, Az, mr3 * dvz);
+                t[p][0] += Ax;
+                t[p][1] += Ay;
+                t[p][2] += Az;
+                t[p][3] += Jx;
+                t[p][4] += Jy;
+                t[p][5] += Jz;
+                t[p][6] += fmaf(m3b, Ax, fmaf(m6a, Jx, mr3 * dax));
+                t[p][7] += fmaf(m3b, Ay, fmaf(m6a, Jy, mr3 * day));
+                t[p][8] += fmaf(m3b, Az, fmaf(m6a, Jz, mr3 * daz));
+                t[p][9] += mrinv;
+            }
+        };
+        if (own) {
+            for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
+        } else if (cnt == H6_JT) {
+#pragma unroll 4
+            for (int jj = 0; jj < H6_JT; ++jj) body(jj, std::false_type{});
+        } else {
+#pragma unroll 2
+            for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
+        }
+#pragma unroll
+        for (int p = 0; p < IPT; ++p)
+#pragma unroll
+            for (int c = 0; c < H6_VALS; ++c) {
+                if (DS)
+                    ds_add(H[p][c], L[p][c], t[p][c]);
+                else
+                    H[p][c] += t[p][c];
+                t[p][c] = 0.f;
+            }
+
+        __syncthreads();  // every warp is done with this stage
+        if (s_abort) {
+            if (tid == 0) drain_ring<H6_NS>(s_full, 0u, kt, my_tiles);
+            break;
+        }
+        if (tid == 0 && kt + H6_NS < my_tiles) issue(kt + H6_NS);
+    }
+    if (s_abort) {
+        if (tid == 0) atomicOr(err, DERR_TIMEOUT);
+        return;
+    }
+#pragma unroll
+    for (int p = 0; p < IPT; ++p) {
+        const int kk = blockIdx.x * IB + p * NT + tid;
+        if (kk >= n_i) continue;
+        if (nsplit == 1) {
+            double v[H6_VALS];
+#pragma unroll
+            for (int c = 0; c < H6_VALS; ++c) v[c] = ds_to_double(dsf{H[p][c], L[p][c]});
+            store6(out, kk, v, err);
+        } else {
+#pragma unroll
+            for (int c = 0; c < H6_VALS; ++c)
+                part[((size_t)split * H6_VALS + c) * pld + kk] = make_float2(H[p][c], L[p][c]);
+        }
+    }
+}
+
+// ---- K2, FP64 ---------------------------------------------------------------
+
+// One i-particle per thread; the j-set (predicted FP64 position, velocity,
+// acceleration and mass: 80 bytes per particle) goes through shared memory in
+// tiles of H6_JT64. grid.y splits the j-range.
+__global__ void __launch_bounds__(H6_T64)
+    k_force6_tile64(StateDev s, const int *__restrict__ idx, int n_i, double eps2,
+                    double *__restrict__ part, long long pld, Out6 out, unsigned *err)
+{
+    __shared__ double sj[10][H6_JT64];
+    const int nj = s.n;
+    const int nsplit = gridDim.y, split = blockIdx.y;
+    const int ntiles = (nj + H6_JT64 - 1) / H6_JT64;
+    const int tile0 = (int)((long long)ntiles * split / nsplit);
+    const int tile1 = (int)((long long)ntiles * (split + 1) / nsplit);
+    const int k = min(blockIdx.x * H6_T64 + (int)threadIdx.x, n_i - 1);
+    const int ii = member6(idx, k, nj, err);
+    double xi[3], vi[3], ai[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xi[c] = s.pos_p[c * s.ld + ii];
+        vi[c] = s.vel_p[c * s.ld + ii];
+        ai[c] = s.acc_p[c * s.ld + ii];
+    }
+    double acc[H6_VALS];
+#pragma unroll
+    for (int c = 0; c < H6_VALS; ++c) acc[c] = 0.0;
+    for (int tt = tile0; tt < tile1; ++tt) {
+        const int jbase = tt * H6_JT64;
+        const int cnt = min(H6_JT64, nj - jbase);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += H6_T64) {
+            const int j = jbase + q;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                sj[c][q] = s.pos_p[c * s.ld + j];
+                sj[3 + c][q] = s.vel_p[c * s.ld + j];
+                sj[6 + c][q] = s.acc_p[c * s.ld + j];
+            }
+            sj[9][q] = s.m[j];
+        }
+        __syncthreads();
+        for (int q = 0; q < cnt; ++q) {
+            if (jbase + q == ii) continue;
+            const double dx = sj[0][q] - xi[0], dy = sj[1][q] - xi[1], dz = sj[2][q] - xi[2];
+            const double dvx = sj[3][q] - vi[0], dvy = sj[4][q] - vi[1], dvz = sj[5][q] - vi[2];
+            const double dax = sj[6][q] - ai[0], day = sj[7][q] - ai[1], daz = sj[8][q] - ai[2];
+            const double r2 = eps2 + dx * dx + dy * dy + dz * dz;
+            const double rinv = rsqrt(r2);
+            const double rinv2 = rinv * rinv;
+            const double mrinv = sj[9][q] * rinv;
+            const double mr3 = mrinv * rinv2;
+            const double alpha = (dx * dvx + dy * dvy + dz * dvz) * rinv2;
+            const double beta =
+                (dvx * dvx + dvy * dvy + dvz * dvz + dx * dax + dy * day + dz * daz) * rinv2 +
+                alpha * alpha;
+            const double A[3] = {mr3 * dx, mr3 * dy, mr3 * dz};
+            const double dv[3] = {dvx, dvy, dvz}, da[3] = {dax, day, daz};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double J = mr3 * dv[c] - 3.0 * alpha * A[c];
+                acc[c] += A[c];
+                acc[3 + c] += J;
+                acc[6 + c] += mr3 * da[c] - 6.0 * alpha * J - 3.0 * beta * A[c];
+            }
+            acc[9] += mrinv;
+        }
+    }
+    const int kk = blockIdx.x * H6_T64 + threadIdx.x;
+    if (kk >= n_i) return;
+    if (nsplit == 1) {
+        store6(out, kk, acc, err);
+    } else {
+#pragma unroll
+        for (int c = 0; c < H6_VALS; ++c) part[((size_t)split * H6_VALS + c) * pld + kk] = acc[c];
+    }
+}
+
+// ---- K3 --------------------------------------------------------------------------
+
+// One thread per (component, slot): the nsplit partial sums in split order.
+template <bool DS>
+__global__ void k_force6_reduce(const void *__restrict__ part, long long pld, int nsplit, int n_i,
+                                Out6 out, unsigned *err)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)n_i * H6_VALS) return;
+    const int c = (int)(q / n_i), k = (int)(q % n_i);
+    double v;
+    if (DS) {
+        const float2 *p = static_cast<const float2 *>(part);
+        dsf a{0.f, 0.f};
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const float2 w = __ldg(p + ((size_t)sp * H6_VALS + c) * pld + k);
+            ds_acc(a, dsf{w.x, w.y});
+        }
+        v = ds_to_double(a);
+    } else {
+        const double *p = static_cast<const double *>(part);
+        v = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) v += __ldg(p + ((size_t)sp * H6_VALS + c) * pld + k);
+    }
+    if (c == 9) {
+        v = -v;
+        if (out.pot) out.pot[k] = v;
+    } else {
+        double *dst = c < 3 ? out.acc : (c < 6 ? out.jerk : out.snap);
+        if (dst) dst[(c % 3) * out.ld + k] = v;
+    }
+    if (!isfinite(v)) atomicOr(err, DERR_NONFINITE);
+}
+
+// ---- K4 --------------------------------------------------------------------------
+
+// Slot k: the order-6 corrector from the start-of-step x0, v0, a0, j0, s0 and
+// the new a1, j1, s1 (f, slot-indexed); the crackle at the end of the step from
+// the quintic through both ends (mid-point expansion, T = dt/2); the new step
+// from Aarseth's criterion on (a, jerk, snap, crackle), quantized as in the
+// 4th-order path. The quintic's k-th derivative carries the force rounding
+// (~1e-7 of |a| for double-single pairs) divided by T^k: a criterion on the 4th
+// and 5th collapses the steps to dt_min, and the crackle is used above its
+// rounding floor only (prm.noise), else a particle whose step once got small
+// (a close encounter) could not grow it again.
+__global__ void k_correct6(StateDev s, const int *__restrict__ act, int na, double t_new, Out6 f,
+                           StepParams prm, SchedDev *sd, unsigned *err,
+                           unsigned long long *dtmin_hits)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) sd->t_cur = t_new;
+    if (k >= na) return;
+    const int i = act ? act[k] : k;
+    const double dt = t_new - s.t[i];
+    const double dt_old = s.dt[i];
+    const double T = 0.5 * dt;
+    const double iT = prm.shared_dt > 0.0 ? 1.0 / T : ldexp(1.0, -ilogb(T));
+    const double iT3 = iT * iT * iT, iT5 = iT3 * iT * iT;
+    double a1v[3], j1v[3], s1v[3], a3v[3];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long q = c * s.ld + i;
+        const double x0 = s.pos[q], v0 = s.vel[q], a0 = s.acc[q], j0 = s.jerk[q], s0 = s.snap[q];
+        const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
+        const double s1 = f.snap[c * f.ld + k];
+        // v1 = v0 + dt/2 (a0 + a1) - dt^2/10 (j1 - j0) + dt^3/120 (s0 + s1)
+        const double v1 = v0 + dt * fma(dt, fma(dt, (s0 + s1) * (1.0 / 120.0),
+                                                -0.1 * (j1 - j0)), 0.5 * (a0 + a1));
+        // x1 = x0 + dt/2 (v0 + v1) - dt^2/10 (a1 - a0) + dt^3/120 (j0 + j1)
+        const double x1 = x0 + dt * fma(dt, fma(dt, (j0 + j1) * (1.0 / 120.0),
+                                                -0.1 * (a1 - a0)), 0.5 * (v0 + v1));
+        const double Am = 0.5 * (a1 - a0);
+        const double Jp = 0.5 * (j1 + j0), Jm = 0.5 * (j1 - j0);
+        const double Sp = 0.5 * (s1 + s0), Sm = 0.5 * (s1 - s0);
+        const double c5 = (45.0 * Am - 45.0 * T * Jp + 15.0 * T * T * Sm) * iT5;
+        const double c3 = (7.5 * (T * Jp - Am) - 1.5 * T * T * Sm) * iT3;
+        const double c4 = 3.0 * (T * Sp - Jm) * iT3;
+        a3v[c] = c3 + T * (c4 + 0.5 * T * c5);
+        a1v[c] = a1;
+        j1v[c] = j1;
+        s1v[c] = s1;
+        s.pos[q] = x1;
+        s.vel[q] = v1;
+        s.acc[q] = a1;
+        s.jerk[q] = j1;
+        s.snap[q] = s1;
+        s.crk[q] = a3v[c];
+        finite = finite && isfinite(x1) && isfinite(v1);
+    }
+    if (!finite) atomicOr(err, DERR_NONFINITE);
+    double dt_new;
+    if (prm.shared_dt > 0.0) {
+        dt_new = prm.shared_dt;
+    } else {
+        // Aarseth's criterion with the evaluated snap as a2 and the crackle as a3:
+        // dt^2 = eta (|a||s| + |j|^2) / (|j||c| + |s|^2), the crackle's magnitude
+        // reduced by its rounding floor 30 noise |a| / T^3 (the forces' relative
+        // rounding enters it through (a1 - a0) / T^3 with coefficients 7.5 + 22.5);
+        // below the floor it counts as zero
+        const double A = dot3(a1v, a1v), J = dot3(j1v, j1v), S = dot3(s1v, s1v);
+        const double cn = sqrt(dot3(a3v, a3v));
+        const double cfl = 30.0 * prm.noise * sqrt(A) / (T * T * T);
+        const double ce = cn > cfl ? cn - cfl : 0.0;
+        const double num = prm.eta * (sqrt(A * S) + J);
+        const double den = sqrt(J) * ce + S;
+        bool clamped;
+        dt_new = quantize_sq(num, den, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
+        if (clamped && dtmin_hits) atomicAdd(dtmin_hits, 1ull);
+        const int lo = step_level(dt_old, prm.dt_max), ln = step_level(dt_new, prm.dt_max);
+        if (lo != ln) {
+            hist_add(sd->hist, lo, -1);
+            hist_add(sd->hist, ln, +1);
+        }
+    }
+    s.t[i] = t_new;
+    s.dt[i] = dt_new;
+}
+
+}  // namespace
+
+// ---- host side ---------------------------------------------------------------------
+
+cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned *err,
+                            cudaStream_t st)
+{
+    if (s.n <= 0) return cudaSuccess;
+    const int bs = 256, g = (s.n + bs - 1) / bs;
+    if (want_rec)
+        k_predict6<true><<<g, bs, 0, st>>>(s, t, err);
+    else
+        k_predict6<false><<<g, bs, 0, st>>>(s, t, err);
+    return cudaGetLastError();
+}
+
+// About four CTAs per SM in all (two resident per SM of the FP32 kernel, two
+// waves), the j-range cut into at most one split per 4 tiles.
+ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
+{
+    ForcePlan p{};
+    p.kind = 0;
+    const bool f64 = (variant == NB_F64);
+    // two i-particles per thread halve the shared-memory loads per pair once there
+    // are enough i-blocks to go round
+    p.ipt = (!f64 && n_i >= 8 * 32 * H6_NWARP) ? 2 : 1;
+    p.threads = f64 ? H6_T64 : 32 * H6_NWARP * p.ipt;  // i-particles per CTA
+    p.jt = f64 ? H6_JT64 : H6_JT;
+    p.nwj = 1;
+    const long long nblk = (n_i + p.threads - 1) / p.threads;
+    const long long ntiles = (n_j + p.jt - 1) / p.jt;
+    const long long target = 4LL * std::max(num_sms, 1);
+    long long ns = (target + nblk - 1) / std::max(nblk, 1LL);
+    ns = std::min(ns, std::max(1LL, ntiles / 4));
+    p.nsplit = (int)std::max(1LL, std::min(ns, 1024LL));
+    return p;
+}
+
+size_t plan6_partial_doubles(const ForcePlan &p, int n_i)
+{
+    if (p.nsplit <= 1) return 0;
+    return (size_t)p.nsplit * H6_VALS * (size_t)n_i;  // float2 (DS) or double: 8 bytes each
+}
+
+cudaError_t launch_force6(int variant, const ForcePlan &p, const StateDev &s, const int *idx,
+                          int n_i, double eps2, double *part, const Out6 &out, unsigned *err,
+                          cudaStream_t st, cudaEvent_t *ev)
+{
+    if (n_i <= 0) return cudaSuccess;
+    const long long pld = n_i;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (variant == NB_F64) {
+        dim3 grid((n_i + H6_T64 - 1) / H6_T64, p.nsplit);
+        k_force6_tile64<<<grid, H6_T64, 0, st>>>(s, idx, n_i, eps2, part, pld, out, err);
+    } else {
+        const int ntiles = (s.n + H6_JT - 1) / H6_JT;
+        const int nt = 32 * H6_NWARP, ib = nt * p.ipt;
+        dim3 grid((n_i + ib - 1) / ib, p.nsplit);
+        const size_t smem = (size_t)H6_NS * H6_JT * DS6_REC * sizeof(float4);
+        float2 *pp = reinterpret_cast<float2 *>(part);
+        const float e2 = (float)eps2;
+        if (variant == NB_F32DS && p.ipt == 2)
+            k_force6_tile32<true, 2><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
+                                                             pp, pld, out, err);
+        else if (variant == NB_F32DS)
+            k_force6_tile32<true, 1><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
+                                                             pp, pld, out, err);
+        else if (p.ipt == 2)
+            k_force6_tile32<false, 2><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
+                                                              pp, pld, out, err);
+        else
+            k_force6_tile32<false, 1><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
+                                                              pp, pld, out, err);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ev) {
+        cudaEventRecord(ev[1], st);
+        cudaEventRecord(ev[2], st);
+    }
+    if (p.nsplit > 1) {
+        const long long total = (long long)n_i * H6_VALS;
+        const int bs = 256;
+        const int g = (int)((total + bs - 1) / bs);
+        if (variant == NB_F64)
+            k_force6_reduce<false><<<g, bs, 0, st>>>(part, pld, p.nsplit, n_i, out, err);
+        else
+            k_force6_reduce<true><<<g, bs, 0, st>>>(part, pld, p.nsplit, n_i, out, err);
+        e = cudaGetLastError();
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    return e;
+}
+
+cudaError_t launch_correct6(const StateDev &s, const int *act, int n_a, double t_new,
+                            const Out6 &f, const StepParams &p, SchedDev *sd, unsigned *err,
+                            unsigned long long *dtmin_hits, cudaStream_t st)
+{
+    const int bs = 128;
+    const int g = std::max(1, (n_a + bs - 1) / bs);
+    k_correct6<<<g, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

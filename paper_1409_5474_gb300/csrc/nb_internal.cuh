@@ -24,6 +24,11 @@ enum : unsigned {
 // stored as int bits (read only to recognise the self pair of a gathered i-set).
 constexpr int DS_REC = 3;  // float4 per record
 
+// j-record of the 6th-order scheme, 64 bytes: the 48-byte record followed by
+// r[3] = {ax, ay, az, 0}, the FP32 predicted acceleration (the snap term
+// differentiates along it).
+constexpr int DS6_REC = 4;
+
 // Vector-field output with a row stride: component c of slot k is p[c*ld + k].
 struct Out3 {
     double *acc;
@@ -168,10 +173,15 @@ struct StateDev {
     double *t, *dt;
     double *pos_p, *vel_p;            // predicted [3][ld]
     float4 *rec;                      // DS records [n][3]
+    // 6th-order scheme only (null otherwise): snap, crackle and the predicted
+    // acceleration [3][ld], and the 64-byte records [n][DS6_REC]
+    double *snap, *crk, *acc_p;
+    float4 *rec6;
 };
 
 struct StepParams {
     double eta, eta_s, dt_min, dt_max, shared_dt;
+    double noise;  // 6th order: relative rounding noise of the forces (crackle floor); 0: none
 };
 
 // Step levels: dt = dt_max * 2^-k, k in [0, NLEVEL).
@@ -283,6 +293,46 @@ struct SchedJob {
 };
 cudaError_t launch_sched_predict_multi(const SchedJob *jobs, int njobs, int nblocks,
                                        double dt_max, bool want_rec, cudaStream_t st);
+
+// The same for the 6th-order scheme: the prediction runs through the crackle
+// term and writes pos_p, vel_p, acc_p and (want_rec) the 64-byte records to
+// rec6; act receives the due set in ascending index (no gathered records).
+cudaError_t launch_sched_predict6(const StateDev &s, SchedDev *sd, unsigned long long *status,
+                                  int *act, Mailbox *mail_dev, double dt_max, bool want_rec,
+                                  unsigned *err, cudaStream_t st);
+
+// ---- 6th-order Hermite (hermite6.cu) ------------------------------------------
+
+// Outputs of a 6th-order evaluation (slot-indexed rows of stride ld).
+struct Out6 {
+    double *acc, *jerk, *snap, *pot;
+    long long ld;
+};
+
+// K1 of the 6th-order scheme for all particles: pos_p, vel_p, acc_p at time t
+// (Taylor series through the crackle) and, with want_rec, the 64-byte records.
+cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned *err,
+                            cudaStream_t st);
+
+// Plan of a 6th-order evaluation: CTA shape and j-splits.
+ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms);
+size_t plan6_partial_doubles(const ForcePlan &p, int n_i);
+
+// K2 + K3 of the 6th-order scheme: acc, jerk, snap and pot of the members
+// idx[k] (idx null: k) of the system s, from every other particle of s, at
+// the predicted state (rec6 for the FP32 kinds; pos_p, vel_p, acc_p for FP64).
+// part: plan6_partial_doubles scratch. ev (optional): {force start, force end,
+// reduce start, reduce end}.
+cudaError_t launch_force6(int variant, const ForcePlan &p, const StateDev &s, const int *idx,
+                          int n_i, double eps2, double *part, const Out6 &out, unsigned *err,
+                          cudaStream_t st, cudaEvent_t *ev);
+
+// K4 of the 6th-order scheme for the n_a particles act[k] (act null: k) to
+// time t_new: corrector, end-of-step crackle, the generalised step criterion
+// and block quantization (or the shared step), level histogram, sd->t_cur.
+cudaError_t launch_correct6(const StateDev &s, const int *act, int n_a, double t_new,
+                            const Out6 &f, const StepParams &p, SchedDev *sd, unsigned *err,
+                            unsigned long long *dtmin_hits, cudaStream_t st);
 
 // ---- fused persistent block steps (persist.cu) ------------------------------
 

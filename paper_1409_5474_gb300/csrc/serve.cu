@@ -178,7 +178,7 @@ nb_handle acquire_handle(nb_server s, int cap, size_t *bytes)
 
 StepParams server_params(nb_server s)
 {
-    StepParams p;
+    StepParams p{};
     p.eta = s->cfg.eta;
     p.eta_s = s->cfg.eta;
     p.dt_min = std::ldexp(1.0, -30);

@@ -263,7 +263,7 @@ cudaError_t launch_init_steps(const StateDev &s, const Out3 &f, const StepParams
 
 // K5 + K1 for one tile of one system (ntiles CTAs serve the system; each takes
 // its tile number from a ticket, so tiles start in order).
-template <bool REC>
+template <bool REC, int ORD = 4>
 __device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
                                            unsigned long long *status, int *act, float4 *irec,
                                            Mailbox *mail, double dt_max, unsigned *err,
@@ -313,7 +313,12 @@ __device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
     for (int r = 0; r < SCHED_PER_THREAD; ++r) {
         const int i = base + r * SCHED_THREADS + tid;
         bool due = false;
-        if (i < s.n) due = predict_one<REC>(s, i, tn, keep[r]);
+        if (i < s.n) {
+            if (ORD == 6)
+                due = predict6_one<REC>(s, i, tn);
+            else
+                due = predict_one<REC>(s, i, tn, keep[r]);
+        }
         const unsigned b = __ballot_sync(0xffffffffu, due);
         if (lane == 0) s_flags[r * (SCHED_THREADS / 32) + warp] = b;
     }
@@ -414,7 +419,7 @@ __device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
             const int i = base + r * SCHED_THREADS + tid;
             const int slot = excl + s_woff[w] + __popc(b & ((1u << lane) - 1u));
             act[slot] = i;
-            if (REC) {
+            if (REC && ORD == 4) {
                 float4 *g = irec + (size_t)DS_REC * slot;
                 g[0] = keep[r][0];
                 g[1] = keep[r][1];
@@ -441,12 +446,12 @@ __device__ __forceinline__ void sched_body(const StateDev &s, SchedDev *sd,
     }
 }
 
-template <bool REC>
+template <bool REC, int ORD>
 __global__ void __launch_bounds__(SCHED_THREADS)
     k_sched_predict(StateDev s, SchedDev *sd, unsigned long long *status, int *act,
                     float4 *irec, Mailbox *mail, double dt_max, unsigned *err)
 {
-    sched_body<REC>(s, sd, status, act, irec, mail, dt_max, err, gridDim.x);
+    sched_body<REC, ORD>(s, sd, status, act, irec, mail, dt_max, err, gridDim.x);
 }
 
 // K5 + K1 of many systems in one launch (each system's tiles as above).
@@ -466,11 +471,25 @@ cudaError_t launch_sched_predict(const StateDev &s, SchedDev *sd, unsigned long 
 {
     const int g = (s.n + SCHED_TILE - 1) / SCHED_TILE;
     if (want_rec)
-        k_sched_predict<true><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, irec, mail_dev,
-                                                           dt_max, err);
+        k_sched_predict<true, 4><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, irec,
+                                                              mail_dev, dt_max, err);
     else
-        k_sched_predict<false><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, irec, mail_dev,
-                                                            dt_max, err);
+        k_sched_predict<false, 4><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, irec,
+                                                               mail_dev, dt_max, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sched_predict6(const StateDev &s, SchedDev *sd, unsigned long long *status,
+                                  int *act, Mailbox *mail_dev, double dt_max, bool want_rec,
+                                  unsigned *err, cudaStream_t st)
+{
+    const int g = (s.n + SCHED_TILE - 1) / SCHED_TILE;
+    if (want_rec)
+        k_sched_predict<true, 6><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, nullptr,
+                                                              mail_dev, dt_max, err);
+    else
+        k_sched_predict<false, 6><<<g, SCHED_THREADS, 0, st>>>(s, sd, status, act, nullptr,
+                                                               mail_dev, dt_max, err);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,43 @@ __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn,
     return due;
 }
 
+// The 6th-order prediction of particle i to time tn (FP64 Taylor series through
+// the crackle term, in Horner form): pos_p, vel_p, acc_p and, when REC, its
+// 64-byte record (the 48-byte record plus the FP32 predicted acceleration).
+// Returns whether the particle is due at tn.
+template <bool REC>
+__device__ __forceinline__ bool predict6_one(const StateDev &s, int i, double tn)
+{
+    const double ti = s.t[i];
+    const double d = tn - ti;
+    const double h2 = d * 0.5, h3 = d * (1.0 / 3.0), h4 = d * 0.25, h5 = d * 0.2;
+    const bool due = (ti + s.dt[i] == tn);
+    double xp[3], vp[3], ap[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long q = c * s.ld + i;
+        const double x = s.pos[q], v = s.vel[q], a = s.acc[q], j = s.jerk[q];
+        const double sn = s.snap[q], cr = s.crk[q];
+        // x + d (v + d/2 (a + d/3 (j + d/4 (s + d/5 c)))) and likewise for v, a
+        xp[c] = fma(d, fma(h2, fma(h3, fma(h4, fma(h5, cr, sn), j), a), v), x);
+        vp[c] = fma(d, fma(h2, fma(h3, fma(h4, cr, sn), j), a), v);
+        ap[c] = fma(d, fma(h2, fma(h3, cr, sn), j), a);
+        s.pos_p[q] = xp[c];
+        s.vel_p[q] = vp[c];
+        s.acc_p[q] = ap[c];
+    }
+    if (REC) {
+        float4 r[3];
+        make_record(xp, vp, s.m[i], i, r);
+        float4 *rr = s.rec6 + (size_t)DS6_REC * i;
+        rr[0] = r[0];
+        rr[1] = r[1];
+        rr[2] = r[2];
+        rr[3] = make_float4(f32_trunc(ap[0]), f32_trunc(ap[1]), f32_trunc(ap[2]), 0.f);
+    }
+    return due;
+}
+
 // ---- step criterion and block quantization ---------------------------------
 
 __device__ __forceinline__ double norm3(double x, double y, double z)

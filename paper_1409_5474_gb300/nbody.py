@@ -58,7 +58,7 @@ class nb_config(ctypes.Structure):
                 ("dt_min", ctypes.c_double), ("shared_dt", ctypes.c_double),
                 ("budget_bytes", ctypes.c_size_t), ("device", ctypes.c_int),
                 ("flags", ctypes.c_int), ("fused_max_na", ctypes.c_int),
-                ("n_corr", ctypes.c_int)]
+                ("n_corr", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class nb_plan(ctypes.Structure):
@@ -158,6 +158,9 @@ _SIGS = [
     ("nb_force_dev", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
     ("nb_force_ext", ctypes.c_int, [_H, ctypes.c_int, _D, _D, _D, _D, _D]),
+    ("nb_force_snap", ctypes.c_int, [_H, _I, ctypes.c_int, _D, _D, _D, _D]),
+    ("nb_get_snap", ctypes.c_int, [_H, _D, _D]),
+    ("nb_set_snap", ctypes.c_int, [_H, _D, _D]),
     ("nb_correct", ctypes.c_int, [_H, _I, ctypes.c_int, ctypes.c_double]),
     ("nb_step", ctypes.c_int, [_H, ctypes.c_double, ctypes.POINTER(nb_stats)]),
     ("nb_energy", ctypes.c_int, [_H, _D, _D]),
@@ -331,6 +334,36 @@ def nb_force(h, idx=None, n_i=None):
     pot = np.empty(n_i)
     _check(load().nb_force(h, ip, n_i, _dp(acc), _dp(jerk), _dp(pot)), "nb_force", h)
     return acc, jerk, pot
+
+
+def nb_force_snap(h, idx=None, n_i=None):
+    """Order-6 handles: acc, jerk, snap (3, n_i) and pot (n_i,) on members idx."""
+    if idx is None:
+        n_i = _n(h) if n_i is None else int(n_i)
+        ip = None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        n_i = idx.shape[0]
+        ip = idx.ctypes.data_as(_I)
+    acc, jerk, snap = (np.empty((3, n_i)) for _ in range(3))
+    pot = np.empty(n_i)
+    _check(load().nb_force_snap(h, ip, n_i, _dp(acc), _dp(jerk), _dp(snap), _dp(pot)),
+           "nb_force_snap", h)
+    return acc, jerk, snap, pot
+
+
+def nb_get_snap(h):
+    """Order-6 handles: (snap, crackle), each (3, n)."""
+    n = _n(h)
+    snap, crk = np.empty((3, n)), np.empty((3, n))
+    _check(load().nb_get_snap(h, _dp(snap), _dp(crk)), "nb_get_snap", h)
+    return snap, crk
+
+
+def nb_set_snap(h, snap, crackle) -> None:
+    n = _n(h)
+    _check(load().nb_set_snap(h, _dp(_f64(snap, (3, n))), _dp(_f64(crackle, (3, n)))),
+           "nb_set_snap", h)
 
 
 def nb_force_dev(h, idx_ptr, n_i, acc_ptr, jerk_ptr, pot_ptr) -> None:
@@ -708,6 +741,15 @@ class System:
 
     def force_ext(self, pos, vel):
         return nb_force_ext(self.h, pos, vel)
+
+    def force_snap(self, idx=None):
+        return nb_force_snap(self.h, idx)
+
+    def snap(self):
+        return nb_get_snap(self.h)
+
+    def set_snap(self, snap, crackle):
+        nb_set_snap(self.h, snap, crackle)
 
     def correct(self, idx, t):
         nb_correct(self.h, idx, t)

@@ -1,0 +1,208 @@
+"""The 6th-order Hermite scheme on the GPU (nb_config.order = 6) against the oracle's
+6th-order scheme: the pair force with snap at several tiles and a ragged tail (F32-DS,
+F64), shared and block steps, energy, checkpoint / resume, and the argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1409_5474_gb300 import ic
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_rms(got, ref):
+    return np.sqrt(((got - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+# force gates (relative RMS over the i-set): acc, jerk, snap, pot
+GATES = {"f32ds": (1e-6, 1e-5, 1e-4, 1e-6), "f64": (1e-12, 1e-11, 1e-10, 1e-12)}
+
+
+def _predicted_oracle_state(s, t):
+    """The oracle's prediction of the GPU system's state (and snap, crackle) to t."""
+    g = s.state()
+    snap, crk = s.snap()
+    return oracle.predict6(t, g["t"], g["pos"].T, g["vel"].T, g["acc"].T, g["jerk"].T,
+                           snap.T, crk.T), g["m"]
+
+
+@pytest.mark.parametrize("variant", ["f32ds", "f64"])
+def test_force_snap_matches_oracle(nb, variant):
+    """N = 3000 (23 full j-tiles of 128 and a ragged one), lognormal masses: one block
+    step taken so that accelerations, snap and crackle are non-trivial, then the
+    predicted state at a later time; a ragged i-set with duplicates against the oracle."""
+    n, eps = 3000, 0.01
+    p = ic.plummer(n, 80, masses="lognormal")
+    with nb.System(p.m, p.pos, p.vel, variant=variant, eps=eps, eta=0.02, order=6,
+                   device=0) as s:
+        s.step(1.0 / 64)
+        t = 1.0 / 64 + 1.0 / 1024
+        s.predict(t)
+        rng = np.random.default_rng(81)
+        idx = rng.integers(0, n, size=777).astype(np.int32)
+        idx[:5] = idx[5]                              # duplicates
+        acc, jerk, snap, pot = s.force_snap(idx)
+        (pp, vp, ap), m = _predicted_oracle_state(s, t)
+    ra, rj, rs, rp = oracle.force6(m, pp, vp, ap, eps * eps, idx)
+    ga, gj, gs, gp = GATES[variant]
+    assert _rel_rms(acc.T, ra) < ga
+    assert _rel_rms(jerk.T, rj) < gj
+    assert _rel_rms(snap.T, rs) < gs
+    assert _rel_rms(pot, rp) < gp
+
+
+def test_force_snap_all_particles_small(nb):
+    """Every particle of a small system (fewer than one tile, one i-block)."""
+    p = ic.plummer(100, 82)
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=0.02, eta=0.02, eta_s=0.01, order=6,
+                   device=0) as s:
+        nb.nb_init(s.h)
+        s.predict(0.0)
+        acc, jerk, snap, pot = s.force_snap()
+        g = s.state()
+        snap0, crk0 = s.snap()
+    ra, rj, rs, rp = oracle.force6(p.m, p.pos, p.vel, g["acc"].T, 0.02 ** 2)
+    assert _rel_rms(acc.T, ra) < 1e-6 and _rel_rms(jerk.T, rj) < 1e-5
+    assert _rel_rms(snap.T, rs) < 1e-4 and _rel_rms(pot, rp) < 1e-6
+    # the handle's start-up (two passes) is the oracle's: acc, jerk, snap, zero crackle
+    st = oracle.State6(p.m, p.pos, p.vel)
+    oracle.hermite6_run(st, 0.0, 0.02 ** 2, eta=0.02, eta_s=0.01)
+    assert _rel_rms(g["acc"].T, st.acc) < 1e-6 and _rel_rms(g["jerk"].T, st.jerk) < 1e-5
+    assert _rel_rms(snap0.T, st.snap) < 1e-4
+    assert not crk0.any()
+    np.testing.assert_array_equal(g["dt"], st.dt)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+def test_shared_steps_vs_oracle(nb, variant):
+    """N = 256, 32 shared steps of 1/256: the oracle's 6th-order state."""
+    p = ic.plummer(256, 83)
+    eps, dt = 1.0 / 64, 1.0 / 256
+    st = oracle.State6(p.m, p.pos, p.vel)
+    _, o_inter = oracle.hermite6_run(st, 32 * dt, eps * eps, dt_shared=dt)
+    with nb.System(p.m, p.pos, p.vel, variant=variant, eps=eps, shared_dt=dt, order=6,
+                   device=0) as s:
+        stats = s.step(32 * dt)
+        g = s.state()
+        snap, crk = s.snap()
+    assert stats["interactions"] == o_inter     # two start-up passes + 32 steps
+    tol = (1e-11, 1e-10) if variant == "f64" else (1e-6, 1e-5)
+    assert np.abs(g["pos"].T - st.pos).max() < tol[0]
+    assert np.abs(g["vel"].T - st.vel).max() < tol[1]
+    assert _rel_rms(snap.T, st.snap) < (1e-9 if variant == "f64" else 1e-4)
+    assert _rel_rms(crk.T, st.crackle) < (1e-7 if variant == "f64" else 1e-2)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32ds"])
+def test_block_steps_vs_oracle(nb, variant):
+    """Block steps (eta = 0.02) over 1/16 time unit: the oracle's schedule (FP64 pairs:
+    the same block-step count) and state."""
+    p = ic.plummer(512, 84)
+    eps = 0.01
+    st = oracle.State6(p.m, p.pos, p.vel)
+    # the crackle's rounding floor of the double-single pairs (2^-23), none for FP64
+    noise = 2.0 ** -23 if variant == "f32ds" else 0.0
+    o_steps, o_inter = oracle.hermite6_run(st, 1.0 / 16, eps * eps, eta=0.02, eta_s=0.01,
+                                           dt_max=1.0 / 16, noise=noise)
+    with nb.System(p.m, p.pos, p.vel, variant=variant, eps=eps, eta=0.02, eta_s=0.01,
+                   dt_max=1.0 / 16, order=6, device=0) as s:
+        stats = s.step(1.0 / 16)
+        g = s.state()
+    np.testing.assert_array_equal(g["t"], 1.0 / 16)
+    if variant == "f64":
+        assert stats["block_steps"] == o_steps
+        np.testing.assert_array_equal(g["dt"], st.dt)
+        assert np.abs(g["pos"].T - st.pos).max() < 1e-10
+    else:
+        assert abs(stats["block_steps"] - o_steps) <= 0.02 * o_steps
+        assert np.abs(g["pos"].T - st.pos).max() < 1e-5
+
+
+def test_energy_drift_block_steps(nb):
+    """N = 1024 Plummer, eps = 1/64, eta = 0.02, block steps to t = 1/4 in F32-DS."""
+    p = ic.plummer(1024, 85)
+    eps = 1.0 / 64
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.02, eta_s=0.01,
+                   order=6, device=0) as s:
+        k0, w0 = s.energy()
+        s.step(0.25)
+        k1, w1 = s.energy()
+    assert abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0) < 1e-6
+
+
+def test_close_encounter_steps_recover(nb):
+    """N = 65536 Plummer with eps = 1e-3 (close encounters at r < eps) in F32-DS for 1/16
+    time unit: no step is clamped at dt_min and the smallest step stays above 2^-20 (without
+    the crackle's rounding floor a pair that had met closely kept a step of 2^-30)."""
+    p = ic.plummer(65536, ic.MASTER_SEED, masses="equal")
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=1e-3, eta=0.02, eta_s=0.01,
+                   order=6, device=0) as s:
+        for k in range(1, 9):
+            stats = s.step(k / 128)
+            assert stats["dt_min_hits"] == 0, k
+            assert s.state()["dt"].min() >= 2.0 ** -20, k
+
+
+def test_checkpoint_resume_is_bitwise(nb):
+    p = ic.plummer(700, 86)
+    kw = dict(variant="f32ds", eps=0.01, eta=0.02, order=6, device=0)
+    with nb.System(p.m, p.pos, p.vel, **kw) as a:
+        a.step(1.0 / 8)
+        ga = a.state()
+    with nb.System(p.m, p.pos, p.vel, **kw) as b:
+        b.step(1.0 / 16)
+        gb = b.state()
+        snap, crk = b.snap()
+    with nb.System(p.m, p.pos, p.vel, **kw) as c:
+        c.set_state(gb)
+        with pytest.raises(nb.NBodyError) as e:
+            c.step(1.0 / 8)
+        assert e.value.status == nb.NB_ERR_STATE
+        c.set_snap(snap, crk)
+        c.step(1.0 / 8)
+        gc = c.state()
+    for k in ("pos", "vel", "acc", "jerk", "t", "dt"):
+        np.testing.assert_array_equal(ga[k], gc[k])
+
+
+def test_host_calls_equal_step(nb):
+    """nb_predict + nb_force_snap + nb_correct on all particles at the shared step
+    reproduce nb_step in shared-step mode bitwise."""
+    p = ic.plummer(300, 87)
+    kw = dict(variant="f32ds", eps=0.02, shared_dt=1.0 / 128, order=6, device=0)
+    with nb.System(p.m, p.pos, p.vel, **kw) as a:
+        a.step(2.0 / 128)
+        ga = a.state()
+    with nb.System(p.m, p.pos, p.vel, **kw) as b:
+        nb.nb_init(b.h)
+        for k in (1, 2):
+            t = k / 128
+            b.predict(t)
+            b.force_snap()
+            b.correct(None, t)
+        gb = b.state()
+    for k in ("pos", "vel", "acc", "jerk"):
+        np.testing.assert_array_equal(ga[k], gb[k])
+
+
+def test_order6_argument_checks(nb):
+    p = ic.plummer(64, 88)
+    with nb.System(p.m, p.pos, p.vel, eps=0.01, device=0) as s4:
+        s4.predict(0.0)
+        with pytest.raises(nb.NBodyError) as e:
+            s4.force_snap()
+        assert e.value.status == nb.NB_ERR_ARG
+    for bad in (dict(order=5), dict(order=6, n_corr=2), dict(order=6, variant="f32")):
+        with pytest.raises(nb.NBodyError) as e:
+            nb.System(p.m, p.pos, p.vel, eps=0.01, device=0, **bad)
+        assert e.value.status == nb.NB_ERR_ARG
+    with nb.System(p.m, p.pos, p.vel, eps=0.01, order=6, eta=0.02, device=0) as s6:
+        with pytest.raises(nb.NBodyError) as e:
+            nb.nb_autotune(s6.h, 1)
+        assert e.value.status == nb.NB_ERR_ARG
+        s6.predict(0.0)
+        with pytest.raises(nb.NBodyError) as e:
+            s6.force_ext(p.pos[:4], p.vel[:4])
+        assert e.value.status == nb.NB_ERR_ARG

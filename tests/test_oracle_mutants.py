@@ -62,7 +62,11 @@ MUTANTS = [
     ("crackle coefficient 15 -> 12", "(15.0 * (T * Jp - Am)", "(12.0 * (T * Jp - Am)"),
     ("crackle left at the mid-point", "a3_end[c] = c3 + c4 * T + c5 * T * T / 2.0;", "a3_end[c] = c3;"),
     ("pop sign", "a4_end[c] = c4 + c5 * T;", "a4_end[c] = c4 - c5 * T;"),
-    ("criterion6 exponent 1/3 -> 1/2", "eta * cbrt(num / den)", "eta * sqrt(num / den)"),
+    ("criterion6 pop instead of crackle", "ce[c] = a3[c] * ((cn - cfl) / cn);",
+     "ce[c] = a4[c] * ((cn - cfl) / cn);"),
+    ("criterion6 crackle floor ignored", "if (cn > cfl)", "if (cn > 0.0 * cfl)"),
+    ("criterion6 jerk instead of snap", "orc_aarseth_dt(a1 + r, j1 + r, s1 + r, ce, eta)",
+     "orc_aarseth_dt(a1 + r, j1 + r, j1 + r, ce, eta)"),
     ("crackle not kept", "s->crk[q + c] = a3[c];", "s->crk[q + c] = 0.0;"),
     ("scheduler6 takes a particle early", "if (due == t_next)", "if (due <= t_next + s->dt[i] / 2)"),
     ("initial snap without accelerations", "memcpy(aj, s->acc, sizeof(double) * 3 * (size_t)n);",
