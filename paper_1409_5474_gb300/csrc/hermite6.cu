@@ -92,9 +92,15 @@ __device__ __forceinline__ void store6(const Out6 &out, int k, double v[H6_VALS]
 
 // ---- K2, FP32 / double-single ---------------------------------------------------
 
-// IPT i-particles per thread share each j-record loaded from shared memory.
-template <bool DS, int IPT>
-__global__ void __launch_bounds__(32 * H6_NWARP, 1)
+// IPT i-particles per thread share each j-record loaded from shared memory. The
+// CTA's 8 warps are NWI warp columns (different i-particles) x NWJ warp rows
+// (the same i-particles, sharing out each j-tile: row g takes j = g, g + NWJ,
+// ...), so that a small due set still spreads over the SM; rows are added in
+// shared memory at the end, in fixed order. Two CTAs per SM (16 warps) hide the
+// pair arithmetic's latencies better than one; the two-particle variant then
+// spills a few bytes outside the j-loop, and still runs 2-12% faster.
+template <bool DS, int IPT, int NWJ>
+__global__ void __launch_bounds__(32 * H6_NWARP, 2)
     k_force6_tile32(const float4 *__restrict__ jrec, int nj, const int *__restrict__ idx,
                     int n_i, float eps2f, int ntiles, float2 *__restrict__ part, long long pld,
                     Out6 out, unsigned *err)
@@ -103,9 +109,11 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 1)
     __shared__ __align__(8) uint64_t s_full[H6_NS];
     __shared__ int s_abort;
 
-    constexpr int NT = 32 * H6_NWARP;
-    constexpr int IB = NT * IPT;
-    const int tid = threadIdx.x;
+    constexpr int NWI = H6_NWARP / NWJ;
+    constexpr int IB = 32 * NWI * IPT;
+    static_assert(NWI * NWJ == H6_NWARP, "warp grid");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wi = warp % NWI, wj = warp / NWI;
     const int nsplit = gridDim.y, split = blockIdx.y;
     const int tile0 = (int)((long long)ntiles * split / nsplit);
     const int tile1 = (int)((long long)ntiles * (split + 1) / nsplit);
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 1)
     float vx[IPT], vy[IPT], vz[IPT], ax[IPT], ay[IPT], az[IPT];
 #pragma unroll
     for (int p = 0; p < IPT; ++p) {
-        const int k = min(blockIdx.x * IB + p * NT + tid, n_i - 1);
+        const int k = min(blockIdx.x * IB + p * (32 * NWI) + wi * 32 + lane, n_i - 1);
         ii[p] = member6(idx, k, nj, err);
         const float4 *r = jrec + (size_t)DS6_REC * ii[p];
         const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
@@ -224,13 +232,13 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 1)
             }
         };
         if (own) {
-            for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
+            for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::true_type{});
         } else if (cnt == H6_JT) {
 #pragma unroll 4
-            for (int jj = 0; jj < H6_JT; ++jj) body(jj, std::false_type{});
+            for (int jj = wj; jj < H6_JT; jj += NWJ) body(jj, std::false_type{});
         } else {
 #pragma unroll 2
-            for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
+            for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::false_type{});
         }
 #pragma unroll
         for (int p = 0; p < IPT; ++p)
@@ -254,9 +262,36 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 1)
         if (tid == 0) atomicOr(err, DERR_TIMEOUT);
         return;
     }
+    if (NWJ > 1) {
+        // add the warp rows in order 0..NWJ-1 (the tile ring is free: every copy has landed)
+        float2 *s_red = reinterpret_cast<float2 *>(s_tile6);  // [NWJ][H6_VALS][IB]
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int slot = p * (32 * NWI) + wi * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < H6_VALS; ++c)
+                s_red[(wj * H6_VALS + c) * IB + slot] = make_float2(H[p][c], L[p][c]);
+        }
+        __syncthreads();
+        if (wj != 0) return;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) {
+            const int slot = p * (32 * NWI) + wi * 32 + lane;
+#pragma unroll
+            for (int c = 0; c < H6_VALS; ++c) {
+                dsf v{H[p][c], L[p][c]};
+                for (int g = 1; g < NWJ; ++g) {
+                    const float2 w = s_red[(g * H6_VALS + c) * IB + slot];
+                    ds_acc(v, dsf{w.x, w.y});
+                }
+                H[p][c] = v.hi;
+                L[p][c] = v.lo;
+            }
+        }
+    }
 #pragma unroll
     for (int p = 0; p < IPT; ++p) {
-        const int kk = blockIdx.x * IB + p * NT + tid;
+        const int kk = blockIdx.x * IB + p * (32 * NWI) + wi * 32 + lane;
         if (kk >= n_i) continue;
         if (nsplit == 1) {
             double v[H6_VALS];
@@ -351,28 +386,35 @@ __global__ void __launch_bounds__(H6_T64)
 
 // ---- K3 --------------------------------------------------------------------------
 
-// One thread per (component, slot): the nsplit partial sums in split order.
+// One warp per (component, slot): lane l adds splits l, l + 32, ... in order, then
+// a fixed xor tree, so the result does not depend on the order the CTAs ran in.
 template <bool DS>
 __global__ void k_force6_reduce(const void *__restrict__ part, long long pld, int nsplit, int n_i,
                                 Out6 out, unsigned *err)
 {
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (long long)n_i * H6_VALS) return;
+    const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (q >= (long long)n_i * H6_VALS) return;  // whole warps leave together
     const int c = (int)(q / n_i), k = (int)(q % n_i);
     double v;
     if (DS) {
         const float2 *p = static_cast<const float2 *>(part);
         dsf a{0.f, 0.f};
-        for (int sp = 0; sp < nsplit; ++sp) {
+        for (int sp = lane; sp < nsplit; sp += 32) {
             const float2 w = __ldg(p + ((size_t)sp * H6_VALS + c) * pld + k);
             ds_acc(a, dsf{w.x, w.y});
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ds_acc(a, ds_shfl_xor(a, o));
         v = ds_to_double(a);
     } else {
         const double *p = static_cast<const double *>(part);
         v = 0.0;
-        for (int sp = 0; sp < nsplit; ++sp) v += __ldg(p + ((size_t)sp * H6_VALS + c) * pld + k);
+        for (int sp = lane; sp < nsplit; sp += 32) v += __ldg(p + ((size_t)sp * H6_VALS + c) * pld + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     }
+    if (lane != 0) return;
     if (c == 9) {
         v = -v;
         if (out.pot) out.pot[k] = v;
@@ -468,6 +510,35 @@ __global__ void k_correct6(StateDev s, const int *__restrict__ act, int na, doub
     s.dt[i] = dt_new;
 }
 
+// Resident CTAs per SM of a FP32 / double-single variant (occupancy API, cached).
+template <bool DS, int IPT, int NWJ>
+int occ6()
+{
+    static int v = -1;
+    if (v < 0) {
+        int b = 0;
+        const size_t smem = (size_t)H6_NS * H6_JT * DS6_REC * sizeof(float4);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force6_tile32<DS, IPT, NWJ>,
+                                                          32 * H6_NWARP, smem) != cudaSuccess) {
+            cudaGetLastError();
+            b = 1;
+        }
+        v = std::max(b, 1);
+    }
+    return v;
+}
+
+int occ6_of(bool ds, int ipt, int nwj)
+{
+    if (ipt == 2) return ds ? occ6<true, 2, 1>() : occ6<false, 2, 1>();
+    switch (nwj) {
+    case 8: return ds ? occ6<true, 1, 8>() : occ6<false, 1, 8>();
+    case 4: return ds ? occ6<true, 1, 4>() : occ6<false, 1, 4>();
+    case 2: return ds ? occ6<true, 1, 2>() : occ6<false, 1, 2>();
+    default: return ds ? occ6<true, 1, 1>() : occ6<false, 1, 1>();
+    }
+}
+
 }  // namespace
 
 // ---- host side ---------------------------------------------------------------------
@@ -484,25 +555,39 @@ cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned
     return cudaGetLastError();
 }
 
-// About four CTAs per SM in all (two resident per SM of the FP32 kernel, two
-// waves), the j-range cut into at most one split per 4 tiles.
+
+// The CTA shape from the size of the due set: two i-particles per thread once
+// there are enough i-blocks to go round, warp rows sharing each j-tile below 256
+// (8 rows for 32 or fewer). Then the j-splits: at least two waves of resident
+// CTAs, and among up to twice that many splits the count whose last wave is the
+// fullest (a 2.1-wave grid idles most SMs for its last tenth); at most one split
+// per j-tile.
 ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
 {
     ForcePlan p{};
     p.kind = 0;
     const bool f64 = (variant == NB_F64);
-    // two i-particles per thread halve the shared-memory loads per pair once there
-    // are enough i-blocks to go round
     p.ipt = (!f64 && n_i >= 8 * 32 * H6_NWARP) ? 2 : 1;
-    p.threads = f64 ? H6_T64 : 32 * H6_NWARP * p.ipt;  // i-particles per CTA
+    p.nwj = f64 ? 1 : (n_i <= 32 ? 8 : n_i <= 64 ? 4 : n_i <= 128 ? 2 : 1);
+    p.threads = f64 ? H6_T64 : 32 * (H6_NWARP / p.nwj) * p.ipt;  // i-particles per CTA
     p.jt = f64 ? H6_JT64 : H6_JT;
-    p.nwj = 1;
     const long long nblk = (n_i + p.threads - 1) / p.threads;
     const long long ntiles = (n_j + p.jt - 1) / p.jt;
-    const long long target = 4LL * std::max(num_sms, 1);
-    long long ns = (target + nblk - 1) / std::max(nblk, 1LL);
-    ns = std::min(ns, std::max(1LL, ntiles / 4));
-    p.nsplit = (int)std::max(1LL, std::min(ns, 1024LL));
+    const long long cap = std::max(1LL, f64 ? ntiles / 4 : ntiles);
+    const long long slots =
+        (long long)std::max(num_sms, 1) * (f64 ? 4 : occ6_of(variant == NB_F32DS, p.ipt, p.nwj));
+    const long long ns0 = std::min(cap, std::max(1LL, (2 * slots + nblk - 1) / nblk));
+    long long best = ns0;
+    double best_eff = 0.0;
+    for (long long ns = ns0; ns <= std::min(cap, 2 * ns0); ++ns) {
+        const double waves = (double)(nblk * ns) / (double)slots;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = ns;
+        }
+    }
+    p.nsplit = (int)std::min(best, 1024LL);
     return p;
 }
 
@@ -524,23 +609,26 @@ cudaError_t launch_force6(int variant, const ForcePlan &p, const StateDev &s, co
         k_force6_tile64<<<grid, H6_T64, 0, st>>>(s, idx, n_i, eps2, part, pld, out, err);
     } else {
         const int ntiles = (s.n + H6_JT - 1) / H6_JT;
-        const int nt = 32 * H6_NWARP, ib = nt * p.ipt;
+        const int nt = 32 * H6_NWARP;
+        const int ib = 32 * (H6_NWARP / p.nwj) * p.ipt;
         dim3 grid((n_i + ib - 1) / ib, p.nsplit);
         const size_t smem = (size_t)H6_NS * H6_JT * DS6_REC * sizeof(float4);
         float2 *pp = reinterpret_cast<float2 *>(part);
         const float e2 = (float)eps2;
-        if (variant == NB_F32DS && p.ipt == 2)
-            k_force6_tile32<true, 2><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
-                                                             pp, pld, out, err);
-        else if (variant == NB_F32DS)
-            k_force6_tile32<true, 1><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
-                                                             pp, pld, out, err);
-        else if (p.ipt == 2)
-            k_force6_tile32<false, 2><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
-                                                              pp, pld, out, err);
+        auto go = [&](auto kern) {
+            kern<<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles, pp, pld, out, err);
+        };
+        const bool ds = (variant == NB_F32DS);
+        if (p.ipt == 2)
+            ds ? go(k_force6_tile32<true, 2, 1>) : go(k_force6_tile32<false, 2, 1>);
+        else if (p.nwj == 8)
+            ds ? go(k_force6_tile32<true, 1, 8>) : go(k_force6_tile32<false, 1, 8>);
+        else if (p.nwj == 4)
+            ds ? go(k_force6_tile32<true, 1, 4>) : go(k_force6_tile32<false, 1, 4>);
+        else if (p.nwj == 2)
+            ds ? go(k_force6_tile32<true, 1, 2>) : go(k_force6_tile32<false, 1, 2>);
         else
-            k_force6_tile32<false, 1><<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles,
-                                                              pp, pld, out, err);
+            ds ? go(k_force6_tile32<true, 1, 1>) : go(k_force6_tile32<false, 1, 1>);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -549,7 +637,7 @@ cudaError_t launch_force6(int variant, const ForcePlan &p, const StateDev &s, co
         cudaEventRecord(ev[2], st);
     }
     if (p.nsplit > 1) {
-        const long long total = (long long)n_i * H6_VALS;
+        const long long total = (long long)n_i * H6_VALS * 32;  // a warp per output
         const int bs = 256;
         const int g = (int)((total + bs - 1) / bs);
         if (variant == NB_F64)
