@@ -50,6 +50,7 @@ constexpr int H6_NS = 3;        // ring stages
 constexpr int H6_NWARP = 8;     // warps per FP32 CTA (one i-particle per thread)
 constexpr int H6_T64 = 128;     // threads per FP64 CTA
 constexpr int H6_JT64 = 128;    // j per FP64 shared tile
+constexpr int CORRECT6_THREADS = 128;  // 4 warps x 10 slots (3 lanes per slot)
 
 // ---- K1 ----------------------------------------------------------------------
 
@@ -436,27 +437,33 @@ __global__ void k_force6_reduce(const void *__restrict__ part, long long pld, in
 // and 5th collapses the steps to dt_min, and the crackle is used above its
 // rounding floor only (prm.noise), else a particle whose step once got small
 // (a close encounter) could not grow it again.
-__global__ void k_correct6(StateDev s, const int *__restrict__ act, int na, double t_new, Out6 f,
-                           StepParams prm, SchedDev *sd, unsigned *err,
-                           unsigned long long *dtmin_hits)
+__global__ void __launch_bounds__(CORRECT6_THREADS)
+    k_correct6(StateDev s, const int *__restrict__ act, int na, double t_new, Out6 f,
+               StepParams prm, SchedDev *sd, unsigned *err, unsigned long long *dtmin_hits)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) sd->t_cur = t_new;
-    if (k >= na) return;
-    const int i = act ? act[k] : k;
-    const double dt = t_new - s.t[i];
-    const double dt_old = s.dt[i];
-    const double T = 0.5 * dt;
-    const double iT = prm.shared_dt > 0.0 ? 1.0 / T : ldexp(1.0, -ilogb(T));
-    const double iT3 = iT * iT * iT, iT5 = iT3 * iT * iT;
-    double a1v[3], j1v[3], s1v[3], a3v[3];
-    bool finite = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    // three lanes per slot (component c = lane % 3 of slot lane / 3; lanes 30, 31
+    // idle), so that the FP64 dependency chains of the three components run side by side
+    const int lane = threadIdx.x & 31;
+    const int warp_g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int k = warp_g * 10 + lane / 3;
+    const int c = lane % 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sd->t_cur = t_new;
+    const bool mine = lane < 30 && k < na;
+    double a1 = 0.0, j1 = 0.0, s1 = 0.0, a3 = 0.0, dt = 1.0, dt_old = 0.0, T = 0.5;
+    int i = 0;
+    bool fin = true;
+    if (mine) {
+        i = act ? act[k] : k;
+        dt = t_new - s.t[i];
+        dt_old = s.dt[i];
+        T = 0.5 * dt;
+        const double iT = prm.shared_dt > 0.0 ? 1.0 / T : ldexp(1.0, -ilogb(T));
+        const double iT3 = iT * iT * iT, iT5 = iT3 * iT * iT;
         const long long q = c * s.ld + i;
         const double x0 = s.pos[q], v0 = s.vel[q], a0 = s.acc[q], j0 = s.jerk[q], s0 = s.snap[q];
-        const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
-        const double s1 = f.snap[c * f.ld + k];
+        a1 = f.acc[c * f.ld + k];
+        j1 = f.jerk[c * f.ld + k];
+        s1 = f.snap[c * f.ld + k];
         // v1 = v0 + dt/2 (a0 + a1) - dt^2/10 (j1 - j0) + dt^3/120 (s0 + s1)
         const double v1 = v0 + dt * fma(dt, fma(dt, (s0 + s1) * (1.0 / 120.0),
                                                 -0.1 * (j1 - j0)), 0.5 * (a0 + a1));
@@ -469,19 +476,29 @@ __global__ void k_correct6(StateDev s, const int *__restrict__ act, int na, doub
         const double c5 = (45.0 * Am - 45.0 * T * Jp + 15.0 * T * T * Sm) * iT5;
         const double c3 = (7.5 * (T * Jp - Am) - 1.5 * T * T * Sm) * iT3;
         const double c4 = 3.0 * (T * Sp - Jm) * iT3;
-        a3v[c] = c3 + T * (c4 + 0.5 * T * c5);
-        a1v[c] = a1;
-        j1v[c] = j1;
-        s1v[c] = s1;
+        a3 = c3 + T * (c4 + 0.5 * T * c5);
         s.pos[q] = x1;
         s.vel[q] = v1;
         s.acc[q] = a1;
         s.jerk[q] = j1;
         s.snap[q] = s1;
-        s.crk[q] = a3v[c];
-        finite = finite && isfinite(x1) && isfinite(v1);
+        s.crk[q] = a3;
+        fin = isfinite(x1) && isfinite(v1);
     }
-    if (!finite) atomicOr(err, DERR_NONFINITE);
+    // the slot's three components on its first lane
+    const int l0 = lane - c;
+    double a1v[3], j1v[3], s1v[3], a3v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int src = min(31, l0 + q);
+        a1v[q] = __shfl_sync(0xffffffffu, a1, src);
+        j1v[q] = __shfl_sync(0xffffffffu, j1, src);
+        s1v[q] = __shfl_sync(0xffffffffu, s1, src);
+        a3v[q] = __shfl_sync(0xffffffffu, a3, src);
+    }
+    const unsigned bad = __ballot_sync(0xffffffffu, mine && !fin);
+    if (!mine || c != 0) return;
+    if (bad & (7u << l0)) atomicOr(err, DERR_NONFINITE);
     double dt_new;
     if (prm.shared_dt > 0.0) {
         dt_new = prm.shared_dt;
@@ -654,9 +671,9 @@ cudaError_t launch_correct6(const StateDev &s, const int *act, int n_a, double t
                             const Out6 &f, const StepParams &p, SchedDev *sd, unsigned *err,
                             unsigned long long *dtmin_hits, cudaStream_t st)
 {
-    const int bs = 128;
-    const int g = std::max(1, (n_a + bs - 1) / bs);
-    k_correct6<<<g, bs, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits);
+    const int slots = 10 * (CORRECT6_THREADS / 32);
+    const int g = std::max(1, (n_a + slots - 1) / slots);
+    k_correct6<<<g, CORRECT6_THREADS, 0, st>>>(s, act, n_a, t_new, f, p, sd, err, dtmin_hits);
     return cudaGetLastError();
 }
 
