@@ -47,7 +47,7 @@ namespace {
 constexpr int H6_VALS = 10;     // acc 3, jerk 3, snap 3, pot 1 per i-particle
 constexpr int H6_JT = 128;      // j-records per tile
 constexpr int H6_NS = 3;        // ring stages
-constexpr int H6_NWARP = 8;     // warps per FP32 CTA (one i-particle per thread)
+constexpr int H6_NWARP = 8;     // warps per FP32 CTA
 constexpr int H6_T64 = 128;     // threads per FP64 CTA
 constexpr int H6_JT64 = 128;    // j per FP64 shared tile
 constexpr int CORRECT6_THREADS = 128;  // 4 warps x 10 slots (3 lanes per slot)
