@@ -74,3 +74,33 @@ def test_missing_library_fails_loudly(tmp_path):
             nbody.load(str(tmp_path / "none.so"))
     finally:
         nbody._lib = saved
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the C compiler
+    gives the header's struct of the same name (a field added on one side only fails)."""
+    import subprocess
+    from paper_1409_5474_gb300 import nbody
+    structs = [nbody.nb_config, nbody.nb_plan, nbody.nb_stats, nbody.nb_server_cfg,
+               nbody.nb_request, nbody.nb_result, nbody.nb_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nbody.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field in st._fields_:
+            f = field[0]
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_vals = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        name = st.__name__
+        assert c_vals[(name, "size")] == ctypes.sizeof(st), name
+        for field in st._fields_:
+            f = field[0]
+            assert c_vals[(name, f)] == getattr(st, f).offset, (name, f)

@@ -206,3 +206,31 @@ def test_order6_argument_checks(nb):
         with pytest.raises(nb.NBodyError) as e:
             s6.force_ext(p.pos[:4], p.vel[:4])
         assert e.value.status == nb.NB_ERR_ARG
+
+
+def test_single_particle_and_circular_pair(nb):
+    """Degenerate sizes: one particle moves on a straight line with dt = dt_max and zero
+    derivatives; a softened circular pair in FP64 shared steps follows the oracle's
+    6th-order orbit to rounding over one period."""
+    m = np.array([1.0])
+    pos = np.array([[0.1, -0.2, 0.3]])
+    vel = np.array([[0.5, 0.25, -1.0]])
+    with nb.System(m, pos, vel, variant="f32ds", eps=0.01, eta=0.02, order=6, device=0) as s:
+        s.step(0.5)
+        g = s.state()
+        snap, crk = s.snap()
+    np.testing.assert_allclose(g["pos"].T, pos + 0.5 * vel, rtol=0, atol=1e-15)
+    assert g["dt"][0] == 1.0 / 16 and not g["acc"].any() and not snap.any() and not crk.any()
+    d, eps = 1.0, 0.3
+    omega = math.sqrt(1.0 / (d * d + eps * eps) ** 1.5)
+    m2 = np.array([0.5, 0.5])
+    p2 = np.array([[-d / 2, 0, 0], [d / 2, 0, 0]])
+    v2 = np.array([[0, -omega * d / 2, 0], [0, omega * d / 2, 0]])
+    dt = 2 * math.pi / omega / 64
+    st = oracle.State6(m2, p2, v2)
+    oracle.hermite6_run(st, math.inf, eps * eps, dt_shared=dt, max_steps=64)
+    with nb.System(m2, p2, v2, variant="f64", eps=eps, shared_dt=dt, order=6, device=0) as s:
+        s.step(64 * dt)
+        g = s.state()
+    assert np.abs(g["pos"].T - st.pos).max() < 1e-13
+    assert np.abs(g["pos"].T - p2).max() < 1e-6   # back where it started after one period
