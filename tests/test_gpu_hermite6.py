@@ -230,7 +230,8 @@ def test_single_particle_and_circular_pair(nb):
     st = oracle.State6(m2, p2, v2)
     oracle.hermite6_run(st, math.inf, eps * eps, dt_shared=dt, max_steps=64)
     with nb.System(m2, p2, v2, variant="f64", eps=eps, shared_dt=dt, order=6, device=0) as s:
-        s.step(64 * dt)
+        stats = s.step(64.5 * dt)         # 64 steps: the 65th would end past 64.5 dt
         g = s.state()
+    assert stats["block_steps"] == 64
     assert np.abs(g["pos"].T - st.pos).max() < 1e-13
     assert np.abs(g["pos"].T - p2).max() < 1e-6   # back where it started after one period
