@@ -235,3 +235,24 @@ def test_single_particle_and_circular_pair(nb):
     assert stats["block_steps"] == 64
     assert np.abs(g["pos"].T - st.pos).max() < 1e-13
     assert np.abs(g["pos"].T - p2).max() < 1e-6   # back where it started after one period
+
+
+def test_full_size_h6block65536_sampled(nb):
+    """The bench's 6th-order configuration at full size (N = 65536, eps = 1e-3, eta =
+    0.02): after 1/64 time unit the snap force on a seeded 512-particle sample of the
+    predicted state (positions, velocities, accelerations) against the oracle."""
+    p = ic.plummer(65536, ic.MASTER_SEED, masses="equal")
+    eps = 1e-3
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.02, eta_s=0.01, order=6,
+                   device=0) as s:
+        s.step(1.0 / 64)
+        t = 1.0 / 64 + 1.0 / 4096
+        s.predict(t)
+        rng = np.random.default_rng(65537)
+        sample = np.sort(rng.choice(65536, size=512, replace=False)).astype(np.int32)
+        acc, jerk, snap, pot = s.force_snap(sample)
+        (pp, vp, ap), m = _predicted_oracle_state(s, t)
+    ra, rj, rs, rp = oracle.force6(m, pp, vp, ap, eps * eps, sample)
+    ga, gj, gs, gp = GATES["f32ds"]
+    assert _rel_rms(acc.T, ra) < ga and _rel_rms(jerk.T, rj) < gj
+    assert _rel_rms(snap.T, rs) < gs and _rel_rms(pot, rp) < gp
