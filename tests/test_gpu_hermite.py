@@ -216,23 +216,24 @@ def test_double_single_against_fp64_pairs_block_steps(nb):
 
 def test_full_size_block65536_sampled(nb):
     """The bench's block-step configuration at full size (Plummer N = 65536, eps = 1e-3,
-    eta = 0.01, autotuned plans, fused small steps): after 1/64 time unit the planned force
-    on a seeded 512-particle sample of the predicted state against the oracle, the fused
-    kernel having taken steps, and the energy."""
+    eta = 0.01, autotuned plans, fused small steps): after 1/16 time unit (one dt_max, all
+    particles synchronised) the planned force on a seeded 512-particle sample of the
+    predicted state against the oracle, the fused kernel having taken steps, and the
+    energy."""
     p = ic.plummer(65536, ic.MASTER_SEED, masses="equal")
     eps = 1e-3
     with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.01, device=0) as s:
         nb.nb_autotune(s.h, 1)
         k0, w0 = s.energy()
-        stats = s.step(1.0 / 64)
+        stats = s.step(1.0 / 16)
         assert stats["fused_steps"] > 0 and stats["block_steps"] > stats["fused_steps"] > 0
+        k1, w1 = s.energy()
         g = s.state()
-        t = 1.0 / 64 + 1.0 / 4096
+        t = 1.0 / 16 + 1.0 / 4096
         s.predict(t)
         rng = np.random.default_rng(65536)
         sample = np.sort(rng.choice(65536, size=512, replace=False)).astype(np.int32)
         acc, jerk, pot = s.force(sample)
-        k1, w1 = s.energy()
     pp, vp = oracle.predict(t, g["t"], g["pos"].T, g["vel"].T, g["acc"].T, g["jerk"].T)
     ra, rj, rp = oracle.force(g["m"], pp, vp, eps * eps, idx=sample)
     rel = lambda x, y: np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum())
