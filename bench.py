@@ -69,12 +69,13 @@ WORKLOADS = {
                            "1/16 time unit = 32 graph-replayed steps of all clusters"),
     "serve": dict(n=64, n_lo=2 ** 8, n_hi=2 ** 18, t_span=0.125, eta=0.01, dt_max=1.0 / 16,
                   variant="f32ds", kind="serve", eps=None, masses="galaxy",
-                  rates=(8.0, 32.0, 1e6),
+                  rates=(1e6,), sweep_fracs=(0.1, 0.5, 1.0, 2.0),
                   desc="Poisson stream of 64 requests on subsystems of 11 Plummer galaxies "
                        "with a 1% central point mass, N log-uniform in [2^8, 2^18], half one "
                        "force evaluation, half 1/8 time unit of block steps (eta=0.01, "
                        "dt_max=1/16), eps = 1/(4 N^(1/3)); one bench step = the whole stream at "
-                       "the saturating rate"),
+                       "the saturating rate (all requests at once); then the arrival rate is "
+                       "swept at 0.1x-2x the measured saturation rate"),
     "ext65536": dict(n=65536, n_ext=65536, eps=1e-3, variant="f32ds", masses="equal", kind="ext",
                      desc="field-particle service (nb_force_ext): the force of a Plummer j-set of "
                           "N=65536 (eps=1e-3) on 65536 external particles of a second Plummer "
@@ -966,10 +967,15 @@ def run_serve(args, wl, variant, dist, rank, world, local):
         timed.append(summarise(*run_stream(wl["rates"][-1])))
     st1 = srv.stats()
     clocks = sampler.stop()
+    # arrival rates relative to saturation: the requests per second the server sustains
+    # when all arrive at once (count / makespan of the timed streams)
+    r_sat = len(base) / (sum(t["makespan_s"] for t in timed) / len(timed))
     sweep = []
-    for rate in wl["rates"][:-1]:
+    for frac in wl["sweep_fracs"]:
+        rate = frac * r_sat
         reqs, res = run_stream(rate)
-        sweep.append({"rate_hz": rate, "server": summarise(reqs, res)})
+        sweep.append({"rate_hz": rate, "frac_of_saturation": frac,
+                      "server": summarise(reqs, res)})
 
     # one request per launch: pre-created engine handles, requests served in arrival order
     systems = [nbody.System(p.m, p.pos, p.vel, variant=variant, eps=e, eta=wl["eta"],
@@ -1007,8 +1013,8 @@ def run_serve(args, wl, variant, dist, rank, world, local):
 
     for row in sweep:
         row["one_request_per_launch"] = fifo(row["rate_hz"])
-    sat = {"rate_hz": wl["rates"][-1], "server": timed[-1],
-           "one_request_per_launch": fifo(wl["rates"][-1])}
+    sat = {"rate_hz": wl["rates"][-1], "frac_of_saturation": None, "server": timed[-1],
+           "one_request_per_launch": fifo(wl["rates"][-1]), "saturation_rate_hz": r_sat}
     sweep.append(sat)
     srv_stats = {k: st1[k] - st0[k] for k in ("ticks", "force_launches", "interactions",
                                                "busy_s", "completed", "kernel_launches")}
