@@ -13,17 +13,20 @@
 // bytes instead of 48), the prediction runs through the crackle term, and the
 // corrector is the order-6 two-point quadrature with the crackle, pop and 5th
 // derivative of the acceleration taken from the quintic through (a, jerk,
-// snap) at both ends of the step.
+// snap) at both ends of the step; the step criterion uses the crackle only (see
+// k_correct6).
 //
 // Kernels:
 //   k_predict6           K1 for all particles (the block scheduler has its own
 //                        order-6 instantiation in step.cu)
-//   k_force6_tile32<DS>  K2, FP32 / double-single pairs: a CTA of 8 warps owns
-//                        256 i-particles (one per thread), j-tiles of 128
-//                        records stream through a 3-stage ring of bulk copies
-//                        (TMA engine, mbarrier completion, bounded waits);
-//                        FP32 sums per tile are folded into double-single
-//                        totals; grid.y splits the j-range
+//   k_force6_tile32<DS, IPT, NWJ>
+//                        K2, FP32 / double-single pairs: a CTA of 8 warps holds
+//                        IPT i-particles per thread in 8/NWJ warp columns, NWJ
+//                        warp rows share each j-tile; j-tiles of 128 records
+//                        stream through a 3-stage ring of bulk copies (TMA
+//                        engine, mbarrier completion, bounded waits); FP32 sums
+//                        per tile are folded into double-single totals;
+//                        grid.y splits the j-range
 //   k_force6_tile64      K2, FP64 pairs (the correctness variant)
 //   k_force6_reduce<DS>  K3: the splits of each output added in fixed order
 //   k_correct6           K4: corrector, end-of-step crackle, step criterion,
