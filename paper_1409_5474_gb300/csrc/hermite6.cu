@@ -579,7 +579,8 @@ cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned
 // The CTA shape from the size of the due set: two i-particles per thread once
 // there are enough i-blocks to go round, warp rows sharing each j-tile below 256
 // (8 rows for 32 or fewer). Then the j-splits: at least two waves of resident
-// CTAs, and among up to twice that many splits the count whose last wave is the
+// CTAs (one for the warp-row shapes, whose CTAs are short: 8-14% faster there),
+// and among up to twice that many splits the count whose last wave is the
 // fullest (a 2.1-wave grid idles most SMs for its last tenth); at most one split
 // per j-tile.
 ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
@@ -596,7 +597,8 @@ ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
     const long long cap = std::max(1LL, f64 ? ntiles / 4 : ntiles);
     const long long slots =
         (long long)std::max(num_sms, 1) * (f64 ? 4 : occ6_of(variant == NB_F32DS, p.ipt, p.nwj));
-    const long long ns0 = std::min(cap, std::max(1LL, (2 * slots + nblk - 1) / nblk));
+    const long long waves = p.nwj > 1 ? 1 : 2;
+    const long long ns0 = std::min(cap, std::max(1LL, (waves * slots + nblk - 1) / nblk));
     long long best = ns0;
     double best_eff = 0.0;
     for (long long ns = ns0; ns <= std::min(cap, 2 * ns0); ++ns) {
