@@ -123,6 +123,12 @@ def parse_args(argv=None):
     ap.add_argument("--requests", type=int, default=None,
                     help="serve: requests in the stream (default 64)")
     ap.add_argument("--n-hi", type=int, default=None, help="serve: largest request N")
+    ap.add_argument("--n-i", type=int, default=None,
+                    help="full2p20: evaluate the force on a seeded i-subset of this size only "
+                         "(profiling of the mid-size due sets of block steps)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="block65536: skip the full2p20 and serve measurements that the default "
+                         "line carries as extra keys")
     return ap.parse_args(argv)
 
 
@@ -158,6 +164,15 @@ def aggregate(per_rank):
     units = sum(u for u, _ in per_rank)
     secs = max(s for _, s in per_rank)
     return units, secs
+
+
+def emit(args, line):
+    """Print the JSON line, or hand it to the caller that measures a sub-workload."""
+    cap = getattr(args, "capture", None)
+    if cap is not None:
+        cap.append(line)
+    else:
+        print(json.dumps(line), flush=True)
 
 
 class Dist:
@@ -293,8 +308,10 @@ def stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms, planned_inter,
 ORACLE_BLOCK_STEPS = 64
 
 
-def oracle_sample(wl, particles):
-    """One bounded oracle sample of the workload; returns (interactions, seconds, desc)."""
+def oracle_sample(wl, particles, keep=None):
+    """One bounded oracle sample of the workload; returns (interactions, seconds, desc).
+    keep (a dict), for a full evaluation: receives the sample's indices and the oracle's
+    acc, jerk, pot on them."""
     import oracle
     if wl["kind"] == "batch":
         # 32 seeded clusters spanning the size range, 64 shared steps each
@@ -346,8 +363,10 @@ def oracle_sample(wl, particles):
         ni = 4096
         idx = rng.choice(particles.n, size=ni, replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        oracle.force(particles.m, particles.pos, particles.vel, eps2, idx=idx)
+        ra, rj, rp = oracle.force(particles.m, particles.pos, particles.vel, eps2, idx=idx)
         dt = time.perf_counter() - t0
+        if keep is not None:
+            keep.update(idx=idx, acc=ra, jerk=rj, pot=rp)
         return float(ni) * particles.n, dt, (
             f"oracle force on a seeded {ni}-particle i-subset against all {particles.n} j")
     if wl.get("order", 4) == 6:
@@ -421,7 +440,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(wl, args.workload, variant),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": desc + " (per step)"},
+                             "kind": "oracle", "build": oracle.CFLAGS,
+                             "sample": desc + " (per step)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -491,14 +511,15 @@ def run_ours(args):
             w1 = time.perf_counter()
             stream.synchronize()
             return st["interactions"], e0.elapsed_time(e1), w1 - w0, st["kernel_launches"], st, out
-        # full evaluation: predict to t0 and one N^2 force
+        # full evaluation: predict to t0 and one N^2 force (or the force on an i-subset)
         before = nbody.nb_get_stats(h)
         w0 = time.perf_counter()
         if host_state is not None:
             nbody.nb_set_particles(h, p.m, p.pos.T, p.vel.T, 0.0)
         e0.record(stream)
         nbody.nb_predict(h, 0.0)
-        nbody.nb_force_dev(h, 0, n, bufs[0:3].data_ptr(), bufs[3:6].data_ptr(), bufs[6].data_ptr())
+        nbody.nb_force_dev(h, d_idx.data_ptr() if d_idx is not None else 0, n_i,
+                           bufs[0:3].data_ptr(), bufs[3:6].data_ptr(), bufs[6].data_ptr())
         e1.record(stream)
         host = bufs.cpu()                                  # D2H of acc, jerk, pot
         w1 = time.perf_counter()
@@ -509,7 +530,12 @@ def run_ours(args):
                                                     "force_launches")}
         return d["interactions"], e0.elapsed_time(e1), w1 - w0, d["kernel_launches"], d, host
 
-    bufs = torch.empty((7, n), dtype=torch.float64, device="cuda") if wl["kind"] == "force" else None
+    n_i = min(args.n_i, n) if (args.n_i and wl["kind"] == "force") else n
+    d_idx = None
+    if n_i < n:
+        sub_idx = np.sort(np.random.default_rng(1500).choice(n, size=n_i, replace=False))
+        d_idx = torch.from_numpy(sub_idx.astype(np.int32)).cuda()
+    bufs = torch.empty((7, n_i), dtype=torch.float64, device="cuda") if wl["kind"] == "force" else None
     host_state = None
     for k in range(args.warmup):
         one_step(k, None)
@@ -625,23 +651,86 @@ def run_ours(args):
                 "h2d_bytes_per_step": (n * (15 if order == 4 else 21) * 8)
                 if wl["kind"] == "evolve" else n * 7 * 8,
                 "d2h_bytes_per_step": (n * (15 if order == 4 else 21) * 8)
-                if wl["kind"] == "evolve" else n * 7 * 8},
+                if wl["kind"] == "evolve" else n_i * 7 * 8},
         "gpu_launches": launches,
         "plans": ("autotuned (nb_autotune, %.1f s untimed set-up)" % t_tune) if plan_table
                  else "built-in heuristic",
         "interactions": tot_inter,
         "clocks": clocks,
     }
+    if n_i < n:
+        line["config"]["n_i"] = n_i
+        line["config"]["desc"] += " [force on a seeded %d-particle i-subset]" % n_i
     if world == 1 and not args.no_cpu_baseline:
         import oracle
-        inter, secs_c, desc = oracle_sample(wl, p)
+        keep = {}
+        inter, secs_c, desc = oracle_sample(wl, p, keep)
         line["cpu_baseline"] = {"value": inter / secs_c / 1e9, "unit": UNIT,
-                                "cores": oracle.num_threads(), "kind": "oracle", "sample": desc,
+                                "cores": oracle.num_threads(), "kind": "oracle", "build": oracle.CFLAGS, "sample": desc,
                                 "seconds": secs_c}
-    print(json.dumps(line), flush=True)
+        if wl["kind"] == "force" and n_i == n and "idx" in keep:
+            # the GPU's last evaluation against the oracle's values on the timed sample
+            g = np.asarray(host_state)[:, keep["idx"]]
+            line["cpu_baseline"]["gpu_error"] = force_errors(
+                g[0:3].T, g[3:6].T, g[6], keep["acc"], keep["jerk"], keep["pot"])
     sysm.close()
+    if (args.workload == "block65536" and world == 1 and not args.no_extras
+            and getattr(args, "capture", None) is None):
+        line.update(extras(args))
+    emit(args, line)
     dist.close()
     return 0
+
+
+def force_errors(acc, jerk, pot, ra, rj, rp):
+    """Error of GPU forces against the oracle's on the same particles: relative RMS over
+    the set and the per-particle max and median of |d_i| / |ref_i|, per quantity."""
+    out = {}
+    for name, got, ref in (("acc", acc, ra), ("jerk", jerk, rj), ("pot", pot, rp)):
+        got = np.asarray(got, dtype=np.float64)
+        ref = np.asarray(ref, dtype=np.float64)
+        d = got - ref
+        if ref.ndim == 1:
+            per = np.abs(d) / np.abs(ref)
+        else:
+            per = np.linalg.norm(d, axis=1) / np.linalg.norm(ref, axis=1)
+        out[name] = {"rel_rms": float(np.sqrt((d ** 2).sum() / (ref ** 2).sum())),
+                     "max": float(per.max()), "median": float(np.median(per))}
+    out["particles"] = int(np.asarray(rp).shape[0])
+    return out
+
+
+def extras(args):
+    """The two targets that the default line carries beside block65536: one full N = 2^20
+    evaluation (three timed repeats, its roofline and its error against the oracle on the
+    cpu_baseline sample) and the request loop on the config-5 stream at the saturating
+    rate (p50 / p99 latency and G/s against one request per launch; no rate sweep)."""
+    out = {}
+    sub = argparse.Namespace(**vars(args))
+    sub.workload, sub.steps, sub.warmup, sub.n, sub.n_i = "full2p20", 3, 1, None, None
+    sub.variant, sub.capture, sub.no_extras = None, [], True
+    run_ours(sub)
+    f = sub.capture[0]
+    out["full2p20"] = {k: f.get(k) for k in ("value", "unit", "steps", "warmup", "ms_per_step",
+                                             "fp32_peak_frac", "roofline", "e2e", "clocks",
+                                             "gpu_launches", "cpu_baseline", "config")}
+    sub = argparse.Namespace(**vars(args))
+    sub.workload, sub.steps, sub.warmup, sub.variant = "serve", 1, 1, None
+    sub.requests, sub.n_hi, sub.capture, sub.no_extras = None, None, [], True
+    sub.no_cpu_baseline, sub.serve_sweep = True, False
+    run_serve(sub, workload(sub), "f32ds", Dist(1, None), 0, 1,
+              int(os.environ.get("LOCAL_RANK", "0")))
+    v = sub.capture[0]
+    one = v["one_request_per_launch"]
+    out["serve"] = {"value": v["value"], "unit": v["unit"], "latency": v["latency"],
+                    "makespan_s": v["sweep"][-1]["server"]["makespan_s"],
+                    "one_request_per_launch": {"value": one["throughput"], "unit": UNIT,
+                                               "latency": one["latency"],
+                                               "makespan_s": one["makespan_s"]},
+                    "fp32_peak_frac": v["fp32_peak_frac"], "clocks": v["clocks"],
+                    "gpu_launches": v["gpu_launches"], "server_stats": v["server_stats"],
+                    "config": v["config"]}
+    return out
 
 
 def run_batch(args, wl, variant, dist, rank, world, local):
@@ -720,9 +809,9 @@ def run_batch(args, wl, variant, dist, rank, world, local):
         import oracle
         inter, secs_c, desc = oracle_sample(wl, None)
         line["cpu_baseline"] = {"value": inter / secs_c / 1e9, "unit": UNIT,
-                                "cores": oracle.num_threads(), "kind": "oracle", "sample": desc,
+                                "cores": oracle.num_threads(), "kind": "oracle", "build": oracle.CFLAGS, "sample": desc,
                                 "seconds": secs_c}
-    print(json.dumps(line), flush=True)
+    emit(args, line)
     bt.close()
     dist.close()
     return 0
@@ -800,10 +889,10 @@ def run_ext(args, wl, variant, dist, rank, world, local):
         oracle.force_ext(p.m, p.pos, p.vel, wl["eps"] ** 2, ipos[:, :ni].T, ivel[:, :ni].T)
         secs_c = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": ni * p.n / secs_c / 1e9, "unit": UNIT,
-                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "cores": oracle.num_threads(), "kind": "oracle", "build": oracle.CFLAGS,
                                 "sample": "oracle force_ext of the j-set on the first %d "
                                           "external particles" % ni, "seconds": secs_c}
-    print(json.dumps(line), flush=True)
+    emit(args, line)
     sysm.close()
     dist.close()
     return 0
@@ -872,7 +961,7 @@ def run_bridge(args, wl, variant, dist, rank, world, local):
         "gpu_launches": int(sa["kernel_launches"] + sb["kernel_launches"]),
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    emit(args, line)
     A.close()
     B.close()
     dist.close()
@@ -971,7 +1060,7 @@ def run_serve(args, wl, variant, dist, rank, world, local):
     # when all arrive at once (count / makespan of the timed streams)
     r_sat = len(base) / (sum(t["makespan_s"] for t in timed) / len(timed))
     sweep = []
-    for frac in wl["sweep_fracs"]:
+    for frac in (wl["sweep_fracs"] if getattr(args, "serve_sweep", True) else ()):
         rate = frac * r_sat
         reqs, res = run_stream(rate)
         sweep.append({"rate_hz": rate, "frac_of_saturation": frac,
@@ -1069,11 +1158,11 @@ def run_serve(args, wl, variant, dist, rank, world, local):
                 break
         secs_c = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": inter_c / secs_c / 1e9, "unit": UNIT,
-                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "cores": oracle.num_threads(), "kind": "oracle", "build": oracle.CFLAGS,
                                 "sample": "oracle force on the %d smallest force requests" % used,
                                 "seconds": secs_c}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        emit(args, line)
     srv.close()
     dist.close()
     return 0

@@ -504,12 +504,17 @@ int nb_selftest_wait(int which, double limit_s, int device);
  * The call returns after the results are in the output buffers.
  * It calls no cudaMalloc, cudaFree or other allocating routine: the partial
  * sums of its j-split live in a file-scope device array of
- * NB_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU which loads the
- * library holds until the process exits. The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture. All calls share
- * the one array, so calls that overlap on the GPU (other streams, other
- * threads) race: serialise them. Sizes: n_i <= NB_STATIC_MAX_NI, else
+ * NB_STATIC_SCRATCH_DOUBLES doubles (8 MiB). CUDA loads device code lazily, so
+ * that array and the kernels of this call take their device memory on their
+ * first use on a device, not when the library is loaded. The first call on a
+ * device (any n_i, with that device current) is therefore a warm-up: it looks
+ * up the array's device address (cudaGetSymbolAddress), loads the kernels and
+ * runs them once on an empty i-set, and synchronises the stream. Make it with
+ * n_i = 0 (acc, jerk, pot may be NULL then) before a pool allocator takes the
+ * device memory and before any stream capture; from then on the device holds
+ * the array until the process exits and no call allocates. All calls share
+ * the one array, its error word and its split counter, so calls that overlap
+ * on the GPU (other streams, other threads) race: serialise them. Sizes: n_i <= NB_STATIC_MAX_NI, else
  * NB_ERR_ARG; an index outside [0, n_j) gives NB_ERR_ARG, a non-finite result
  * NB_ERR_NONFINITE, a CUDA failure NB_ERR_CUDA. */
 #define NB_STATIC_MAX_NI 1024

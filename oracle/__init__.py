@@ -45,11 +45,16 @@ _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 
 
+# gcc flags of the oracle: binary64 as written (no FMA contraction, no fast-math, no
+# reassociation), so the x86 build host and the Arm GPU host compute the same bits; no
+# -march=native for the same reason.
+CFLAGS = "-O3 -std=c11 -fopenmp -ffp-contract=off -fno-fast-math"
+
+
 def compile_source(src: str, out: str) -> str:
-    """gcc flags of the oracle: binary64 as written (no FMA contraction, no fast-math)."""
+    """Compile an oracle source with CFLAGS into a shared library."""
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, src, "-lm"]
+    cmd = (["gcc"] + CFLAGS.split() + ["-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"])
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

@@ -1611,6 +1611,24 @@ static cudaError_t dispatch32(const ForcePlan &p, const JSet &js, const ISet &is
     }
 }
 
+cudaError_t warm_force_jmode64(cudaStream_t st)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, k_force_jmode64<1, 128>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, k_force_jmode64<2, 128>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, k_force_jmode64<4, 128>)) != cudaSuccess)
+        return e;
+    // an empty i-set: the i-loop does not run and one CTA writes nothing
+    const JSet js{};
+    ISet is{};
+    is.member = true;
+    k_force_jmode64<1, 128><<<1, 128, 0, st>>>(js, is, 0.0, nullptr, 0, nullptr, Out3{}, nullptr);
+    k_force_jmode64<2, 128><<<1, 128, 0, st>>>(js, is, 0.0, nullptr, 0, nullptr, Out3{}, nullptr);
+    k_force_jmode64<4, 128><<<1, 128, 0, st>>>(js, is, 0.0, nullptr, 0, nullptr, Out3{}, nullptr);
+    return cudaGetLastError();
+}
+
 static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is, double eps2,
                               double *part, unsigned *cnt, Out3 out, unsigned *err,
                               cudaStream_t st)

@@ -99,6 +99,11 @@ cudaError_t launch_force(int variant, const ForcePlan &plan, const JSet &js, con
                          double eps2, double *part, unsigned *counters, Out3 out, unsigned *err,
                          cudaStream_t st, cudaEvent_t *ev);
 
+// Load the FP64 j-parallel force kernels (every i-per-thread variant) on the
+// current device and run each once on an empty i-set, so that a later launch
+// takes no lazy module load (a device allocation).
+cudaError_t warm_force_jmode64(cudaStream_t st);
+
 // ---- batched systems -------------------------------------------------------
 
 // One work item of a batched evaluation: i-rows [i0, i0 + ni) of irec against

@@ -8,11 +8,16 @@
 // buffers for inputs and outputs; the only scratch this call needs, the
 // partial sums of its j-split, lives in the fixed array below.
 //
-// The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (8 MiB) until the process exits. Host code cannot use the
-// symbol itself as a device address, so on the first call on each device the
-// call looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it.
+// The array is a file-scope __device__ variable (8 MiB). CUDA loads a
+// library's device code lazily, so the array, and the force kernels this call
+// launches, take their device memory when they are first used on a device,
+// not when the library is loaded; from then on the device holds them until the
+// process exits. Host code cannot use the symbol itself as a device address,
+// so the first call on each device (with that device current) looks the
+// address up with cudaGetSymbolAddress, caches it, and loads and runs the
+// kernels once on an empty i-set. That first call is the per-device warm-up:
+// a caller whose pool allocator will own the device memory makes it, with
+// n_i = 0, before the pool takes the memory, and no later call allocates.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -41,8 +46,9 @@ struct StaticSlot {
 StaticSlot g_slots[kMaxDevices];
 std::mutex g_slots_mu;
 
-// Per-device set-up: the device addresses of the two static arrays.
-int static_slot(int dev, StaticSlot *out)
+// Per-device set-up: the device addresses of the static arrays (which loads
+// this file's device code), then the force kernels loaded and run once.
+int static_slot(int dev, cudaStream_t st, StaticSlot *out)
 {
     std::lock_guard<std::mutex> lk(g_slots_mu);
     StaticSlot &s = g_slots[dev];
@@ -68,6 +74,12 @@ int static_slot(int dev, StaticSlot *out)
             cudaGetLastError();
             return NB_ERR_CUDA;
         }
+        if (nb::warm_force_jmode64(st) != cudaSuccess ||
+            cudaMemsetAsync(s.err, 0, sizeof(unsigned), st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return NB_ERR_CUDA;
+        }
         s.ready = true;
     }
     *out = s;
@@ -84,16 +96,16 @@ extern "C" int nb_force_static(int n_j, const double *m, const double *pos, cons
     if (n_i < 0 || n_i > NB_STATIC_MAX_NI) return NB_ERR_ARG;
     if (!idx && n_i > n_j) return NB_ERR_ARG;
     if (!(eps >= 0.0) || eps != eps) return NB_ERR_ARG;
-    if (n_i == 0) return NB_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return NB_ERR_CUDA;
     }
-    StaticSlot slot;
-    int rc = static_slot(dev, &slot);
-    if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    StaticSlot slot;
+    int rc = static_slot(dev, st, &slot);  // the warm-up, on the first call on this device
+    if (rc) return rc;
+    if (n_i == 0) return NB_OK;
 
     nb::JSet js{};
     js.n = n_j;

@@ -74,3 +74,38 @@ def test_batch_errors(nb):
     with pytest.raises(nb.NBodyError) as e:
         nb.nb_batch_create(cfg, [10], [0.1], 0.0)
     assert e.value.status == nb.NB_ERR_ARG
+
+
+@pytest.mark.slow
+def test_full_size_batch4096_sampled_clusters(nb):
+    """Config 4 at its own size: the 4096 clusters of the bench (N log-uniform in
+    [16, 4096], seeded as the bench seeds them, about 3e6 particles), CTA size chosen by
+    the autotuner, four graph-replayed shared steps of dt = 1/512. Ten clusters across the
+    size range, the largest and the smallest among them, against the oracle run cluster by
+    cluster: positions and velocities per particle, and the energy."""
+    systems = ic.cluster_batch(4096, 16, 4096)
+    sizes = np.array([len(p.m) for p in systems])
+    eps = ic.cluster_eps(sizes)
+    dt, nsteps = 1.0 / 512, 4
+    with nb.Batch(systems, eps, dt, variant="f32ds", device=0) as b:
+        assert b.autotune() in (64, 128, 256)
+        st = b.step(nsteps)
+        pos, vel, t = b.get()
+        k, w = b.energy()
+    assert t == nsteps * dt and st["block_steps"] == nsteps
+    order = np.argsort(sizes, kind="stable")
+    picks = sorted(set(order[np.linspace(0, len(order) - 1, 9).round().astype(int)].tolist())
+                   | {int(order[-2])})
+    assert sizes[picks].max() == sizes.max() and sizes[picks].min() == sizes.min()
+    for s in picks:
+        p = systems[s]
+        o = oracle.State(p.m, p.pos, p.vel)
+        oracle.hermite_run(o, np.inf, eps[s] ** 2, dt_shared=dt, max_steps=nsteps)
+        gp, gv = b.system(s, pos).T, b.system(s, vel).T
+        scale = np.abs(p.pos).max()
+        dpos = np.linalg.norm(gp - o.pos, axis=1).max() / scale
+        dvel = np.linalg.norm(gv - o.vel, axis=1).max() / np.abs(p.vel).max()
+        print("cluster %d N=%d: max |dx|/scale %.2e, max |dv|/scale %.2e" % (s, sizes[s], dpos, dvel))
+        assert dpos < 1e-7 and dvel < 1e-6, (s, sizes[s], dpos, dvel)
+        ko, wo = oracle.energy(p.m, o.pos, o.vel, eps[s] ** 2)
+        assert abs(k[s] - ko) < 1e-6 * abs(ko) and abs(w[s] - wo) < 1e-6 * abs(wo), s

@@ -239,3 +239,38 @@ def test_full_size_block65536_sampled(nb):
     rel = lambda x, y: np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum())
     assert rel(acc.T, ra) < 1e-6 and rel(jerk.T, rj) < 1e-5 and rel(pot, rp) < 1e-6
     assert abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0) < 1e-6
+
+
+@pytest.mark.slow
+def test_full_size_block65536_first_64_block_steps_vs_oracle(nb):
+    """Config 2 at full size: the bench's system (Plummer N = 65536, eps = 1e-3, eta = 0.01,
+    dt_max = 1/16, F32-DS with autotuned plans and the fused small-step kernel) from t = 0
+    through the block time the oracle reaches after its initial evaluation and first 64
+    block steps (the run the bench's CPU baseline times). The GPU takes the same number of
+    block steps (within 2), gives at least 99% of the particles the same time and step,
+    and the particles at the same time agree in position to 1e-5 (the force's FP32 rounding
+    grows through the corrector) and in velocity to 1e-4."""
+    import math
+    p = ic.plummer(65536, ic.MASTER_SEED)
+    eps = 1e-3
+    st = oracle.State(p.m, p.pos, p.vel)
+    o_steps, o_inter = oracle.hermite_run(st, math.inf, eps * eps, eta=0.01, dt_max=1.0 / 16,
+                                          max_steps=64)
+    assert o_steps == 64
+    t64 = float(st.t.max())
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.01, dt_max=1.0 / 16,
+                   device=0) as s:
+        nb.nb_autotune(s.h, 3)
+        stats = s.step(t64)
+        g = s.state()
+    print("block steps GPU %d oracle %d; interactions GPU %.4g oracle %.4g"
+          % (stats["block_steps"], o_steps, stats["interactions"], o_inter))
+    assert abs(stats["block_steps"] - o_steps) <= 2
+    assert stats["interactions"] == pytest.approx(o_inter, rel=0.02)
+    same = (g["t"] == st.t) & (g["dt"] == st.dt)
+    assert same.mean() > 0.99, same.mean()
+    dx = np.linalg.norm(g["pos"].T[same] - st.pos[same], axis=1).max()
+    dv = np.linalg.norm(g["vel"].T[same] - st.vel[same], axis=1).max()
+    print("same time and step: %d of %d; max |dx| %.2e, max |dv| %.2e"
+          % (same.sum(), same.size, dx, dv))
+    assert dx < 1e-5 and dv < 1e-4
