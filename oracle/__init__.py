@@ -16,7 +16,7 @@ Every routine follows a passage of the paper (Portegies Zwart & Bedorf,
   4th-order Hermite predictor-corrector with individual block steps
   (Sect. II, III, VI);
 - ``hermite_run``: the block-step (or shared-step) integration loop;
-- ``force6``, ``predict6``, ``correct6_one``, ``hermite6_run``: the
+- ``force6``, ``predict6``, ``correct6_one``, ``aarseth6_dt``, ``hermite6_run``: the
   6th-order Hermite scheme (acc, jerk and snap per pair; Sect. II, the >= 4th-order
   integrators with individual steps that direct codes use);
 - ``kick``, ``bridge_run``: the 2nd-order kick-drift-kick coupling of two
@@ -117,9 +117,13 @@ def _bind(lib):
     lib.orc_predict6.argtypes = [ctypes.c_int, ctypes.c_double] + [_D] * 10
     lib.orc_correct6_one.argtypes = [ctypes.c_double] + [_D] * 13
     lib.orc_hermite6_run.argtypes = ([ctypes.c_int] + [_D] * 9
-                                     + [ctypes.c_double] * 8
+                                     + [ctypes.c_double] * 7
+                                     + [ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong,
+                                        ctypes.c_double]
                                      + [ctypes.c_long, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_long), _D])
+    lib.orc_aarseth6_dt.argtypes = [_D] * 6 + [ctypes.c_double]
+    lib.orc_aarseth6_dt.restype = ctypes.c_double
     lib.orc_hermite6_run.restype = ctypes.c_int
     lib.orc_num_threads.restype = ctypes.c_int
     return lib
@@ -340,11 +344,26 @@ class State6(State):
         self.crackle = np.zeros((n, 3)) if crackle is None else _f64(crackle, (n, 3)).copy()
 
 
+CRITERIA6 = {"aarseth": 0, "generalised": 1}
+
+
+def aarseth6_dt(a, a1, a2, a3, a4, a5, eta):
+    """The published order-6 step criterion (Aarseth's form generalised to a .. a5)."""
+    lib = _load()
+    return float(lib.orc_aarseth6_dt(*[_p(_f64(v, (3,))) for v in (a, a1, a2, a3, a4, a5)],
+                                     float(eta)))
+
+
 def hermite6_run(state: State6, t_end, eps2, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30,
-                 dt_max=1.0 / 16, dt_shared=0.0, max_steps=0, noise=0.0):
+                 dt_max=1.0 / 16, dt_shared=0.0, max_steps=0, noise=0.0, criterion="aarseth",
+                 perturb=0.0, seed=0):
     """Advance ``state`` in place with the 6th-order Hermite scheme and block (or shared)
     steps to t_end; ``noise``: the forces' relative rounding noise, which sets the floor
     under the crackle in the step criterion (0: exact forces, no floor).
+    ``criterion``: "aarseth" (Aarseth's form on a, jerk, snap, crackle; the default) or
+    "generalised" (the published order-6 criterion on a .. a5; ``noise`` unused).
+    ``perturb`` > 0: seeded relative noise of that size on every evaluated a, jerk and snap
+    of the block steps (a model of reduced-precision forces for the criterion study).
     Returns (n_block_steps, n_interactions)."""
     lib = _load()
     steps = ctypes.c_long(0)
@@ -354,7 +373,8 @@ def hermite6_run(state: State6, t_end, eps2, eta=0.02, eta_s=0.01, dt_min=2.0 **
                               _p(state.acc), _p(state.jerk), _p(state.snap),
                               _p(state.crackle), _p(state.t), _p(state.dt), float(eps2),
                               float(eta), float(eta_s), float(dt_min), float(dt_max),
-                              float(dt_shared), float(noise), float(t_end), int(max_steps), init,
+                              float(dt_shared), float(noise), CRITERIA6[criterion],
+                              float(perturb), int(seed), float(t_end), int(max_steps), init,
                               ctypes.byref(steps), ctypes.byref(inter))
     if rc != 0:
         raise MemoryError("oracle scratch allocation failed")

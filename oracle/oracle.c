@@ -638,11 +638,13 @@ void orc_predict6(int n, double t, const double *tj, const double *pos,
  *   c3 = (15 (T Jp - Am) - 3 T^2 Sm) / (2 T^3)
  *   c4 = 3 (T Sp - Jm) / T^3
  * and at t1 = mid + T: a3 = c3 + c4 T + c5 T^2/2, a4 = c4 + c5 T, a5 = c5.
- * The k-th derivative carries the force's rounding error divided by T^k; the
- * step criterion of the block steps takes a, jerk, snap (evaluated) and the
+ * The k-th derivative carries the force's rounding error divided by T^k. The
+ * block steps' default criterion takes a, jerk, snap (evaluated) and the
  * crackle a3 only (Aarseth's form, orc_aarseth_dt with a2 = snap, a3 =
- * crackle): with FP32 pair arithmetic (rounding ~1e-7 of |a|), a criterion on
- * a4 and a5 sees mostly noise at small T and drives the steps down to dt_min.
+ * crackle); the published order-6 criterion on a3, a4 and a5
+ * (orc_aarseth6_dt) is the alternative. With forces rounded at ~1e-7 of |a|
+ * (FP32 pair arithmetic), a4 and a5 are mostly noise at small T and that
+ * criterion drives the steps down to dt_min (shown with perturb_forces).
  */
 void orc_correct6_one(double dt, const double x0[3], const double v0[3],
                       const double a0[3], const double j0[3],
@@ -666,6 +668,68 @@ void orc_correct6_one(double dt, const double x0[3], const double v0[3],
         a3_end[c] = c3 + c4 * T + c5 * T * T / 2.0;
         a4_end[c] = c4 + c5 * T;
         a5_end[c] = c5;
+    }
+}
+
+/*
+ * The step criterion that Nitadori & Makino publish for their order-p Hermite
+ * schemes (Aarseth's form generalised to higher derivatives), for p = 6:
+ *   dt = eta ( (sqrt(|a| |a2|) + |a1|) / (sqrt(|a3| |a5|) + |a4|) )^(1/3),
+ * with a1 = jerk, a2 = snap and a3, a4, a5 the end-of-step crackle, pop and
+ * 5th derivative from the corrector (orc_correct6_one). A zero denominator
+ * gives +inf (dt_max after quantization).
+ */
+double orc_aarseth6_dt(const double a[3], const double a1[3],
+                       const double a2[3], const double a3[3],
+                       const double a4[3], const double a5[3], double eta)
+{
+    double num = sqrt(norm3(a) * norm3(a2)) + norm3(a1);
+    double den = sqrt(norm3(a3) * norm3(a5)) + norm3(a4);
+    if (den == 0.0)
+        return INFINITY;
+    return eta * cbrt(num / den);
+}
+
+/* Step criteria of the 6th-order block steps (orc_hermite6_run's crit). */
+enum { ORC_CRIT_AARSETH_CRACKLE = 0, ORC_CRIT_GENERALISED = 1 };
+
+/*
+ * Force noise for the criterion study (orc_hermite6_run's perturb): a value
+ * uniform in [-1, 1) that is a pure function of (seed, step, particle, slot),
+ * from SplitMix64's output function (Steele, Lea & Flood 2014) applied to the
+ * chained keys. It models the rounding of reduced-precision forces; the
+ * oracle's own forces are exact to ~1e-16 and take no noise unless asked.
+ */
+static unsigned long long splitmix64(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double noise_unit(unsigned long long seed, long step, int i, int slot)
+{
+    unsigned long long h = splitmix64(seed);
+    h = splitmix64(h ^ (unsigned long long)step);
+    h = splitmix64(h ^ (((unsigned long long)(unsigned)i << 4) | (unsigned)slot));
+    return (double)(h >> 11) * 0x1.0p-52 - 1.0;
+}
+
+/* a, jerk, snap of the na active particles each change by perturb times their
+ * own magnitude times noise_unit, per component. */
+static void perturb_forces(int na, const int *active, long step,
+                           unsigned long long seed, double perturb, double *a1,
+                           double *j1, double *s1)
+{
+    for (int k = 0; k < na; k++) {
+        size_t r = 3 * (size_t)k;
+        double na1 = norm3(a1 + r), nj1 = norm3(j1 + r), ns1 = norm3(s1 + r);
+        for (int c = 0; c < 3; c++) {
+            a1[r + c] += perturb * na1 * noise_unit(seed, step, active[k], c);
+            j1[r + c] += perturb * nj1 * noise_unit(seed, step, active[k], 3 + c);
+            s1[r + c] += perturb * ns1 * noise_unit(seed, step, active[k], 6 + c);
+        }
     }
 }
 
@@ -709,14 +773,18 @@ static void initialise6(orc_state6 *s, double eta_s, double dt_min,
  *   3. evaluate acc, jerk, snap of the active particles from the predicted
  *      positions, velocities and accelerations;
  *   4. correct them (orc_correct6_one) and give each a new step from the
- *      end-of-step a, jerk, snap and crackle (orc_aarseth_dt, quantized), or
+ *      end-of-step a, jerk, snap and crackle (orc_aarseth_dt, quantized; or
+ *      with crit = ORC_CRIT_GENERALISED from a .. a5, orc_aarseth6_dt), or
  *      dt_shared.
+ * perturb > 0: the evaluated a, jerk, snap first take seeded relative noise.
  * Scratch: pp, vp, ap (n,3); a1, j1, s1 (n,3) and p1 (n) for the active set.
  */
-static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
-                       double dt_max, double dt_shared, int *active, double *pp,
-                       double *vp, double *ap, double *a1, double *j1, double *s1,
-                       double *p1, double *t_out)
+static int block_step6(orc_state6 *s, double eta, double noise, int crit,
+                       double perturb, unsigned long long seed, long step,
+                       double dt_min, double dt_max, double dt_shared,
+                       int *active, double *pp, double *vp, double *ap,
+                       double *a1, double *j1, double *s1, double *p1,
+                       double *t_out)
 {
     int n = s->n;
     double t_next = INFINITY;
@@ -732,6 +800,8 @@ static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
     orc_predict6(n, t_next, s->t, s->pos, s->vel, s->acc, s->jerk, s->snap,
                  s->crk, pp, vp, ap);
     orc_force6_idx(n, s->m, pp, vp, ap, s->eps2, na, active, a1, j1, s1, p1);
+    if (perturb > 0.0)
+        perturb_forces(na, active, step, seed, perturb, a1, j1, s1);
     for (int k = 0; k < na; k++) {
         int i = active[k];
         size_t q = 3 * (size_t)i, r = 3 * (size_t)k;
@@ -742,6 +812,9 @@ static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
         double dt_new;
         if (dt_shared > 0.0) {
             dt_new = dt_shared;
+        } else if (crit == ORC_CRIT_GENERALISED) {
+            double raw = orc_aarseth6_dt(a1 + r, j1 + r, s1 + r, a3, a4, a5, eta);
+            dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
         } else {
             /* Aarseth's criterion with the evaluated snap as a2 and the
              * interpolated crackle as a3 (the 5th and 4th derivatives stay
@@ -759,8 +832,6 @@ static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
             double raw = orc_aarseth_dt(a1 + r, j1 + r, s1 + r, ce, eta);
             dt_new = orc_quantize(raw, dt, t_next, dt_min, dt_max);
         }
-        (void)a4;
-        (void)a5;
         for (int c = 0; c < 3; c++) {
             s->pos[q + c] = xn[c];
             s->vel[q + c] = vn[c];
@@ -785,6 +856,12 @@ static int block_step6(orc_state6 *s, double eta, double noise, double dt_min,
  * given derivatives, times and steps are used (a resumed run).
  * noise >= 0 is the relative rounding noise of the forces for the crackle's
  * floor in the step criterion (block_step6); 0 for exact forces.
+ * crit: ORC_CRIT_AARSETH_CRACKLE (Aarseth's form on a, jerk, snap and the
+ * crackle above its floor; the default) or ORC_CRIT_GENERALISED (the
+ * published order-6 criterion, orc_aarseth6_dt; noise is not used).
+ * perturb > 0 adds seeded relative noise of that size to every evaluated
+ * a, jerk and snap of the block steps (perturb_forces; for the study of the
+ * criteria under reduced-precision forces), 0 leaves the forces exact.
  * Counters as orc_hermite_run (the initial evaluation counts twice: it takes
  * two passes). Returns 0, or -1 if a scratch allocation failed.
  */
@@ -792,7 +869,8 @@ int orc_hermite6_run(int n, const double *m, double *pos, double *vel,
                      double *acc, double *jerk, double *snap, double *crackle,
                      double *t, double *dt, double eps2, double eta,
                      double eta_s, double dt_min, double dt_max,
-                     double dt_shared, double noise, double t_end, long max_steps,
+                     double dt_shared, double noise, int crit, double perturb,
+                     unsigned long long seed, double t_end, long max_steps,
                      int init, long *n_block_steps, double *n_interactions)
 {
     orc_state6 s = {n, eps2, (double *)m, pos, vel, acc, jerk, snap, crackle, t, dt};
@@ -820,8 +898,9 @@ int orc_hermite6_run(int n, const double *m, double *pos, double *vel,
         if (!(t_next <= t_end)) /* also ends a run whose times became NaN */
             break;
         double tn;
-        int na = block_step6(&s, eta, noise, dt_min, dt_max, dt_shared, active, pp,
-                             vp, ap, a1, j1, s1, p1, &tn);
+        int na = block_step6(&s, eta, noise, crit, perturb, seed, steps, dt_min,
+                             dt_max, dt_shared, active, pp, vp, ap, a1, j1, s1,
+                             p1, &tn);
         inter += (double)na * (double)n;
         steps++;
     }

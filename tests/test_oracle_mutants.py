@@ -3,7 +3,8 @@
 Each case copies ``oracle/oracle.c``, plants one plausible slip (a wrong factor,
 sign, power, operand order, dropped term), compiles the copy on the CPU, points
 the oracle wrapper at it and runs the pin tests of ``test_oracle_force.py``,
-``test_oracle_hermite.py`` and ``test_oracle_hermite6.py``; at least one pin must fail
+``test_oracle_hermite.py``, ``test_oracle_hermite6.py`` and ``test_oracle_criteria.py``;
+at least one pin must fail
 for every mutant. The
 unmodified source must pass them all.
 """
@@ -15,6 +16,7 @@ import oracle
 
 from . import test_oracle_force as F
 from . import test_oracle_hermite as H
+from . import test_oracle_criteria as C
 from . import test_oracle_hermite6 as H6
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
@@ -71,6 +73,15 @@ MUTANTS = [
     ("scheduler6 takes a particle early", "if (due == t_next)", "if (due <= t_next + s->dt[i] / 2)"),
     ("initial snap without accelerations", "memcpy(aj, s->acc, sizeof(double) * 3 * (size_t)n);",
      "(void)0;"),
+    ("generalised criterion: square root for the cube root", "return eta * cbrt(num / den);",
+     "return eta * sqrt(num / den);"),
+    ("generalised criterion: pop and 5th derivative swapped",
+     "double den = sqrt(norm3(a3) * norm3(a5)) + norm3(a4);",
+     "double den = sqrt(norm3(a3) * norm3(a4)) + norm3(a5);"),
+    ("generalised criterion never selected", "} else if (crit == ORC_CRIT_GENERALISED) {",
+     "} else if (crit == -1) {"),
+    ("force noise on the acceleration dropped",
+     "a1[r + c] += perturb * na1 * noise_unit(seed, step, active[k], c);", "(void)na1;"),
 ]
 
 
@@ -104,6 +115,7 @@ def _pins():
         ("pec_block", H.test_iterated_corrector_block_steps_energy),
     ]
     out += [("h6_" + k[5:], getattr(H6, k)) for k in sorted(dir(H6)) if k.startswith("test_")]
+    out += [("crit_" + k[5:], getattr(C, k)) for k in sorted(dir(C)) if k.startswith("test_")]
     return out
 
 
