@@ -287,10 +287,10 @@ def stage_bandwidth(wl, n, fused_steps, fused_stage_ms, other_ms, planned_inter,
         g = PREDICT_BYTES * n * fused_steps / (fused_stage_ms[0] / 1e3) / 1e9
         out["fused_predict_stage_gbs"] = g
         out["fused_predict_stage_us_per_step"] = 1e3 * fused_stage_ms[0] / fused_steps
-    if fused_steps and fused_stage_ms[2] > 0:
+    if fused_steps and fused_stage_ms[1] > 0:
         # the j-records every fused step's force stage reads (48 B per particle, from L2)
-        out["fused_force_stage_record_gbs"] = 48.0 * n * fused_steps / (fused_stage_ms[2] / 1e3) / 1e9
-        out["fused_force_stage_us_per_step"] = 1e3 * fused_stage_ms[2] / fused_steps
+        out["fused_force_stage_record_gbs"] = 48.0 * n * fused_steps / (fused_stage_ms[1] / 1e3) / 1e9
+        out["fused_force_stage_us_per_step"] = 1e3 * fused_stage_ms[1] / fused_steps
     if other_ms.get("correct_ms"):
         g = CORRECT_BYTES * (planned_inter / n) / (other_ms["correct_ms"] / 1e3) / 1e9
         out["planned_correct_gbs"] = g
@@ -643,8 +643,8 @@ def run_ours(args):
                     "rel_drift": abs(energy1 - energy0) / abs(energy0),
                     "over_time_units": args.steps * wl["step_t"]}
                    if energy0 is not None else None),
-        "fused_stage_ms": {"predict_flags": fused_stage_ms[0], "gather": fused_stage_ms[1],
-                           "force": fused_stage_ms[2], "reduce_correct": fused_stage_ms[3]},
+        "fused_stage_ms": {"predict": fused_stage_ms[0], "force": fused_stage_ms[1],
+                           "reduce_correct": fused_stage_ms[2], "step_barrier": fused_stage_ms[3]},
         "by_log2_active": {k: [round(x, 3) if isinstance(x, float) else x for x in v]
                            for k, v in hist.items()},
         "e2e": {"value": e2e_units / e2e_secs / 1e9, "unit": UNIT,

@@ -129,7 +129,8 @@ typedef struct nb_stats {
     long long fused_steps;      /* block steps taken inside the fused kernel */
     long long fused_launches;   /* fused-kernel launches */
     double fused_ms;            /* fused-kernel time (NB_FLAG_TIMING) */
-    double fused_stage_ms[4];   /* fused kernel: predict + flags, gather, force, reduce + correct */
+    double fused_stage_ms[4];   /* fused kernel: predict, force (small due sets: with their
+                                 * reduction and corrector), reduce + correct, step barrier */
     double fused_step_ms_hist[32]; /* fused kernel: step time by floor(log2(N_active)) */
 } nb_stats;
 

@@ -319,6 +319,8 @@ int check_err(nb_handle h)
         return fail(h, NB_ERR_ARG, "prediction time is before some particle's own time");
     if (e & DERR_UNSYNC)
         return fail(h, NB_ERR_STATE, "the particles are not synchronised at the system time");
+    if (e & DERR_SCHED)
+        return fail(h, NB_ERR_STATE, "the due set disagrees with the step-level histogram");
     return fail(h, NB_ERR_NONFINITE,
                 "non-finite force or state (coincident particles with eps = 0?)");
 }
@@ -752,10 +754,11 @@ bool fused_ready(nb_handle h)
     if ((h->n + g - 1) / g > FUSED_MAX_WORDS * 32) return false;
     if (!h->fused_cnt) {
         const size_t part = fused_part_float2s(g, NB_FUSED_MAX_NA);
-        const size_t add = part * sizeof(float2) + g * sizeof(int) + 256 + sizeof(FusedStats);
+        const size_t add =
+            part * sizeof(float2) + fused_cnt_ints(g) * sizeof(int) + 256 + sizeof(FusedStats);
         if (h->cfg.budget_bytes && h->bytes + add > h->cfg.budget_bytes) return false;
         if (cudaMalloc(&h->fused_part, part * sizeof(float2)) != cudaSuccess ||
-            cudaMalloc(&h->fused_cnt, g * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&h->fused_cnt, fused_cnt_ints(g) * sizeof(int)) != cudaSuccess ||
             cudaMalloc(&h->fused_bar, 256) != cudaSuccess ||
             cudaMalloc(&h->fused_stats, sizeof(FusedStats)) != cudaSuccess ||
             cudaMemset(h->fused_stats, 0, sizeof(FusedStats)) != cudaSuccess) {

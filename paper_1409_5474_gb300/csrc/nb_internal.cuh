@@ -16,6 +16,7 @@ enum : unsigned {
     DERR_BACKWARD = 4u,   // prediction to a time before a particle's own time
     DERR_BADINDEX = 8u,   // an i-set index outside [0, n_j) (replaced by 0)
     DERR_UNSYNC = 16u,    // a particle's own time differs from the system time
+    DERR_SCHED = 32u,     // the due set disagrees with the step-level histogram
 };
 
 // Double-single j-record, 48 bytes per particle (see DS_REC):
@@ -346,7 +347,10 @@ struct FusedStats {
     unsigned long long steps;
     double interactions;
     unsigned long long active_hist[32];
-    unsigned long long phase_ns[4];     // CTA 0's time in stages A, B, C, D (globaltimer)
+    unsigned long long phase_ns[4];     // CTA 0's time (globaltimer) in: prediction (and the
+                                        // hand-off's gather), force (small due sets: with
+                                        // their reduction and corrector), reduction +
+                                        // corrector, the end-of-step barrier
     unsigned long long step_ns_hist[32];  // step time by floor(log2 N_active)
 };
 
@@ -371,7 +375,8 @@ struct FusedArgs {
     int na_max;
     double t_end;
     float2 *part;
-    int *cnt;
+    int *cnt;      // fused_cnt_ints(grid): per-CTA due counts, then the two due-set
+                   // counters and the tickets of the small-set groups (zeroed at launch)
     unsigned *bar;
     unsigned *err;
     unsigned long long *dtmin_hits;
@@ -380,6 +385,13 @@ struct FusedArgs {
 
 constexpr int FUSED_THREADS = 256;
 constexpr int FUSED_MAX_WORDS = 256;  // due-flag words per CTA: n <= 8192 x grid
+// Due sets of up to FUSED_SMALL_NA particles take the small-set path of the
+// fused kernel (groups of four due particles, a ticket per group).
+constexpr int FUSED_SMALL_NA = 16;
+
+// Ints of the fused kernel's counter array: grid per-CTA counts, 2 due-set
+// counters, FUSED_SMALL_NA / 4 tickets (padded).
+inline size_t fused_cnt_ints(int grid) { return (size_t)grid + 64; }
 
 // CTAs of the fused launch on this device (one per SM); 0 if the kernel cannot
 // be launched cooperatively.

@@ -369,6 +369,286 @@ __device__ __forceinline__ void chunking(int na, int n, int grid, int total_warp
     nchunk = (n + jc - 1) / jc;
 }
 
+// ---- small due sets: groups of four due slots, a ticket per group ----------
+
+// An item of a small due set is one group of four due slots (slots 4g ..
+// 4g + 3; idle slots copy the last due one) against one j-chunk; the CTA's
+// eight warps split the chunk, every lane loads up to SMALL_JPL j-records at
+// once before any arithmetic (one L2 round trip per batch), FP32 sums of a
+// batch are folded into double-single totals, which meet in a fixed xor tree
+// per warp and a fixed-order sum over the warps: one double-single partial
+// per (group, chunk) and output q = 7 p + component. The CTA that completes a
+// group's last chunk (its ticket) sums the group's partials in a fixed order
+// and corrects the group's particles, so no grid barrier separates the force
+// from the corrector.
+constexpr int SMALL_JPL = 4;
+constexpr int SMALL_CHUNK_MAX_J = 2 * SMALL_JPL * 32 * (FUSED_THREADS / 32);  // 2048
+constexpr int SMALL_Q = 28;  // outputs of a group: 4 slots x 7 components
+
+// The j-chunks of a small due set (a function of (na, n, grid) only): about one
+// item per CTA, at most two batches per lane, at least 32 j per chunk.
+__device__ __forceinline__ void small_chunking(int na, int n, int grid, int &nchunk, int &jc)
+{
+    const int ng = (na + 3) / 4;
+    int nc = max((grid + ng - 1) / ng, (n + SMALL_CHUNK_MAX_J - 1) / SMALL_CHUNK_MAX_J);
+    nc = max(1, min(nc, (n + 31) / 32));
+    jc = (n + nc - 1) / nc;
+    jc = (jc + 31) & ~31;
+    nchunk = (n + jc - 1) / jc;
+}
+
+// Output q of slot k (component c = q % 7; c == 6 is the positive potential sum).
+__device__ __forceinline__ void store_out(const Out3 &f, int k, int c, double v, unsigned *err)
+{
+    if (c < 3)
+        f.acc[c * f.ld + k] = v;
+    else if (c < 6)
+        f.jerk[(c - 3) * f.ld + k] = v;
+    else
+        f.pot[k] = v = -v;
+    if (!isfinite(v)) atomicOr(err, DERR_NONFINITE);
+}
+
+// The group's sums (in chunk order within each of 8 interleaved subsets, then
+// the subsets in order) and the corrector of its due particles.
+__device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, int nchunk,
+                                             double tn, float *s_fin)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    __threadfence();
+    if (tid < 8 * SMALL_Q) {
+        const int q = tid % SMALL_Q, sub = tid / SMALL_Q;
+        const float2 *base = a.part + (size_t)g * nchunk * SMALL_Q + q;
+        dsf acc{0.f, 0.f};
+        int c = sub;
+        for (; c + 24 < nchunk; c += 32) {
+            const float2 x0 = __ldcg(base + (size_t)c * SMALL_Q);
+            const float2 x1 = __ldcg(base + (size_t)(c + 8) * SMALL_Q);
+            const float2 x2 = __ldcg(base + (size_t)(c + 16) * SMALL_Q);
+            const float2 x3 = __ldcg(base + (size_t)(c + 24) * SMALL_Q);
+            ds_acc(acc, dsf{x0.x, x0.y});
+            ds_acc(acc, dsf{x1.x, x1.y});
+            ds_acc(acc, dsf{x2.x, x2.y});
+            ds_acc(acc, dsf{x3.x, x3.y});
+        }
+        for (; c < nchunk; c += 8) {
+            const float2 x = __ldcg(base + (size_t)c * SMALL_Q);
+            ds_acc(acc, dsf{x.x, x.y});
+        }
+        s_fin[2 * tid] = acc.hi;
+        s_fin[2 * tid + 1] = acc.lo;
+    }
+    __syncthreads();
+    if (tid < SMALL_Q) {
+        dsf v{s_fin[2 * tid], s_fin[2 * tid + 1]};
+#pragma unroll
+        for (int sub = 1; sub < 8; ++sub) {
+            const int r = sub * SMALL_Q + tid;
+            ds_acc(v, dsf{s_fin[2 * r], s_fin[2 * r + 1]});
+        }
+        const int k = 4 * g + tid / 7;
+        if (k < na) store_out(a.f, k, tid % 7, ds_to_double(v), a.err);
+    }
+    if (tid == 0) a.cnt[gridDim.x + 2 + g] = 0;  // re-arm the group's ticket
+    __syncthreads();
+    if (warp < 4)
+        correct_lanes(a.s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, 4 * g + warp, 0,
+                      true, true);
+}
+
+template <bool DS>
+__device__ __forceinline__ void small_item(const FusedArgs &a, int na, int n, int g, int c,
+                                           int nchunk, int jc, double tn, float2 (*s_red)[SMALL_Q],
+                                           float *s_fin, int *s_last)
+{
+    constexpr int G = 4, NW = FUSED_THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float eps2f = a.eps2f;
+    float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
+    int iid[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        const int slot = min(4 * g + p, na - 1);
+        const float4 *r = a.irec + (size_t)DS_REC * slot;
+        const float4 A = __ldcg(r), B = __ldcg(r + 1), C = __ldcg(r + 2);
+        xh[p] = A.x; yh[p] = A.y; zh[p] = A.z;
+        xl[p] = B.x; yl[p] = B.y; zl[p] = B.z;
+        vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
+        iid[p] = __float_as_int(B.w);
+    }
+    dsf S[G][7];
+#pragma unroll
+    for (int p = 0; p < G; ++p)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) S[p][q] = dsf{0.f, 0.f};
+    const int j0 = c * jc, j1 = min(n, j0 + jc);
+    const int per_w = (((j1 - j0) + NW - 1) / NW + 31) & ~31;
+    const int wj0 = j0 + warp * per_w, wj1 = min(j1, wj0 + per_w);
+    const float4 *jr = a.s.rec;
+    for (int jb = wj0; jb < wj1; jb += 32 * SMALL_JPL) {
+        float4 A[SMALL_JPL], B[SMALL_JPL], C[SMALL_JPL];
+        int jj[SMALL_JPL];
+#pragma unroll
+        for (int u = 0; u < SMALL_JPL; ++u) {
+            const int j = jb + lane + 32 * u;
+            jj[u] = j < wj1 ? j : -2;
+            if (j < wj1) {
+                A[u] = __ldcg(jr + (size_t)DS_REC * j);
+                C[u] = __ldcg(jr + (size_t)DS_REC * j + 2);
+                B[u] = DS ? __ldcg(jr + (size_t)DS_REC * j + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                A[u] = B[u] = C[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+            float ta0 = 0.f, ta1 = 0.f, ta2 = 0.f, tj0 = 0.f, tj1 = 0.f, tj2 = 0.f, tp = 0.f;
+#pragma unroll
+            for (int u = 0; u < SMALL_JPL; ++u) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (A[u].x - xh[p]) + (B[u].x - xl[p]);
+                    dy = (A[u].y - yh[p]) + (B[u].y - yl[p]);
+                    dz = (A[u].z - zh[p]) + (B[u].z - zl[p]);
+                } else {
+                    dx = A[u].x - xh[p];
+                    dy = A[u].y - yh[p];
+                    dz = A[u].z - zh[p];
+                }
+                const float dvx = C[u].x - vx[p], dvy = C[u].y - vy[p], dvz = C[u].z - vz[p];
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float rinv = rsqrtf(r2);
+                // the self pair and the padding slots (jj -2) contribute nothing
+                rinv = (jj[u] == iid[p] || jj[u] < 0) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = A[u].w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float beta = -3.f * ((mr3 * rinv2) * rv);
+                tp += mrinv;
+                ta0 = fmaf(mr3, dx, ta0);
+                ta1 = fmaf(mr3, dy, ta1);
+                ta2 = fmaf(mr3, dz, ta2);
+                tj0 = fmaf(beta, dx, fmaf(mr3, dvx, tj0));
+                tj1 = fmaf(beta, dy, fmaf(mr3, dvy, tj1));
+                tj2 = fmaf(beta, dz, fmaf(mr3, dvz, tj2));
+            }
+            ds_acc(S[p][0], dsf{ta0, 0.f});
+            ds_acc(S[p][1], dsf{ta1, 0.f});
+            ds_acc(S[p][2], dsf{ta2, 0.f});
+            ds_acc(S[p][3], dsf{tj0, 0.f});
+            ds_acc(S[p][4], dsf{tj1, 0.f});
+            ds_acc(S[p][5], dsf{tj2, 0.f});
+            ds_acc(S[p][6], dsf{tp, 0.f});
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int p = 0; p < G; ++p)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) ds_acc(S[p][q], ds_shfl_xor(S[p][q], o));
+    if (lane == 0) {
+#pragma unroll
+        for (int p = 0; p < G; ++p)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) s_red[warp][p * 7 + q] = make_float2(S[p][q].hi, S[p][q].lo);
+    }
+    __syncthreads();
+    if (tid < SMALL_Q) {
+        dsf v{s_red[0][tid].x, s_red[0][tid].y};
+#pragma unroll
+        for (int w = 1; w < NW; ++w) ds_acc(v, dsf{s_red[w][tid].x, s_red[w][tid].y});
+        a.part[((size_t)g * nchunk + c) * SMALL_Q + tid] = make_float2(v.hi, v.lo);
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) *s_last = (atomicAdd(a.cnt + gridDim.x + 2 + g, 1) == nchunk - 1);
+    __syncthreads();
+    if (*s_last) small_finish(a, na, g, nchunk, tn, s_fin);
+    __syncthreads();  // s_red, s_fin and s_last are free for the next item
+}
+
+// ---- the hand-off step -----------------------------------------------------
+
+// A step the fused kernel does not take (due set larger than na_max): predict
+// every particle to tn (FP64 pos_p, vel_p and records), then gather the due
+// set in ascending index (act, irec), exactly as K5 + K1 would, for the
+// planned kernels the caller runs next. Returns false when a grid barrier
+// gave up.
+__device__ __forceinline__ bool handoff_predict_gather(const FusedArgs &a, double tn, int p0,
+                                                       int p1, int nwords, unsigned *s_flags,
+                                                       int *s_woff, int *s_wsum, int &s_total,
+                                                       int &s_base, unsigned &gen)
+{
+    constexpr int NT = FUSED_THREADS, NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, bid = blockIdx.x;
+    const StateDev &s = a.s;
+    for (int w0 = 0; w0 < nwords; w0 += NW) {
+        const int i = p0 + w0 * 32 + tid;
+        float4 rec[DS_REC];
+        bool due = false;
+        if (i < p1) due = predict_one<true>(s, i, tn, rec);
+        const unsigned b = __ballot_sync(0xffffffffu, due);
+        if (lane == 0 && w0 + warp < nwords) s_flags[w0 + warp] = b;
+    }
+    __syncthreads();
+    // word offsets inside the CTA (exclusive scan of the popcounts)
+    for (int w0 = 0; w0 < nwords; w0 += NT) {
+        const int w = w0 + tid;
+        const int v = w < nwords ? __popc(s_flags[w]) : 0;
+        const int incl = warp_incl_scan(v);
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int x = lane < NW ? s_wsum[lane] : 0;
+            const int xi = warp_incl_scan(x);
+            if (lane < NW) s_wsum[lane] = xi - x;
+            if (lane == NW - 1) s_total = xi;
+        }
+        __syncthreads();
+        const int carry = (w0 == 0) ? 0 : s_base;  // total of the previous rounds
+        if (w < nwords) s_woff[w] = carry + s_wsum[warp] + incl - v;
+        __syncthreads();
+        if (tid == 0) s_base = carry + s_total;
+        __syncthreads();
+    }
+    if (tid == 0) a.cnt[bid] = nwords > 0 ? s_base : 0;
+    if (!grid_barrier(a.bar, gen)) return false;
+    // this CTA's offset; gather its due particles
+    if (warp == 0) {
+        int before = 0;
+        for (int q = lane; q < bid; q += 32) before += __ldcg(a.cnt + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+        if (lane == 0) s_base = before;
+    }
+    __syncthreads();
+    const int base = s_base;
+    for (int w = warp; w < nwords; w += NW) {
+        const unsigned b = s_flags[w];
+        if (b & (1u << lane)) {
+            const int i = p0 + w * 32 + lane;
+            const int slot = base + s_woff[w] + __popc(b & ((1u << lane) - 1u));
+            a.act[slot] = i;
+            const float4 *r = s.rec + (size_t)DS_REC * i;
+            float4 *g = a.irec + (size_t)DS_REC * slot;
+            g[0] = __ldcg(r);
+            g[1] = __ldcg(r + 1);
+            g[2] = __ldcg(r + 2);
+        }
+    }
+    (void)G;
+    return grid_barrier(a.bar, gen);
+}
+
+// ---- the kernel ------------------------------------------------------------
+
 template <bool DS>
 __global__ void __launch_bounds__(FUSED_THREADS)
     k_fused_steps(FusedArgs a)
@@ -377,10 +657,12 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     __shared__ unsigned s_flags[FUSED_MAX_WORDS];
     __shared__ int s_woff[FUSED_MAX_WORDS];
     __shared__ int s_wsum[NW];
-    __shared__ int s_total, s_base, s_na;
+    __shared__ int s_total, s_base, s_na, s_last;
     __shared__ double s_tn;
     __shared__ unsigned long long s_hist[32], s_step_ns[32], s_phase[4];
     __shared__ __align__(16) float4 s_tile[2][DS_REC * FUSED_TILE];
+    float2(*s_red)[SMALL_Q] = reinterpret_cast<float2(*)[SMALL_Q]>(&s_tile[0][0]);
+    float *s_fin = reinterpret_cast<float *>(&s_tile[1][0]);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, bid = blockIdx.x;
     const StateDev &s = a.s;
@@ -390,7 +672,9 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     const int nwords = (p1 - p0 + 31) / 32;
     const int total_warps = G * NW;
     const int gw = bid * NW + warp;
+    int *dcnt = a.cnt + G;  // two due-set counters, used in alternate steps
     unsigned gen = 0;
+    int par = 0;
     bool ok = true;
     double t_cur = __ldcg(&a.sd->t_cur);
     const unsigned long long epoch = __ldcg(&a.sd->seq);
@@ -401,102 +685,49 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     unsigned long long t_mark = 0;  // CTA 0, thread 0: stage boundaries
     if (bid == 0 && tid == 0) t_mark = globaltimer_ns();
     unsigned long long t_step = t_mark;
+    auto mark = [&](int ph) {
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[ph] += t - t_mark;
+            t_mark = t;
+        }
+    };
 
     for (;;) {
-        // A: t_next = next multiple after t_cur of the smallest occupied step
+        // t_next = next multiple after t_cur of the smallest occupied step; the
+        // due particles are exactly those whose step divides t_next (every t_i
+        // is a multiple of dt_i and t_i <= t_cur < t_i + dt_i), so the due count
+        // is the histogram's sum over the levels k >= k0
         if (warp == 0) {
             static_assert(NLEVEL == 64, "two ballot words of levels");
-            const bool o0 = __ldcg(a.sd->hist + lane) > 0;
-            const bool o1 = __ldcg(a.sd->hist + 32 + lane) > 0;
-            const unsigned b0 = __ballot_sync(0xffffffffu, o0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, o1);
+            const int h0 = __ldcg(a.sd->hist + lane);
+            const int h1 = __ldcg(a.sd->hist + 32 + lane);
+            const unsigned b0 = __ballot_sync(0xffffffffu, h0 > 0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, h1 > 0);
+            const int kmax = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : 0);
+            const double dm = ldexp(a.prm.dt_max, -kmax);
+            const double q = floor(t_cur * (1.0 / dm)) + 1.0;
+            const unsigned long long qi = q < 9.0e18 ? (unsigned long long)q : 0ull;
+            const int k0 = qi ? max(0, kmax - (__ffsll((long long)qi) - 1)) : NLEVEL;
+            int c = (lane >= k0 ? h0 : 0) + (lane + 32 >= k0 ? h1 : 0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
             if (lane == 0) {
-                const int kmax = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : 0);
-                const double dm = ldexp(a.prm.dt_max, -kmax);
-                s_tn = (floor(t_cur * (1.0 / dm)) + 1.0) * dm;
+                s_tn = q * dm;
+                s_na = c;
             }
         }
         __syncthreads();
         const double tn = s_tn;
-        for (int w0 = 0; w0 < nwords; w0 += NW) {
-            const int i = p0 + w0 * 32 + tid;
-            float4 rec[DS_REC];
-            bool due = false;
-            if (i < p1) due = predict_one<true>(s, i, tn, rec);
-            const unsigned b = __ballot_sync(0xffffffffu, due);
-            if (lane == 0 && w0 + warp < nwords) s_flags[w0 + warp] = b;
-        }
-        __syncthreads();
-        // word offsets inside the CTA (exclusive scan of the popcounts)
-        for (int w0 = 0; w0 < nwords; w0 += NT) {
-            const int w = w0 + tid;
-            const int v = w < nwords ? __popc(s_flags[w]) : 0;
-            const int incl = warp_incl_scan(v);
-            if (lane == 31) s_wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                const int x = lane < NW ? s_wsum[lane] : 0;
-                const int xi = warp_incl_scan(x);
-                if (lane < NW) s_wsum[lane] = xi - x;
-                if (lane == NW - 1) s_total = xi;
-            }
-            __syncthreads();
-            const int carry = (w0 == 0) ? 0 : s_base;  // total of the previous rounds
-            if (w < nwords) s_woff[w] = carry + s_wsum[warp] + incl - v;
-            __syncthreads();
-            if (tid == 0) s_base = carry + s_total;
-            __syncthreads();
-        }
-        if (tid == 0) a.cnt[bid] = nwords > 0 ? s_base : 0;
-        if (!(ok = grid_barrier(a.bar, gen))) break;
-        if (bid == 0 && tid == 0) {
-            const unsigned long long t = globaltimer_ns();
-            s_phase[0] += t - t_mark;
-            t_mark = t;
-        }
-
-        // B: this CTA's offset and the due count; gather the due set
-        if (warp == 0) {
-            int before = 0, all = 0;
-            for (int q = lane; q < G; q += 32) {
-                const int c = __ldcg(a.cnt + q);
-                all += c;
-                if (q < bid) before += c;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                before += __shfl_xor_sync(0xffffffffu, before, o);
-                all += __shfl_xor_sync(0xffffffffu, all, o);
-            }
-            if (lane == 0) {
-                s_base = before;
-                s_na = all;
-            }
-        }
-        __syncthreads();
-        const int na = s_na, base = s_base;
-        for (int w = warp; w < nwords; w += NW) {
-            const unsigned b = s_flags[w];
-            if (b & (1u << lane)) {
-                const int i = p0 + w * 32 + lane;
-                const int slot = base + s_woff[w] + __popc(b & ((1u << lane) - 1u));
-                a.act[slot] = i;
-                const float4 *r = s.rec + (size_t)DS_REC * i;
-                float4 *g = a.irec + (size_t)DS_REC * slot;
-                g[0] = __ldcg(r);
-                g[1] = __ldcg(r + 1);
-                g[2] = __ldcg(r + 2);
-            }
-        }
-        const bool stop = !(tn <= a.t_end) || na < 1 || na > a.na_max;
-        if (!(ok = grid_barrier(a.bar, gen))) break;
-        if (bid == 0 && tid == 0) {
-            const unsigned long long t = globaltimer_ns();
-            s_phase[1] += t - t_mark;
-            t_mark = t;
-        }
-        if (stop) {
+        const int na = s_na;
+        if (!(tn <= a.t_end) || na < 1 || na > a.na_max) {
             // hand the step to the caller exactly as the scheduler kernel would
+            if (tn <= a.t_end && na >= 1) {
+                ok = handoff_predict_gather(a, tn, p0, p1, nwords, s_flags, s_woff, s_wsum,
+                                            s_total, s_base, gen);
+                mark(0);
+                if (!ok) break;
+            }
             if (bid == 0 && tid == 0) {
                 a.sd->t_cur = t_cur;
                 a.sd->n_active = na;
@@ -509,67 +740,103 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             break;
         }
 
-        // C: pair force, warp items (4 due slots x one j-chunk)
-        int nchunk, jc;
-        bool cta_mode;
-        chunking(na, n, G, total_warps, nchunk, jc, cta_mode);
-        if (cta_mode) {
-            const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
-            for (int it = bid; it < nsb * nchunk; it += G) {
-                const int sb = it / nchunk, c = it - sb * nchunk;
-                const int j0 = c * jc;
-                cta_item<DS>(a, na, FUSED_CTA_SLOTS * sb, j0, min(n, j0 + jc), c, s_tile);
-            }
-        } else {
-            const int ng = (na + 3) / 4;
-            for (int it = gw; it < ng * nchunk; it += total_warps) {
-                const int g = it / nchunk, c = it - g * nchunk;
-                const int j0 = c * jc;
-                warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
+        // predict every particle of this CTA's range to tn (records only: the
+        // corrector recomputes the FP64 prediction of the due ones); the due
+        // ones take slots of the due set (in no particular order: each
+        // particle's forces do not depend on its slot) with their records
+        for (int w0 = 0; w0 < nwords; w0 += NW) {
+            const int i = p0 + w0 * 32 + tid;
+            float4 rec[DS_REC];
+            bool due = false;
+            if (i < p1) due = predict_one<true, false>(s, i, tn, rec);
+            const unsigned b = __ballot_sync(0xffffffffu, due);
+            if (b) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(dcnt + par, __popc(b));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (due) {
+                    const int slot = base + __popc(b & ((1u << lane) - 1u));
+                    a.act[slot] = i;
+                    float4 *g = a.irec + (size_t)DS_REC * slot;
+                    g[0] = rec[0];
+                    g[1] = rec[1];
+                    g[2] = rec[2];
+                }
             }
         }
         if (!(ok = grid_barrier(a.bar, gen))) break;
-        if (bid == 0 && tid == 0) {
-            const unsigned long long t = globaltimer_ns();
-            s_phase[2] += t - t_mark;
-            t_mark = t;
+        mark(0);
+        if (__ldcg(dcnt + par) != na) {  // the histogram and the states disagree
+            if (bid == 0 && tid == 0) atomicOr(a.err, DERR_SCHED);
+            break;
         }
+        if (bid == 0 && tid == 0) dcnt[par ^ 1] = 0;  // the next step's counter
 
-        // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
-        for (int k = gw; k < na; k += total_warps) {
-            // lane l holds chunks l, l + 32, l + 64, l + 96, all loaded at once
-            constexpr int CPL = FUSED_MAX_CHUNKS / 32;
-            float2 x[CPL][7];
+        if (na <= FUSED_SMALL_NA) {
+            // force, then (by the CTA that completes a group) reduction + corrector
+            int nchunk, jc;
+            small_chunking(na, n, G, nchunk, jc);
+            const int ng = (na + 3) / 4;
+            for (int it = bid; it < ng * nchunk; it += G) {
+                const int g = it / nchunk, c = it - g * nchunk;
+                small_item<DS>(a, na, n, g, c, nchunk, jc, tn, s_red, s_fin, &s_last);
+            }
+            mark(1);
+        } else {
+            // C: pair force, warp items (4 due slots x one j-chunk) or CTA items
+            int nchunk, jc;
+            bool cta_mode;
+            chunking(na, n, G, total_warps, nchunk, jc, cta_mode);
+            if (cta_mode) {
+                const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
+                for (int it = bid; it < nsb * nchunk; it += G) {
+                    const int sb = it / nchunk, c = it - sb * nchunk;
+                    const int j0 = c * jc;
+                    cta_item<DS>(a, na, FUSED_CTA_SLOTS * sb, j0, min(n, j0 + jc), c, s_tile);
+                }
+            } else {
+                const int ng = (na + 3) / 4;
+                for (int it = gw; it < ng * nchunk; it += total_warps) {
+                    const int g = it / nchunk, c = it - g * nchunk;
+                    const int j0 = c * jc;
+                    warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
+                }
+            }
+            if (!(ok = grid_barrier(a.bar, gen))) break;
+            mark(1);
+            // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
+            for (int k = gw; k < na; k += total_warps) {
+                // lane l holds chunks l, l + 32, l + 64, l + 96, all loaded at once
+                constexpr int CPL = FUSED_MAX_CHUNKS / 32;
+                float2 x[CPL][7];
 #pragma unroll
-            for (int u = 0; u < CPL; ++u)
+                for (int u = 0; u < CPL; ++u)
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) {
+                        const int c = lane + 32 * u;
+                        x[u][q] = c < nchunk ? __ldcg(a.part + ((size_t)c * 7 + q) * na + k)
+                                             : make_float2(0.f, 0.f);
+                    }
+                dsf v[7];
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
-                    const int c = lane + 32 * u;
-                    x[u][q] = c < nchunk ? __ldcg(a.part + ((size_t)c * 7 + q) * na + k)
-                                         : make_float2(0.f, 0.f);
+                    v[q] = dsf{x[0][q].x, x[0][q].y};
+#pragma unroll
+                    for (int u = 1; u < CPL; ++u) ds_acc(v[q], dsf{x[u][q].x, x[u][q].y});
                 }
-            dsf v[7];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                v[q] = dsf{x[0][q].x, x[0][q].y};
+                for (int q = 0; q < 7; ++q)
 #pragma unroll
-                for (int u = 1; u < CPL; ++u) ds_acc(v[q], dsf{x[u][q].x, x[u][q].y});
-            }
+                    for (int o = 16; o > 0; o >>= 1) ds_acc(v[q], ds_shfl_xor(v[q], o));
+                if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ds_acc(v[q], ds_shfl_xor(v[q], o));
-            if (lane == 0) {
-                const Out3 &f = a.f;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    f.acc[q * f.ld + k] = ds_to_double(v[q]);
-                    f.jerk[q * f.ld + k] = ds_to_double(v[3 + q]);
+                    for (int q = 0; q < 7; ++q) store_out(a.f, k, q, ds_to_double(v[q]), a.err);
                 }
-                f.pot[k] = -ds_to_double(v[6]);
+                __syncwarp();
+                correct_lanes(s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, k, 0, true,
+                              true);
             }
-            __syncwarp();
-            correct_lanes(s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, k, 0, true);
+            mark(2);
         }
         if (bid == 0 && tid == 0) {
             ++steps;
@@ -579,6 +846,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             s_hist[lg] += 1ull;
         }
         t_cur = tn;
+        par ^= 1;
         if (!(ok = grid_barrier(a.bar, gen))) break;
         if (bid == 0 && tid == 0) {
             const unsigned long long t = globaltimer_ns();
@@ -648,6 +916,9 @@ size_t fused_part_float2s(int grid, int na_max)
 cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    // the due-set counters and the group tickets
+    e = cudaMemsetAsync(a.cnt + grid, 0, (fused_cnt_ints(grid) - grid) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     FusedArgs copy = a;
     void *args[] = {&copy};

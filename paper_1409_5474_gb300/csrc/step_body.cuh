@@ -70,9 +70,10 @@ __device__ __forceinline__ void make_record(const double x[3], const double v[3]
 }
 
 // Predict particle i to time tn (FP64 Taylor series to the jerk term), write
-// pos_p / vel_p and, when REC, its double-single j-record (also left in rec[]);
-// returns whether the particle is due at tn (t_i + dt_i == tn).
-template <bool REC>
+// pos_p / vel_p (unless !STORE_P) and, when REC, its double-single j-record
+// (also left in rec[]); returns whether the particle is due at tn
+// (t_i + dt_i == tn).
+template <bool REC, bool STORE_P = true>
 __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn, float4 rec[3])
 {
     const double ti = s.t[i];
@@ -86,8 +87,10 @@ __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn,
         const double x = s.pos[q], v = s.vel[q], a = s.acc[q], j = s.jerk[q];
         xp[c] = fma(fma(fma(j, d6, 0.5 * a), d, v), d, x);
         vp[c] = fma(fma(j, d2h, a), d, v);
-        s.pos_p[q] = xp[c];
-        s.vel_p[q] = vp[c];
+        if (STORE_P) {
+            s.pos_p[q] = xp[c];
+            s.vel_p[q] = vp[c];
+        }
     }
     if (REC) {
         make_record(xp, vp, s.m[i], i, rec);
@@ -413,7 +416,7 @@ __device__ __forceinline__ void correct_lanes(const StateDev &s, const int *act,
                                               double t_new, const Out3 &f, const StepParams &prm,
                                               SchedDev *sd, unsigned *err,
                                               unsigned long long *dtmin_hits, int k, int lane0,
-                                              bool valid)
+                                              bool valid, bool xp_from_state = false)
 {
     const int lane = threadIdx.x & 31;
     const int c = lane - lane0;
@@ -428,7 +431,8 @@ __device__ __forceinline__ void correct_lanes(const StateDev &s, const int *act,
         dt_old = s.dt[i];
         double dt2, idt2, idt3;
         step_factors(dt, prm, dt2, idt2, idt3);
-        fin = correct_component(s, f, i, k, c, dt, dt2, idt2, idt3, a1, j1, a2e, a3e);
+        fin = correct_component(s, f, i, k, c, dt, dt2, idt2, idt3, a1, j1, a2e, a3e,
+                                xp_from_state);
     }
     double a1v[3], j1v[3], a2v[3], a3v[3];
 #pragma unroll
