@@ -5,8 +5,8 @@ Every comparison gates the relative RMS over the i-set, sqrt(sum |d|^2 / sum |re
 and the per-particle maximum of |d_i| / |ref_i| (PP_GATES), and prints both with the
 per-particle median. RMS gates:
   F64 pairs:          acc, jerk, pot <= 1e-12
-  F32 double-single:  acc, pot <= 1e-6; jerk <= 1e-5 (FP32 velocities; the
-                      jerk's v - 3(r.v)r/s2 cancels)
+  F32 double-single:  acc, pot <= 1e-6 (the force); jerk <= 2e-6 (FP32 velocities;
+                      the jerk's v - 3(r.v)r/s2 cancels; measured <= 6.7e-7)
   F32 plain:          reported, sanity bound 1e-3 only
 Sizes span the tile and warp edges (1, 2, 3, 31, 32, 33, 1023, 4097 = 32*128+1)
 and every launch mode (j-parallel warps for N_i <= 32, tiles with and without
@@ -21,9 +21,12 @@ from tests.errstats import fmt, rel_rms, report
 
 pytestmark = pytest.mark.gpu
 
-GATES = {"f64": (1e-12, 1e-12, 1e-12), "f32ds": (1e-6, 1e-5, 1e-6), "f32": (1e-3, 1e-2, 1e-3)}
-# per-particle maximum of |d_i| / |ref_i| (acc, jerk, pot) over the i-set
-PP_GATES = {"f64": (1e-10, 1e-9, 1e-10), "f32ds": (1e-5, 1e-3, 1e-5), "f32": (1e-1, 1.0, 1e-1)}
+GATES = {"f64": (1e-12, 1e-12, 1e-12), "f32ds": (1e-6, 2e-6, 1e-6), "f32": (1e-3, 1e-2, 1e-3)}
+# per-particle maximum of |d_i| / |ref_i| (acc, jerk, pot) over the i-set: 3-15x the largest
+# value measured over these tests on GB300 (F32-DS 1.1e-6 / 7.6e-6 / 2.0e-7; FP64
+# 9.1e-15 / 2.2e-14 / 8.7e-16; plain FP32 1.0e-5 / 9.7e-5 / 1.4e-6). A particle whose net
+# force nearly cancels has a large relative error at any precision, hence max >> RMS.
+PP_GATES = {"f64": (1e-13, 3e-13, 1e-14), "f32ds": (1e-5, 1e-4, 2e-6), "f32": (1e-4, 1e-3, 2e-5)}
 
 
 def _system(n, seed, spread=1.0, offset=0.0):
@@ -232,7 +235,7 @@ def test_autotune_table_and_parity(nb):
             nb.nb_set_plan_table(s.h, [(0, 3, 1)])
         assert e.value.status == nb.NB_ERR_ARG
     ra, rj, rp = oracle.force(m, pos, vel, 1e-6)
-    assert rel_rms(acc.T, ra) <= 1e-6 and rel_rms(jerk.T, rj) <= 1e-5
+    assert rel_rms(acc.T, ra) <= 1e-6 and rel_rms(jerk.T, rj) <= 2e-6
 
 
 @pytest.mark.parametrize("which", [0, 1], ids=["mbarrier", "grid_barrier"])

@@ -18,9 +18,11 @@ def _rel_rms(got, ref):
 
 
 # force gates (relative RMS over the i-set): acc, jerk, snap, pot
-GATES = {"f32ds": (1e-6, 1e-5, 1e-4, 1e-6), "f64": (1e-12, 1e-11, 1e-10, 1e-12)}
-# per-particle maximum of |d_i| / |ref_i|: acc, jerk, snap, pot
-PP_GATES = {"f32ds": (1e-5, 1e-3, 1e-2, 1e-5), "f64": (1e-10, 1e-9, 1e-8, 1e-10)}
+GATES = {"f32ds": (1e-6, 2e-6, 1e-6, 1e-6), "f64": (1e-12, 1e-11, 1e-10, 1e-12)}
+# per-particle maximum of |d_i| / |ref_i|: acc, jerk, snap, pot (3-15x the largest value
+# measured here on GB300: F32-DS 4.7e-7 / 1.9e-6 / 6.4e-6 / 2.0e-7, FP64 9.1e-15 / 2.1e-14
+# / 7.3e-14 / 8.7e-16)
+PP_GATES = {"f32ds": (1e-5, 1e-4, 1e-4, 2e-6), "f64": (1e-13, 3e-13, 1e-12, 1e-14)}
 
 
 def _gate6(variant, got, ref, tag=None):
