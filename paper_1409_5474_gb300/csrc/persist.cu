@@ -740,16 +740,15 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             break;
         }
 
-        // predict every particle of this CTA's range to tn (records only, in
-        // double-single arithmetic: the corrector recomputes the FP64
-        // prediction of the due ones); the due ones take slots of the due set
-        // (in no particular order: each particle's forces do not depend on its
-        // slot) with their records
+        // predict every particle of this CTA's range to tn (records only: the
+        // corrector recomputes the FP64 prediction of the due ones); the due
+        // ones take slots of the due set (in no particular order: each
+        // particle's forces do not depend on its slot) with their records
         for (int w0 = 0; w0 < nwords; w0 += NW) {
             const int i = p0 + w0 * 32 + tid;
             float4 rec[DS_REC];
             bool due = false;
-            if (i < p1) due = predict_rec_ds(s, i, tn, rec);
+            if (i < p1) due = predict_one<true, false>(s, i, tn, rec);
             const unsigned b = __ballot_sync(0xffffffffu, due);
             if (b) {
                 int base = 0;

@@ -9,7 +9,6 @@
 #include <math.h>
 
 #include "nb_internal.cuh"
-#include "ds.cuh"
 
 namespace nb {
 
@@ -100,62 +99,6 @@ __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn,
         rr[1] = rec[1];
         rr[2] = rec[2];
     }
-    return due;
-}
-
-// Double-single product x y (TwoProd of the high parts by FMA, cross terms
-// added, renormalised).
-__device__ __forceinline__ dsf ds_mul(dsf x, dsf y)
-{
-    const float p = x.hi * y.hi;
-    float e = fmaf(x.hi, y.hi, -p);
-    e = fmaf(x.hi, y.lo, e);
-    e = fmaf(x.lo, y.hi, e);
-    const float h = p + e;
-    return dsf{h, e - (h - p)};
-}
-
-// K1 for one particle in double-single arithmetic: the j-record of particle i
-// at tn (written to s.rec and left in rec[]) from its FP64 state split into
-// FP32 pairs, x_p = x + d (v + d (a/2 + d j/6)) with x, v, a and d = tn - t_i
-// as pairs and the jerk term in FP32 (its share of the displacement is small;
-// on increments |a| d^2 <= 1e-2, |j| d^3 <= 1e-5 the position differs from the
-// FP64 series by <= 2.5e-13), v_p = v + d (a + d j/2) in FP32 (the record's
-// precision). Two FP64 operations per particle instead of ~22: GB300's FP64
-// pipe is narrow. Returns whether the particle is due at tn.
-__device__ __forceinline__ bool predict_rec_ds(const StateDev &s, int i, double tn, float4 rec[3])
-{
-    const double ti = s.t[i];
-    const bool due = (ti + s.dt[i] == tn);
-    float dh, dl;
-    split_ds(tn - ti, dh, dl);
-    const dsf d{dh, dl};
-    float xh[3], xl[3], vp[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long q = c * s.ld + i;
-        float ph, pl, qh, ql, ah, al;
-        split_ds(s.pos[q], ph, pl);
-        split_ds(s.vel[q], qh, ql);
-        split_ds(s.acc[q], ah, al);
-        const float jf = f32_trunc(s.jerk[q]);
-        dsf w{0.5f * ah, 0.5f * al};
-        ds_acc(w, dsf{dh * (jf * (1.f / 6.f)), 0.f});
-        dsf u{qh, ql};
-        ds_acc(u, ds_mul(d, w));
-        dsf x{ph, pl};
-        ds_acc(x, ds_mul(d, u));
-        xh[c] = x.hi;
-        xl[c] = x.lo;
-        vp[c] = fmaf(dh, fmaf(dh, 0.5f * jf, ah), qh);
-    }
-    rec[0] = make_float4(xh[0], xh[1], xh[2], f32_trunc(s.m[i]));
-    rec[1] = make_float4(xl[0], xl[1], xl[2], __int_as_float(i));
-    rec[2] = make_float4(vp[0], vp[1], vp[2], 0.f);
-    float4 *rr = s.rec + (size_t)DS_REC * i;
-    rr[0] = rec[0];
-    rr[1] = rec[1];
-    rr[2] = rec[2];
     return due;
 }
 
