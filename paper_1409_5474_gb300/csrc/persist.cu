@@ -97,144 +97,35 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
-// K2 for one warp item: due slots k0 .. k0 + 3 (gathered records in irec)
-// against j-records [j0, j1) of the system; the lanes take j = j0 + lane,
-// j0 + lane + 32, ...; FP32 sums over at most 32 j per lane are folded into
-// double-single totals, which meet in a fixed xor tree; lane q < 28 stores
-// total q = (slot q / 7, component q % 7) to the chunk's partials.
-template <bool DS>
-__device__ __forceinline__ void warp_item(const FusedArgs &a, int na, int k0, int j0, int j1,
-                                          int chunk)
-{
-    constexpr int G = 4;
-    const int lane = threadIdx.x & 31;
-    const float eps2f = a.eps2f;
-    float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
-    int iid[G];
-#pragma unroll
-    for (int p = 0; p < G; ++p) {
-        const int slot = min(k0 + p, na - 1);  // idle slots copy the last one
-        const float4 *r = a.irec + (size_t)DS_REC * slot;
-        const float4 A = __ldcg(r), B = __ldcg(r + 1), C = __ldcg(r + 2);
-        xh[p] = A.x; yh[p] = A.y; zh[p] = A.z;
-        xl[p] = B.x; yl[p] = B.y; zl[p] = B.z;
-        vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
-        iid[p] = __float_as_int(B.w);
-    }
-    dsf S[G][7];
-#pragma unroll
-    for (int p = 0; p < G; ++p)
-#pragma unroll
-        for (int c = 0; c < 7; ++c) S[p][c] = dsf{0.f, 0.f};
-    const float4 *jr = a.s.rec;
-    for (int jb = j0; jb < j1; jb += 32 * 32) {
-        const int je = min(j1, jb + 32 * 32);
-        float ta[G][3], tjv[G][3], tp[G];
-#pragma unroll
-        for (int p = 0; p < G; ++p) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) ta[p][c] = tjv[p][c] = 0.f;
-            tp[p] = 0.f;
-        }
-#pragma unroll 2
-        for (int j = jb + lane; j < je; j += 32) {
-            const float4 A = __ldcg(jr + (size_t)DS_REC * j);
-            const float4 C = __ldcg(jr + (size_t)DS_REC * j + 2);
-            float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (DS) B = __ldcg(jr + (size_t)DS_REC * j + 1);
-#pragma unroll
-            for (int p = 0; p < G; ++p) {
-                float dx, dy, dz;
-                if (DS) {
-                    dx = (A.x - xh[p]) + (B.x - xl[p]);
-                    dy = (A.y - yh[p]) + (B.y - yl[p]);
-                    dz = (A.z - zh[p]) + (B.z - zl[p]);
-                } else {
-                    dx = A.x - xh[p];
-                    dy = A.y - yh[p];
-                    dz = A.z - zh[p];
-                }
-                const float dvx = C.x - vx[p], dvy = C.y - vy[p], dvz = C.z - vz[p];
-                float r2 = fmaf(dx, dx, eps2f);
-                r2 = fmaf(dy, dy, r2);
-                r2 = fmaf(dz, dz, r2);
-                float rv = dx * dvx;
-                rv = fmaf(dy, dvy, rv);
-                rv = fmaf(dz, dvz, rv);
-                float rinv = rsqrtf(r2);
-                rinv = (j == iid[p]) ? 0.f : rinv;
-                const float rinv2 = rinv * rinv;
-                const float mrinv = A.w * rinv;
-                const float mr3 = mrinv * rinv2;
-                const float beta = -3.f * ((mr3 * rinv2) * rv);
-                tp[p] += mrinv;
-                ta[p][0] = fmaf(mr3, dx, ta[p][0]);
-                ta[p][1] = fmaf(mr3, dy, ta[p][1]);
-                ta[p][2] = fmaf(mr3, dz, ta[p][2]);
-                tjv[p][0] = fmaf(beta, dx, fmaf(mr3, dvx, tjv[p][0]));
-                tjv[p][1] = fmaf(beta, dy, fmaf(mr3, dvy, tjv[p][1]));
-                tjv[p][2] = fmaf(beta, dz, fmaf(mr3, dvz, tjv[p][2]));
-            }
-        }
-#pragma unroll
-        for (int p = 0; p < G; ++p) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ds_acc(S[p][c], dsf{ta[p][c], 0.f});
-                ds_acc(S[p][3 + c], dsf{tjv[p][c], 0.f});
-            }
-            ds_acc(S[p][6], dsf{tp[p], 0.f});
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < G; ++p)
-#pragma unroll
-        for (int c = 0; c < 7; ++c) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ds_acc(S[p][c], ds_shfl_xor(S[p][c], o));
-        }
-#pragma unroll
-    for (int q = 0; q < G * 7; ++q) {
-        const int p = q / 7, c = q % 7;
-        if (lane == q && k0 + p < na)
-            a.part[((size_t)chunk * 7 + c) * na + k0 + p] = make_float2(S[p][c].hi, S[p][c].lo);
-    }
-}
-
-// K2 for one CTA item (steps with at least 29 due particles): the CTA's
-// eight warps take four due slots each (slots k0 .. k0 + 31) against the
-// j-records [j0, j1), staged through shared memory in tiles of FUSED_TILE
-// records (double-buffered, the next tile's loads in flight during the
-// arithmetic); lanes take the tile's records l, l + 32, ...; double-single
-// totals per warp as in warp_item.
+// K2 for one tile item (due sets larger than FUSED_SMALL_NA): 32 due slots
+// (slots k0 .. k0 + 31, one per lane; idle lanes copy the last due slot)
+// against the j-records [j0, j1), staged through shared memory in tiles of
+// FUSED_TILE records (double-buffered: the next tile's loads are in flight
+// during the arithmetic). The CTA's eight warps hold the same 32 slots and
+// split every tile (warp w takes records w, w + 8, ...), so no lane sums have
+// to meet in a shuffle tree; FP32 sums over about 128 pairs are folded into
+// double-single totals, and the warps' totals are added in fixed order through
+// shared memory: one partial per (slot, chunk).
 constexpr int FUSED_TILE = 256;
+constexpr int FUSED_IB = 32;        // due slots per tile item
+constexpr int FUSED_TILE_FOLD = 4;  // tiles per FP32 partial sum (4 x 32 pairs per thread)
 
 template <bool DS>
-__device__ __forceinline__ void cta_item(const FusedArgs &a, int na, int k0, int j0, int j1,
-                                         int chunk, float4 (*s_tile)[DS_REC * FUSED_TILE])
+__device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, int j0, int j1,
+                                          int chunk, float4 (*s_tile)[DS_REC * FUSED_TILE])
 {
-    constexpr int G = 4, NT = FUSED_THREADS, PF = (DS_REC * FUSED_TILE + NT - 1) / NT;
+    constexpr int NT = FUSED_THREADS, NW = NT / 32, PF = (DS_REC * FUSED_TILE + NT - 1) / NT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int kw = k0 + G * warp;
-    const bool active = kw < na;  // warp-uniform
     const float eps2f = a.eps2f;
-    float xh[G], yh[G], zh[G], xl[G], yl[G], zl[G], vx[G], vy[G], vz[G];
-    int iid[G];
+    const float4 *ir = a.irec + (size_t)DS_REC * min(k0 + lane, na - 1);
+    const float4 I0 = __ldcg(ir), I1 = __ldcg(ir + 1), I2 = __ldcg(ir + 2);
+    const float xh = I0.x, yh = I0.y, zh = I0.z, xl = I1.x, yl = I1.y, zl = I1.z;
+    const float vx = I2.x, vy = I2.y, vz = I2.z;
+    const int iid = __float_as_int(I1.w);
+    float A_h[3], A_l[3], J_h[3], J_l[3], P_h = 0.f, P_l = 0.f;
 #pragma unroll
-    for (int p = 0; p < G; ++p) {
-        const int slot = min(kw + p, na - 1);
-        const float4 *r = a.irec + (size_t)DS_REC * slot;
-        const float4 A = __ldcg(r), B = __ldcg(r + 1), C = __ldcg(r + 2);
-        xh[p] = A.x; yh[p] = A.y; zh[p] = A.z;
-        xl[p] = B.x; yl[p] = B.y; zl[p] = B.z;
-        vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
-        iid[p] = __float_as_int(B.w);
-    }
-    dsf S[G][7];
-#pragma unroll
-    for (int p = 0; p < G; ++p)
-#pragma unroll
-        for (int c = 0; c < 7; ++c) S[p][c] = dsf{0.f, 0.f};
+    for (int c = 0; c < 3; ++c) A_h[c] = A_l[c] = J_h[c] = J_l[c] = 0.f;
+    float ta[3] = {0.f, 0.f, 0.f}, tja[3] = {0.f, 0.f, 0.f}, tjb[3] = {0.f, 0.f, 0.f}, tp = 0.f;
     const float4 *jr = a.s.rec;
     const int ntile = (j1 - j0 + FUSED_TILE - 1) / FUSED_TILE;
     float4 pf[PF];
@@ -262,108 +153,111 @@ __device__ __forceinline__ void cta_item(const FusedArgs &a, int na, int k0, int
         const int tb = j0 + t * FUSED_TILE;
         const int cnt = min(FUSED_TILE, j1 - tb);
         if (t + 1 < ntile) fetch(t + 1);
-        if (active) {
-            const float4 *T = s_tile[t & 1];
-            float ta[G][3], tjv[G][3], tp[G];
-#pragma unroll
-            for (int p = 0; p < G; ++p) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) ta[p][c] = tjv[p][c] = 0.f;
-                tp[p] = 0.f;
+        const float4 *T = s_tile[t & 1];
+        // the pair of a slot with itself in this tile for any lane? (warp-uniform)
+        const bool own = __any_sync(0xffffffffu, iid >= tb && iid < tb + cnt);
+        auto body = [&](int jj, bool masked) {
+            const float4 A = T[DS_REC * jj];
+            const float4 C = T[DS_REC * jj + 2];
+            float4 B;
+            if (DS) B = T[DS_REC * jj + 1];
+            float dx, dy, dz;
+            if (DS) {
+                dx = (A.x - xh) + (B.x - xl);
+                dy = (A.y - yh) + (B.y - yl);
+                dz = (A.z - zh) + (B.z - zl);
+            } else {
+                dx = A.x - xh;
+                dy = A.y - yh;
+                dz = A.z - zh;
             }
-#pragma unroll 2
-            for (int jj = lane; jj < cnt; jj += 32) {
-                const int j = tb + jj;
-                const float4 A = T[DS_REC * jj];
-                const float4 C = T[DS_REC * jj + 2];
-                float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (DS) B = T[DS_REC * jj + 1];
+            const float dvx = C.x - vx, dvy = C.y - vy, dvz = C.z - vz;
+            float r2 = fmaf(dx, dx, eps2f);
+            r2 = fmaf(dy, dy, r2);
+            r2 = fmaf(dz, dz, r2);
+            float rv = dx * dvx;
+            rv = fmaf(dy, dvy, rv);
+            rv = fmaf(dz, dvz, rv);
+            float rinv = rsqrtf(r2);
+            if (masked) rinv = (tb + jj == iid) ? 0.f : rinv;
+            const float rinv2 = rinv * rinv;
+            const float mrinv = A.w * rinv;
+            const float mr3 = mrinv * rinv2;
+            const float beta = (mr3 * rinv2) * rv;
+            tp += mrinv;
+            ta[0] = fmaf(mr3, dx, ta[0]);
+            ta[1] = fmaf(mr3, dy, ta[1]);
+            ta[2] = fmaf(mr3, dz, ta[2]);
+            tja[0] = fmaf(mr3, dvx, tja[0]);
+            tja[1] = fmaf(mr3, dvy, tja[1]);
+            tja[2] = fmaf(mr3, dvz, tja[2]);
+            tjb[0] = fmaf(beta, dx, tjb[0]);
+            tjb[1] = fmaf(beta, dy, tjb[1]);
+            tjb[2] = fmaf(beta, dz, tjb[2]);
+        };
+        if (own) {
+            for (int jj = warp; jj < cnt; jj += NW) body(jj, true);
+        } else {
+#pragma unroll 4
+            for (int jj = warp; jj < cnt; jj += NW) body(jj, false);
+        }
+        if ((t + 1) % FUSED_TILE_FOLD == 0 || t + 1 == ntile) {
 #pragma unroll
-                for (int p = 0; p < G; ++p) {
-                    float dx, dy, dz;
-                    if (DS) {
-                        dx = (A.x - xh[p]) + (B.x - xl[p]);
-                        dy = (A.y - yh[p]) + (B.y - yl[p]);
-                        dz = (A.z - zh[p]) + (B.z - zl[p]);
-                    } else {
-                        dx = A.x - xh[p];
-                        dy = A.y - yh[p];
-                        dz = A.z - zh[p];
-                    }
-                    const float dvx = C.x - vx[p], dvy = C.y - vy[p], dvz = C.z - vz[p];
-                    float r2 = fmaf(dx, dx, eps2f);
-                    r2 = fmaf(dy, dy, r2);
-                    r2 = fmaf(dz, dz, r2);
-                    float rv = dx * dvx;
-                    rv = fmaf(dy, dvy, rv);
-                    rv = fmaf(dz, dvz, rv);
-                    float rinv = rsqrtf(r2);
-                    rinv = (j == iid[p]) ? 0.f : rinv;
-                    const float rinv2 = rinv * rinv;
-                    const float mrinv = A.w * rinv;
-                    const float mr3 = mrinv * rinv2;
-                    const float beta = -3.f * ((mr3 * rinv2) * rv);
-                    tp[p] += mrinv;
-                    ta[p][0] = fmaf(mr3, dx, ta[p][0]);
-                    ta[p][1] = fmaf(mr3, dy, ta[p][1]);
-                    ta[p][2] = fmaf(mr3, dz, ta[p][2]);
-                    tjv[p][0] = fmaf(beta, dx, fmaf(mr3, dvx, tjv[p][0]));
-                    tjv[p][1] = fmaf(beta, dy, fmaf(mr3, dvy, tjv[p][1]));
-                    tjv[p][2] = fmaf(beta, dz, fmaf(mr3, dvz, tjv[p][2]));
+            for (int c = 0; c < 3; ++c) {
+                const float jt = fmaf(-3.f, tjb[c], tja[c]);
+                if (DS) {
+                    ds_add(A_h[c], A_l[c], ta[c]);
+                    ds_add(J_h[c], J_l[c], jt);
+                } else {
+                    A_h[c] += ta[c];
+                    J_h[c] += jt;
                 }
+                ta[c] = tja[c] = tjb[c] = 0.f;
             }
-#pragma unroll
-            for (int p = 0; p < G; ++p) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ds_acc(S[p][c], dsf{ta[p][c], 0.f});
-                    ds_acc(S[p][3 + c], dsf{tjv[p][c], 0.f});
-                }
-                ds_acc(S[p][6], dsf{tp[p], 0.f});
-            }
+            if (DS)
+                ds_add(P_h, P_l, tp);
+            else
+                P_h += tp;
+            tp = 0.f;
         }
         if (t + 1 < ntile) stash((t + 1) & 1);
         __syncthreads();
     }
-    if (active) {
+    // the warps' totals, added in order 0..7 (the tile buffers are free now)
+    float2 *s_red = reinterpret_cast<float2 *>(&s_tile[0][0]);  // [NW][7][32]
+    const float2 mine[7] = {make_float2(A_h[0], A_l[0]), make_float2(A_h[1], A_l[1]),
+                            make_float2(A_h[2], A_l[2]), make_float2(J_h[0], J_l[0]),
+                            make_float2(J_h[1], J_l[1]), make_float2(J_h[2], J_l[2]),
+                            make_float2(P_h, P_l)};
 #pragma unroll
-        for (int p = 0; p < G; ++p)
+    for (int c = 0; c < 7; ++c) s_red[(warp * 7 + c) * 32 + lane] = mine[c];
+    __syncthreads();
+    if (warp == 0 && k0 + lane < na) {
 #pragma unroll
-            for (int c = 0; c < 7; ++c) {
+        for (int c = 0; c < 7; ++c) {
+            dsf v{mine[c].x, mine[c].y};
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ds_acc(S[p][c], ds_shfl_xor(S[p][c], o));
+            for (int w = 1; w < NW; ++w) {
+                const float2 x = s_red[(w * 7 + c) * 32 + lane];
+                ds_acc(v, dsf{x.x, x.y});
             }
-#pragma unroll
-        for (int q = 0; q < G * 7; ++q) {
-            const int p = q / 7, c = q % 7;
-            if (lane == q && kw + p < na)
-                a.part[((size_t)chunk * 7 + c) * na + kw + p] =
-                    make_float2(S[p][c].hi, S[p][c].lo);
+            a.part[((size_t)chunk * 7 + c) * na + k0 + lane] = make_float2(v.hi, v.lo);
         }
     }
+    __syncthreads();  // s_red is the tile buffer of the next item
 }
 
-// The j-chunks of a step with na due particles on n (a function of (na, n,
-// grid) only): with at least eight groups of four due slots the CTAs take
-// items of 32 slots (cta mode), about four per CTA; otherwise warps take items of
-// four slots, about two per warp. At least 256 j per chunk, at most
-// FUSED_MAX_CHUNKS chunks.
+// The j-chunks of a step with na (> FUSED_SMALL_NA) due particles on n (a
+// function of (na, n, grid) only): one round of items over the grid, at most
+// FUSED_MAX_CHUNKS chunks (the reduction's lanes hold four each) of at least
+// FUSED_TILE j.
 constexpr int FUSED_MAX_CHUNKS = 128;
-constexpr int FUSED_CTA_SLOTS = 4 * (FUSED_THREADS / 32);
 
-__device__ __forceinline__ void chunking(int na, int n, int grid, int total_warps, int &nchunk,
-                                         int &jc, bool &cta_mode)
+__device__ __forceinline__ void tile_chunking(int na, int n, int grid, int &nchunk, int &jc)
 {
-    const int ng = (na + 3) / 4;
-    cta_mode = ng >= FUSED_THREADS / 32;
-    int nc;
-    if (cta_mode) {
-        const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
-        nc = (4 * grid + nsb - 1) / nsb;
-    } else {
-        nc = (2 * total_warps + ng - 1) / ng;
-    }
-    nc = max(1, min(min(nc, (n + 255) / 256), FUSED_MAX_CHUNKS));
+    const int nib = (na + FUSED_IB - 1) / FUSED_IB;
+    int nc = max(1, grid / nib);
+    nc = max(1, min(min(nc, (n + FUSED_TILE - 1) / FUSED_TILE), FUSED_MAX_CHUNKS));
     jc = (n + nc - 1) / nc;
     jc = (jc + 31) & ~31;
     nchunk = (n + jc - 1) / jc;
@@ -783,24 +677,14 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             }
             mark(1);
         } else {
-            // C: pair force, warp items (4 due slots x one j-chunk) or CTA items
+            // C: pair force, tile items (32 due slots x one j-chunk)
             int nchunk, jc;
-            bool cta_mode;
-            chunking(na, n, G, total_warps, nchunk, jc, cta_mode);
-            if (cta_mode) {
-                const int nsb = (na + FUSED_CTA_SLOTS - 1) / FUSED_CTA_SLOTS;
-                for (int it = bid; it < nsb * nchunk; it += G) {
-                    const int sb = it / nchunk, c = it - sb * nchunk;
-                    const int j0 = c * jc;
-                    cta_item<DS>(a, na, FUSED_CTA_SLOTS * sb, j0, min(n, j0 + jc), c, s_tile);
-                }
-            } else {
-                const int ng = (na + 3) / 4;
-                for (int it = gw; it < ng * nchunk; it += total_warps) {
-                    const int g = it / nchunk, c = it - g * nchunk;
-                    const int j0 = c * jc;
-                    warp_item<DS>(a, na, 4 * g, j0, min(n, j0 + jc), c);
-                }
+            tile_chunking(na, n, G, nchunk, jc);
+            const int nib = (na + FUSED_IB - 1) / FUSED_IB;
+            for (int it = bid; it < nib * nchunk; it += G) {
+                const int ib = it / nchunk, c = it - ib * nchunk;
+                const int j0 = c * jc;
+                tile_item<DS>(a, na, FUSED_IB * ib, j0, min(n, j0 + jc), c, s_tile);
             }
             if (!(ok = grid_barrier(a.bar, gen))) break;
             mark(1);
@@ -907,10 +791,15 @@ int fused_grid(int device)
 
 size_t fused_part_float2s(int grid, int na_max)
 {
-    // warp items: nchunk * na <= (2 W / ceil(na/4) + 1) * na <= 8 W + na for W warps;
-    // CTA items: nchunk * na <= (4 G / ceil(na/32) + 1) * na <= 128 G + na = 16 W + na
-    const size_t w = (size_t)grid * (FUSED_THREADS / 32);
-    return 7 * (16 * w + (size_t)na_max + 64);
+    // tile items: nchunk * na <= FUSED_MAX_CHUNKS * FUSED_IB for one i-block, else
+    // (G / nib) * na <= G * FUSED_IB; small sets: ng * nchunk * 28 with ng <= 4 and
+    // nchunk <= max(G, n / 2048 + 1) <= 4 G + 1 (n <= 8192 G)
+    const size_t g = (size_t)grid;
+    size_t need = 7 * (g * FUSED_IB + (size_t)FUSED_MAX_CHUNKS * FUSED_IB + 64);
+    const size_t small = (size_t)(FUSED_SMALL_NA / 4) * (4 * g + 2) * SMALL_Q;
+    if (small > need) need = small;
+    (void)na_max;
+    return need;
 }
 
 cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st)
