@@ -275,8 +275,8 @@ __device__ __forceinline__ void tile_chunking(int na, int n, int grid, int &nchu
 // group's last chunk (its ticket) sums the group's partials in a fixed order
 // and corrects the group's particles, so no grid barrier separates the force
 // from the corrector.
-constexpr int SMALL_JPL = 4;
-constexpr int SMALL_CHUNK_MAX_J = 2 * SMALL_JPL * 32 * (FUSED_THREADS / 32);  // 2048
+constexpr int SMALL_JPL = 2;
+constexpr int SMALL_CHUNK_MAX_J = 2048;  // j per small-set chunk: 8 per lane
 constexpr int SMALL_Q = 28;  // outputs of a group: 4 slots x 7 components
 
 // The j-chunks of a small due set (a function of (na, n, grid) only): about one
@@ -303,31 +303,31 @@ __device__ __forceinline__ void store_out(const Out3 &f, int k, int c, double v,
     if (!isfinite(v)) atomicOr(err, DERR_NONFINITE);
 }
 
-// The group's sums (in chunk order within each of 8 interleaved subsets, then
-// the subsets in order) and the corrector of its due particles.
+// The group's sums (each of SMALL_SUBS threads per output adds a contiguous
+// range of chunks in order, all its loads in flight at once; the ranges are
+// then added in order) and the corrector of its due particles.
+constexpr int SMALL_SUBS = FUSED_THREADS / SMALL_Q;  // 9 ranges per output
+constexpr int SMALL_BATCH = 16;                       // loads in flight per thread
+
 __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, int nchunk,
                                              double tn, float *s_fin)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
     __threadfence();
-    if (tid < 8 * SMALL_Q) {
+    if (tid < SMALL_SUBS * SMALL_Q) {
         const int q = tid % SMALL_Q, sub = tid / SMALL_Q;
+        const int len = (nchunk + SMALL_SUBS - 1) / SMALL_SUBS;
+        const int c0 = sub * len, c1 = min(nchunk, c0 + len);
         const float2 *base = a.part + (size_t)g * nchunk * SMALL_Q + q;
         dsf acc{0.f, 0.f};
-        int c = sub;
-        for (; c + 24 < nchunk; c += 32) {
-            const float2 x0 = __ldcg(base + (size_t)c * SMALL_Q);
-            const float2 x1 = __ldcg(base + (size_t)(c + 8) * SMALL_Q);
-            const float2 x2 = __ldcg(base + (size_t)(c + 16) * SMALL_Q);
-            const float2 x3 = __ldcg(base + (size_t)(c + 24) * SMALL_Q);
-            ds_acc(acc, dsf{x0.x, x0.y});
-            ds_acc(acc, dsf{x1.x, x1.y});
-            ds_acc(acc, dsf{x2.x, x2.y});
-            ds_acc(acc, dsf{x3.x, x3.y});
-        }
-        for (; c < nchunk; c += 8) {
-            const float2 x = __ldcg(base + (size_t)c * SMALL_Q);
-            ds_acc(acc, dsf{x.x, x.y});
+        for (int cb = c0; cb < c1; cb += SMALL_BATCH) {
+            float2 x[SMALL_BATCH];
+#pragma unroll
+            for (int u = 0; u < SMALL_BATCH; ++u)
+                x[u] = cb + u < c1 ? __ldcg(base + (size_t)(cb + u) * SMALL_Q)
+                                   : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < SMALL_BATCH; ++u) ds_acc(acc, dsf{x[u].x, x[u].y});
         }
         s_fin[2 * tid] = acc.hi;
         s_fin[2 * tid + 1] = acc.lo;
@@ -336,7 +336,7 @@ __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, 
     if (tid < SMALL_Q) {
         dsf v{s_fin[2 * tid], s_fin[2 * tid + 1]};
 #pragma unroll
-        for (int sub = 1; sub < 8; ++sub) {
+        for (int sub = 1; sub < SMALL_SUBS; ++sub) {
             const int r = sub * SMALL_Q + tid;
             ds_acc(v, dsf{s_fin[2 * r], s_fin[2 * r + 1]});
         }
@@ -638,23 +638,30 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         // corrector recomputes the FP64 prediction of the due ones); the due
         // ones take slots of the due set (in no particular order: each
         // particle's forces do not depend on its slot) with their records
-        for (int w0 = 0; w0 < nwords; w0 += NW) {
-            const int i = p0 + w0 * 32 + tid;
-            float4 rec[DS_REC];
-            bool due = false;
-            if (i < p1) due = predict_one<true, false>(s, i, tn, rec);
-            const unsigned b = __ballot_sync(0xffffffffu, due);
-            if (b) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(dcnt + par, __popc(b));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (due) {
-                    const int slot = base + __popc(b & ((1u << lane) - 1u));
-                    a.act[slot] = i;
-                    float4 *g = a.irec + (size_t)DS_REC * slot;
-                    g[0] = rec[0];
-                    g[1] = rec[1];
-                    g[2] = rec[2];
+        for (int w0 = 0; w0 < nwords; w0 += 2 * NW) {
+            // two particles per thread, both states loaded before any arithmetic
+            const int i0 = p0 + w0 * 32 + tid, i1 = i0 + NT;
+            PState q0, q1;
+            if (i0 < p1) pstate_load(s, i0, q0);
+            if (i1 < p1) pstate_load(s, i1, q1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = h ? i1 : i0;
+                float4 rec[DS_REC];
+                const bool due = i < p1 && predict_rec_from(s, h ? q1 : q0, i, tn, rec);
+                const unsigned b = __ballot_sync(0xffffffffu, due);
+                if (b) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(dcnt + par, __popc(b));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (due) {
+                        const int slot = base + __popc(b & ((1u << lane) - 1u));
+                        a.act[slot] = i;
+                        float4 *g = a.irec + (size_t)DS_REC * slot;
+                        g[0] = rec[0];
+                        g[1] = rec[1];
+                        g[2] = rec[2];
+                    }
                 }
             }
         }

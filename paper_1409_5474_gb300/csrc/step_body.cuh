@@ -102,6 +102,49 @@ __device__ __forceinline__ bool predict_one(const StateDev &s, int i, double tn,
     return due;
 }
 
+// The state K1 reads for one particle, so that a thread can have the loads of
+// several particles in flight before any arithmetic.
+struct PState {
+    double t, dt, m, x[3], v[3], a[3], j[3];
+};
+
+__device__ __forceinline__ void pstate_load(const StateDev &s, int i, PState &q)
+{
+    q.t = s.t[i];
+    q.dt = s.dt[i];
+    q.m = s.m[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long k = c * s.ld + i;
+        q.x[c] = s.pos[k];
+        q.v[c] = s.vel[k];
+        q.a[c] = s.acc[k];
+        q.j[c] = s.jerk[k];
+    }
+}
+
+// K1 on a loaded state: the same arithmetic (and bits) as predict_one, the
+// double-single j-record written to s.rec and left in rec[]; whether the
+// particle is due at tn.
+__device__ __forceinline__ bool predict_rec_from(const StateDev &s, const PState &q, int i,
+                                                 double tn, float4 rec[3])
+{
+    const double d = tn - q.t;
+    const double d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
+    double xp[3], vp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xp[c] = fma(fma(fma(q.j[c], d6, 0.5 * q.a[c]), d, q.v[c]), d, q.x[c]);
+        vp[c] = fma(fma(q.j[c], d2h, q.a[c]), d, q.v[c]);
+    }
+    make_record(xp, vp, q.m, i, rec);
+    float4 *rr = s.rec + (size_t)DS_REC * i;
+    rr[0] = rec[0];
+    rr[1] = rec[1];
+    rr[2] = rec[2];
+    return q.t + q.dt == tn;
+}
+
 // The 6th-order prediction of particle i to time tn (FP64 Taylor series through
 // the crackle term, in Horner form): pos_p, vel_p, acc_p and, when REC, its
 // 64-byte record (the 48-byte record plus the FP32 predicted acceleration).
