@@ -289,7 +289,8 @@ typedef struct nb_plan {
     int nsplit; /* j-range splits (>= 1; clamped to the j-set) */
 } nb_plan;
 
-/* The plan used for an evaluation of n_i i-particles on the current j-set. */
+/* The plan used for an evaluation of n_i i-particles on the current j-set
+ * (for an entry nb_autotune wrote: with its split count scaled, see there). */
 int nb_plan_for(nb_handle h, int n_i, nb_plan *out);
 
 /* Set the plan table (n <= 32 entries, entry b for bucket b; kind -1 entries
@@ -301,7 +302,11 @@ int nb_get_plan_table(nb_handle h, nb_plan *table /* 32 entries */);
 /* Autotuner: for every bucket up to the current N, times candidate plans
  * (kind, nwj, nsplit around the heuristic) on the handle's own particles with
  * CUDA events, reps repetitions each, and stores the fastest in the plan
- * table. The particle state is left unchanged; the prediction is not (the
+ * table. Bucket b is timed at n_i = min(2^b, N); for the other sizes of the
+ * bucket a tuned tile or warp-group entry keeps the number of CTAs it was
+ * timed with (its split count scales with the count of i-blocks), so that it
+ * fills the same waves of the GPU. Entries set by nb_set_plan_table are used
+ * as given. The particle state is left unchanged; the prediction is not (the
  * j-set is predicted to the latest own time), so call nb_predict again before
  * a manual nb_force. */
 int nb_autotune(nb_handle h, int reps);

@@ -164,6 +164,7 @@ struct nb_handle_s {
     Timer timer;
     std::string msg;
     nb_plan plans[32];  // plan table by bucket ceil(log2 n_i); kind -1 = heuristic
+    bool plan_tuned[32] = {};  // entry b was timed by nb_autotune at n_i = min(2^b, n)
 };
 
 namespace {
@@ -345,10 +346,38 @@ int bucket_of(int n_i)
     return b;
 }
 
+// CTAs of one j-split of a plan on n_i i-particles (i-blocks or warp groups).
+static long long blocks_of(const ForcePlan &p, int variant, int n_i)
+{
+    if (p.kind == 1) {
+        if (variant == NB_F64) return 1;
+        const long long groups = (n_i + p.ipt - 1) / p.ipt;
+        const long long nw = p.threads / 32;
+        return (groups + nw - 1) / nw;
+    }
+    const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
+    return (n_i + ib - 1) / ib;
+}
+
 ForcePlan plan_for(nb_handle h, int variant, int n_i)
 {
-    const nb_plan &e = h->plans[bucket_of(n_i)];
-    if (e.kind >= 0 && variant == h->cfg.variant) return plan_from_entry(e, variant, n_i, h->n);
+    const int b = bucket_of(n_i);
+    const nb_plan &e = h->plans[b];
+    if (e.kind >= 0 && variant == h->cfg.variant) {
+        ForcePlan p = plan_from_entry(e, variant, n_i, h->n);
+        if (h->plan_tuned[b] && p.kind != 2) {
+            // the tuner timed the bucket at n_i = min(2^b, n): keep that plan's CTA
+            // count (its waves) for the other sizes of the bucket
+            const int n_ref = (int)std::min<long long>(1LL << b, h->n);
+            const long long ref = blocks_of(p, variant, n_ref), act = blocks_of(p, variant, n_i);
+            if (ref != act && act > 0) {
+                nb_plan scaled = e;
+                scaled.nsplit = (int)std::max(1LL, ((long long)e.nsplit * ref + act / 2) / act);
+                p = plan_from_entry(scaled, variant, n_i, h->n);
+            }
+        }
+        return p;
+    }
     return plan_force(variant, n_i, h->n, h->num_sms);
 }
 
@@ -1722,7 +1751,10 @@ int nb_set_plan_table(nb_handle h, const nb_plan *table, int n)
 {
     if (!h) return NB_ERR_ARG;
     if (!table) {
-        for (auto &e : h->plans) e = nb_plan{-1, 1, 1};
+        for (int b = 0; b < 32; ++b) {
+            h->plans[b] = nb_plan{-1, 1, 1};
+            h->plan_tuned[b] = false;
+        }
         return NB_OK;
     }
     if (n < 0 || n > 32) return fail(h, NB_ERR_ARG, "plan table has %d entries (max 32)", n);
@@ -1733,7 +1765,10 @@ int nb_set_plan_table(nb_handle h, const nb_plan *table, int n)
         if (e.kind == 0 && !(e.nwj == 1 || e.nwj == 4 || e.nwj == 8))
             return fail(h, NB_ERR_ARG, "plan entry %d: nwj must be 1, 4 or 8", b);
     }
-    for (int b = 0; b < 32; ++b) h->plans[b] = b < n ? table[b] : nb_plan{-1, 1, 1};
+    for (int b = 0; b < 32; ++b) {
+        h->plans[b] = b < n ? table[b] : nb_plan{-1, 1, 1};
+        h->plan_tuned[b] = false;
+    }
     return NB_OK;
 }
 
@@ -1850,7 +1885,10 @@ int nb_autotune(nb_handle h, int reps)
                 best_e = entry_of(p);
             }
         }
-        if (rc == NB_OK) h->plans[b] = best_e;
+        if (rc == NB_OK) {
+            h->plans[b] = best_e;
+            h->plan_tuned[b] = true;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(32 * NWI * NWJ, 2)
     constexpr int IB = 32 * NWI * IPT;
     constexpr int NPAIR = JT / 2;
     static_assert(NT >= 3 * NPAIR, "the transpose takes one thread per (pair, part)");
-    // tiles per FP32 partial sum: about 128 pairs per thread between folds
-    constexpr int FOLD = (128 * NWJ / JT) > 1 ? (128 * NWJ / JT) : 1;
+    // tiles per FP32 partial sum: about 128 terms in each half of a packed sum between folds
+    constexpr int FOLD = (256 * NWJ / JT) > 1 ? (256 * NWJ / JT) : 1;
     float4 *s_pair = s_tile + (size_t)NS * JT * DS_REC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wi = warp % NWI, wj = warp / NWI;
