@@ -234,7 +234,6 @@ __global__ void __launch_bounds__(32 * NWI * NWJ, 2)
     constexpr int NT = 32 * NWI * NWJ;
     constexpr int IB = 32 * NWI * IPT;
     constexpr int NPAIR = JT / 2;
-    static_assert(NT >= 3 * NPAIR, "the transpose takes one thread per (pair, part)");
     // tiles per FP32 partial sum: about 128 terms in each half of a packed sum between folds
     constexpr int FOLD = (256 * NWJ / JT) > 1 ? (256 * NWJ / JT) : 1;
     float4 *s_pair = s_tile + (size_t)NS * JT * DS_REC;
@@ -372,8 +371,8 @@ __global__ void __launch_bounds__(32 * NWI * NWJ, 2)
         if (cnt == JT) {
             // full tile: transpose it into j-pairs, {x_hi} {y_hi} {z_hi} {m} {x_lo}
             // {y_lo} {z_lo} {index} {vx} {vy} {vz} of j = 2q, 2q + 1 side by side
-            if (tid < 3 * NPAIR) {
-                const int q = tid % NPAIR, part = tid / NPAIR;
+            for (int x = tid; x < 3 * NPAIR; x += NT) {
+                const int q = x % NPAIR, part = x / NPAIR;
                 const float4 u = T[DS_REC * (2 * q) + part];
                 const float4 v = T[DS_REC * (2 * q + 1) + part];
                 float4 *P = s_pair + 6 * q + 2 * part;
@@ -1484,7 +1483,8 @@ __global__ void __launch_bounds__(NT)
 // Plans and launchers.
 // ---------------------------------------------------------------------------
 
-constexpr int JT32 = 128;
+constexpr int JT32 = 128;    // j-tile of the batched items
+constexpr int JT_TILE = 256;  // j-tile of the tile kernel
 constexpr int NS32 = 3;
 constexpr int JT64 = 64;
 constexpr int NS64 = 3;
@@ -1555,7 +1555,7 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
     p.kind = 0;
     p.ipt = 2;
     p.threads = 256;
-    p.jt = JT32;
+    p.jt = JT_TILE;
     p.nwj = n_i >= 65536 ? 1 : (n_i >= 8192 ? 4 : 8);
     const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
     const long long nblk = (n_i + ib - 1) / ib;
@@ -1591,7 +1591,7 @@ ForcePlan plan_from_entry(const nb_plan &e, int variant, int n_i, int n_j)
     } else {
         p.ipt = 2;
         p.threads = 256;
-        p.jt = JT32;
+        p.jt = JT_TILE;
         p.nwj = (e.nwj == 4 || e.nwj == 8) ? e.nwj : 1;
     }
     const int ntiles = (n_j + p.jt - 1) / p.jt;
@@ -1610,14 +1610,17 @@ static cudaError_t go_tile32(const JSet &js, const ISet &is, float eps2f, int ns
                              double *part, unsigned *cnt, Out3 out, unsigned *err,
                              cudaStream_t st)
 {
-    auto kern = k_force_tile32<VAR, IPT, NWI, NWJ, JT32, NS32>;
+    auto kern = k_force_tile32<VAR, IPT, NWI, NWJ, JT_TILE, NS32>;
     constexpr int NT = 32 * NWI * NWJ;
     constexpr int IB = 32 * NWI * IPT;
-    // the ring (18 KB) and the transposed tile (6 KB); the warp-row sums reuse them
-    const size_t ring = (size_t)(NS32 + 1) * JT32 * DS_REC * sizeof(float4);
+    // the ring (36 KB) and the transposed tile (12 KB); the warp-row sums reuse them
+    const size_t ring = (size_t)(NS32 + 1) * JT_TILE * DS_REC * sizeof(float4);
     const size_t red = NWJ > 1 ? (size_t)NWJ * 7 * IB * sizeof(double) : 0;  // <= 28 KB
     const size_t smem = ring > red ? ring : red;
-    const int ntiles = (js.n + JT32 - 1) / JT32;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = (js.n + JT_TILE - 1) / JT_TILE;
     dim3 grid((is.n + IB - 1) / IB, nsplit);
     kern<<<grid, NT, smem, st>>>(js.rec32, js.n, is, eps2f, ntiles, part, is.n, cnt, out, err);
     return cudaGetLastError();
@@ -1819,11 +1822,14 @@ static int tile_occ()
 {
     constexpr int NT = 32 * NWI * NWJ;
     constexpr int IB = 32 * NWI * 2;
-    const size_t ring = (size_t)(NS32 + 1) * JT32 * DS_REC * sizeof(float4);
+    const size_t ring = (size_t)(NS32 + 1) * JT_TILE * DS_REC * sizeof(float4);
     const size_t red = NWJ > 1 ? (size_t)NWJ * 7 * IB * sizeof(double) : 0;
+    const size_t smem = ring > red ? ring : red;
+    auto kern = k_force_tile32<VAR, 2, NWI, NWJ, JT_TILE, NS32>;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, k_force_tile32<VAR, 2, NWI, NWJ, JT32, NS32>, NT, ring > red ? ring : red) !=
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 1;
