@@ -538,9 +538,37 @@ __global__ void __launch_bounds__(32 * NWI * NWJ, 2)
             }
         }
     }
-    if (nsplit > 1)
-        finish_split_ds<NT>(nsplit, blockIdx.x * IB, IB, is.n, reinterpret_cast<float2 *>(part),
-                            pld, counters + blockIdx.x, out, err);
+    // with nsplit > 1 the partials are summed by k_tile_split_reduce, launched next
+    (void)counters;
+}
+
+// K3 of the tile kernel: one thread per output (component c of slot k) adds the
+// nsplit double-single partials in the order s = 0, 1, ... (the partials of
+// consecutive slots are adjacent, so the loads of a warp are coalesced), eight
+// loads in flight at a time.
+__global__ void __launch_bounds__(256)
+    k_tile_split_reduce(const float2 *__restrict__ part, long long pld, int nsplit, int n_i,
+                        Out3 out, unsigned *err)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 7LL * n_i) return;
+    const int c = (int)(q / n_i), k = (int)(q % n_i);
+    const float2 *p = part + (size_t)c * pld + k;
+    const size_t stride = (size_t)7 * pld;
+    dsf sum{0.f, 0.f};
+    int sp = 0;
+    for (; sp + 8 <= nsplit; sp += 8) {
+        float2 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = __ldcg(p + (size_t)(sp + u) * stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) ds_acc(sum, dsf{x[u].x, x[u].y});
+    }
+    for (; sp < nsplit; ++sp) {
+        const float2 x = __ldcg(p + (size_t)sp * stride);
+        ds_acc(sum, dsf{x.x, x.y});
+    }
+    store_component(out, c, k, ds_to_double(sum), err);
 }
 
 
@@ -1623,6 +1651,11 @@ static cudaError_t go_tile32(const JSet &js, const ISet &is, float eps2f, int ns
     const int ntiles = (js.n + JT_TILE - 1) / JT_TILE;
     dim3 grid((is.n + IB - 1) / IB, nsplit);
     kern<<<grid, NT, smem, st>>>(js.rec32, js.n, is, eps2f, ntiles, part, is.n, cnt, out, err);
+    if (nsplit > 1) {
+        const long long outs = 7LL * is.n;
+        k_tile_split_reduce<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(
+            reinterpret_cast<const float2 *>(part), is.n, nsplit, is.n, out, err);
+    }
     return cudaGetLastError();
 }
 
