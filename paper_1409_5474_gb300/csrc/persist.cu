@@ -101,31 +101,40 @@ __device__ __forceinline__ int warp_incl_scan(int v)
 // (slots k0 .. k0 + 31, one per lane; idle lanes copy the last due slot)
 // against the j-records [j0, j1), staged through shared memory in tiles of
 // FUSED_TILE records (double-buffered: the next tile's loads are in flight
-// during the arithmetic). The CTA's eight warps hold the same 32 slots and
-// split every tile (warp w takes records w, w + 8, ...), so no lane sums have
-// to meet in a shuffle tree; FP32 sums over about 128 pairs are folded into
-// double-single totals, and the warps' totals are added in fixed order through
-// shared memory: one partial per (slot, chunk).
+// during the arithmetic). A tile is stored as j-pairs, the values of records
+// 2q and 2q + 1 side by side, so that the pair terms of two j run in one
+// packed FP32x2 instruction (__fadd2_rn / __fmul2_rn / __ffma2_rn; each lane
+// holds its due particle in both halves). The CTA's eight warps hold the same
+// 32 slots and split every tile (warp w takes pairs w, w + 8, ...), so no lane
+// sums have to meet in a shuffle tree; FP32 sums (about 128 terms per half)
+// are folded into double-single totals, and the warps' totals are added in
+// fixed order through shared memory: one partial per (slot, chunk).
 constexpr int FUSED_TILE = 256;
 constexpr int FUSED_IB = 32;        // due slots per tile item
-constexpr int FUSED_TILE_FOLD = 4;  // tiles per FP32 partial sum (4 x 32 pairs per thread)
+constexpr int FUSED_TILE_FOLD = 8;  // tiles per FP32 partial sum (8 x 16 terms per half)
 
 template <bool DS>
 __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, int j0, int j1,
                                           int chunk, float4 (*s_tile)[DS_REC * FUSED_TILE])
 {
     constexpr int NT = FUSED_THREADS, NW = NT / 32, PF = (DS_REC * FUSED_TILE + NT - 1) / NT;
+    constexpr int NPAIR = FUSED_TILE / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float eps2f = a.eps2f;
     const float4 *ir = a.irec + (size_t)DS_REC * min(k0 + lane, na - 1);
     const float4 I0 = __ldcg(ir), I1 = __ldcg(ir + 1), I2 = __ldcg(ir + 2);
-    const float xh = I0.x, yh = I0.y, zh = I0.z, xl = I1.x, yl = I1.y, zl = I1.z;
-    const float vx = I2.x, vy = I2.y, vz = I2.z;
+    // the due particle, negated, in both halves
+    const float2 nxh = make_float2(-I0.x, -I0.x), nyh = make_float2(-I0.y, -I0.y);
+    const float2 nzh = make_float2(-I0.z, -I0.z), nxl = make_float2(-I1.x, -I1.x);
+    const float2 nyl = make_float2(-I1.y, -I1.y), nzl = make_float2(-I1.z, -I1.z);
+    const float2 nvx = make_float2(-I2.x, -I2.x), nvy = make_float2(-I2.y, -I2.y);
+    const float2 nvz = make_float2(-I2.z, -I2.z), e2 = make_float2(a.eps2f, a.eps2f);
     const int iid = __float_as_int(I1.w);
     float A_h[3], A_l[3], J_h[3], J_l[3], P_h = 0.f, P_l = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) A_h[c] = A_l[c] = J_h[c] = J_l[c] = 0.f;
-    float ta[3] = {0.f, 0.f, 0.f}, tja[3] = {0.f, 0.f, 0.f}, tjb[3] = {0.f, 0.f, 0.f}, tp = 0.f;
+    float2 ta[3], tja[3], tjb[3], tp = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ta[c] = tja[c] = tjb[c] = make_float2(0.f, 0.f);
     const float4 *jr = a.s.rec;
     const int ntile = (j1 - j0 + FUSED_TILE - 1) / FUSED_TILE;
     float4 pf[PF];
@@ -138,11 +147,21 @@ __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, in
             pf[u] = q < m ? __ldcg(jr + (size_t)DS_REC * tb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
+    // float4 part p of record r goes to the pair layout: {p.x of 2q, p.x of 2q+1,
+    // p.y of 2q, p.y of 2q+1} and {p.z ..., p.w ...} at float4 6q + 2p, 6q + 2p + 1
     auto stash = [&](int buf) {
+        float *P = reinterpret_cast<float *>(s_tile[buf]);
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
             const int q = tid + u * NT;
-            if (q < DS_REC * FUSED_TILE) s_tile[buf][q] = pf[u];
+            if (q < DS_REC * FUSED_TILE) {
+                const int r = q / DS_REC, part = q % DS_REC, h = r & 1;
+                float *d = P + 4 * (6 * (r >> 1) + 2 * part);
+                d[h] = pf[u].x;
+                d[2 + h] = pf[u].y;
+                d[4 + h] = pf[u].z;
+                d[6 + h] = pf[u].w;
+            }
         }
     };
     __syncthreads();  // the buffers are free (a previous item may still read them)
@@ -154,71 +173,83 @@ __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, in
         const int cnt = min(FUSED_TILE, j1 - tb);
         if (t + 1 < ntile) fetch(t + 1);
         const float4 *T = s_tile[t & 1];
-        // the pair of a slot with itself in this tile for any lane? (warp-uniform)
-        const bool own = __any_sync(0xffffffffu, iid >= tb && iid < tb + cnt);
-        auto body = [&](int jj, bool masked) {
-            const float4 A = T[DS_REC * jj];
-            const float4 C = T[DS_REC * jj + 2];
-            float4 B;
-            if (DS) B = T[DS_REC * jj + 1];
-            float dx, dy, dz;
+        // a tile with a lane's own particle or a ragged end masks per half (warp-uniform)
+        const bool masked =
+            __any_sync(0xffffffffu, iid >= tb && iid < tb + cnt) || cnt < FUSED_TILE;
+        auto body = [&](int q, bool msk) {
+            const float4 *P = T + 6 * q;
+            const float4 q0 = P[0], q1 = P[1], q4 = P[4], q5 = P[5];
+            float2 dx, dy, dz;
             if (DS) {
-                dx = (A.x - xh) + (B.x - xl);
-                dy = (A.y - yh) + (B.y - yl);
-                dz = (A.z - zh) + (B.z - zl);
+                const float4 q2 = P[2], q3 = P[3];
+                dx = __fadd2_rn(__fadd2_rn(make_float2(q0.x, q0.y), nxh),
+                                __fadd2_rn(make_float2(q2.x, q2.y), nxl));
+                dy = __fadd2_rn(__fadd2_rn(make_float2(q0.z, q0.w), nyh),
+                                __fadd2_rn(make_float2(q2.z, q2.w), nyl));
+                dz = __fadd2_rn(__fadd2_rn(make_float2(q1.x, q1.y), nzh),
+                                __fadd2_rn(make_float2(q3.x, q3.y), nzl));
             } else {
-                dx = A.x - xh;
-                dy = A.y - yh;
-                dz = A.z - zh;
+                dx = __fadd2_rn(make_float2(q0.x, q0.y), nxh);
+                dy = __fadd2_rn(make_float2(q0.z, q0.w), nyh);
+                dz = __fadd2_rn(make_float2(q1.x, q1.y), nzh);
             }
-            const float dvx = C.x - vx, dvy = C.y - vy, dvz = C.z - vz;
-            float r2 = fmaf(dx, dx, eps2f);
-            r2 = fmaf(dy, dy, r2);
-            r2 = fmaf(dz, dz, r2);
-            float rv = dx * dvx;
-            rv = fmaf(dy, dvy, rv);
-            rv = fmaf(dz, dvz, rv);
-            float rinv = rsqrtf(r2);
-            if (masked) rinv = (tb + jj == iid) ? 0.f : rinv;
-            const float rinv2 = rinv * rinv;
-            const float mrinv = A.w * rinv;
-            const float mr3 = mrinv * rinv2;
-            const float beta = (mr3 * rinv2) * rv;
-            tp += mrinv;
-            ta[0] = fmaf(mr3, dx, ta[0]);
-            ta[1] = fmaf(mr3, dy, ta[1]);
-            ta[2] = fmaf(mr3, dz, ta[2]);
-            tja[0] = fmaf(mr3, dvx, tja[0]);
-            tja[1] = fmaf(mr3, dvy, tja[1]);
-            tja[2] = fmaf(mr3, dvz, tja[2]);
-            tjb[0] = fmaf(beta, dx, tjb[0]);
-            tjb[1] = fmaf(beta, dy, tjb[1]);
-            tjb[2] = fmaf(beta, dz, tjb[2]);
+            const float2 dvx = __fadd2_rn(make_float2(q4.x, q4.y), nvx);
+            const float2 dvy = __fadd2_rn(make_float2(q4.z, q4.w), nvy);
+            const float2 dvz = __fadd2_rn(make_float2(q5.x, q5.y), nvz);
+            float2 r2 = __ffma2_rn(dx, dx, e2);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            float2 rv = __fmul2_rn(dx, dvx);
+            rv = __ffma2_rn(dy, dvy, rv);
+            rv = __ffma2_rn(dz, dvz, rv);
+            float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            if (msk) {
+                const int ja = tb + 2 * q;  // the self pair and records past the end: nothing
+                rinv.x = (ja == iid || 2 * q >= cnt) ? 0.f : rinv.x;
+                rinv.y = (ja + 1 == iid || 2 * q + 1 >= cnt) ? 0.f : rinv.y;
+            }
+            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+            const float2 mrinv = __fmul2_rn(make_float2(q1.z, q1.w), rinv);
+            const float2 mr3 = __fmul2_rn(mrinv, rinv2);
+            const float2 beta = __fmul2_rn(__fmul2_rn(mr3, rinv2), rv);
+            tp = __fadd2_rn(tp, mrinv);
+            ta[0] = __ffma2_rn(mr3, dx, ta[0]);
+            ta[1] = __ffma2_rn(mr3, dy, ta[1]);
+            ta[2] = __ffma2_rn(mr3, dz, ta[2]);
+            tja[0] = __ffma2_rn(mr3, dvx, tja[0]);
+            tja[1] = __ffma2_rn(mr3, dvy, tja[1]);
+            tja[2] = __ffma2_rn(mr3, dvz, tja[2]);
+            tjb[0] = __ffma2_rn(beta, dx, tjb[0]);
+            tjb[1] = __ffma2_rn(beta, dy, tjb[1]);
+            tjb[2] = __ffma2_rn(beta, dz, tjb[2]);
         };
-        if (own) {
-            for (int jj = warp; jj < cnt; jj += NW) body(jj, true);
+        const int npair = (cnt + 1) / 2;
+        if (masked) {
+            for (int q = warp; q < npair; q += NW) body(q, true);
         } else {
 #pragma unroll 4
-            for (int jj = warp; jj < cnt; jj += NW) body(jj, false);
+            for (int q = warp; q < NPAIR; q += NW) body(q, false);
         }
         if ((t + 1) % FUSED_TILE_FOLD == 0 || t + 1 == ntile) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float jt = fmaf(-3.f, tjb[c], tja[c]);
+                const float sa = ta[c].x + ta[c].y;
+                const float jt = fmaf(-3.f, tjb[c].x + tjb[c].y, tja[c].x + tja[c].y);
                 if (DS) {
-                    ds_add(A_h[c], A_l[c], ta[c]);
+                    ds_add(A_h[c], A_l[c], sa);
                     ds_add(J_h[c], J_l[c], jt);
                 } else {
-                    A_h[c] += ta[c];
+                    A_h[c] += sa;
                     J_h[c] += jt;
                 }
-                ta[c] = tja[c] = tjb[c] = 0.f;
+                ta[c] = tja[c] = tjb[c] = make_float2(0.f, 0.f);
             }
+            const float sp = tp.x + tp.y;
             if (DS)
-                ds_add(P_h, P_l, tp);
+                ds_add(P_h, P_l, sp);
             else
-                P_h += tp;
-            tp = 0.f;
+                P_h += sp;
+            tp = make_float2(0.f, 0.f);
         }
         if (t + 1 < ntile) stash((t + 1) & 1);
         __syncthreads();
