@@ -343,13 +343,23 @@ constexpr int SMALL_BATCH = 16;                       // loads in flight per thr
 __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, int nchunk,
                                              double tn, float *s_fin)
 {
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __threadfence();
+    // warps 0..3, lanes 0..2: the start-of-step state of slot 4 g + warp, component
+    // lane, requested before the partial sums
+    const int k = 4 * g + warp, c = lane;
+    const bool mine = warp < 4 && lane < 3 && k < na;
+    CState q{};
+    int i = 0;
+    if (mine) {
+        i = __ldcg(a.act + k);
+        cstate_load(a.s, i, c, q);
+    }
     if (tid < SMALL_SUBS * SMALL_Q) {
-        const int q = tid % SMALL_Q, sub = tid / SMALL_Q;
+        const int o = tid % SMALL_Q, sub = tid / SMALL_Q;
         const int len = (nchunk + SMALL_SUBS - 1) / SMALL_SUBS;
         const int c0 = sub * len, c1 = min(nchunk, c0 + len);
-        const float2 *base = a.part + (size_t)g * nchunk * SMALL_Q + q;
+        const float2 *base = a.part + (size_t)g * nchunk * SMALL_Q + o;
         dsf acc{0.f, 0.f};
         for (int cb = c0; cb < c1; cb += SMALL_BATCH) {
             float2 x[SMALL_BATCH];
@@ -364,6 +374,7 @@ __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, 
         s_fin[2 * tid + 1] = acc.lo;
     }
     __syncthreads();
+    double *s_res = reinterpret_cast<double *>(s_fin + 512);  // [28]: acc, jerk, P per slot
     if (tid < SMALL_Q) {
         dsf v{s_fin[2 * tid], s_fin[2 * tid + 1]};
 #pragma unroll
@@ -371,14 +382,18 @@ __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, 
             const int r = sub * SMALL_Q + tid;
             ds_acc(v, dsf{s_fin[2 * r], s_fin[2 * r + 1]});
         }
-        const int k = 4 * g + tid / 7;
-        if (k < na) store_out(a.f, k, tid % 7, ds_to_double(v), a.err);
+        const double x = ds_to_double(v);
+        s_res[tid] = x;
+        if (4 * g + tid / 7 < na && !isfinite(x)) atomicOr(a.err, DERR_NONFINITE);
     }
     if (tid == 0) a.cnt[gridDim.x + 2 + g] = 0;  // re-arm the group's ticket
     __syncthreads();
-    if (warp < 4)
-        correct_lanes(a.s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, 4 * g + warp, 0,
-                      true, true);
+    if (warp < 4) {
+        const double a1 = mine ? s_res[7 * warp + c] : 0.0;
+        const double j1 = mine ? s_res[7 * warp + 3 + c] : 0.0;
+        correct_lanes_pre(a.s, i, k, c, 0, mine, tn, q, a1, j1, a.prm, a.sd, a.err,
+                          a.dtmin_hits);
+    }
 }
 
 template <bool DS>
@@ -728,6 +743,15 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             mark(1);
             // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
             for (int k = gw; k < na; k += total_warps) {
+                // lanes 0..2: the particle's start-of-step state (component = lane),
+                // requested with the chunk partials
+                const bool mine = lane < 3;
+                CState cs{};
+                int i = 0;
+                if (mine) {
+                    i = __ldcg(a.act + k);
+                    cstate_load(s, i, lane, cs);
+                }
                 // lane l holds chunks l, l + 32, l + 64, l + 96, all loaded at once
                 constexpr int CPL = FUSED_MAX_CHUNKS / 32;
                 float2 x[CPL][7];
@@ -750,13 +774,22 @@ __global__ void __launch_bounds__(FUSED_THREADS)
                 for (int q = 0; q < 7; ++q)
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) ds_acc(v[q], ds_shfl_xor(v[q], o));
-                if (lane == 0) {
+                // every lane holds the totals now; lane c takes component c
+                double a1 = 0.0, j1 = 0.0;
 #pragma unroll
-                    for (int q = 0; q < 7; ++q) store_out(a.f, k, q, ds_to_double(v[q]), a.err);
+                for (int c = 0; c < 3; ++c)
+                    if (lane == c) {
+                        a1 = ds_to_double(v[c]);
+                        j1 = ds_to_double(v[3 + c]);
+                    }
+                if (lane == 0) {
+                    bool fin = true;
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) fin = fin && isfinite(ds_to_double(v[q]));
+                    if (!fin) atomicOr(a.err, DERR_NONFINITE);
                 }
-                __syncwarp();
-                correct_lanes(s, a.act, na, tn, a.f, a.prm, a.sd, a.err, a.dtmin_hits, k, 0, true,
-                              true);
+                correct_lanes_pre(s, i, k, lane, 0, mine, tn, cs, a1, j1, a.prm, a.sd, a.err,
+                                  a.dtmin_hits);
             }
             mark(2);
         }

@@ -292,6 +292,38 @@ static __device__ double quantize_log2(int e, double dt_old, double t_new, doubl
 
 // ---- K4 --------------------------------------------------------------------
 
+// The Hermite corrector of one component from the start-of-step x, v, a0, j0,
+// the predicted xp, vp and the new a1, j1: x1, v1 and the end-of-step a2
+// (a2 + dt a3) and a3 for the step criterion.
+__device__ __forceinline__ void hermite_correct(double xp, double vp, double a0, double j0,
+                                                double a1, double j1, double dt, double dt2,
+                                                double idt2, double idt3, double &x1,
+                                                double &v1, double &a2eo, double &a3eo)
+{
+    // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
+    // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
+    // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
+    // v1 = vp + dt (A2/6 + A3/24) - the same corrector in fewer FP64 steps
+    const double da = a0 - a1;
+    const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
+    const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
+    x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), xp);
+    v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), vp);
+    const double a2 = A2 * idt2, a3 = A3 * idt3;
+    a2eo = a2 + dt * a3;
+    a3eo = a3;
+}
+
+// The FP64 prediction over dt from the start-of-step state (the K1 formula,
+// the same bits as the predictor).
+__device__ __forceinline__ void predict_xv(double x, double v, double a0, double j0, double dt,
+                                           double &xp, double &vp)
+{
+    const double d = dt, d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
+    xp = fma(fma(fma(j0, d6, 0.5 * a0), d, v), d, x);
+    vp = fma(fma(j0, d2h, a0), d, v);
+}
+
 // K4, component c of active slot k (particle i): the Hermite corrector of x, v
 // with the new acc/jerk f (slot-indexed). The predicted x_p, v_p are read from
 // pos_p / vel_p, or, with xp_from_state (the iterated corrector, which has
@@ -308,29 +340,15 @@ __device__ __forceinline__ void correct_values(const StateDev &s, const Out3 &f,
     const double a0 = s.acc[q], j0 = s.jerk[q];
     const double a1 = f.acc[c * f.ld + k], j1 = f.jerk[c * f.ld + k];
     double xp, vp;
-    if (xp_from_state) {
-        const double x = s.pos[q], v = s.vel[q];
-        const double d = dt, d6 = d * (1.0 / 6.0), d2h = 0.5 * d;
-        xp = fma(fma(fma(j0, d6, 0.5 * a0), d, v), d, x);
-        vp = fma(fma(j0, d2h, a0), d, v);
-    } else {
+    if (xp_from_state)
+        predict_xv(s.pos[q], s.vel[q], a0, j0, dt, xp, vp);
+    else {
         xp = s.pos_p[q];
         vp = s.vel_p[q];
     }
-    // with A2 = a2 dt^2 and A3 = a3 dt^3 (the Hermite interpolant's 2nd and
-    // 3rd derivatives, scaled): A2 = -6 (a0 - a1) - dt (4 j0 + 2 j1),
-    // A3 = 12 (a0 - a1) + 6 dt (j0 + j1); x1 = xp + dt^2 (A2/24 + A3/120),
-    // v1 = vp + dt (A2/6 + A3/24) - the same corrector in fewer FP64 steps
-    const double da = a0 - a1;
-    const double A3 = fma(6.0 * dt, j0 + j1, 12.0 * da);
-    const double A2 = fma(-dt, fma(4.0, j0, 2.0 * j1), -6.0 * da);
-    x1 = fma(dt2, fma(A3, 1.0 / 120.0, A2 * (1.0 / 24.0)), xp);
-    v1 = fma(dt, fma(A3, 1.0 / 24.0, A2 * (1.0 / 6.0)), vp);
-    const double a2 = A2 * idt2, a3 = A3 * idt3;
+    hermite_correct(xp, vp, a0, j0, a1, j1, dt, dt2, idt2, idt3, x1, v1, a2eo, a3eo);
     a1o = a1;
     j1o = j1;
-    a2eo = a2 + dt * a3;
-    a3eo = a3;
 }
 
 // K4, component c of active slot k: correct_values, then the new pos, vel,
@@ -491,6 +509,68 @@ __device__ __forceinline__ void correct_lanes(const StateDev &s, const int *act,
         if (bad & (7u << lane0)) atomicOr(err, DERR_NONFINITE);
         correct_step(s, i, t_new, dt, dt_old, a1v, j1v, a2v, a3v, prm, sd, dtmin_hits);
     }
+}
+
+// The start-of-step state of component c of a particle, loaded ahead of its
+// corrector (so that the loads overlap other work).
+struct CState {
+    double x, v, a0, j0, t, dt;
+};
+
+__device__ __forceinline__ void cstate_load(const StateDev &s, int i, int c, CState &q)
+{
+    const long long k = c * s.ld + i;
+    q.x = s.pos[k];
+    q.v = s.vel[k];
+    q.a0 = s.acc[k];
+    q.j0 = s.jerk[k];
+    q.t = s.t[i];
+    q.dt = s.dt[i];
+}
+
+// K4 for active slot k (particle i) by three lanes of a warp (component
+// c = lane - lane0 on the lanes where mine holds; every lane of the warp calls
+// this) from a preloaded state q and the new acc / jerk component a1, j1: the
+// same arithmetic as correct_lanes with the prediction recomputed from the
+// state.
+__device__ __forceinline__ void correct_lanes_pre(const StateDev &s, int i, int k, int c,
+                                                  int lane0, bool mine, double t_new,
+                                                  const CState &q, double a1, double j1,
+                                                  const StepParams &prm, SchedDev *sd,
+                                                  unsigned *err, unsigned long long *dtmin_hits)
+{
+    const int lane = threadIdx.x & 31;
+    double a2e = 0.0, a3e = 0.0, dt = 1.0;
+    bool fin = true;
+    if (mine) {
+        if (k == 0 && c == 0) sd->t_cur = t_new;
+        dt = t_new - q.t;
+        double dt2, idt2, idt3, xp, vp, x1, v1;
+        step_factors(dt, prm, dt2, idt2, idt3);
+        predict_xv(q.x, q.v, q.a0, q.j0, dt, xp, vp);
+        hermite_correct(xp, vp, q.a0, q.j0, a1, j1, dt, dt2, idt2, idt3, x1, v1, a2e, a3e);
+        const long long qq = c * s.ld + i;
+        s.pos[qq] = x1;
+        s.vel[qq] = v1;
+        s.acc[qq] = a1;
+        s.jerk[qq] = j1;
+        fin = isfinite(x1) && isfinite(v1);
+    }
+    double a1v[3], j1v[3], a2v[3], a3v[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int src = min(31, lane0 + u);
+        a1v[u] = __shfl_sync(0xffffffffu, a1, src);
+        j1v[u] = __shfl_sync(0xffffffffu, j1, src);
+        a2v[u] = __shfl_sync(0xffffffffu, a2e, src);
+        a3v[u] = __shfl_sync(0xffffffffu, a3e, src);
+    }
+    const unsigned bad = __ballot_sync(0xffffffffu, mine && !fin);
+    if (mine && c == 0) {
+        if (bad & (7u << lane0)) atomicOr(err, DERR_NONFINITE);
+        correct_step(s, i, t_new, dt, q.dt, a1v, j1v, a2v, a3v, prm, sd, dtmin_hits);
+    }
+    (void)lane;
 }
 
 // ---- bounded waits and ordered status words ---------------------------------
