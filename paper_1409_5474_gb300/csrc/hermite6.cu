@@ -24,9 +24,11 @@
 //                        IPT i-particles per thread in 8/NWJ warp columns, NWJ
 //                        warp rows share each j-tile; j-tiles of 128 records
 //                        stream through a 3-stage ring of bulk copies (TMA
-//                        engine, mbarrier completion, bounded waits); FP32 sums
-//                        per tile are folded into double-single totals;
-//                        grid.y splits the j-range
+//                        engine, mbarrier completion, bounded waits); a full
+//                        tile is transposed into j-pairs and its pair terms run
+//                        on packed FP32x2 arithmetic, two j per instruction;
+//                        FP32 sums per tile are folded into double-single
+//                        totals; grid.y splits the j-range
 //   k_force6_tile64      K2, FP64 pairs (the correctness variant)
 //   k_force6_reduce<DS>  K3: the splits of each output added in fixed order
 //   k_correct6           K4: corrector, end-of-step crackle, step criterion,
@@ -101,15 +103,21 @@ __device__ __forceinline__ void store6(const Out6 &out, int k, double v[H6_VALS]
 // (the same i-particles, sharing out each j-tile: row g takes j = g, g + NWJ,
 // ...), so that a small due set still spreads over the SM; rows are added in
 // shared memory at the end, in fixed order. Two CTAs per SM (16 warps) hide the
-// pair arithmetic's latencies better than one; the two-particle variant then
-// spills a few bytes outside the j-loop, and still runs 2-12% faster.
+// pair arithmetic's latencies better than one. A full j-tile is rewritten once in
+// shared memory as j-pairs (each float4 part of records 2q and 2q + 1 interleaved
+// component by component), so that the pair terms of two j run on the packed
+// FP32x2 instructions (half the issue slots of scalar FP32 at the same lane rate),
+// with the i-particle's values duplicated in both lanes; a tile that holds the
+// i-particle itself, or the ragged last tile, takes the scalar body. One
+// i-particle per thread: a second one with the packed sums spills registers.
 template <bool DS, int IPT, int NWJ>
 __global__ void __launch_bounds__(32 * H6_NWARP, 2)
     k_force6_tile32(const float4 *__restrict__ jrec, int nj, const int *__restrict__ idx,
                     int n_i, float eps2f, int ntiles, float2 *__restrict__ part, long long pld,
                     Out6 out, unsigned *err)
 {
-    extern __shared__ __align__(128) float4 s_tile6[];  // H6_NS * H6_JT * DS6_REC
+    // H6_NS ring stages of H6_JT records, then the current tile as j-pairs
+    extern __shared__ __align__(128) float4 s_tile6[];
     __shared__ __align__(8) uint64_t s_full[H6_NS];
     __shared__ int s_abort;
 
@@ -138,14 +146,21 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 2)
         vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
         ax[p] = d.x; ay[p] = d.y; az[p] = d.z;
     }
+    constexpr int NPAIR = H6_JT / 2;
+    float4 *s_pair = s_tile6 + (size_t)H6_NS * H6_JT * DS6_REC;
+    const float2 e2 = make_float2(eps2f, eps2f);
 
     // double-single totals (hi, lo) and the FP32 sums of the current tile (folded
     // after every tile: 128 pairs per sum)
     float H[IPT][H6_VALS], L[IPT][H6_VALS], t[IPT][H6_VALS];
+    float2 t2[IPT][H6_VALS];  // the packed path's sums: even and odd j of the pairs
 #pragma unroll
     for (int p = 0; p < IPT; ++p)
 #pragma unroll
-        for (int c = 0; c < H6_VALS; ++c) H[p][c] = L[p][c] = t[p][c] = 0.f;
+        for (int c = 0; c < H6_VALS; ++c) {
+            H[p][c] = L[p][c] = t[p][c] = 0.f;
+            t2[p][c] = make_float2(0.f, 0.f);
+        }
 
     if (tid == 0) {
         s_abort = 0;
@@ -235,11 +250,93 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 2)
                 t[p][9] += mrinv;
             }
         };
-        if (own) {
+        if (cnt == H6_JT) {
+            // full tile: transposed into j-pairs (each float4 part of records 2q and
+            // 2q + 1 side by side) for the packed FP32x2 pair terms, two j at a time
+            for (int x = tid; x < DS6_REC * NPAIR; x += 32 * H6_NWARP) {
+                const int q = x % NPAIR, part6 = x / NPAIR;
+                const float4 u = T[DS6_REC * (2 * q) + part6];
+                const float4 v = T[DS6_REC * (2 * q + 1) + part6];
+                float4 *Pp = s_pair + 2 * DS6_REC * q + 2 * part6;
+                Pp[0] = make_float4(u.x, v.x, u.y, v.y);
+                Pp[1] = make_float4(u.z, v.z, u.w, v.w);
+            }
+            __syncthreads();
+            if (own) {
+                for (int jj = wj; jj < H6_JT; jj += NWJ) body(jj, std::true_type{});
+            } else {
+#pragma unroll 2
+                for (int q = wj; q < NPAIR; q += NWJ) {
+                    const float4 *Pp = s_pair + 2 * DS6_REC * q;
+                    const float4 q0 = Pp[0], q1 = Pp[1], q4 = Pp[4], q5 = Pp[5], q6 = Pp[6],
+                                 q7 = Pp[7];
+                    float4 q2, q3;
+                    if (DS) {
+                        q2 = Pp[2];
+                        q3 = Pp[3];
+                    }
+#pragma unroll
+                    for (int p = 0; p < IPT; ++p) {
+                        float2 dx, dy, dz;
+                        if (DS) {
+                            dx = __fadd2_rn(__fadd2_rn(make_float2(q0.x, q0.y), make_float2(-xh[p], -xh[p])),
+                                            __fadd2_rn(make_float2(q2.x, q2.y), make_float2(-xl[p], -xl[p])));
+                            dy = __fadd2_rn(__fadd2_rn(make_float2(q0.z, q0.w), make_float2(-yh[p], -yh[p])),
+                                            __fadd2_rn(make_float2(q2.z, q2.w), make_float2(-yl[p], -yl[p])));
+                            dz = __fadd2_rn(__fadd2_rn(make_float2(q1.x, q1.y), make_float2(-zh[p], -zh[p])),
+                                            __fadd2_rn(make_float2(q3.x, q3.y), make_float2(-zl[p], -zl[p])));
+                        } else {
+                            dx = __fadd2_rn(make_float2(q0.x, q0.y), make_float2(-xh[p], -xh[p]));
+                            dy = __fadd2_rn(make_float2(q0.z, q0.w), make_float2(-yh[p], -yh[p]));
+                            dz = __fadd2_rn(make_float2(q1.x, q1.y), make_float2(-zh[p], -zh[p]));
+                        }
+                        const float2 dvx = __fadd2_rn(make_float2(q4.x, q4.y), make_float2(-vx[p], -vx[p]));
+                        const float2 dvy = __fadd2_rn(make_float2(q4.z, q4.w), make_float2(-vy[p], -vy[p]));
+                        const float2 dvz = __fadd2_rn(make_float2(q5.x, q5.y), make_float2(-vz[p], -vz[p]));
+                        const float2 dax = __fadd2_rn(make_float2(q6.x, q6.y), make_float2(-ax[p], -ax[p]));
+                        const float2 day = __fadd2_rn(make_float2(q6.z, q6.w), make_float2(-ay[p], -ay[p]));
+                        const float2 daz = __fadd2_rn(make_float2(q7.x, q7.y), make_float2(-az[p], -az[p]));
+                        float2 r2 = __ffma2_rn(dx, dx, e2);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        float2 rv = __fmul2_rn(dx, dvx);
+                        rv = __ffma2_rn(dy, dvy, rv);
+                        rv = __ffma2_rn(dz, dvz, rv);
+                        float2 w2 = __fmul2_rn(dvx, dvx);  // |v|^2 + r.a
+                        w2 = __ffma2_rn(dvy, dvy, w2);
+                        w2 = __ffma2_rn(dvz, dvz, w2);
+                        w2 = __ffma2_rn(dx, dax, w2);
+                        w2 = __ffma2_rn(dy, day, w2);
+                        w2 = __ffma2_rn(dz, daz, w2);
+                        const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                        const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                        const float2 mrinv = __fmul2_rn(make_float2(q1.z, q1.w), rinv);
+                        const float2 mr3 = __fmul2_rn(mrinv, rinv2);
+                        const float2 alpha = __fmul2_rn(rv, rinv2);
+                        const float2 beta = __ffma2_rn(alpha, alpha, __fmul2_rn(w2, rinv2));
+                        const float2 m3a = __fmul2_rn(make_float2(-3.f, -3.f), alpha);
+                        const float2 m6a = __fmul2_rn(make_float2(-6.f, -6.f), alpha);
+                        const float2 m3b = __fmul2_rn(make_float2(-3.f, -3.f), beta);
+                        const float2 Ax = __fmul2_rn(mr3, dx), Ay = __fmul2_rn(mr3, dy),
+                                     Az = __fmul2_rn(mr3, dz);
+                        const float2 Jx = __ffma2_rn(m3a, Ax, __fmul2_rn(mr3, dvx));
+                        const float2 Jy = __ffma2_rn(m3a, Ay, __fmul2_rn(mr3, dvy));
+                        const float2 Jz = __ffma2_rn(m3a, Az, __fmul2_rn(mr3, dvz));
+                        t2[p][0] = __fadd2_rn(t2[p][0], Ax);
+                        t2[p][1] = __fadd2_rn(t2[p][1], Ay);
+                        t2[p][2] = __fadd2_rn(t2[p][2], Az);
+                        t2[p][3] = __fadd2_rn(t2[p][3], Jx);
+                        t2[p][4] = __fadd2_rn(t2[p][4], Jy);
+                        t2[p][5] = __fadd2_rn(t2[p][5], Jz);
+                        t2[p][6] = __fadd2_rn(t2[p][6], __ffma2_rn(m3b, Ax, __ffma2_rn(m6a, Jx, __fmul2_rn(mr3, dax))));
+                        t2[p][7] = __fadd2_rn(t2[p][7], __ffma2_rn(m3b, Ay, __ffma2_rn(m6a, Jy, __fmul2_rn(mr3, day))));
+                        t2[p][8] = __fadd2_rn(t2[p][8], __ffma2_rn(m3b, Az, __ffma2_rn(m6a, Jz, __fmul2_rn(mr3, daz))));
+                        t2[p][9] = __fadd2_rn(t2[p][9], mrinv);
+                    }
+                }
+            }
+        } else if (own) {
             for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::true_type{});
-        } else if (cnt == H6_JT) {
-#pragma unroll 4
-            for (int jj = wj; jj < H6_JT; jj += NWJ) body(jj, std::false_type{});
         } else {
 #pragma unroll 2
             for (int jj = wj; jj < cnt; jj += NWJ) body(jj, std::false_type{});
@@ -248,11 +345,13 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 2)
         for (int p = 0; p < IPT; ++p)
 #pragma unroll
             for (int c = 0; c < H6_VALS; ++c) {
+                const float sum = t[p][c] + (t2[p][c].x + t2[p][c].y);
                 if (DS)
-                    ds_add(H[p][c], L[p][c], t[p][c]);
+                    ds_add(H[p][c], L[p][c], sum);
                 else
-                    H[p][c] += t[p][c];
+                    H[p][c] += sum;
                 t[p][c] = 0.f;
+                t2[p][c] = make_float2(0.f, 0.f);
             }
 
         __syncthreads();  // every warp is done with this stage
@@ -537,7 +636,7 @@ int occ6()
     static int v = -1;
     if (v < 0) {
         int b = 0;
-        const size_t smem = (size_t)H6_NS * H6_JT * DS6_REC * sizeof(float4);
+        const size_t smem = (size_t)(H6_NS + 1) * H6_JT * DS6_REC * sizeof(float4);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_force6_tile32<DS, IPT, NWJ>,
                                                           32 * H6_NWARP, smem) != cudaSuccess) {
             cudaGetLastError();
@@ -550,7 +649,6 @@ int occ6()
 
 int occ6_of(bool ds, int ipt, int nwj)
 {
-    if (ipt == 2) return ds ? occ6<true, 2, 1>() : occ6<false, 2, 1>();
     switch (nwj) {
     case 8: return ds ? occ6<true, 1, 8>() : occ6<false, 1, 8>();
     case 4: return ds ? occ6<true, 1, 4>() : occ6<false, 1, 4>();
@@ -576,9 +674,8 @@ cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned
 }
 
 
-// The CTA shape from the size of the due set: two i-particles per thread once
-// there are enough i-blocks to go round, warp rows sharing each j-tile below 256
-// (8 rows for 32 or fewer). Then the j-splits: at least two waves of resident
+// The CTA shape from the size of the due set: one i-particle per thread, warp
+// rows sharing each j-tile below 256 (8 rows for 32 or fewer). Then the j-splits: at least two waves of resident
 // CTAs (one for the warp-row shapes, whose CTAs are short: 8-14% faster there),
 // and among up to twice that many splits the count whose last wave is the
 // fullest (a 2.1-wave grid idles most SMs for its last tenth); at most one split
@@ -588,7 +685,7 @@ ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
     ForcePlan p{};
     p.kind = 0;
     const bool f64 = (variant == NB_F64);
-    p.ipt = (!f64 && n_i >= 8 * 32 * H6_NWARP) ? 2 : 1;
+    p.ipt = 1;  // the packed pair terms already give each thread two j per step
     p.nwj = f64 ? 1 : (n_i <= 32 ? 8 : n_i <= 64 ? 4 : n_i <= 128 ? 2 : 1);
     p.threads = f64 ? H6_T64 : 32 * (H6_NWARP / p.nwj) * p.ipt;  // i-particles per CTA
     p.jt = f64 ? H6_JT64 : H6_JT;
@@ -634,16 +731,14 @@ cudaError_t launch_force6(int variant, const ForcePlan &p, const StateDev &s, co
         const int nt = 32 * H6_NWARP;
         const int ib = 32 * (H6_NWARP / p.nwj) * p.ipt;
         dim3 grid((n_i + ib - 1) / ib, p.nsplit);
-        const size_t smem = (size_t)H6_NS * H6_JT * DS6_REC * sizeof(float4);
+        const size_t smem = (size_t)(H6_NS + 1) * H6_JT * DS6_REC * sizeof(float4);
         float2 *pp = reinterpret_cast<float2 *>(part);
         const float e2 = (float)eps2;
         auto go = [&](auto kern) {
             kern<<<grid, nt, smem, st>>>(s.rec6, s.n, idx, n_i, e2, ntiles, pp, pld, out, err);
         };
         const bool ds = (variant == NB_F32DS);
-        if (p.ipt == 2)
-            ds ? go(k_force6_tile32<true, 2, 1>) : go(k_force6_tile32<false, 2, 1>);
-        else if (p.nwj == 8)
+        if (p.nwj == 8)
             ds ? go(k_force6_tile32<true, 1, 8>) : go(k_force6_tile32<false, 1, 8>);
         else if (p.nwj == 4)
             ds ? go(k_force6_tile32<true, 1, 4>) : go(k_force6_tile32<false, 1, 4>);
