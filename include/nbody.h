@@ -73,6 +73,7 @@ extern "C" {
 #define NB_FLAG_NO_FUSED 2
 #define NB_FUSED_MAX_NA 4096      /* upper bound of nb_config.fused_max_na */
 #define NB_FUSED_DEFAULT_NA 1024  /* fused_max_na = 0 */
+#define NB_FUSED6_MAX_NA 32       /* largest due set of the order-6 fused kernel */
 
 typedef struct nb_config {
     int n_max;           /* particle capacity of the handle, >= 1 */
@@ -98,8 +99,9 @@ typedef struct nb_config {
                           * and predicts through the crackle (Sect. II: >= 4th-order
                           * integrators with individual steps; the cited 6th-order Hermite
                           * scheme of Nitadori & Makino). Order 6 needs NB_F32DS or NB_F64
-                          * pairs and n_corr <= 1, and has
-                          * no fused steps, plan table, external i-sets or bridge calls. Its
+                          * pairs and n_corr <= 1, and has no plan table, external i-sets
+                          * or bridge calls; its fused kernel (NB_F32DS) takes due sets of
+                          * up to min(fused_max_na, NB_FUSED6_MAX_NA) particles. Its
                           * steps follow Aarseth's criterion with the evaluated snap as a2
                           * and the end-of-step crackle as a3 (eta ~ 0.01-0.04). */
 } nb_config;

@@ -623,9 +623,13 @@ int do_init6(nb_handle h, double t0)
     return NB_OK;
 }
 
+bool fused_ready(nb_handle h);
+FusedArgs fused_args(nb_handle h, double t_end, const Out3 &f);
+
 // Block (or shared) steps of the 6th-order scheme to t_end: the order-6
-// scheduler + predictor publishes (t_next, N_active), then the force on the
-// due set and the corrector are queued; shared steps need no scheduler.
+// scheduler + predictor (or the order-6 fused kernel, which takes the steps
+// with small due sets itself) publishes (t_next, N_active), then the force on
+// the due set and the corrector are queued; shared steps need no scheduler.
 int step6_loop(nb_handle h, double t_end, const std::function<void(int)> &count_step)
 {
     StateDev s = state_of(h);
@@ -652,12 +656,22 @@ int step6_loop(nb_handle h, double t_end, const std::function<void(int)> &count_
         }
         return NB_OK;
     }
+    const bool fused = fused_ready(h);
+    const FusedArgs fa = fused ? fused_args(h, t_end, Out3{}) : FusedArgs{};
     auto launch_sched = [&]() -> int {
         h->seq_next++;
-        int r = timed(h, T_SCHED, [&] {
-            return launch_sched_predict6(s, h->sd, h->sched_status, h->act, h->mail_d,
-                                         prm.dt_max, rec, h->d_err, h->stream);
-        });
+        int r;
+        if (fused) {
+            r = timed(h, T_FUSED, [&] {
+                return launch_fused_steps(fa, h->fused_grid, true, 6, h->stream);
+            });
+            h->stats.fused_launches++;
+        } else {
+            r = timed(h, T_SCHED, [&] {
+                return launch_sched_predict6(s, h->sd, h->sched_status, h->act, h->mail_d,
+                                             prm.dt_max, rec, h->d_err, h->stream);
+            });
+        }
         if (r) return r;
         CK(h, cudaEventRecord(h->ev_sched, h->stream));
         return NB_OK;
@@ -683,6 +697,11 @@ int step6_loop(nb_handle h, double t_end, const std::function<void(int)> &count_
         count_step(na);
         rc = launch_sched();
         if (rc) return rc;
+    }
+    if (fused) {
+        // the fused kernel took steps of its own: the last block time is on the device
+        CK(h, cudaMemcpyAsync(&h->t_cur, &h->sd->t_cur, sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
     }
     return NB_OK;
 }
@@ -775,14 +794,14 @@ int iterate_corrector(nb_handle h, const StateDev &s, const int *act, int n_a, d
 bool fused_ready(nb_handle h)
 {
     if (h->cfg.variant == NB_F64 || (h->cfg.flags & NB_FLAG_NO_FUSED) ||
-        h->cfg.shared_dt > 0.0 || h->cfg.n_corr > 1 || order6(h))
+        h->cfg.shared_dt > 0.0 || h->cfg.n_corr > 1)
         return false;
-    if (h->fused_grid < 0) h->fused_grid = fused_grid(h->dev);
+    if (h->fused_grid < 0) h->fused_grid = fused_grid(h->dev, h->cfg.order);
     const int g = h->fused_grid;
     if (g <= 0) return false;
     if ((h->n + g - 1) / g > FUSED_MAX_WORDS * 32) return false;
     if (!h->fused_cnt) {
-        const size_t part = fused_part_float2s(g, NB_FUSED_MAX_NA);
+        const size_t part = fused_part_float2s(g, NB_FUSED_MAX_NA, h->cfg.order);
         const size_t add =
             part * sizeof(float2) + fused_cnt_ints(g) * sizeof(int) + 256 + sizeof(FusedStats);
         if (h->cfg.budget_bytes && h->bytes + add > h->cfg.budget_bytes) return false;
@@ -807,6 +826,32 @@ bool fused_ready(nb_handle h)
         h->bytes += add;
     }
     return true;
+}
+
+// The arguments of the fused launches of nb_step to t_end (f: the order-4
+// kernel's force outputs).
+FusedArgs fused_args(nb_handle h, double t_end, const Out3 &f)
+{
+    FusedArgs fa{};
+    fa.s = state_of(h);
+    fa.sd = h->sd;
+    fa.act = h->act;
+    fa.irec = h->irec;
+    fa.mail = h->mail_d;
+    fa.f = f;
+    fa.prm = params_of(h);
+    fa.eps2f = (float)(h->cfg.eps * h->cfg.eps);
+    fa.na_max = h->cfg.fused_max_na > 0 ? std::min(h->cfg.fused_max_na, NB_FUSED_MAX_NA)
+                                        : NB_FUSED_DEFAULT_NA;
+    if (order6(h)) fa.na_max = std::min(fa.na_max, FUSED6_MAX_NA);
+    fa.t_end = t_end;
+    fa.part = h->fused_part;
+    fa.cnt = h->fused_cnt;
+    fa.bar = h->fused_bar;
+    fa.err = h->d_err;
+    fa.dtmin_hits = h->d_dtmin;
+    fa.stats = h->fused_stats;
+    return fa;
 }
 
 // Add the steps the fused kernel took to the handle's counters (and clear them).
@@ -1575,33 +1620,13 @@ int nb_step(nb_handle h, double t_end, nb_stats *st)
         // to the mailbox; the force, corrector and the next scheduler launch are
         // queued as soon as it is read
         const bool fused = fused_ready(h);
-        FusedArgs fa{};
-        if (fused) {
-            fa.s = s;
-            fa.sd = h->sd;
-            fa.act = h->act;
-            fa.irec = h->irec;
-            fa.mail = h->mail_d;
-            fa.f = f;
-            fa.prm = prm;
-            fa.eps2f = (float)(h->cfg.eps * h->cfg.eps);
-            fa.na_max = h->cfg.fused_max_na > 0
-                            ? std::min(h->cfg.fused_max_na, NB_FUSED_MAX_NA)
-                            : NB_FUSED_DEFAULT_NA;
-            fa.t_end = t_end;
-            fa.part = h->fused_part;
-            fa.cnt = h->fused_cnt;
-            fa.bar = h->fused_bar;
-            fa.err = h->d_err;
-            fa.dtmin_hits = h->d_dtmin;
-            fa.stats = h->fused_stats;
-        }
+        const FusedArgs fa = fused ? fused_args(h, t_end, f) : FusedArgs{};
         auto launch_sched = [&]() -> int {
             const unsigned long long ep = h->seq_next++;
             int r;
             if (fused) {
                 r = timed(h, T_FUSED, [&] {
-                    return launch_fused_steps(fa, h->fused_grid, h->cfg.variant == NB_F32DS,
+                    return launch_fused_steps(fa, h->fused_grid, h->cfg.variant == NB_F32DS, 4,
                                               h->stream);
                 });
                 h->stats.fused_launches++;

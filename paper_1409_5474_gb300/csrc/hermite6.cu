@@ -530,15 +530,8 @@ __global__ void k_force6_reduce(const void *__restrict__ part, long long pld, in
 
 // ---- K4 --------------------------------------------------------------------------
 
-// Slot k: the order-6 corrector from the start-of-step x0, v0, a0, j0, s0 and
-// the new a1, j1, s1 (f, slot-indexed); the crackle at the end of the step from
-// the quintic through both ends (mid-point expansion, T = dt/2); the new step
-// from Aarseth's criterion on (a, jerk, snap, crackle), quantized as in the
-// 4th-order path. The quintic's k-th derivative carries the force rounding
-// (~1e-7 of |a| for double-single pairs) divided by T^k: a criterion on the 4th
-// and 5th collapses the steps to dt_min, and the crackle is used above its
-// rounding floor only (prm.noise), else a particle whose step once got small
-// (a close encounter) could not grow it again.
+// Slot k: the order-6 corrector (correct6_lanes_pre) from the start-of-step state
+// and the new a1, j1, s1 (f, slot-indexed).
 __global__ void __launch_bounds__(CORRECT6_THREADS)
     k_correct6(StateDev s, const int *__restrict__ act, int na, double t_new, Out6 f,
                StepParams prm, SchedDev *sd, unsigned *err, unsigned long long *dtmin_hits)
@@ -549,84 +542,19 @@ __global__ void __launch_bounds__(CORRECT6_THREADS)
     const int warp_g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int k = warp_g * 10 + lane / 3;
     const int c = lane % 3;
-    if (blockIdx.x == 0 && threadIdx.x == 0) sd->t_cur = t_new;
     const bool mine = lane < 30 && k < na;
-    double a1 = 0.0, j1 = 0.0, s1 = 0.0, a3 = 0.0, dt = 1.0, dt_old = 0.0, T = 0.5;
+    C6State q{};
+    double a1 = 0.0, j1 = 0.0, s1 = 0.0;
     int i = 0;
-    bool fin = true;
     if (mine) {
         i = act ? act[k] : k;
-        dt = t_new - s.t[i];
-        dt_old = s.dt[i];
-        T = 0.5 * dt;
-        const double iT = prm.shared_dt > 0.0 ? 1.0 / T : ldexp(1.0, -ilogb(T));
-        const double iT3 = iT * iT * iT, iT5 = iT3 * iT * iT;
-        const long long q = c * s.ld + i;
-        const double x0 = s.pos[q], v0 = s.vel[q], a0 = s.acc[q], j0 = s.jerk[q], s0 = s.snap[q];
+        c6state_load(s, i, c, q);
         a1 = f.acc[c * f.ld + k];
         j1 = f.jerk[c * f.ld + k];
         s1 = f.snap[c * f.ld + k];
-        // v1 = v0 + dt/2 (a0 + a1) - dt^2/10 (j1 - j0) + dt^3/120 (s0 + s1)
-        const double v1 = v0 + dt * fma(dt, fma(dt, (s0 + s1) * (1.0 / 120.0),
-                                                -0.1 * (j1 - j0)), 0.5 * (a0 + a1));
-        // x1 = x0 + dt/2 (v0 + v1) - dt^2/10 (a1 - a0) + dt^3/120 (j0 + j1)
-        const double x1 = x0 + dt * fma(dt, fma(dt, (j0 + j1) * (1.0 / 120.0),
-                                                -0.1 * (a1 - a0)), 0.5 * (v0 + v1));
-        const double Am = 0.5 * (a1 - a0);
-        const double Jp = 0.5 * (j1 + j0), Jm = 0.5 * (j1 - j0);
-        const double Sp = 0.5 * (s1 + s0), Sm = 0.5 * (s1 - s0);
-        const double c5 = (45.0 * Am - 45.0 * T * Jp + 15.0 * T * T * Sm) * iT5;
-        const double c3 = (7.5 * (T * Jp - Am) - 1.5 * T * T * Sm) * iT3;
-        const double c4 = 3.0 * (T * Sp - Jm) * iT3;
-        a3 = c3 + T * (c4 + 0.5 * T * c5);
-        s.pos[q] = x1;
-        s.vel[q] = v1;
-        s.acc[q] = a1;
-        s.jerk[q] = j1;
-        s.snap[q] = s1;
-        s.crk[q] = a3;
-        fin = isfinite(x1) && isfinite(v1);
     }
-    // the slot's three components on its first lane
-    const int l0 = lane - c;
-    double a1v[3], j1v[3], s1v[3], a3v[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int src = min(31, l0 + q);
-        a1v[q] = __shfl_sync(0xffffffffu, a1, src);
-        j1v[q] = __shfl_sync(0xffffffffu, j1, src);
-        s1v[q] = __shfl_sync(0xffffffffu, s1, src);
-        a3v[q] = __shfl_sync(0xffffffffu, a3, src);
-    }
-    const unsigned bad = __ballot_sync(0xffffffffu, mine && !fin);
-    if (!mine || c != 0) return;
-    if (bad & (7u << l0)) atomicOr(err, DERR_NONFINITE);
-    double dt_new;
-    if (prm.shared_dt > 0.0) {
-        dt_new = prm.shared_dt;
-    } else {
-        // Aarseth's criterion with the evaluated snap as a2 and the crackle as a3:
-        // dt^2 = eta (|a||s| + |j|^2) / (|j||c| + |s|^2), the crackle's magnitude
-        // reduced by its rounding floor 30 noise |a| / T^3 (the forces' relative
-        // rounding enters it through (a1 - a0) / T^3 with coefficients 7.5 + 22.5);
-        // below the floor it counts as zero
-        const double A = dot3(a1v, a1v), J = dot3(j1v, j1v), S = dot3(s1v, s1v);
-        const double cn = sqrt(dot3(a3v, a3v));
-        const double cfl = 30.0 * prm.noise * sqrt(A) / (T * T * T);
-        const double ce = cn > cfl ? cn - cfl : 0.0;
-        const double num = prm.eta * (sqrt(A * S) + J);
-        const double den = sqrt(J) * ce + S;
-        bool clamped;
-        dt_new = quantize_sq(num, den, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
-        if (clamped && dtmin_hits) atomicAdd(dtmin_hits, 1ull);
-        const int lo = step_level(dt_old, prm.dt_max), ln = step_level(dt_new, prm.dt_max);
-        if (lo != ln) {
-            hist_add(sd->hist, lo, -1);
-            hist_add(sd->hist, ln, +1);
-        }
-    }
-    s.t[i] = t_new;
-    s.dt[i] = dt_new;
+    correct6_lanes_pre(s, i, k, c, lane - c, mine, t_new, q, a1, j1, s1, prm, sd, err,
+                       dtmin_hits);
 }
 
 // Resident CTAs per SM of a FP32 / double-single variant (occupancy API, cached).

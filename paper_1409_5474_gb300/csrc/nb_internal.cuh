@@ -358,11 +358,12 @@ struct FusedStats {
 // state is corrected at sd->t_cur with a valid level histogram (as after K4):
 // it takes block steps while the due set has at most na_max members and
 // t_next <= t_end; at the first step that fails either test it has predicted
-// every particle to that t_next and gathered the due set (act, irec), then
-// publishes (epoch, t_next, N_active) to the mailbox exactly as K5 + K1 do,
-// so the caller continues with the planned kernels. part: j-chunk partials
-// (fused_part_floats2(grid, na_max) float2); cnt: grid ints; bar: 3 words,
-// zero at launch (the launcher clears them).
+// every particle to that t_next and gathered the due set (act, and at order 4
+// irec), then publishes (epoch, t_next, N_active) to the mailbox exactly as
+// K5 + K1 do, so the caller continues with the planned kernels. part: j-chunk
+// partials (fused_part_float2s(grid, na_max, order) float2); cnt:
+// fused_cnt_ints(grid) ints; bar: 3 words, zero at launch (the launcher clears
+// them). The order-6 kernel (na_max <= FUSED6_MAX_NA) uses neither irec nor f.
 struct FusedArgs {
     StateDev s;
     SchedDev *sd;
@@ -388,15 +389,18 @@ constexpr int FUSED_MAX_WORDS = 256;  // due-flag words per CTA: n <= 8192 x gri
 // Due sets of up to FUSED_SMALL_NA particles take the small-set path of the
 // fused kernel (groups of four due particles, a ticket per group).
 constexpr int FUSED_SMALL_NA = 16;
+// The 6th-order fused kernel takes due sets of up to FUSED6_MAX_NA particles,
+// all on its small-set path; larger ones go to the planned kernels.
+constexpr int FUSED6_MAX_NA = NB_FUSED6_MAX_NA;
 
 // Ints of the fused kernel's counter array: grid per-CTA counts, 2 due-set
-// counters, FUSED_SMALL_NA / 4 tickets (padded).
+// counters, the tickets of the small-set groups (at most FUSED6_MAX_NA / 4; padded).
 inline size_t fused_cnt_ints(int grid) { return (size_t)grid + 64; }
 
-// CTAs of the fused launch on this device (one per SM); 0 if the kernel cannot
-// be launched cooperatively.
-int fused_grid(int device);
-size_t fused_part_float2s(int grid, int na_max);
+// CTAs of the fused launch of the order-4 or order-6 kernel on this device (one
+// or two per SM); 0 if the kernel cannot be launched cooperatively.
+int fused_grid(int device, int order);
+size_t fused_part_float2s(int grid, int na_max, int order);
 
 // Self-checks of the bounded device waits: a wait that nothing completes (an
 // mbarrier without arrivals; a grid barrier one CTA never reaches) gives up
@@ -404,7 +408,8 @@ size_t fused_part_float2s(int grid, int na_max);
 cudaError_t launch_selftest_mbar(unsigned *err, unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_selftest_barrier(unsigned *bar, unsigned *err, unsigned long long limit_ns,
                                     cudaStream_t st);
-cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st);
+cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, int order,
+                               cudaStream_t st);
 
 // Bridge kicks (Sect. V): vel += dt * acc (SoA rows of strides ld, lda);
 // acc, jerk := a slot-indexed evaluation f for all particles; DERR_UNSYNC when

@@ -310,12 +310,13 @@ constexpr int SMALL_JPL = 2;
 constexpr int SMALL_CHUNK_MAX_J = 2048;  // j per small-set chunk: 8 per lane
 constexpr int SMALL_Q = 28;  // outputs of a group: 4 slots x 7 components
 
-// The j-chunks of a small due set (a function of (na, n, grid) only): about one
-// item per CTA, at most two batches per lane, at least 32 j per chunk.
+// The j-chunks of a small due set (a function of (na, n, grid) only): at most one
+// item per CTA while the chunks hold at most SMALL_CHUNK_MAX_J j (at most two
+// batches per lane), at least 32 j per chunk.
 __device__ __forceinline__ void small_chunking(int na, int n, int grid, int &nchunk, int &jc)
 {
     const int ng = (na + 3) / 4;
-    int nc = max((grid + ng - 1) / ng, (n + SMALL_CHUNK_MAX_J - 1) / SMALL_CHUNK_MAX_J);
+    int nc = max(grid / ng, (n + SMALL_CHUNK_MAX_J - 1) / SMALL_CHUNK_MAX_J);
     nc = max(1, min(nc, (n + 31) / 32));
     jc = (n + nc - 1) / nc;
     jc = (jc + 31) & ~31;
@@ -513,13 +514,56 @@ __device__ __forceinline__ void small_item(const FusedArgs &a, int na, int n, in
     __syncthreads();  // s_red, s_fin and s_last are free for the next item
 }
 
+// t_next = next multiple after t_cur of the smallest occupied step; the due
+// particles are exactly those whose step divides t_next (every t_i is a
+// multiple of dt_i and t_i <= t_cur < t_i + dt_i), so the due count is the
+// level histogram's sum over the levels k >= k0. Warp 0 of the CTA; lane 0
+// writes s_tn and s_na.
+__device__ __forceinline__ void next_block_time(const FusedArgs &a, double t_cur, double &s_tn,
+                                                int &s_na)
+{
+    static_assert(NLEVEL == 64, "two ballot words of levels");
+    const int lane = threadIdx.x & 31;
+    const int h0 = __ldcg(a.sd->hist + lane);
+    const int h1 = __ldcg(a.sd->hist + 32 + lane);
+    const unsigned b0 = __ballot_sync(0xffffffffu, h0 > 0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, h1 > 0);
+    const int kmax = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : 0);
+    const double dm = ldexp(a.prm.dt_max, -kmax);
+    const double q = floor(t_cur * (1.0 / dm)) + 1.0;
+    const unsigned long long qi = q < 9.0e18 ? (unsigned long long)q : 0ull;
+    const int k0 = qi ? max(0, kmax - (__ffsll((long long)qi) - 1)) : NLEVEL;
+    int c = (lane >= k0 ? h0 : 0) + (lane + 32 >= k0 ? h1 : 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+        s_tn = q * dm;
+        s_na = c;
+    }
+}
+
+// Publish the end of a launch: the block time reached and, for a step handed
+// to the caller, (epoch, t_next, N_active) in the mailbox like K5 + K1.
+__device__ __forceinline__ void publish(const FusedArgs &a, double t_cur, double tn, int na,
+                                        unsigned long long epoch)
+{
+    a.sd->t_cur = t_cur;
+    a.sd->n_active = na;
+    a.mail->t_next = tn;
+    a.mail->n_active = na;
+    __threadfence_system();
+    a.mail->seq = epoch;
+    a.sd->seq = epoch + 1ull;
+}
+
 // ---- the hand-off step -----------------------------------------------------
 
 // A step the fused kernel does not take (due set larger than na_max): predict
-// every particle to tn (FP64 pos_p, vel_p and records), then gather the due
-// set in ascending index (act, irec), exactly as K5 + K1 would, for the
-// planned kernels the caller runs next. Returns false when a grid barrier
-// gave up.
+// every particle to tn (FP64 pos_p, vel_p (and acc_p at order 6) and records),
+// then gather the due set in ascending index (act, and at order 4 irec),
+// exactly as K5 + K1 would, for the planned kernels the caller runs next.
+// Returns false when a grid barrier gave up.
+template <int ORD>
 __device__ __forceinline__ bool handoff_predict_gather(const FusedArgs &a, double tn, int p0,
                                                        int p1, int nwords, unsigned *s_flags,
                                                        int *s_woff, int *s_wsum, int &s_total,
@@ -531,9 +575,15 @@ __device__ __forceinline__ bool handoff_predict_gather(const FusedArgs &a, doubl
     const StateDev &s = a.s;
     for (int w0 = 0; w0 < nwords; w0 += NW) {
         const int i = p0 + w0 * 32 + tid;
-        float4 rec[DS_REC];
         bool due = false;
-        if (i < p1) due = predict_one<true>(s, i, tn, rec);
+        if (i < p1) {
+            if (ORD == 6) {
+                due = predict6_one<true>(s, i, tn);
+            } else {
+                float4 rec[DS_REC];
+                due = predict_one<true>(s, i, tn, rec);
+            }
+        }
         const unsigned b = __ballot_sync(0xffffffffu, due);
         if (lane == 0 && w0 + warp < nwords) s_flags[w0 + warp] = b;
     }
@@ -576,11 +626,13 @@ __device__ __forceinline__ bool handoff_predict_gather(const FusedArgs &a, doubl
             const int i = p0 + w * 32 + lane;
             const int slot = base + s_woff[w] + __popc(b & ((1u << lane) - 1u));
             a.act[slot] = i;
-            const float4 *r = s.rec + (size_t)DS_REC * i;
-            float4 *g = a.irec + (size_t)DS_REC * slot;
-            g[0] = __ldcg(r);
-            g[1] = __ldcg(r + 1);
-            g[2] = __ldcg(r + 2);
+            if (ORD == 4) {
+                const float4 *r = s.rec + (size_t)DS_REC * i;
+                float4 *g = a.irec + (size_t)DS_REC * slot;
+                g[0] = __ldcg(r);
+                g[1] = __ldcg(r + 1);
+                g[2] = __ldcg(r + 2);
+            }
         }
     }
     (void)G;
@@ -634,49 +686,20 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     };
 
     for (;;) {
-        // t_next = next multiple after t_cur of the smallest occupied step; the
-        // due particles are exactly those whose step divides t_next (every t_i
-        // is a multiple of dt_i and t_i <= t_cur < t_i + dt_i), so the due count
-        // is the histogram's sum over the levels k >= k0
-        if (warp == 0) {
-            static_assert(NLEVEL == 64, "two ballot words of levels");
-            const int h0 = __ldcg(a.sd->hist + lane);
-            const int h1 = __ldcg(a.sd->hist + 32 + lane);
-            const unsigned b0 = __ballot_sync(0xffffffffu, h0 > 0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, h1 > 0);
-            const int kmax = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : 0);
-            const double dm = ldexp(a.prm.dt_max, -kmax);
-            const double q = floor(t_cur * (1.0 / dm)) + 1.0;
-            const unsigned long long qi = q < 9.0e18 ? (unsigned long long)q : 0ull;
-            const int k0 = qi ? max(0, kmax - (__ffsll((long long)qi) - 1)) : NLEVEL;
-            int c = (lane >= k0 ? h0 : 0) + (lane + 32 >= k0 ? h1 : 0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            if (lane == 0) {
-                s_tn = q * dm;
-                s_na = c;
-            }
-        }
+        // the next block time and its due count
+        if (warp == 0) next_block_time(a, t_cur, s_tn, s_na);
         __syncthreads();
         const double tn = s_tn;
         const int na = s_na;
         if (!(tn <= a.t_end) || na < 1 || na > a.na_max) {
             // hand the step to the caller exactly as the scheduler kernel would
             if (tn <= a.t_end && na >= 1) {
-                ok = handoff_predict_gather(a, tn, p0, p1, nwords, s_flags, s_woff, s_wsum,
-                                            s_total, s_base, gen);
+                ok = handoff_predict_gather<4>(a, tn, p0, p1, nwords, s_flags, s_woff, s_wsum,
+                                               s_total, s_base, gen);
                 mark(0);
                 if (!ok) break;
             }
-            if (bid == 0 && tid == 0) {
-                a.sd->t_cur = t_cur;
-                a.sd->n_active = na;
-                a.mail->t_next = tn;
-                a.mail->n_active = na;
-                __threadfence_system();
-                a.mail->seq = epoch;
-                a.sd->seq = epoch + 1ull;
-            }
+            if (bid == 0 && tid == 0) publish(a, t_cur, tn, na, epoch);
             break;
         }
 
@@ -828,6 +851,361 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
 }
 
+// ---- the 6th-order scheme -----------------------------------------------------
+
+// Small due sets of the 6th-order scheme take the same steps as the 4th-order
+// small path: every CTA predicts its particle range (64-byte records: the
+// double-single record plus the FP32 predicted acceleration), the due ones
+// take slots; groups of four due slots meet j-chunks in items, and the CTA
+// that completes a group's last chunk (its ticket) sums the group's partials
+// in a fixed order and runs the order-6 corrector. Ten outputs per slot (acc,
+// jerk, snap, P); larger due sets are handed to the caller's planned kernels.
+constexpr int F6_Q = 40;                          // outputs of a group: 4 slots x 10
+constexpr int F6_SUBS = FUSED_THREADS / F6_Q;     // 6 ranges per output
+constexpr int F6_JPL = 2;                         // j-records per lane and batch
+constexpr int F6_CHUNK_MAX_J = 4096;              // j per chunk: 16 per lane
+
+// The j-chunks of an order-6 small due set (a function of (na, n, grid) only):
+// at most one item per CTA while the chunks hold at most F6_CHUNK_MAX_J j, at
+// least 32 j per chunk.
+__device__ __forceinline__ void small6_chunking(int na, int n, int grid, int &nchunk, int &jc)
+{
+    const int ng = (na + 3) / 4;
+    int nc = max(grid / ng, (n + F6_CHUNK_MAX_J - 1) / F6_CHUNK_MAX_J);
+    nc = max(1, min(nc, (n + 31) / 32));
+    jc = (n + nc - 1) / nc;
+    jc = (jc + 31) & ~31;
+    nchunk = (n + jc - 1) / jc;
+}
+
+__device__ __forceinline__ void small6_finish(const FusedArgs &a, int na, int g, int nchunk,
+                                              double tn, float *s_fin)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __threadfence();
+    // warps 0..3, lanes 0..2: the start-of-step state of slot 4 g + warp, component
+    // lane, requested before the partial sums
+    const int k = 4 * g + warp, c = lane;
+    const bool mine = warp < 4 && lane < 3 && k < na;
+    C6State q{};
+    int i = 0;
+    if (mine) {
+        i = __ldcg(a.act + k);
+        c6state_load(a.s, i, c, q);
+    }
+    if (tid < F6_SUBS * F6_Q) {
+        const int o = tid % F6_Q, sub = tid / F6_Q;
+        const int len = (nchunk + F6_SUBS - 1) / F6_SUBS;
+        const int c0 = sub * len, c1 = min(nchunk, c0 + len);
+        const float2 *base = a.part + (size_t)g * nchunk * F6_Q + o;
+        dsf acc{0.f, 0.f};
+        for (int cb = c0; cb < c1; cb += SMALL_BATCH) {
+            float2 x[SMALL_BATCH];
+#pragma unroll
+            for (int u = 0; u < SMALL_BATCH; ++u)
+                x[u] = cb + u < c1 ? __ldcg(base + (size_t)(cb + u) * F6_Q)
+                                   : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < SMALL_BATCH; ++u) ds_acc(acc, dsf{x[u].x, x[u].y});
+        }
+        s_fin[2 * tid] = acc.hi;
+        s_fin[2 * tid + 1] = acc.lo;
+    }
+    __syncthreads();
+    double *s_res = reinterpret_cast<double *>(s_fin + 2 * F6_SUBS * F6_Q);  // [40]
+    if (tid < F6_Q) {
+        dsf v{s_fin[2 * tid], s_fin[2 * tid + 1]};
+#pragma unroll
+        for (int sub = 1; sub < F6_SUBS; ++sub) {
+            const int r = sub * F6_Q + tid;
+            ds_acc(v, dsf{s_fin[2 * r], s_fin[2 * r + 1]});
+        }
+        const double x = ds_to_double(v);
+        s_res[tid] = x;
+        if (4 * g + tid / 10 < na && !isfinite(x)) atomicOr(a.err, DERR_NONFINITE);
+    }
+    if (tid == 0) a.cnt[gridDim.x + 2 + g] = 0;  // re-arm the group's ticket
+    __syncthreads();
+    if (warp < 4) {
+        const double a1 = mine ? s_res[10 * warp + c] : 0.0;
+        const double j1 = mine ? s_res[10 * warp + 3 + c] : 0.0;
+        const double s1 = mine ? s_res[10 * warp + 6 + c] : 0.0;
+        correct6_lanes_pre(a.s, i, k, c, 0, mine, tn, q, a1, j1, s1, a.prm, a.sd, a.err,
+                           a.dtmin_hits);
+    }
+}
+
+// One item: group g (slots 4 g .. 4 g + 3; idle slots repeat the last due one)
+// against j-chunk c. The eight warps split the chunk; every lane loads up to
+// F6_JPL records before any arithmetic and sums its (at most 16) j in FP32; the
+// lanes' sums meet as double-single values in a fixed xor tree per warp and a
+// fixed-order sum over the warps: one double-single partial per (group, chunk) and output
+// q = 10 p + component (component 9: the positive potential sum).
+template <bool DS>
+__device__ __forceinline__ void small6_item(const FusedArgs &a, int na, int n, int g, int c,
+                                            int nchunk, int jc, double tn,
+                                            float2 (*s_red)[F6_Q], float4 (*s_i)[DS6_REC],
+                                            float *s_fin, int *s_last)
+{
+    constexpr int G = 4, NW = FUSED_THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float eps2f = a.eps2f;
+    // the group's four i-records in shared memory (read back as broadcasts, which
+    // keeps the kernel within the registers of two CTAs per SM)
+    if (tid < G * DS6_REC) {
+        const int i = __ldcg(a.act + min(4 * g + tid / DS6_REC, na - 1));
+        s_i[tid / DS6_REC][tid % DS6_REC] = __ldcg(a.s.rec6 + (size_t)DS6_REC * i + tid % DS6_REC);
+    }
+    __syncthreads();
+    int iid[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) iid[p] = __float_as_int(s_i[p][1].w);
+    // FP32 sums per lane (at most F6_CHUNK_MAX_J / 256 = 16 terms each)
+    float t[G][10];
+#pragma unroll
+    for (int p = 0; p < G; ++p)
+#pragma unroll
+        for (int q = 0; q < 10; ++q) t[p][q] = 0.f;
+    const int j0 = c * jc, j1 = min(n, j0 + jc);
+    const int per_w = (((j1 - j0) + NW - 1) / NW + 31) & ~31;
+    const int wj0 = j0 + warp * per_w, wj1 = min(j1, wj0 + per_w);
+    const float4 *jr = a.s.rec6;
+    for (int jb = wj0; jb < wj1; jb += 32 * F6_JPL) {
+        float4 A[F6_JPL], B[F6_JPL], C[F6_JPL], D[F6_JPL];
+        int jj[F6_JPL];
+#pragma unroll
+        for (int u = 0; u < F6_JPL; ++u) {
+            const int j = jb + lane + 32 * u;
+            jj[u] = j < wj1 ? j : -2;
+            if (j < wj1) {
+                const float4 *r = jr + (size_t)DS6_REC * j;
+                A[u] = __ldcg(r);
+                C[u] = __ldcg(r + 2);
+                D[u] = __ldcg(r + 3);
+                B[u] = DS ? __ldcg(r + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                A[u] = B[u] = C[u] = D[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+            const float4 I0 = s_i[p][0], I1 = s_i[p][1], I2 = s_i[p][2], I3 = s_i[p][3];
+#pragma unroll
+            for (int u = 0; u < F6_JPL; ++u) {
+                float dx, dy, dz;
+                if (DS) {
+                    dx = (A[u].x - I0.x) + (B[u].x - I1.x);
+                    dy = (A[u].y - I0.y) + (B[u].y - I1.y);
+                    dz = (A[u].z - I0.z) + (B[u].z - I1.z);
+                } else {
+                    dx = A[u].x - I0.x;
+                    dy = A[u].y - I0.y;
+                    dz = A[u].z - I0.z;
+                }
+                const float dvx = C[u].x - I2.x, dvy = C[u].y - I2.y, dvz = C[u].z - I2.z;
+                const float dax = D[u].x - I3.x, day = D[u].y - I3.y, daz = D[u].z - I3.z;
+                float r2 = fmaf(dx, dx, eps2f);
+                r2 = fmaf(dy, dy, r2);
+                r2 = fmaf(dz, dz, r2);
+                float rv = dx * dvx;
+                rv = fmaf(dy, dvy, rv);
+                rv = fmaf(dz, dvz, rv);
+                float w2 = dvx * dvx;  // |v|^2 + r.a
+                w2 = fmaf(dvy, dvy, w2);
+                w2 = fmaf(dvz, dvz, w2);
+                w2 = fmaf(dx, dax, w2);
+                w2 = fmaf(dy, day, w2);
+                w2 = fmaf(dz, daz, w2);
+                float rinv = rsqrtf(r2);
+                // the self pair and the padding slots (jj -2) contribute nothing
+                rinv = (jj[u] == iid[p] || jj[u] < 0) ? 0.f : rinv;
+                const float rinv2 = rinv * rinv;
+                const float mrinv = A[u].w * rinv;
+                const float mr3 = mrinv * rinv2;
+                const float alpha = rv * rinv2;
+                const float beta = fmaf(alpha, alpha, w2 * rinv2);
+                const float m3a = -3.f * alpha, m6a = -6.f * alpha, m3b = -3.f * beta;
+                const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+                const float Jx = fmaf(m3a, Ax, mr3 * dvx);
+                const float Jy = fmaf(m3a, Ay, mr3 * dvy);
+                const float Jz = fmaf(m3a, Az, mr3 * dvz);
+                t[p][0] += Ax;
+                t[p][1] += Ay;
+                t[p][2] += Az;
+                t[p][3] += Jx;
+                t[p][4] += Jy;
+                t[p][5] += Jz;
+                t[p][6] += fmaf(m3b, Ax, fmaf(m6a, Jx, mr3 * dax));
+                t[p][7] += fmaf(m3b, Ay, fmaf(m6a, Jy, mr3 * day));
+                t[p][8] += fmaf(m3b, Az, fmaf(m6a, Jz, mr3 * daz));
+                t[p][9] += mrinv;
+            }
+        }
+    }
+    // the lanes' sums, one slot at a time (fewer live registers)
+#pragma unroll
+    for (int p = 0; p < G; ++p) {
+        dsf S[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) S[q] = dsf{t[p][q], 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 10; ++q) ds_acc(S[q], ds_shfl_xor(S[q], o));
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 10; ++q) s_red[warp][p * 10 + q] = make_float2(S[q].hi, S[q].lo);
+        }
+    }
+    __syncthreads();
+    if (tid < F6_Q) {
+        dsf v{s_red[0][tid].x, s_red[0][tid].y};
+#pragma unroll
+        for (int w = 1; w < NW; ++w) ds_acc(v, dsf{s_red[w][tid].x, s_red[w][tid].y});
+        a.part[((size_t)g * nchunk + c) * F6_Q + tid] = make_float2(v.hi, v.lo);
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) *s_last = (atomicAdd(a.cnt + gridDim.x + 2 + g, 1) == nchunk - 1);
+    __syncthreads();
+    if (*s_last) small6_finish(a, na, g, nchunk, tn, s_fin);
+    __syncthreads();  // s_red, s_fin and s_last are free for the next item
+}
+
+// The 6th-order fused kernel: the 4th-order kernel's loop with the small path
+// only (due sets of up to FUSED6_MAX_NA particles).
+template <bool DS>
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
+    k_fused_steps6(FusedArgs a)
+{
+    constexpr int NT = FUSED_THREADS, NW = NT / 32;
+    __shared__ unsigned s_flags[FUSED_MAX_WORDS];
+    __shared__ int s_woff[FUSED_MAX_WORDS];
+    __shared__ int s_wsum[NW];
+    __shared__ int s_total, s_base, s_na, s_last;
+    __shared__ double s_tn;
+    __shared__ unsigned long long s_hist[32], s_step_ns[32], s_phase[4];
+    __shared__ float2 s_red[NW][F6_Q];
+    __shared__ float4 s_i[4][DS6_REC];
+    __shared__ __align__(8) float s_fin[2 * F6_SUBS * F6_Q + 2 * F6_Q];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, bid = blockIdx.x;
+    const StateDev &s = a.s;
+    const int n = s.n;
+    const int per = (n + G - 1) / G;
+    const int p0 = min(n, bid * per), p1 = min(n, p0 + per);
+    const int nwords = (p1 - p0 + 31) / 32;
+    int *dcnt = a.cnt + G;  // two due-set counters, used in alternate steps
+    unsigned gen = 0;
+    int par = 0;
+    bool ok = true;
+    double t_cur = __ldcg(&a.sd->t_cur);
+    const unsigned long long epoch = __ldcg(&a.sd->seq);
+    unsigned long long steps = 0;
+    double inter = 0.0;
+    if (tid < 32) s_hist[tid] = s_step_ns[tid] = 0ull;
+    if (tid < 4) s_phase[tid] = 0ull;
+    unsigned long long t_mark = 0;  // CTA 0, thread 0: stage boundaries
+    if (bid == 0 && tid == 0) t_mark = globaltimer_ns();
+    unsigned long long t_step = t_mark;
+    auto mark = [&](int ph) {
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[ph] += t - t_mark;
+            t_mark = t;
+        }
+    };
+
+    for (;;) {
+        if (warp == 0) next_block_time(a, t_cur, s_tn, s_na);
+        __syncthreads();
+        const double tn = s_tn;
+        const int na = s_na;
+        if (!(tn <= a.t_end) || na < 1 || na > a.na_max) {
+            if (tn <= a.t_end && na >= 1) {
+                ok = handoff_predict_gather<6>(a, tn, p0, p1, nwords, s_flags, s_woff, s_wsum,
+                                               s_total, s_base, gen);
+                mark(0);
+                if (!ok) break;
+            }
+            if (bid == 0 && tid == 0) publish(a, t_cur, tn, na, epoch);
+            break;
+        }
+
+        // predict this CTA's range to tn (records only); the due particles take
+        // slots of the due set in no particular order
+        for (int w0 = 0; w0 < nwords; w0 += 2 * NW) {
+            const int i0 = p0 + w0 * 32 + tid, i1 = i0 + NT;
+            // two particles per thread, both states loaded before any arithmetic
+            PState6 q0, q1;
+            if (i0 < p1) pstate6_load(s, i0, q0);
+            if (i1 < p1) pstate6_load(s, i1, q1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = h ? i1 : i0;
+                const bool due = i < p1 && predict6_rec_from(s, h ? q1 : q0, i, tn);
+                const unsigned b = __ballot_sync(0xffffffffu, due);
+                if (b) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(dcnt + par, __popc(b));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (due) a.act[base + __popc(b & ((1u << lane) - 1u))] = i;
+                }
+            }
+        }
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        mark(0);
+        if (__ldcg(dcnt + par) != na) {  // the histogram and the states disagree
+            if (bid == 0 && tid == 0) atomicOr(a.err, DERR_SCHED);
+            break;
+        }
+        if (bid == 0 && tid == 0) dcnt[par ^ 1] = 0;  // the next step's counter
+
+        {
+            int nchunk, jc;
+            small6_chunking(na, n, G, nchunk, jc);
+            const int ng = (na + 3) / 4;
+            for (int it = bid; it < ng * nchunk; it += G) {
+                const int g = it / nchunk, c = it - g * nchunk;
+                small6_item<DS>(a, na, n, g, c, nchunk, jc, tn, s_red, s_i, s_fin, &s_last);
+            }
+            mark(1);
+        }
+        if (bid == 0 && tid == 0) {
+            ++steps;
+            inter += (double)na * (double)n;
+            int lg = 0;
+            while ((2LL << lg) <= na && lg < 31) ++lg;
+            s_hist[lg] += 1ull;
+        }
+        t_cur = tn;
+        par ^= 1;
+        if (!(ok = grid_barrier(a.bar, gen))) break;
+        if (bid == 0 && tid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            s_phase[3] += t - t_mark;
+            t_mark = t;
+            int lg = 0;
+            while ((2LL << lg) <= na && lg < 31) ++lg;
+            s_step_ns[lg] += t - t_step;
+            t_step = t;
+        }
+    }
+    if (!ok && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+    if (bid == 0) {
+        __syncthreads();
+        if (tid == 0) {
+            a.stats->steps += steps;
+            a.stats->interactions += inter;
+        }
+        if (tid < 32) {
+            a.stats->active_hist[tid] += s_hist[tid];
+            a.stats->step_ns_hist[tid] += s_step_ns[tid];
+        }
+        if (tid < 4) a.stats->phase_ns[tid] += s_phase[tid];
+    }
+}
+
 // Self-check of the bounded grid barrier: CTA 0 never arrives, the others give
 // up after limit_ns, raise the abort flag and report DERR_TIMEOUT.
 __global__ void k_selftest_barrier(unsigned *bar, unsigned *err, unsigned long long limit_ns)
@@ -846,13 +1224,15 @@ cudaError_t launch_selftest_barrier(unsigned *bar, unsigned *err, unsigned long 
     return cudaLaunchCooperativeKernel((const void *)k_selftest_barrier, 4, 64, args, 0, st);
 }
 
-int fused_grid(int device)
+int fused_grid(int device, int order)
 {
     int coop = 0, sms = 0, per = 0;
+    const void *fn = order == 6 ? (const void *)k_fused_steps6<true>
+                                : (const void *)k_fused_steps<true>;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_steps<true>, FUSED_THREADS,
-                                                      0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, FUSED_THREADS, 0) !=
+            cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -860,8 +1240,12 @@ int fused_grid(int device)
     return sms * (per >= 2 ? 2 : 1);
 }
 
-size_t fused_part_float2s(int grid, int na_max)
+size_t fused_part_float2s(int grid, int na_max, int order)
 {
+    if (order == 6) {
+        // groups <= FUSED6_MAX_NA / 4, chunks <= max(G, n / 4096 + 1) <= 4 G + 1
+        return (size_t)(FUSED6_MAX_NA / 4) * (4 * (size_t)grid + 2) * F6_Q;
+    }
     // tile items: nchunk * na <= FUSED_MAX_CHUNKS * FUSED_IB for one i-block, else
     // (G / nib) * na <= G * FUSED_IB; small sets: ng * nchunk * 28 with ng <= 4 and
     // nchunk <= max(G, n / 2048 + 1) <= 4 G + 1 (n <= 8192 G)
@@ -873,7 +1257,7 @@ size_t fused_part_float2s(int grid, int na_max)
     return need;
 }
 
-cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream_t st)
+cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, int order, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
@@ -882,7 +1266,11 @@ cudaError_t launch_fused_steps(const FusedArgs &a, int grid, bool ds, cudaStream
     if (e != cudaSuccess) return e;
     FusedArgs copy = a;
     void *args[] = {&copy};
-    const void *fn = ds ? (const void *)k_fused_steps<true> : (const void *)k_fused_steps<false>;
+    const void *fn;
+    if (order == 6)
+        fn = ds ? (const void *)k_fused_steps6<true> : (const void *)k_fused_steps6<false>;
+    else
+        fn = ds ? (const void *)k_fused_steps<true> : (const void *)k_fused_steps<false>;
     return cudaLaunchCooperativeKernel(fn, grid, FUSED_THREADS, args, 0, st);
 }
 

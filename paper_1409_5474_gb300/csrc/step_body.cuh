@@ -182,6 +182,55 @@ __device__ __forceinline__ bool predict6_one(const StateDev &s, int i, double tn
     return due;
 }
 
+// The state the 6th-order K1 reads for one particle (loads of several particles
+// in flight before any arithmetic).
+struct PState6 {
+    double t, dt, m, x[3], v[3], a[3], j[3], sn[3], cr[3];
+};
+
+__device__ __forceinline__ void pstate6_load(const StateDev &s, int i, PState6 &q)
+{
+    q.t = s.t[i];
+    q.dt = s.dt[i];
+    q.m = s.m[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long k = c * s.ld + i;
+        q.x[c] = s.pos[k];
+        q.v[c] = s.vel[k];
+        q.a[c] = s.acc[k];
+        q.j[c] = s.jerk[k];
+        q.sn[c] = s.snap[k];
+        q.cr[c] = s.crk[k];
+    }
+}
+
+// predict6_one on a loaded state, the 64-byte record only (the same arithmetic
+// and bits; no FP64 pos_p / vel_p / acc_p: the order-6 corrector starts from
+// the start-of-step state); whether the particle is due at tn.
+__device__ __forceinline__ bool predict6_rec_from(const StateDev &s, const PState6 &q, int i,
+                                                  double tn)
+{
+    const double d = tn - q.t;
+    const double h2 = d * 0.5, h3 = d * (1.0 / 3.0), h4 = d * 0.25, h5 = d * 0.2;
+    double xp[3], vp[3], ap[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xp[c] = fma(d, fma(h2, fma(h3, fma(h4, fma(h5, q.cr[c], q.sn[c]), q.j[c]), q.a[c]),
+                           q.v[c]), q.x[c]);
+        vp[c] = fma(d, fma(h2, fma(h3, fma(h4, q.cr[c], q.sn[c]), q.j[c]), q.a[c]), q.v[c]);
+        ap[c] = fma(d, fma(h2, fma(h3, q.cr[c], q.sn[c]), q.j[c]), q.a[c]);
+    }
+    float4 r[3];
+    make_record(xp, vp, q.m, i, r);
+    float4 *rr = s.rec6 + (size_t)DS6_REC * i;
+    rr[0] = r[0];
+    rr[1] = r[1];
+    rr[2] = r[2];
+    rr[3] = make_float4(f32_trunc(ap[0]), f32_trunc(ap[1]), f32_trunc(ap[2]), 0.f);
+    return q.t + q.dt == tn;
+}
+
 // ---- step criterion and block quantization ---------------------------------
 
 __device__ __forceinline__ double norm3(double x, double y, double z)
@@ -571,6 +620,116 @@ __device__ __forceinline__ void correct_lanes_pre(const StateDev &s, int i, int 
         correct_step(s, i, t_new, dt, q.dt, a1v, j1v, a2v, a3v, prm, sd, dtmin_hits);
     }
     (void)lane;
+}
+
+// ---- K4 of the 6th-order scheme ---------------------------------------------
+
+// The start-of-step state of component c of a particle for the order-6 corrector.
+struct C6State {
+    double x, v, a0, j0, s0, t, dt;
+};
+
+__device__ __forceinline__ void c6state_load(const StateDev &s, int i, int c, C6State &q)
+{
+    const long long k = c * s.ld + i;
+    q.x = s.pos[k];
+    q.v = s.vel[k];
+    q.a0 = s.acc[k];
+    q.j0 = s.jerk[k];
+    q.s0 = s.snap[k];
+    q.t = s.t[i];
+    q.dt = s.dt[i];
+}
+
+// The order-6 corrector of slot k (particle i) by three lanes of a warp
+// (component c on lane lane0 + c where mine holds; every lane of the warp calls
+// this) from the start-of-step state q and the new a1, j1, s1: x1 and v1 from
+// the two-point expansion through (a, jerk, snap) at both ends, the crackle at
+// the end of the step from the quintic through both ends (mid-point expansion,
+// T = dt/2); the new step from Aarseth's criterion on (a, jerk, snap, crackle),
+// quantized as in the 4th-order path. The quintic's k-th derivative carries the
+// force rounding (~1e-7 of |a| for double-single pairs) divided by T^k: a
+// criterion on the 4th and 5th collapses the steps to dt_min, and the crackle
+// is used above its rounding floor only (prm.noise), else a particle whose step
+// once got small (a close encounter) could not grow it again.
+__device__ __forceinline__ void correct6_lanes_pre(const StateDev &s, int i, int k, int c,
+                                                   int lane0, bool mine, double t_new,
+                                                   const C6State &q, double a1, double j1,
+                                                   double s1, const StepParams &prm,
+                                                   SchedDev *sd, unsigned *err,
+                                                   unsigned long long *dtmin_hits)
+{
+    double a3 = 0.0, dt = 1.0, dt_old = 0.0, T = 0.5;
+    bool fin = true;
+    if (mine) {
+        if (k == 0 && c == 0) sd->t_cur = t_new;
+        dt = t_new - q.t;
+        dt_old = q.dt;
+        T = 0.5 * dt;
+        const double iT = prm.shared_dt > 0.0 ? 1.0 / T : ldexp(1.0, -ilogb(T));
+        const double iT3 = iT * iT * iT, iT5 = iT3 * iT * iT;
+        const double x0 = q.x, v0 = q.v, a0 = q.a0, j0 = q.j0, s0 = q.s0;
+        // v1 = v0 + dt/2 (a0 + a1) - dt^2/10 (j1 - j0) + dt^3/120 (s0 + s1)
+        const double v1 = v0 + dt * fma(dt, fma(dt, (s0 + s1) * (1.0 / 120.0),
+                                                -0.1 * (j1 - j0)), 0.5 * (a0 + a1));
+        // x1 = x0 + dt/2 (v0 + v1) - dt^2/10 (a1 - a0) + dt^3/120 (j0 + j1)
+        const double x1 = x0 + dt * fma(dt, fma(dt, (j0 + j1) * (1.0 / 120.0),
+                                                -0.1 * (a1 - a0)), 0.5 * (v0 + v1));
+        const double Am = 0.5 * (a1 - a0);
+        const double Jp = 0.5 * (j1 + j0), Jm = 0.5 * (j1 - j0);
+        const double Sp = 0.5 * (s1 + s0), Sm = 0.5 * (s1 - s0);
+        const double c5 = (45.0 * Am - 45.0 * T * Jp + 15.0 * T * T * Sm) * iT5;
+        const double c3 = (7.5 * (T * Jp - Am) - 1.5 * T * T * Sm) * iT3;
+        const double c4 = 3.0 * (T * Sp - Jm) * iT3;
+        a3 = c3 + T * (c4 + 0.5 * T * c5);
+        const long long qq = c * s.ld + i;
+        s.pos[qq] = x1;
+        s.vel[qq] = v1;
+        s.acc[qq] = a1;
+        s.jerk[qq] = j1;
+        s.snap[qq] = s1;
+        s.crk[qq] = a3;
+        fin = isfinite(x1) && isfinite(v1);
+    }
+    // the slot's three components on its first lane
+    double a1v[3], j1v[3], s1v[3], a3v[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        const int src = min(31, lane0 + u);
+        a1v[u] = __shfl_sync(0xffffffffu, a1, src);
+        j1v[u] = __shfl_sync(0xffffffffu, j1, src);
+        s1v[u] = __shfl_sync(0xffffffffu, s1, src);
+        a3v[u] = __shfl_sync(0xffffffffu, a3, src);
+    }
+    const unsigned bad = __ballot_sync(0xffffffffu, mine && !fin);
+    if (!mine || c != 0) return;
+    if (bad & (7u << lane0)) atomicOr(err, DERR_NONFINITE);
+    double dt_new;
+    if (prm.shared_dt > 0.0) {
+        dt_new = prm.shared_dt;
+    } else {
+        // Aarseth's criterion with the evaluated snap as a2 and the crackle as a3:
+        // dt^2 = eta (|a||s| + |j|^2) / (|j||c| + |s|^2), the crackle's magnitude
+        // reduced by its rounding floor 30 noise |a| / T^3 (the forces' relative
+        // rounding enters it through (a1 - a0) / T^3 with coefficients 7.5 + 22.5);
+        // below the floor it counts as zero
+        const double A = dot3(a1v, a1v), J = dot3(j1v, j1v), S = dot3(s1v, s1v);
+        const double cn = sqrt(dot3(a3v, a3v));
+        const double cfl = 30.0 * prm.noise * sqrt(A) / (T * T * T);
+        const double ce = cn > cfl ? cn - cfl : 0.0;
+        const double num = prm.eta * (sqrt(A * S) + J);
+        const double den = sqrt(J) * ce + S;
+        bool clamped;
+        dt_new = quantize_sq(num, den, dt, t_new, prm.dt_min, prm.dt_max, &clamped);
+        if (clamped && dtmin_hits) atomicAdd(dtmin_hits, 1ull);
+        const int lo = step_level(dt_old, prm.dt_max), ln = step_level(dt_new, prm.dt_max);
+        if (lo != ln) {
+            hist_add(sd->hist, lo, -1);
+            hist_add(sd->hist, ln, +1);
+        }
+    }
+    s.t[i] = t_new;
+    s.dt[i] = dt_new;
 }
 
 // ---- bounded waits and ordered status words ---------------------------------

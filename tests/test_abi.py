@@ -104,3 +104,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         for field in st._fields_:
             f = field[0]
             assert c_vals[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define NB_* of the header has the same value in the binding."""
+    from paper_1409_5474_gb300 import nbody
+    seen = 0
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"^#define\s+(NB_\w+)\s+(-?\d+)\b", open(hdr).read(), flags=re.M):
+            name, value = m.group(1), int(m.group(2))
+            assert getattr(nbody, name) == value, name
+            seen += 1
+    assert seen >= 10

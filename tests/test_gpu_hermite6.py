@@ -265,3 +265,83 @@ def test_full_size_h6block65536_sampled(nb):
         (pp, vp, ap), m = _predicted_oracle_state(s, t)
     ra, rj, rs, rp = oracle.force6(m, pp, vp, ap, eps * eps, sample)
     _gate6("f32ds", (acc, jerk, snap, pot), (ra, rj, rs, rp), "N=65536 sample of 512")
+
+
+def test_fused6_steps_force_vs_oracle(nb):
+    """Single block steps with due sets of at most NB_FUSED6_MAX_NA particles, each taken
+    by the order-6 fused kernel (N = 3000: 24 j-tiles' worth of chunks, groups of four
+    slots with idle ones): the due particles' new acc, jerk and snap are the kernel's force
+    on the j-set predicted to t_next, against the oracle (on the oracle's order-6
+    prediction of the state before the step) and against the planned tile kernel
+    (nb_predict + nb_force_snap on the same state: the same pair terms, summed in another
+    order)."""
+    n, eps = 3000, 0.01
+    p = ic.plummer(n, 89)
+    sizes = []
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.02, eta_s=0.01, order=6,
+                   device=0) as s:
+        s.step(1.0 / 256)
+        for _ in range(300):
+            if len(sizes) >= 6 and max(sizes) > 4:
+                break
+            g0 = s.state()
+            snap0, crk0 = s.snap()
+            t_next = float((g0["t"] + g0["dt"]).min())
+            due = np.nonzero(g0["t"] + g0["dt"] == t_next)[0].astype(np.int32)
+            small = len(due) <= nb.NB_FUSED6_MAX_NA
+            if small:
+                s.predict(t_next)
+                h_acc, h_jerk, h_snap, _ = s.force_snap(due)
+            st = s.step(t_next)
+            assert st["block_steps"] == 1 and st["fused_steps"] == (1 if small else 0), st
+            if not small:
+                continue
+            g1 = s.state()
+            snap1, _ = s.snap()
+            pp, vp, ap = oracle.predict6(t_next, g0["t"], g0["pos"].T, g0["vel"].T, g0["acc"].T,
+                                         g0["jerk"].T, snap0.T, crk0.T)
+            ra, rj, rs, _ = oracle.force6(g0["m"], pp, vp, ap, eps * eps, due)
+            got = {"acc": g1["acc"][:, due].T, "jerk": g1["jerk"][:, due].T,
+                   "snap": snap1[:, due].T}
+            rep = report({"acc": (got["acc"], ra), "jerk": (got["jerk"], rj),
+                          "snap": (got["snap"], rs)})
+            rep_h = report({"acc": (got["acc"], h_acc.T), "jerk": (got["jerk"], h_jerk.T),
+                            "snap": (got["snap"], h_snap.T)})
+            print(len(due), "oracle:", fmt(rep), "| tile kernel:", fmt(rep_h))
+            # per-particle gates: with a handful of due particles the RMS over the set is
+            # one particle's error
+            for q, g_max in zip(("acc", "jerk", "snap"), PP_GATES["f32ds"]):
+                assert rep[q][1] < g_max, (len(due), q, rep[q])
+                assert rep_h[q][1] < g_max, (len(due), q, rep_h[q])
+            np.testing.assert_array_equal(g1["t"][due], t_next)
+            sizes.append(len(due))
+    print("due-set sizes", sizes)
+    assert len(sizes) >= 6 and max(sizes) > 4               # more than one group of slots
+
+
+def test_fused6_matches_separate_launches(nb):
+    """1/16 time unit of order-6 block steps, with and without the fused kernel (N = 5000):
+    the same schedule (block steps, final steps), states equal to the double-single force
+    error, and the hand-over to the planned kernels for due sets above NB_FUSED6_MAX_NA
+    (the oracle takes 126 of its 214 steps here with at most 32 due)."""
+    p = ic.plummer(5000, 90)
+    kw = dict(variant="f32ds", eps=1e-2, eta=0.02, eta_s=0.01, dt_max=1.0 / 16, order=6,
+              device=0)
+    with nb.System(p.m, p.pos, p.vel, **kw) as a:
+        sa = a.step(1.0 / 16)
+        ga = a.state()
+        sna, cra = a.snap()
+    with nb.System(p.m, p.pos, p.vel, flags=nb.NB_FLAG_NO_FUSED, **kw) as b:
+        sb = b.step(1.0 / 16)
+        gb = b.state()
+        snb, crb = b.snap()
+    print(sa["block_steps"], sa["fused_steps"], sb["block_steps"])
+    assert sb["fused_steps"] == 0
+    assert 0.4 * sa["block_steps"] < sa["fused_steps"] < sa["block_steps"]
+    assert abs(sa["block_steps"] - sb["block_steps"]) <= 0.01 * sb["block_steps"]
+    assert sa["interactions"] == pytest.approx(sb["interactions"], rel=0.02)
+    np.testing.assert_array_equal(ga["t"], gb["t"])
+    assert (ga["dt"] == gb["dt"]).mean() > 0.99
+    scale = np.abs(gb["pos"]).max()
+    assert np.abs(ga["pos"] - gb["pos"]).max() < 1e-6 * scale
+    assert _rel_rms(sna, snb) < 1e-3
