@@ -45,11 +45,15 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1]
-// is the generation, bar[2] the abort flag (all zero at launch). The last CTA
-// to arrive resets the count and releases the next generation; the others
-// wait for it, bounded by BARRIER_LIMIT_NS or until another CTA gave up.
-// Returns false once any CTA has given up. gen: thread 0's generation.
+// Grid-wide barrier of a cooperative launch: bar[0] counts the arrivals of the
+// whole launch (generation g is complete once it reaches g x gridDim.x; the
+// comparison is wrap-safe), bar[2] is the abort flag (both zero at launch).
+// Thread 0 of every CTA adds its arrival after a fence (a release) and polls
+// the count with acquire loads, so the last arrival itself releases the
+// waiters; the abort flag and the time limit (BARRIER_LIMIT_NS) are checked
+// every 32 polls. Returns false once this CTA gave up or saw the abort flag; a
+// CTA that gives up never arrives again, so the others stop at their next
+// barrier at the latest. gen: thread 0's generation.
 __device__ bool grid_barrier(unsigned *bar, unsigned &gen,
                              unsigned long long limit_ns = BARRIER_LIMIT_NS)
 {
@@ -57,16 +61,13 @@ __device__ bool grid_barrier(unsigned *bar, unsigned &gen,
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = gen + 1u;
+        const unsigned target = (gen + 1u) * gridDim.x;
         __threadfence();
-        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            st_release_u32(&bar[1], target);
-        } else {
-            const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(&bar[1]) != target) {
+        atomicAdd(&bar[0], 1u);
+        const unsigned long long t0 = globaltimer_ns();
+        for (unsigned it = 1;; ++it) {
+            if ((int)(ld_acquire_u32(&bar[0]) - target) >= 0) break;
+            if ((it & 31u) == 0u) {
                 if (ld_acquire_u32(&bar[2]) != 0u) {
                     ok = 0;
                     break;
@@ -79,8 +80,8 @@ __device__ bool grid_barrier(unsigned *bar, unsigned &gen,
             }
         }
         __threadfence();
-        gen = target;
-        s_ok = ok && ld_acquire_u32(&bar[2]) == 0u;
+        gen += 1u;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
