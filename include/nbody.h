@@ -73,7 +73,7 @@ extern "C" {
 #define NB_FLAG_NO_FUSED 2
 #define NB_FUSED_MAX_NA 4096      /* upper bound of nb_config.fused_max_na */
 #define NB_FUSED_DEFAULT_NA 1024  /* fused_max_na = 0 */
-#define NB_FUSED6_MAX_NA 32       /* largest due set of the order-6 fused kernel */
+#define NB_FUSED6_MAX_NA 64       /* largest due set of the order-6 fused kernel */
 
 typedef struct nb_config {
     int n_max;           /* particle capacity of the handle, >= 1 */

@@ -367,12 +367,13 @@ ForcePlan plan_for(nb_handle h, int variant, int n_i)
         ForcePlan p = plan_from_entry(e, variant, n_i, h->n);
         if (h->plan_tuned[b] && p.kind != 2) {
             // the tuner timed the bucket at n_i = min(2^b, n): keep that plan's CTA
-            // count (its waves) for the other sizes of the bucket
+            // count (its waves) for the other sizes of the bucket, rounded down (a
+            // count rounded up past whole waves adds a nearly empty last wave)
             const int n_ref = (int)std::min<long long>(1LL << b, h->n);
             const long long ref = blocks_of(p, variant, n_ref), act = blocks_of(p, variant, n_i);
             if (ref != act && act > 0) {
                 nb_plan scaled = e;
-                scaled.nsplit = (int)std::max(1LL, ((long long)e.nsplit * ref + act / 2) / act);
+                scaled.nsplit = (int)std::max(1LL, ((long long)e.nsplit * ref) / act);
                 p = plan_from_entry(scaled, variant, n_i, h->n);
             }
         }

@@ -9,7 +9,11 @@
 //   A = m r / r2^(3/2),   J = m v / r2^(3/2) - 3 alpha A,
 //   S = m a / r2^(3/2) - 6 alpha J - 3 beta A,
 // with r, v, a the j-minus-i position, velocity and predicted acceleration and
-// r2 = |r|^2 + eps^2. So the j-records carry the predicted acceleration (64
+// r2 = |r|^2 + eps^2. The FP32 kernels evaluate it expanded in r, v and a, so
+// that every term is one FMA into its running sum: with q = m / r2^(3/2),
+// a3 = -3 alpha and u3 = -3 (|v|^2 + r.a) / r2,
+//   J = q v + (a3 q) r,   S = q a + (2 a3 q) v + ((5/3) a3^2 + u3) q r
+// (57 FP32 operations per pair against 64 for the nested form). So the j-records carry the predicted acceleration (64
 // bytes instead of 48), the prediction runs through the crackle term, and the
 // corrector is the order-6 two-point quadrature with the crackle, pop and 5th
 // derivative of the acceleration taken from the quintic through (a, jerk,
@@ -56,6 +60,7 @@ constexpr int H6_NWARP = 8;     // warps per FP32 CTA
 constexpr int H6_T64 = 128;     // threads per FP64 CTA
 constexpr int H6_JT64 = 128;    // j per FP64 shared tile
 constexpr int CORRECT6_THREADS = 128;  // 4 warps x 10 slots (3 lanes per slot)
+constexpr float F53 = 5.f / 3.f;        // S's r coefficient: (15 alpha^2 - 3 u) = 5/3 a3^2 + u3
 
 // ---- K1 ----------------------------------------------------------------------
 
@@ -231,22 +236,21 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 2)
                 const float rinv2 = rinv * rinv;
                 const float mrinv = P.w * rinv;
                 const float mr3 = mrinv * rinv2;
-                const float alpha = rv * rinv2;
-                const float beta = fmaf(alpha, alpha, w2 * rinv2);
-                const float m3a = -3.f * alpha, m6a = -6.f * alpha, m3b = -3.f * beta;
-                const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
-                const float Jx = fmaf(m3a, Ax, mr3 * dvx);
-                const float Jy = fmaf(m3a, Ay, mr3 * dvy);
-                const float Jz = fmaf(m3a, Az, mr3 * dvz);
-                t[p][0] += Ax;
-                t[p][1] += Ay;
-                t[p][2] += Az;
-                t[p][3] += Jx;
-                t[p][4] += Jy;
-                t[p][5] += Jz;
-                t[p][6] += fmaf(m3b, Ax, fmaf(m6a, Jx, mr3 * dax));
-                t[p][7] += fmaf(m3b, Ay, fmaf(m6a, Jy, mr3 * day));
-                t[p][8] += fmaf(m3b, Az, fmaf(m6a, Jz, mr3 * daz));
+                const float r3 = rinv2 * -3.f;
+                const float m3a = rv * r3;  // -3 alpha
+                const float m3u = w2 * r3;  // -3 (|v|^2 + r.a) / r^2
+                const float k1 = m3a * mr3;
+                const float c1 = k1 + k1;
+                const float c2 = fmaf(m3a, m3a * F53, m3u) * mr3;
+                t[p][0] = fmaf(mr3, dx, t[p][0]);
+                t[p][1] = fmaf(mr3, dy, t[p][1]);
+                t[p][2] = fmaf(mr3, dz, t[p][2]);
+                t[p][3] = fmaf(k1, dx, fmaf(mr3, dvx, t[p][3]));
+                t[p][4] = fmaf(k1, dy, fmaf(mr3, dvy, t[p][4]));
+                t[p][5] = fmaf(k1, dz, fmaf(mr3, dvz, t[p][5]));
+                t[p][6] = fmaf(c2, dx, fmaf(c1, dvx, fmaf(mr3, dax, t[p][6])));
+                t[p][7] = fmaf(c2, dy, fmaf(c1, dvy, fmaf(mr3, day, t[p][7])));
+                t[p][8] = fmaf(c2, dz, fmaf(c1, dvz, fmaf(mr3, daz, t[p][8])));
                 t[p][9] += mrinv;
             }
         };
@@ -312,25 +316,22 @@ __global__ void __launch_bounds__(32 * H6_NWARP, 2)
                         const float2 rinv2 = __fmul2_rn(rinv, rinv);
                         const float2 mrinv = __fmul2_rn(make_float2(q1.z, q1.w), rinv);
                         const float2 mr3 = __fmul2_rn(mrinv, rinv2);
-                        const float2 alpha = __fmul2_rn(rv, rinv2);
-                        const float2 beta = __ffma2_rn(alpha, alpha, __fmul2_rn(w2, rinv2));
-                        const float2 m3a = __fmul2_rn(make_float2(-3.f, -3.f), alpha);
-                        const float2 m6a = __fmul2_rn(make_float2(-6.f, -6.f), alpha);
-                        const float2 m3b = __fmul2_rn(make_float2(-3.f, -3.f), beta);
-                        const float2 Ax = __fmul2_rn(mr3, dx), Ay = __fmul2_rn(mr3, dy),
-                                     Az = __fmul2_rn(mr3, dz);
-                        const float2 Jx = __ffma2_rn(m3a, Ax, __fmul2_rn(mr3, dvx));
-                        const float2 Jy = __ffma2_rn(m3a, Ay, __fmul2_rn(mr3, dvy));
-                        const float2 Jz = __ffma2_rn(m3a, Az, __fmul2_rn(mr3, dvz));
-                        t2[p][0] = __fadd2_rn(t2[p][0], Ax);
-                        t2[p][1] = __fadd2_rn(t2[p][1], Ay);
-                        t2[p][2] = __fadd2_rn(t2[p][2], Az);
-                        t2[p][3] = __fadd2_rn(t2[p][3], Jx);
-                        t2[p][4] = __fadd2_rn(t2[p][4], Jy);
-                        t2[p][5] = __fadd2_rn(t2[p][5], Jz);
-                        t2[p][6] = __fadd2_rn(t2[p][6], __ffma2_rn(m3b, Ax, __ffma2_rn(m6a, Jx, __fmul2_rn(mr3, dax))));
-                        t2[p][7] = __fadd2_rn(t2[p][7], __ffma2_rn(m3b, Ay, __ffma2_rn(m6a, Jy, __fmul2_rn(mr3, day))));
-                        t2[p][8] = __fadd2_rn(t2[p][8], __ffma2_rn(m3b, Az, __ffma2_rn(m6a, Jz, __fmul2_rn(mr3, daz))));
+                        const float2 r3 = __fmul2_rn(rinv2, make_float2(-3.f, -3.f));
+                        const float2 m3a = __fmul2_rn(rv, r3);  // -3 alpha
+                        const float2 m3u = __fmul2_rn(w2, r3);  // -3 (|v|^2 + r.a) / r^2
+                        const float2 k1 = __fmul2_rn(m3a, mr3);
+                        const float2 c1 = __fadd2_rn(k1, k1);
+                        const float2 c2 = __fmul2_rn(
+                            __ffma2_rn(m3a, __fmul2_rn(m3a, make_float2(F53, F53)), m3u), mr3);
+                        t2[p][0] = __ffma2_rn(mr3, dx, t2[p][0]);
+                        t2[p][1] = __ffma2_rn(mr3, dy, t2[p][1]);
+                        t2[p][2] = __ffma2_rn(mr3, dz, t2[p][2]);
+                        t2[p][3] = __ffma2_rn(k1, dx, __ffma2_rn(mr3, dvx, t2[p][3]));
+                        t2[p][4] = __ffma2_rn(k1, dy, __ffma2_rn(mr3, dvy, t2[p][4]));
+                        t2[p][5] = __ffma2_rn(k1, dz, __ffma2_rn(mr3, dvz, t2[p][5]));
+                        t2[p][6] = __ffma2_rn(c2, dx, __ffma2_rn(c1, dvx, __ffma2_rn(mr3, dax, t2[p][6])));
+                        t2[p][7] = __ffma2_rn(c2, dy, __ffma2_rn(c1, dvy, __ffma2_rn(mr3, day, t2[p][7])));
+                        t2[p][8] = __ffma2_rn(c2, dz, __ffma2_rn(c1, dvz, __ffma2_rn(mr3, daz, t2[p][8])));
                         t2[p][9] = __fadd2_rn(t2[p][9], mrinv);
                     }
                 }
@@ -603,10 +604,12 @@ cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned
 
 
 // The CTA shape from the size of the due set: one i-particle per thread, warp
-// rows sharing each j-tile below 256 (8 rows for 32 or fewer). Then the j-splits: at least two waves of resident
-// CTAs (one for the warp-row shapes, whose CTAs are short: 8-14% faster there),
-// and among up to twice that many splits the count whose last wave is the
-// fullest (a 2.1-wave grid idles most SMs for its last tenth); at most one split
+// rows sharing each j-tile below 256 (8 rows for 32 or fewer). Then the
+// j-splits: at least two waves of resident CTAs (one for the warp-row shapes,
+// whose CTAs are short: 8-14% faster there), then the fewest splits, up to
+// eight times that many, whose last wave is at least 97% full, else the
+// fullest (256 i-blocks on 304 slots fill 84% of their last wave at 3 to 6
+// splits: the SMs idled 16% of a full N = 65536 evaluation); at most one split
 // per j-tile.
 ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
 {
@@ -626,13 +629,14 @@ ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
     const long long ns0 = std::min(cap, std::max(1LL, (waves * slots + nblk - 1) / nblk));
     long long best = ns0;
     double best_eff = 0.0;
-    for (long long ns = ns0; ns <= std::min(cap, 2 * ns0); ++ns) {
+    for (long long ns = ns0; ns <= std::min(cap, 8 * ns0); ++ns) {
         const double waves = (double)(nblk * ns) / (double)slots;
         const double eff = waves / std::ceil(waves);
         if (eff > best_eff + 1e-9) {
             best_eff = eff;
             best = ns;
         }
+        if (eff >= 0.97) break;  // the fewest splits whose last wave is nearly full
     }
     p.nsplit = (int)std::min(best, 1024LL);
     return p;

@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 constexpr int F6_Q = 40;                          // outputs of a group: 4 slots x 10
 constexpr int F6_SUBS = FUSED_THREADS / F6_Q;     // 6 ranges per output
 constexpr int F6_JPL = 2;                         // j-records per lane and batch
-constexpr int F6_CHUNK_MAX_J = 4096;              // j per chunk: 16 per lane
+constexpr int F6_CHUNK_MAX_J = 8192;              // j per chunk: 32 per lane
 
 // The j-chunks of an order-6 small due set (a function of (na, n, grid) only):
 // at most one item per CTA while the chunks hold at most F6_CHUNK_MAX_J j, at
@@ -938,7 +938,7 @@ __device__ __forceinline__ void small6_finish(const FusedArgs &a, int na, int g,
 
 // One item: group g (slots 4 g .. 4 g + 3; idle slots repeat the last due one)
 // against j-chunk c. The eight warps split the chunk; every lane loads up to
-// F6_JPL records before any arithmetic and sums its (at most 16) j in FP32; the
+// F6_JPL records before any arithmetic and sums its (at most 32) j in FP32; the
 // lanes' sums meet as double-single values in a fixed xor tree per warp and a
 // fixed-order sum over the warps: one double-single partial per (group, chunk) and output
 // q = 10 p + component (component 9: the positive potential sum).
@@ -961,7 +961,7 @@ __device__ __forceinline__ void small6_item(const FusedArgs &a, int na, int n, i
     int iid[G];
 #pragma unroll
     for (int p = 0; p < G; ++p) iid[p] = __float_as_int(s_i[p][1].w);
-    // FP32 sums per lane (at most F6_CHUNK_MAX_J / 256 = 16 terms each)
+    // FP32 sums per lane (at most F6_CHUNK_MAX_J / 256 = 32 terms each)
     float t[G][10];
 #pragma unroll
     for (int p = 0; p < G; ++p)
@@ -1020,25 +1020,25 @@ __device__ __forceinline__ void small6_item(const FusedArgs &a, int na, int n, i
                 float rinv = rsqrtf(r2);
                 // the self pair and the padding slots (jj -2) contribute nothing
                 rinv = (jj[u] == iid[p] || jj[u] < 0) ? 0.f : rinv;
+                // the order-6 tile kernel's expansion: every term one FMA into its sum
                 const float rinv2 = rinv * rinv;
                 const float mrinv = A[u].w * rinv;
                 const float mr3 = mrinv * rinv2;
-                const float alpha = rv * rinv2;
-                const float beta = fmaf(alpha, alpha, w2 * rinv2);
-                const float m3a = -3.f * alpha, m6a = -6.f * alpha, m3b = -3.f * beta;
-                const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
-                const float Jx = fmaf(m3a, Ax, mr3 * dvx);
-                const float Jy = fmaf(m3a, Ay, mr3 * dvy);
-                const float Jz = fmaf(m3a, Az, mr3 * dvz);
-                t[p][0] += Ax;
-                t[p][1] += Ay;
-                t[p][2] += Az;
-                t[p][3] += Jx;
-                t[p][4] += Jy;
-                t[p][5] += Jz;
-                t[p][6] += fmaf(m3b, Ax, fmaf(m6a, Jx, mr3 * dax));
-                t[p][7] += fmaf(m3b, Ay, fmaf(m6a, Jy, mr3 * day));
-                t[p][8] += fmaf(m3b, Az, fmaf(m6a, Jz, mr3 * daz));
+                const float r3 = rinv2 * -3.f;
+                const float m3a = rv * r3;  // -3 alpha
+                const float m3u = w2 * r3;  // -3 (|v|^2 + r.a) / r^2
+                const float k1 = m3a * mr3;
+                const float c1 = k1 + k1;
+                const float c2 = fmaf(m3a, m3a * (5.f / 3.f), m3u) * mr3;
+                t[p][0] = fmaf(mr3, dx, t[p][0]);
+                t[p][1] = fmaf(mr3, dy, t[p][1]);
+                t[p][2] = fmaf(mr3, dz, t[p][2]);
+                t[p][3] = fmaf(k1, dx, fmaf(mr3, dvx, t[p][3]));
+                t[p][4] = fmaf(k1, dy, fmaf(mr3, dvy, t[p][4]));
+                t[p][5] = fmaf(k1, dz, fmaf(mr3, dvz, t[p][5]));
+                t[p][6] = fmaf(c2, dx, fmaf(c1, dvx, fmaf(mr3, dax, t[p][6])));
+                t[p][7] = fmaf(c2, dy, fmaf(c1, dvy, fmaf(mr3, day, t[p][7])));
+                t[p][8] = fmaf(c2, dz, fmaf(c1, dvz, fmaf(mr3, daz, t[p][8])));
                 t[p][9] += mrinv;
             }
         }
@@ -1244,7 +1244,7 @@ int fused_grid(int device, int order)
 size_t fused_part_float2s(int grid, int na_max, int order)
 {
     if (order == 6) {
-        // groups <= FUSED6_MAX_NA / 4, chunks <= max(G, n / 4096 + 1) <= 4 G + 1
+        // groups <= FUSED6_MAX_NA / 4, chunks <= max(G, n / 8192 + 1) <= 4 G + 1
         return (size_t)(FUSED6_MAX_NA / 4) * (4 * (size_t)grid + 2) * F6_Q;
     }
     // tile items: nchunk * na <= FUSED_MAX_CHUNKS * FUSED_IB for one i-block, else

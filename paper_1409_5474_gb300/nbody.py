@@ -42,7 +42,7 @@ NB_FLAG_TIMING = 1
 NB_FLAG_NO_FUSED = 2
 NB_FUSED_MAX_NA = 4096
 NB_FUSED_DEFAULT_NA = 1024
-NB_FUSED6_MAX_NA = 32
+NB_FUSED6_MAX_NA = 64
 NB_MAX_CORR = 8
 
 

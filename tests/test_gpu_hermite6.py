@@ -323,7 +323,7 @@ def test_fused6_matches_separate_launches(nb):
     """1/16 time unit of order-6 block steps, with and without the fused kernel (N = 5000):
     the same schedule (block steps, final steps), states equal to the double-single force
     error, and the hand-over to the planned kernels for due sets above NB_FUSED6_MAX_NA
-    (the oracle takes 126 of its 214 steps here with at most 32 due)."""
+    (the oracle takes 147 of its 214 steps here with at most 64 due)."""
     p = ic.plummer(5000, 90)
     kw = dict(variant="f32ds", eps=1e-2, eta=0.02, eta_s=0.01, dt_max=1.0 / 16, order=6,
               device=0)
@@ -337,7 +337,7 @@ def test_fused6_matches_separate_launches(nb):
         snb, crb = b.snap()
     print(sa["block_steps"], sa["fused_steps"], sb["block_steps"])
     assert sb["fused_steps"] == 0
-    assert 0.4 * sa["block_steps"] < sa["fused_steps"] < sa["block_steps"]
+    assert 0.5 * sa["block_steps"] < sa["fused_steps"] < sa["block_steps"]
     assert abs(sa["block_steps"] - sb["block_steps"]) <= 0.01 * sb["block_steps"]
     assert sa["interactions"] == pytest.approx(sb["interactions"], rel=0.02)
     np.testing.assert_array_equal(ga["t"], gb["t"])
