@@ -664,7 +664,6 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     const int p0 = min(n, bid * per), p1 = min(n, p0 + per);
     const int nwords = (p1 - p0 + 31) / 32;
     const int total_warps = G * NW;
-    const int gw = bid * NW + warp;
     int *dcnt = a.cnt + G;  // two due-set counters, used in alternate steps
     unsigned gen = 0;
     int par = 0;
@@ -766,7 +765,10 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             if (!(ok = grid_barrier(a.bar, gen))) break;
             mark(1);
             // D: chunk partials -> acc, jerk, pot (fixed order), then the corrector
-            for (int k = gw; k < na; k += total_warps) {
+            // particle k on CTA k % G, warp k / G: the due set spreads over the SMs
+            // (and over each SM's four schedulers) before any SM takes a second
+            // particle, so the FP64 correctors do not queue on one SM's FP64 pipes
+            for (int k = bid + G * warp; k < na; k += total_warps) {
                 // lanes 0..2: the particle's start-of-step state (component = lane),
                 // requested with the chunk partials
                 const bool mine = lane < 3;
