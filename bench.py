@@ -48,8 +48,8 @@ FP64_NOMINAL_TFLOPS = 1.25
 # corrector: index, t, dt, x_p, v_p, a, j, new a, j read (164 B) + x, v, a, j, t, dt written (112 B)
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
 # one-pass ncu capture of the same launch): full N = 2^20 F32-DS evaluation with the
-# built-in plan (2048 i-blocks x 3 j-splits of k_force_tile32, 256-record j-tiles)
-MEASURED_TRAFFIC = {("full2p20", "f32ds", 1 << 20): 454.9e6}
+# built-in plan (2048 i-blocks x 4 j-splits of k_force_tile32, 256-record j-tiles)
+MEASURED_TRAFFIC = {("full2p20", "f32ds", 1 << 20): 348.6e6}
 PREDICT_BYTES = 216
 CORRECT_BYTES = 276
 L2_FLUSH_BYTES = 256 << 20

@@ -1579,7 +1579,10 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
         return p;
     }
     // tiles: 256 threads, 2 i per thread; 8 or 4 warp rows share each j-tile
-    // below 65536 i; about 40 CTAs per SM, at least 16 tiles per split
+    // below 65536 i; about 40 CTAs per SM, at least 16 tiles per split; then, up
+    // to twice that many splits, the fewest whose last wave of resident CTAs is at
+    // least 97% full, else the fullest (N = 2^20: 2048 i-blocks x 3 splits fill
+    // 21% of their 21st wave on 304 slots, x 4 splits 95% of their 27th)
     p.kind = 0;
     p.ipt = 2;
     p.threads = 256;
@@ -1588,7 +1591,21 @@ ForcePlan plan_force(int variant, int n_i, int n_j, int num_sms)
     const long long ib = (long long)(p.threads / p.nwj) * p.ipt;
     const long long nblk = (n_i + ib - 1) / ib;
     const long long ntiles = (n_j + p.jt - 1) / p.jt;
-    p.nsplit = (int)clampll((40LL * num_sms + nblk - 1) / nblk, 1, ntiles / 16 > 1 ? ntiles / 16 : 1);
+    const long long cap = ntiles / 16 > 1 ? ntiles / 16 : 1;
+    const long long ns0 = clampll((40LL * num_sms + nblk - 1) / nblk, 1, cap);
+    const long long slots = (long long)num_sms * tile_blocks_per_sm(variant, p.nwj);
+    long long best = ns0;
+    double best_eff = 0.0;
+    for (long long ns = ns0; ns <= std::min(cap, 2 * ns0); ++ns) {
+        const double waves = (double)(nblk * ns) / (double)slots;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = ns;
+        }
+        if (eff >= 0.97) break;
+    }
+    p.nsplit = (int)best;
     return p;
 }
 
