@@ -415,7 +415,8 @@ int run_force_plan(nb_handle h, int variant, const ForcePlan &p, const ISet &is,
     const double eps2 = h->cfg.eps * h->cfg.eps;
     CK(h, launch_force(variant, p, jset_of(h), is, eps2, h->part, h->split_cnt, out, h->d_err,
                        h->stream, evp));
-    h->stats.kernel_launches += 1;
+    // the FP32 tile kernel's j-split partials are summed by a launch of their own
+    h->stats.kernel_launches += (p.kind == 0 && p.nsplit > 1 && variant != NB_F64) ? 2 : 1;
     int lg = 0;
     while ((2LL << lg) <= is.n && lg < 31) ++lg;
     if (evp) {
