@@ -802,7 +802,7 @@ def run_batch(args, wl, variant, dist, rank, world, local):
                        parallelism=("replicas%d" % world) if world > 1 else "single GPU",
                        cta_threads=threads or "default 128", particles=ntot),
         "fp32_peak_frac": FLOPS_PER_INTERACTION * value * 1e9 / (peak * 1e12),
-        "roofline": {"bound": "alu", "kernel": "k_force_batch32 (batched pair force)",
+        "roofline": {"bound": "alu", "kernel": "k_force_items32 (batched pair force)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "peak_source": "SMs x 128 x 2 x max SM clock %.0f MHz (derived)" % sm_max,
