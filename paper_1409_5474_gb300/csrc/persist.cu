@@ -300,10 +300,10 @@ __device__ __forceinline__ void tile_chunking(int na, int n, int grid, int &nchu
 // An item of a small due set is one group of four due slots (slots 4g ..
 // 4g + 3; idle slots copy the last due one) against one j-chunk; the CTA's
 // eight warps split the chunk, every lane loads up to SMALL_JPL j-records at
-// once before any arithmetic (one L2 round trip per batch), FP32 sums of a
-// batch are folded into double-single totals, which meet in a fixed xor tree
-// per warp and a fixed-order sum over the warps: one double-single partial
-// per (group, chunk) and output q = 7 p + component. The CTA that completes a
+// once before any arithmetic (one L2 round trip per batch), FP32 sums per lane
+// meet in a fixed FP32 xor tree per warp, and the warps' sums in a fixed-order
+// double-single sum: one double-single partial per (group, chunk) and output
+// q = 7 p + component. The CTA that completes a
 // group's last chunk (its ticket) sums the group's partials in a fixed order
 // and corrects the group's particles, so no grid barrier separates the force
 // from the corrector.
@@ -418,11 +418,15 @@ __device__ __forceinline__ void small_item(const FusedArgs &a, int na, int n, in
         vx[p] = C.x; vy[p] = C.y; vz[p] = C.z;
         iid[p] = __float_as_int(B.w);
     }
-    dsf S[G][7];
+    // FP32 sums: per lane over its j (at most SMALL_CHUNK_MAX_J / 256 = 8), then a
+    // fixed xor tree over the warp's 32 lanes (at most 256 terms per sum, fewer
+    // than the 128-term sequential sums of the tile kernels' folds in error);
+    // double-single from the sum over the warps on
+    float S[G][7];
 #pragma unroll
     for (int p = 0; p < G; ++p)
 #pragma unroll
-        for (int q = 0; q < 7; ++q) S[p][q] = dsf{0.f, 0.f};
+        for (int q = 0; q < 7; ++q) S[p][q] = 0.f;
     const int j0 = c * jc, j1 = min(n, j0 + jc);
     const int per_w = (((j1 - j0) + NW - 1) / NW + 31) & ~31;
     const int wj0 = j0 + warp * per_w, wj1 = min(j1, wj0 + per_w);
@@ -479,13 +483,13 @@ __device__ __forceinline__ void small_item(const FusedArgs &a, int na, int n, in
                 tj1 = fmaf(beta, dy, fmaf(mr3, dvy, tj1));
                 tj2 = fmaf(beta, dz, fmaf(mr3, dvz, tj2));
             }
-            ds_acc(S[p][0], dsf{ta0, 0.f});
-            ds_acc(S[p][1], dsf{ta1, 0.f});
-            ds_acc(S[p][2], dsf{ta2, 0.f});
-            ds_acc(S[p][3], dsf{tj0, 0.f});
-            ds_acc(S[p][4], dsf{tj1, 0.f});
-            ds_acc(S[p][5], dsf{tj2, 0.f});
-            ds_acc(S[p][6], dsf{tp, 0.f});
+            S[p][0] += ta0;
+            S[p][1] += ta1;
+            S[p][2] += ta2;
+            S[p][3] += tj0;
+            S[p][4] += tj1;
+            S[p][5] += tj2;
+            S[p][6] += tp;
         }
     }
 #pragma unroll
@@ -493,12 +497,12 @@ __device__ __forceinline__ void small_item(const FusedArgs &a, int na, int n, in
 #pragma unroll
         for (int p = 0; p < G; ++p)
 #pragma unroll
-            for (int q = 0; q < 7; ++q) ds_acc(S[p][q], ds_shfl_xor(S[p][q], o));
+            for (int q = 0; q < 7; ++q) S[p][q] += __shfl_xor_sync(0xffffffffu, S[p][q], o);
     if (lane == 0) {
 #pragma unroll
         for (int p = 0; p < G; ++p)
 #pragma unroll
-            for (int q = 0; q < 7; ++q) s_red[warp][p * 7 + q] = make_float2(S[p][q].hi, S[p][q].lo);
+            for (int q = 0; q < 7; ++q) s_red[warp][p * 7 + q] = make_float2(S[p][q], 0.f);
     }
     __syncthreads();
     if (tid < SMALL_Q) {
@@ -941,8 +945,8 @@ __device__ __forceinline__ void small6_finish(const FusedArgs &a, int na, int g,
 // One item: group g (slots 4 g .. 4 g + 3; idle slots repeat the last due one)
 // against j-chunk c. The eight warps split the chunk; every lane loads up to
 // F6_JPL records before any arithmetic and sums its (at most 32) j in FP32; the
-// lanes' sums meet as double-single values in a fixed xor tree per warp and a
-// fixed-order sum over the warps: one double-single partial per (group, chunk) and output
+// lanes' sums meet in a fixed FP32 xor tree per warp and the warps' sums in a
+// fixed-order double-single sum: one double-single partial per (group, chunk) and output
 // q = 10 p + component (component 9: the positive potential sum).
 template <bool DS>
 __device__ __forceinline__ void small6_item(const FusedArgs &a, int na, int n, int g, int c,
@@ -1045,19 +1049,17 @@ __device__ __forceinline__ void small6_item(const FusedArgs &a, int na, int n, i
             }
         }
     }
-    // the lanes' sums, one slot at a time (fewer live registers)
+    // the lanes' sums in a fixed FP32 xor tree (at most 1024 terms per sum per
+    // warp), one slot at a time; double-single from the sum over the warps on
 #pragma unroll
     for (int p = 0; p < G; ++p) {
-        dsf S[10];
-#pragma unroll
-        for (int q = 0; q < 10; ++q) S[q] = dsf{t[p][q], 0.f};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q < 10; ++q) ds_acc(S[q], ds_shfl_xor(S[q], o));
+            for (int q = 0; q < 10; ++q) t[p][q] += __shfl_xor_sync(0xffffffffu, t[p][q], o);
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 10; ++q) s_red[warp][p * 10 + q] = make_float2(S[q].hi, S[q].lo);
+            for (int q = 0; q < 10; ++q) s_red[warp][p * 10 + q] = make_float2(t[p][q], 0.f);
         }
     }
     __syncthreads();
