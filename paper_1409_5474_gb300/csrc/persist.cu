@@ -340,7 +340,9 @@ __device__ __forceinline__ void store_out(const Out3 &f, int k, int c, double v,
 // range of chunks in order, all its loads in flight at once; the ranges are
 // then added in order) and the corrector of its due particles.
 constexpr int SMALL_SUBS = FUSED_THREADS / SMALL_Q;  // 9 ranges per output
-constexpr int SMALL_BATCH = 16;                       // loads in flight per thread
+// loads in flight per thread: every range of up to 9 x 24 = 216 chunks (the grid's
+// 152 and more) in one L2 round trip
+constexpr int SMALL_BATCH = 24;
 
 __device__ __forceinline__ void small_finish(const FusedArgs &a, int na, int g, int nchunk,
                                              double tn, float *s_fin)
@@ -870,6 +872,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 constexpr int F6_Q = 40;                          // outputs of a group: 4 slots x 10
 constexpr int F6_SUBS = FUSED_THREADS / F6_Q;     // 6 ranges per output
 constexpr int F6_JPL = 2;                         // j-records per lane and batch
+constexpr int F6_BATCH = 26;  // partial loads in flight: 6 x 26 = 156 chunks in one round trip
 constexpr int F6_CHUNK_MAX_J = 8192;              // j per chunk: 32 per lane
 
 // The j-chunks of an order-6 small due set (a function of (na, n, grid) only):
@@ -906,14 +909,14 @@ __device__ __forceinline__ void small6_finish(const FusedArgs &a, int na, int g,
         const int c0 = sub * len, c1 = min(nchunk, c0 + len);
         const float2 *base = a.part + (size_t)g * nchunk * F6_Q + o;
         dsf acc{0.f, 0.f};
-        for (int cb = c0; cb < c1; cb += SMALL_BATCH) {
-            float2 x[SMALL_BATCH];
+        for (int cb = c0; cb < c1; cb += F6_BATCH) {
+            float2 x[F6_BATCH];
 #pragma unroll
-            for (int u = 0; u < SMALL_BATCH; ++u)
+            for (int u = 0; u < F6_BATCH; ++u)
                 x[u] = cb + u < c1 ? __ldcg(base + (size_t)(cb + u) * F6_Q)
                                    : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < SMALL_BATCH; ++u) ds_acc(acc, dsf{x[u].x, x[u].y});
+            for (int u = 0; u < F6_BATCH; ++u) ds_acc(acc, dsf{x[u].x, x[u].y});
         }
         s_fin[2 * tid] = acc.hi;
         s_fin[2 * tid + 1] = acc.lo;
