@@ -617,6 +617,40 @@ ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
     p.kind = 0;
     const bool f64 = (variant == NB_F64);
     p.ipt = 1;  // the packed pair terms already give each thread two j per step
+    if (!f64 && n_i > 256 && n_i < 512) {
+        // 257-511 due particles: the shape (warp rows) and split count of least
+        // estimated time, waves x (i per CTA x j per CTA + about 16384 pair terms of
+        // fixed cost per CTA: prologue, pipeline fill, epilogue), with at least 4 j-tiles
+        // per split; candidates: the split counts just within 1..8 whole waves. The rule
+        // below gives these sizes two half-used i-blocks in two waves of CTAs of 1.7
+        // j-tiles each (87 us per launch at N = 65536, 200 G/s); this model gives 8 warp
+        // rows and one wave (66 us). For 128-255 and 2048-4095 due particles the same
+        // model chose shapes 5% slower than the rule's, so it is not used there.
+        const long long ntiles = (n_j + H6_JT - 1) / H6_JT;
+        const long long cap = std::max(1LL, std::min(ntiles / 4, 1024LL));
+        const bool ds = variant == NB_F32DS;
+        double best_t = -1.0;
+        for (int nwj = 1; nwj <= 8; nwj *= 2) {
+            const long long ib = 32LL * (H6_NWARP / nwj);
+            const long long nblk = (n_i + ib - 1) / ib;
+            const long long slots = (long long)std::max(num_sms, 1) * occ6_of(ds, 1, nwj);
+            for (int k = 0; k <= 9; ++k) {
+                const long long ns =
+                    k == 0 ? 1 : (k == 9 ? cap : std::max(1LL, std::min(cap, k * slots / nblk)));
+                const long long jpc = (ntiles + ns - 1) / ns * H6_JT;
+                const double t = (double)((nblk * ns + slots - 1) / slots) *
+                                 ((double)ib * (double)jpc + 16384.0);
+                if (best_t < 0.0 || t < best_t * (1.0 - 1e-12)) {
+                    best_t = t;
+                    p.nwj = nwj;
+                    p.nsplit = (int)ns;
+                }
+            }
+        }
+        p.threads = 32 * (H6_NWARP / p.nwj);
+        p.jt = H6_JT;
+        return p;
+    }
     p.nwj = f64 ? 1 : (n_i <= 32 ? 8 : n_i <= 64 ? 4 : n_i <= 128 ? 2 : 1);
     p.threads = f64 ? H6_T64 : 32 * (H6_NWARP / p.nwj) * p.ipt;  // i-particles per CTA
     p.jt = f64 ? H6_JT64 : H6_JT;
