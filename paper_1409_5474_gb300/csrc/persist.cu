@@ -3,21 +3,24 @@
 // step with a small due set (the common case of block time steps, Sect. III:
 // most block times have only a few particles due) costs no host round trip
 // and no launch gaps:
-//   A  t_next from the level histogram; every CTA predicts its contiguous
-//      range of particles (K1, FP64 + double-single records) and flags the
-//      due ones;                                            -- barrier
-//   B  the due set is compacted in ascending index (CTA counts, prefix over
-//      the CTAs) with its records gathered; if t_next > t_end or the due set
-//      is larger than na_max the kernel publishes (epoch, t_next, N_active)
-//      to the mailbox like K5 + K1 and returns;             -- barrier
-//   C  pair force (K2): warp items of four due particles against a j-chunk
-//      (lanes over j), or, for larger due sets, CTA items of 32 due particles
-//      whose j-chunk is staged through shared memory; double-single partials
-//      per chunk;                                           -- barrier
-//   D  one warp per due particle sums its chunk partials in chunk order (K3)
-//      and corrects it, three lanes for the three components (K4: Hermite
-//      corrector, Aarseth step, histogram);
-//                                                            -- barrier
+//   A  t_next and the due count from the level histogram; if t_next > t_end
+//      or the due set is larger than na_max, every CTA predicts its range in
+//      full, the due set is gathered in ascending index (CTA counts, prefix)
+//      and the kernel publishes (epoch, t_next, N_active) to the mailbox like
+//      K5 + K1 and returns; else every CTA predicts its contiguous range of
+//      particles (K1, double-single records only) and its due particles take
+//      slots of the due set by warp-aggregated atomics;  -- barrier
+//   C  small due sets: items of four due slots against a j-chunk (lanes over
+//      j); the CTA that completes a group's last chunk (a ticket) sums its
+//      double-single partials in chunk order (K3) and corrects its particles
+//      (K4), three lanes for the three components; larger due sets (order 4):
+//      CTA items of 32 due slots whose j-chunk is staged through shared memory
+//      as j-pairs, double-single partials per chunk;   -- barrier
+//   D  (larger due sets) one warp per due particle sums its chunk partials in
+//      chunk order (K3) and corrects it (K4: Hermite corrector, Aarseth step,
+//      histogram);                                          -- barrier
+// k_fused_steps6 runs the same loop for the 6th-order scheme with the small
+// path only (64-byte records, ten outputs per slot, the order-6 corrector).
 // Every inter-CTA wait is bounded; a CTA that gives up raises the abort flag
 // and all CTAs leave at their next barrier (the host then reports a timeout).
 // This file is compiled with global loads cached in L2 only (-dlcm=cg): data
