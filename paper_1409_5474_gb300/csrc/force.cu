@@ -1318,13 +1318,16 @@ __global__ void __launch_bounds__(256)
 
 
 template <int VAR, int IPT, int NT, int JT, int NS>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 512 / NT)
     k_force_items32(const WorkItem *__restrict__ items, int nitems)
 {
-    extern __shared__ __align__(128) float4 s_tile[];  // NS * JT * DS_REC
+    // NS ring stages of JT records, then the current full tile as j-pairs
+    extern __shared__ __align__(128) float4 s_tile[];
     __shared__ __align__(8) uint64_t s_full[NS];
     __shared__ int s_abort;
     constexpr bool DS = (VAR == NB_F32DS);
+    constexpr int NPAIR = JT / 2;
+    float4 *s_pair = s_tile + (size_t)NS * JT * DS_REC;
     const int tid = threadIdx.x;
 
     if (tid == 0) {
@@ -1340,10 +1343,14 @@ __global__ void __launch_bounds__(NT)
         const WorkItem w = items[it];
         unsigned *err = w.err;
         const float eps2f = w.eps2;
+        const float2 e2 = make_float2(eps2f, eps2f);
         const float4 *__restrict__ jrec = w.jrec;
         const int ntiles = (w.nj + JT - 1) / JT;
 
-        float xh[IPT], yh[IPT], zh[IPT], xl[IPT], yl[IPT], zl[IPT], vx[IPT], vy[IPT], vz[IPT];
+        // the i-particles, negated and duplicated into both halves of a float2 (the
+        // packed pair terms take two j at a time; the scalar path uses .x)
+        float2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT], nvx[IPT], nvy[IPT],
+            nvz[IPT];
         int iid[IPT];
 #pragma unroll
         for (int p = 0; p < IPT; ++p) {
@@ -1352,9 +1359,15 @@ __global__ void __launch_bounds__(NT)
             const float4 a = __ldg(w.irec + (size_t)DS_REC * r);
             const float4 b = __ldg(w.irec + (size_t)DS_REC * r + 1);
             const float4 c = __ldg(w.irec + (size_t)DS_REC * r + 2);
-            xh[p] = a.x; yh[p] = a.y; zh[p] = a.z;
-            xl[p] = b.x; yl[p] = b.y; zl[p] = b.z;
-            vx[p] = c.x; vy[p] = c.y; vz[p] = c.z;
+            nxh[p] = make_float2(-a.x, -a.x);
+            nyh[p] = make_float2(-a.y, -a.y);
+            nzh[p] = make_float2(-a.z, -a.z);
+            nxl[p] = make_float2(-b.x, -b.x);
+            nyl[p] = make_float2(-b.y, -b.y);
+            nzl[p] = make_float2(-b.z, -b.z);
+            nvx[p] = make_float2(-c.x, -c.x);
+            nvy[p] = make_float2(-c.y, -c.y);
+            nvz[p] = make_float2(-c.z, -c.z);
             iid[p] = w.gathered ? __float_as_int(b.w) : r;
         }
         float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
@@ -1388,12 +1401,14 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int p = 0; p < IPT; ++p) own = own || (iid[p] >= jbase && iid[p] < jbase + cnt);
             own = __any_sync(0xffffffffu, own);
-            float ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
+            // FP32 sums of this tile, two lanes each (even and odd j of a pair; the
+            // scalar path adds into .x)
+            float2 ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
 #pragma unroll
             for (int p = 0; p < IPT; ++p) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = 0.f;
-                tp[p] = 0.f;
+                for (int c = 0; c < 3; ++c) ta[p][c] = tja[p][c] = tjb[p][c] = make_float2(0.f, 0.f);
+                tp[p] = make_float2(0.f, 0.f);
             }
             auto body = [&](int jj, auto masked_tag) {
                 constexpr bool MASKED = decltype(masked_tag)::value;
@@ -1405,15 +1420,15 @@ __global__ void __launch_bounds__(NT)
                 for (int p = 0; p < IPT; ++p) {
                     float dx, dy, dz;
                     if (DS) {
-                        dx = (a.x - xh[p]) + (b.x - xl[p]);
-                        dy = (a.y - yh[p]) + (b.y - yl[p]);
-                        dz = (a.z - zh[p]) + (b.z - zl[p]);
+                        dx = (a.x + nxh[p].x) + (b.x + nxl[p].x);
+                        dy = (a.y + nyh[p].x) + (b.y + nyl[p].x);
+                        dz = (a.z + nzh[p].x) + (b.z + nzl[p].x);
                     } else {
-                        dx = a.x - xh[p];
-                        dy = a.y - yh[p];
-                        dz = a.z - zh[p];
+                        dx = a.x + nxh[p].x;
+                        dy = a.y + nyh[p].x;
+                        dz = a.z + nzh[p].x;
                     }
-                    const float dvx = c.x - vx[p], dvy = c.y - vy[p], dvz = c.z - vz[p];
+                    const float dvx = c.x + nvx[p].x, dvy = c.y + nvy[p].x, dvz = c.z + nvz[p].x;
                     float r2 = fmaf(dx, dx, eps2f);
                     r2 = fmaf(dy, dy, r2);
                     r2 = fmaf(dz, dz, r2);
@@ -1426,23 +1441,89 @@ __global__ void __launch_bounds__(NT)
                     const float mrinv = a.w * rinv;
                     const float mr3 = mrinv * rinv2;
                     const float beta = (mr3 * rinv2) * rv;
-                    tp[p] += mrinv;
-                    ta[p][0] = fmaf(mr3, dx, ta[p][0]);
-                    ta[p][1] = fmaf(mr3, dy, ta[p][1]);
-                    ta[p][2] = fmaf(mr3, dz, ta[p][2]);
-                    tja[p][0] = fmaf(mr3, dvx, tja[p][0]);
-                    tja[p][1] = fmaf(mr3, dvy, tja[p][1]);
-                    tja[p][2] = fmaf(mr3, dvz, tja[p][2]);
-                    tjb[p][0] = fmaf(beta, dx, tjb[p][0]);
-                    tjb[p][1] = fmaf(beta, dy, tjb[p][1]);
-                    tjb[p][2] = fmaf(beta, dz, tjb[p][2]);
+                    tp[p].x += mrinv;
+                    ta[p][0].x = fmaf(mr3, dx, ta[p][0].x);
+                    ta[p][1].x = fmaf(mr3, dy, ta[p][1].x);
+                    ta[p][2].x = fmaf(mr3, dz, ta[p][2].x);
+                    tja[p][0].x = fmaf(mr3, dvx, tja[p][0].x);
+                    tja[p][1].x = fmaf(mr3, dvy, tja[p][1].x);
+                    tja[p][2].x = fmaf(mr3, dvz, tja[p][2].x);
+                    tjb[p][0].x = fmaf(beta, dx, tjb[p][0].x);
+                    tjb[p][1].x = fmaf(beta, dy, tjb[p][1].x);
+                    tjb[p][2].x = fmaf(beta, dz, tjb[p][2].x);
                 }
             };
-            if (own) {
+            if (cnt == JT) {
+                // full tile: transposed into j-pairs for the packed FP32x2 pair terms
+                for (int x = tid; x < 3 * NPAIR; x += NT) {
+                    const int q = x % NPAIR, part = x / NPAIR;
+                    const float4 u = T[DS_REC * (2 * q) + part];
+                    const float4 v = T[DS_REC * (2 * q + 1) + part];
+                    float4 *P = s_pair + 6 * q + 2 * part;
+                    P[0] = make_float4(u.x, v.x, u.y, v.y);
+                    P[1] = make_float4(u.z, v.z, u.w, v.w);
+                }
+                __syncthreads();
+                if (own) {
+                    for (int jj = 0; jj < JT; ++jj) body(jj, std::true_type{});
+                } else {
+#pragma unroll 2
+                    for (int q = 0; q < NPAIR; ++q) {
+                        const float4 *P = s_pair + 6 * q;
+                        const float4 q0 = P[0], q1 = P[1], q4 = P[4], q5 = P[5];
+                        float4 q2, q3;
+                        if (DS) {
+                            q2 = P[2];
+                            q3 = P[3];
+                        }
+                        const float2 XH = make_float2(q0.x, q0.y), YH = make_float2(q0.z, q0.w);
+                        const float2 ZH = make_float2(q1.x, q1.y), MJ = make_float2(q1.z, q1.w);
+                        const float2 VX = make_float2(q4.x, q4.y), VY = make_float2(q4.z, q4.w);
+                        const float2 VZ = make_float2(q5.x, q5.y);
+#pragma unroll
+                        for (int p = 0; p < IPT; ++p) {
+                            float2 dx, dy, dz;
+                            if (DS) {
+                                dx = __fadd2_rn(__fadd2_rn(XH, nxh[p]),
+                                                __fadd2_rn(make_float2(q2.x, q2.y), nxl[p]));
+                                dy = __fadd2_rn(__fadd2_rn(YH, nyh[p]),
+                                                __fadd2_rn(make_float2(q2.z, q2.w), nyl[p]));
+                                dz = __fadd2_rn(__fadd2_rn(ZH, nzh[p]),
+                                                __fadd2_rn(make_float2(q3.x, q3.y), nzl[p]));
+                            } else {
+                                dx = __fadd2_rn(XH, nxh[p]);
+                                dy = __fadd2_rn(YH, nyh[p]);
+                                dz = __fadd2_rn(ZH, nzh[p]);
+                            }
+                            const float2 dvx = __fadd2_rn(VX, nvx[p]);
+                            const float2 dvy = __fadd2_rn(VY, nvy[p]);
+                            const float2 dvz = __fadd2_rn(VZ, nvz[p]);
+                            float2 r2 = __ffma2_rn(dx, dx, e2);
+                            r2 = __ffma2_rn(dy, dy, r2);
+                            r2 = __ffma2_rn(dz, dz, r2);
+                            float2 rv = __fmul2_rn(dx, dvx);
+                            rv = __ffma2_rn(dy, dvy, rv);
+                            rv = __ffma2_rn(dz, dvz, rv);
+                            const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                            const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                            const float2 mrinv = __fmul2_rn(MJ, rinv);
+                            const float2 mr3 = __fmul2_rn(mrinv, rinv2);
+                            const float2 beta = __fmul2_rn(__fmul2_rn(mr3, rinv2), rv);
+                            tp[p] = __fadd2_rn(tp[p], mrinv);
+                            ta[p][0] = __ffma2_rn(mr3, dx, ta[p][0]);
+                            ta[p][1] = __ffma2_rn(mr3, dy, ta[p][1]);
+                            ta[p][2] = __ffma2_rn(mr3, dz, ta[p][2]);
+                            tja[p][0] = __ffma2_rn(mr3, dvx, tja[p][0]);
+                            tja[p][1] = __ffma2_rn(mr3, dvy, tja[p][1]);
+                            tja[p][2] = __ffma2_rn(mr3, dvz, tja[p][2]);
+                            tjb[p][0] = __ffma2_rn(beta, dx, tjb[p][0]);
+                            tjb[p][1] = __ffma2_rn(beta, dy, tjb[p][1]);
+                            tjb[p][2] = __ffma2_rn(beta, dz, tjb[p][2]);
+                        }
+                    }
+                }
+            } else if (own) {
                 for (int jj = 0; jj < cnt; ++jj) body(jj, std::true_type{});
-            } else if (cnt == JT) {
-#pragma unroll 4
-                for (int jj = 0; jj < JT; ++jj) body(jj, std::false_type{});
             } else {
 #pragma unroll 2
                 for (int jj = 0; jj < cnt; ++jj) body(jj, std::false_type{});
@@ -1451,21 +1532,24 @@ __global__ void __launch_bounds__(NT)
             for (int p = 0; p < IPT; ++p) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float jt = fmaf(-3.f, tjb[p][c], tja[p][c]);
+                    const float sa = ta[p][c].x + ta[p][c].y;
+                    const float jt = fmaf(-3.f, tjb[p][c].x + tjb[p][c].y,
+                                          tja[p][c].x + tja[p][c].y);
                     if (DS) {
-                        ds_add(A_h[p][c], A_l[p][c], ta[p][c]);
+                        ds_add(A_h[p][c], A_l[p][c], sa);
                         ds_add(J_h[p][c], J_l[p][c], jt);
                     } else {
-                        A_h[p][c] += ta[p][c];
+                        A_h[p][c] += sa;
                         J_h[p][c] += jt;
                     }
                 }
+                const float sp = tp[p].x + tp[p].y;
                 if (DS)
-                    ds_add(P_h[p], P_l[p], tp[p]);
+                    ds_add(P_h[p], P_l[p], sp);
                 else
-                    P_h[p] += tp[p];
+                    P_h[p] += sp;
             }
-            __syncthreads();
+            __syncthreads();  // the stage and the pair buffer are free
             if (s_abort) {
                 if (tid == 0) {
                     drain_ring<NS>(s_full, seq, kt, ntiles);
@@ -1790,7 +1874,7 @@ static cudaError_t dispatch64(const ForcePlan &p, const JSet &js, const ISet &is
 template <int VAR, int NT>
 static cudaError_t go_items(const WorkItem *items, int nitems, int grid, cudaStream_t st)
 {
-    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
+    const size_t smem = (size_t)(NS32 + 1) * JT32 * DS_REC * sizeof(float4);
     k_force_items32<VAR, 2, NT, JT32, NS32><<<grid, NT, smem, st>>>(items, nitems);
     return cudaGetLastError();
 }
@@ -1899,7 +1983,7 @@ int tile_blocks_per_sm(int variant, int nwj)
 int batch_blocks_per_sm(int variant, int threads)
 {
     int nb = 0;
-    const size_t smem = (size_t)NS32 * JT32 * DS_REC * sizeof(float4);
+    const size_t smem = (size_t)(NS32 + 1) * JT32 * DS_REC * sizeof(float4);
     cudaError_t e;
     if (variant == NB_F32DS) {
         e = threads == 64    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
