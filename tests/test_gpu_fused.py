@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 from paper_1409_5474_gb300 import ic
+from tests.errstats import fmt, report
 
 pytestmark = pytest.mark.gpu
 
@@ -88,3 +89,52 @@ def test_fused_f32_variant_and_energy(nb):
         k1, w1 = s.energy()
     assert st["fused_steps"] > 0
     assert abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0) < 1e-4
+
+
+def test_fused_single_steps_both_paths_vs_oracle_and_planned(nb):
+    """Single block steps taken by the fused kernel at N = 8000, through both of its force
+    paths: group items (at most 16 due) and tile items (17 to NB_FUSED_DEFAULT_NA due: 32
+    due slots per item against j-chunks staged in shared memory, then one warp per due
+    particle reducing and correcting). The due particles' new acc and jerk against the
+    oracle on the cubic prediction of the state before the step, and against the planned
+    kernels (nb_predict + nb_force on the same state: the same pair terms summed in
+    another order)."""
+    n, eps = 8000, 0.01
+    p = ic.plummer(n, 63)
+    sizes = []
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.02, device=0) as s:
+        s.step(1.0 / 256)
+        for _ in range(400):
+            if sum(k > 16 for k in sizes) >= 3 and sum(k <= 16 for k in sizes) >= 3:
+                break
+            g0 = s.state()
+            t_next = float((g0["t"] + g0["dt"]).min())
+            due = np.nonzero(g0["t"] + g0["dt"] == t_next)[0].astype(np.int32)
+            fused = len(due) <= nb.NB_FUSED_DEFAULT_NA
+            if fused:
+                s.predict(t_next)
+                h_acc, h_jerk, _ = s.force(due)
+            st = s.step(t_next)
+            assert st["block_steps"] == 1 and st["fused_steps"] == (1 if fused else 0), st
+            if not fused:
+                continue
+            g1 = s.state()
+            d = t_next - g0["t"]
+            x, v, a, j = g0["pos"], g0["vel"], g0["acc"], g0["jerk"]
+            xp = x + d * (v + d * (a / 2 + d * j / 6))
+            vp = v + d * (a + d * j / 2)
+            ra, rj, _ = oracle.force(g0["m"], xp.T, vp.T, eps * eps, idx=due)
+            got_a, got_j = g1["acc"][:, due].T, g1["jerk"][:, due].T
+            rep = report({"acc": (got_a, ra), "jerk": (got_j, rj)})
+            rep_h = report({"acc": (got_a, h_acc.T), "jerk": (got_j, h_jerk.T)})
+            print(len(due), "oracle:", fmt(rep), "| planned:", fmt(rep_h))
+            # per-particle gates of the force tests (F32-DS: acc 1e-5, jerk 1e-4); the
+            # RMS gates where the set is large enough for the RMS to mean one
+            for q, g_max, g_rms in (("acc", 1e-5, 1e-6), ("jerk", 1e-4, 2e-6)):
+                assert rep[q][1] < g_max and rep_h[q][1] < g_max, (len(due), q, rep[q], rep_h[q])
+                if len(due) >= 32:
+                    assert rep[q][0] < g_rms, (len(due), q, rep[q])
+            np.testing.assert_array_equal(g1["t"][due], t_next)
+            sizes.append(len(due))
+    print("due-set sizes", sizes)
+    assert sum(k > 16 for k in sizes) >= 3 and sum(k <= 16 for k in sizes) >= 3, sizes
