@@ -490,7 +490,7 @@ def run_ours(args):
     # plan, which the built-in heuristic already takes from a sweep
     # (a force on an i-subset, --n-i, is tuned too: profiling of the block steps' plans)
     plan_table = (nbody.nb_autotune(h, 3)
-                  if args.autotune and order == 4 and (wl["kind"] == "evolve" or args.n_i)
+                  if args.autotune and (wl["kind"] == "evolve" or args.n_i)
                   else None)
     t_tune = time.perf_counter() - t_tune
 

@@ -99,8 +99,8 @@ typedef struct nb_config {
                           * and predicts through the crackle (Sect. II: >= 4th-order
                           * integrators with individual steps; the cited 6th-order Hermite
                           * scheme of Nitadori & Makino). Order 6 needs NB_F32DS or NB_F64
-                          * pairs and n_corr <= 1, and has no plan table, external i-sets
-                          * or bridge calls; its fused kernel (NB_F32DS) takes due sets of
+                          * pairs and n_corr <= 1, and has no external i-sets or bridge
+                          * calls; its fused kernel (NB_F32DS) takes due sets of
                           * up to min(fused_max_na, NB_FUSED6_MAX_NA) particles. Its
                           * steps follow Aarseth's criterion with the evaluated snap as a2
                           * and the end-of-step crackle as a3 (eta ~ 0.01-0.04). */
@@ -284,7 +284,10 @@ int nb_reset_stats(nb_handle h);
  *           and each holds up to 4 j-records; the split count follows from
  *           the j-set size (nsplit is ignored).
  * A plan changes only the order in which pair terms are summed, not which are
- * summed. Plans are looked up by bucket b = ceil(log2(n_i)) (0..31). */
+ * summed. Plans are looked up by bucket b = ceil(log2(n_i)) (0..31). An
+ * order-6 handle's table holds kind 0 entries only (the 6th-order tile kernel:
+ * nwj = 1, 2, 4 or 8 warp rows of 256 / nwj i-particles each; FP64 pairs use
+ * one warp row). */
 typedef struct nb_plan {
     int kind;   /* 0 tiles, 1 warp groups, 2 tiny sets, -1 = built-in heuristic */
     int nwj;    /* warp rows per CTA (kind 0) */
@@ -310,7 +313,10 @@ int nb_get_plan_table(nb_handle h, nb_plan *table /* 32 entries */);
  * fills the same waves of the GPU. Entries set by nb_set_plan_table are used
  * as given. The particle state is left unchanged; the prediction is not (the
  * j-set is predicted to the latest own time), so call nb_predict again before
- * a manual nb_force. */
+ * a manual nb_force. Order-6 handles (NB_F32DS) time the 6th-order tile kernel
+ * with 1, 2, 4 and 8 warp rows, each at the split counts that fill 1..8 whole
+ * waves, and the built-in plan; an order-6 FP64 handle keeps the built-in plan
+ * (NB_OK, table unchanged). */
 int nb_autotune(nb_handle h, int reps);
 
 /* ---- batched systems -------------------------------------------------------

@@ -557,12 +557,44 @@ int do_init(nb_handle h)
 
 // ---- 6th-order scheme ---------------------------------------------------------
 
+// The 6th-order plan of an evaluation of n_i i-particles: the plan table's entry of
+// its bucket (kind 0) when one is set, else the built-in rule. An entry that
+// nb_autotune timed at n_i = min(2^b, n) keeps its CTA count for the other sizes of
+// the bucket (split count scaled by the ratio of i-blocks, rounded down).
+ForcePlan plan_for6(nb_handle h, int variant, int n_i)
+{
+    const int b = bucket_of(n_i);
+    const nb_plan &e = h->plans[b];
+    if (e.kind == 0 && variant == h->cfg.variant) {
+        nb_plan use = e;
+        if (h->plan_tuned[b]) {
+            const int n_ref = (int)std::min<long long>(1LL << b, h->n);
+            const ForcePlan one = plan6_from_entry(variant, e.nwj, 1, n_i, h->n);
+            const long long ib = (long long)one.threads * one.ipt;
+            const long long ref = (n_ref + ib - 1) / ib, act = (n_i + ib - 1) / ib;
+            if (ref != act && act > 0)
+                use.nsplit = (int)std::max(1LL, ((long long)e.nsplit * ref) / act);
+        }
+        return plan6_from_entry(variant, use.nwj, use.nsplit, n_i, h->n);
+    }
+    return plan_force6(variant, n_i, h->n, h->num_sms);
+}
+
+int run_force6_plan(nb_handle h, int variant, const ForcePlan &p, const int *idx_dev, int n_i,
+                    const Out6 &out);
+
 // acc, jerk, snap and pot of the members idx_dev[k] (null: k) at the predicted
 // state into out; plans, grows scratch, records timers and counters.
 int run_force6(nb_handle h, int variant, const int *idx_dev, int n_i, const Out6 &out)
 {
     if (n_i <= 0) return NB_OK;
-    const ForcePlan p = plan_force6(variant, n_i, h->n, h->num_sms);
+    return run_force6_plan(h, variant, plan_for6(h, variant, n_i), idx_dev, n_i, out);
+}
+
+int run_force6_plan(nb_handle h, int variant, const ForcePlan &p, const int *idx_dev, int n_i,
+                    const Out6 &out)
+{
+    if (n_i <= 0) return NB_OK;
     int rc = grow(h, &h->part, &h->part_cap, std::max<size_t>(plan6_partial_doubles(p, n_i), 1));
     if (rc) return rc;
     cudaEvent_t ev[4];
@@ -1770,7 +1802,8 @@ int nb_plan_for(nb_handle h, int n_i, nb_plan *out)
 {
     if (!h || !out || n_i < 1) return NB_ERR_ARG;
     if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
-    *out = entry_of(plan_for(h, h->cfg.variant, n_i));
+    *out = entry_of(order6(h) ? plan_for6(h, h->cfg.variant, n_i)
+                              : plan_for(h, h->cfg.variant, n_i));
     return NB_OK;
 }
 
@@ -1789,7 +1822,11 @@ int nb_set_plan_table(nb_handle h, const nb_plan *table, int n)
         const nb_plan &e = table[b];
         if (e.kind < -1 || e.kind > 2 || (e.kind >= 0 && e.nsplit < 1))
             return fail(h, NB_ERR_ARG, "plan entry %d is malformed", b);
-        if (e.kind == 0 && !(e.nwj == 1 || e.nwj == 4 || e.nwj == 8))
+        if (order6(h) && e.kind > 0)
+            return fail(h, NB_ERR_ARG, "plan entry %d: order 6 has the tile kind only", b);
+        if (order6(h) && e.kind == 0 && !(e.nwj == 1 || e.nwj == 2 || e.nwj == 4 || e.nwj == 8))
+            return fail(h, NB_ERR_ARG, "plan entry %d: nwj must be 1, 2, 4 or 8", b);
+        if (!order6(h) && e.kind == 0 && !(e.nwj == 1 || e.nwj == 4 || e.nwj == 8))
             return fail(h, NB_ERR_ARG, "plan entry %d: nwj must be 1, 4 or 8", b);
     }
     for (int b = 0; b < 32; ++b) {
@@ -1806,11 +1843,13 @@ int nb_get_plan_table(nb_handle h, nb_plan *table)
     return NB_OK;
 }
 
+int autotune6(nb_handle h, int reps);
+
 int nb_autotune(nb_handle h, int reps)
 {
     if (!h) return NB_ERR_ARG;
-    if (order6(h)) return fail(h, NB_ERR_ARG, "the plan table serves the 4th-order kernels");
     if (!h->have_particles) return fail(h, NB_ERR_STATE, "no particles set");
+    if (order6(h)) return autotune6(h, reps);
     if (reps < 1) reps = 1;
     cudaSetDevice(h->dev);
     const int n = h->n;
@@ -1897,6 +1936,98 @@ int nb_autotune(nb_handle h, int reps)
             for (int r = 0; r < reps; ++r) {
                 CK(h, cudaEventRecord(e0, h->stream));
                 rc = run_force_plan(h, variant, p, is, out);
+                if (rc) break;
+                CK(h, cudaEventRecord(e1, h->stream));
+                CK(h, cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(h, cudaEventElapsedTime(&t, e0, e1));
+                ms.push_back(t);
+            }
+            if (rc) break;
+            std::sort(ms.begin(), ms.end());
+            const double med = ms[ms.size() / 2];
+            if (med < best) {
+                best = med;
+                best_e = entry_of(p);
+            }
+        }
+        if (rc == NB_OK) {
+            h->plans[b] = best_e;
+            h->plan_tuned[b] = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->cfg.flags = saved_flags;
+    h->stats = saved_stats;
+    h->predicted = false;
+    h->last_force_n = -1;
+    if (rc) return rc;
+    return check_err(h);
+}
+
+// nb_autotune of a 6th-order handle (F32-DS pairs; FP64 keeps the built-in rule):
+// for every bucket up to N, at n_i = min(2^b, N) evenly spread members, the
+// 6th-order tile kernel with 1, 2, 4 and 8 warp rows, each with the split counts
+// that fill 1..8 whole waves of resident CTAs (rounded down), and the built-in
+// plan; the fastest median of reps timed launches goes into the plan table.
+int autotune6(nb_handle h, int reps)
+{
+    if (reps < 1) reps = 1;
+    const int variant = h->cfg.variant;
+    if (variant == NB_F64) return NB_OK;
+    cudaSetDevice(h->dev);
+    const int n = h->n;
+    std::vector<double> tt(n);
+    CK(h, cudaMemcpyAsync(tt.data(), h->t, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double tmax = tt[0];
+    for (int i = 1; i < n; ++i) tmax = std::max(tmax, tt[i]);
+    int rc = predict_to(h, tmax);
+    if (rc) return rc;
+    const int saved_flags = h->cfg.flags;
+    h->cfg.flags &= ~NB_FLAG_TIMING;  // the tuner's own events only
+    const nb_stats saved_stats = h->stats;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    const int bmax = bucket_of(n);
+    const long long ntiles = (n + 127) / 128;
+    for (int b = 0; b <= bmax && rc == NB_OK; ++b) {
+        const int n_i = (int)std::min<long long>(1LL << b, n);
+        std::vector<int> idx(n_i);
+        for (int k = 0; k < n_i; ++k) idx[k] = (int)((long long)k * n / n_i);
+        rc = grow(h, &h->d_idx, &h->idx_cap, (size_t)n_i);
+        if (rc) break;
+        rc = grow(h, &h->io, &h->io_cap, 10 * (size_t)n_i);
+        if (rc) break;
+        CK(h, cudaMemcpyAsync(h->d_idx, idx.data(), n_i * sizeof(int), cudaMemcpyHostToDevice,
+                              h->stream));
+        const Out6 out{h->io, h->io + 3 * (size_t)n_i, h->io + 6 * (size_t)n_i,
+                       h->io + 9 * (size_t)n_i, n_i};
+        const ForcePlan base = plan_force6(variant, n_i, n, h->num_sms);
+        std::vector<nb_plan> entries{entry_of(base)};
+        for (int nwj = 1; nwj <= 8; nwj *= 2) {
+            const long long ib = 32LL * (8 / nwj);
+            const long long nblk = (n_i + ib - 1) / ib;
+            const long long slots = (long long)h->num_sms * occ6_blocks(variant, nwj);
+            long long last = 0;
+            for (long long k = 1; k <= 8; ++k) {
+                const long long ns = std::min(std::min(ntiles, 1024LL), std::max(1LL, k * slots / nblk));
+                if (ns != last) entries.push_back(nb_plan{0, nwj, (int)ns});
+                last = ns;
+            }
+        }
+        double best = 1e30;
+        nb_plan best_e = entry_of(base);
+        for (const nb_plan &e : entries) {
+            const ForcePlan p = plan6_from_entry(variant, e.nwj, e.nsplit, n_i, n);
+            rc = run_force6_plan(h, variant, p, h->d_idx, n_i, out);  // warm-up
+            if (rc) break;
+            std::vector<float> ms;
+            for (int r = 0; r < reps; ++r) {
+                CK(h, cudaEventRecord(e0, h->stream));
+                rc = run_force6_plan(h, variant, p, h->d_idx, n_i, out);
                 if (rc) break;
                 CK(h, cudaEventRecord(e1, h->stream));
                 CK(h, cudaEventSynchronize(e1));

@@ -676,6 +676,33 @@ ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms)
     return p;
 }
 
+// The plan of a table entry (F32 / double-single kinds: warp rows nwj in {1, 2, 4,
+// 8}, nsplit j-splits clamped to the j-tiles and to 1024; FP64: one warp row).
+ForcePlan plan6_from_entry(int variant, int nwj, int nsplit, int n_i, int n_j)
+{
+    ForcePlan p{};
+    p.kind = 0;
+    p.ipt = 1;
+    if (variant == NB_F64) {
+        p.nwj = 1;
+        p.threads = H6_T64;
+        p.jt = H6_JT64;
+    } else {
+        p.nwj = (nwj == 2 || nwj == 4 || nwj == 8) ? nwj : 1;
+        p.threads = 32 * (H6_NWARP / p.nwj);
+        p.jt = H6_JT;
+    }
+    const long long ntiles = std::max(1LL, ((long long)n_j + p.jt - 1) / p.jt);
+    p.nsplit = (int)std::max(1LL, std::min<long long>({(long long)nsplit, ntiles, 1024LL}));
+    (void)n_i;
+    return p;
+}
+
+int occ6_blocks(int variant, int nwj)
+{
+    return occ6_of(variant == NB_F32DS, 1, nwj);
+}
+
 size_t plan6_partial_doubles(const ForcePlan &p, int n_i)
 {
     if (p.nsplit <= 1) return 0;

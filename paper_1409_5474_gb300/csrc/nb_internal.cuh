@@ -322,6 +322,10 @@ cudaError_t launch_predict6(const StateDev &s, double t, bool want_rec, unsigned
 
 // Plan of a 6th-order evaluation: CTA shape and j-splits.
 ForcePlan plan_force6(int variant, int n_i, int n_j, int num_sms);
+// The 6th-order plan of a plan-table entry (kind 0: warp rows nwj, nsplit j-splits), and
+// the resident CTAs per SM of the F32 / double-single tile kernel with nwj warp rows.
+ForcePlan plan6_from_entry(int variant, int nwj, int nsplit, int n_i, int n_j);
+int occ6_blocks(int variant, int nwj);
 size_t plan6_partial_doubles(const ForcePlan &p, int n_i);
 
 // K2 + K3 of the 6th-order scheme: acc, jerk, snap and pot of the members

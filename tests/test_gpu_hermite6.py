@@ -210,9 +210,10 @@ def test_order6_argument_checks(nb):
             nb.System(p.m, p.pos, p.vel, eps=0.01, device=0, **bad)
         assert e.value.status == nb.NB_ERR_ARG
     with nb.System(p.m, p.pos, p.vel, eps=0.01, order=6, eta=0.02, device=0) as s6:
-        with pytest.raises(nb.NBodyError) as e:
-            nb.nb_autotune(s6.h, 1)
-        assert e.value.status == nb.NB_ERR_ARG
+        for bad in ([(1, 1, 4)], [(0, 3, 2)], [(0, 2, 0)]):   # kind 1, nwj 3, no splits
+            with pytest.raises(nb.NBodyError) as e:
+                nb.nb_set_plan_table(s6.h, bad)
+            assert e.value.status == nb.NB_ERR_ARG
         s6.predict(0.0)
         with pytest.raises(nb.NBodyError) as e:
             s6.force_ext(p.pos[:4], p.vel[:4])
@@ -345,3 +346,32 @@ def test_fused6_matches_separate_launches(nb):
     scale = np.abs(gb["pos"]).max()
     assert np.abs(ga["pos"] - gb["pos"]).max() < 1e-6 * scale
     assert _rel_rms(sna, snb) < 1e-3
+
+
+@pytest.mark.parametrize("n", [3000, 20000])
+def test_autotuned_plans_force_snap_vs_oracle(nb, n):
+    """nb_autotune on an order-6 handle: every bucket gets a tile-kernel entry (1, 2, 4 or 8
+    warp rows), and the snap force with the tuned plans on i-sets of other sizes than the
+    tuned 2^b (so with scaled split counts) still meets the force gates against the
+    oracle."""
+    p = ic.plummer(n, 91, masses="lognormal")
+    eps = 0.01
+    with nb.System(p.m, p.pos, p.vel, variant="f32ds", eps=eps, eta=0.02, order=6,
+                   device=0) as s:
+        s.step(1.0 / 128)
+        table = nb.nb_autotune(s.h, 2)
+        nb_max = int(np.ceil(np.log2(n)))
+        for b in range(nb_max + 1):
+            assert table[b][0] == 0 and table[b][1] in (1, 2, 4, 8) and table[b][2] >= 1, (b, table[b])
+        assert all(t[0] == -1 for t in table[nb_max + 1:])
+        t = 1.0 / 128 + 1.0 / 2048
+        s.predict(t)
+        rng = np.random.default_rng(92)
+        for n_i in (45, 700, n - 7):
+            plan = nb.nb_plan_for(s.h, n_i)
+            assert plan[0] == 0 and plan[1] in (1, 2, 4, 8)
+            idx = np.sort(rng.choice(n, size=n_i, replace=False)).astype(np.int32)
+            acc, jerk, snap, pot = s.force_snap(idx)
+            (pp, vp, ap), m = _predicted_oracle_state(s, t)
+            ra, rj, rs, rp = oracle.force6(m, pp, vp, ap, eps * eps, idx)
+            _gate6("f32ds", (acc, jerk, snap, pot), (ra, rj, rs, rp), "tuned N=%d n_i=%d" % (n, n_i))
