@@ -101,44 +101,65 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
-// K2 for one tile item (due sets larger than FUSED_SMALL_NA): 32 due slots
-// (slots k0 .. k0 + 31, one per lane; idle lanes copy the last due slot)
+// K2 for one tile item (due sets larger than FUSED_SMALL_NA): 32 IPT due slots
+// (slots k0 + 32 p + lane, p < IPT; idle slots copy the last due one)
 // against the j-records [j0, j1), staged through shared memory in tiles of
 // FUSED_TILE records (double-buffered: the next tile's loads are in flight
 // during the arithmetic). A tile is stored as j-pairs, the values of records
 // 2q and 2q + 1 side by side, so that the pair terms of two j run in one
 // packed FP32x2 instruction (__fadd2_rn / __fmul2_rn / __ffma2_rn; each lane
-// holds its due particle in both halves). The CTA's eight warps hold the same
-// 32 slots and split every tile (warp w takes pairs w, w + 8, ...), so no lane
+// holds its due particles in both halves). The CTA's eight warps hold the same
+// slots and split every tile (warp w takes pairs w, w + 8, ...), so no lane
 // sums have to meet in a shuffle tree; FP32 sums (about 128 terms per half)
 // are folded into double-single totals, and the warps' totals are added in
 // fixed order through shared memory: one partial per (slot, chunk).
 constexpr int FUSED_TILE = 256;
-constexpr int FUSED_IB = 32;        // due slots per tile item
+constexpr int FUSED_IB = 64;        // most due slots per tile item (two per lane)
+// Due sets of at least FUSED_IPT2_NA particles take items of two due slots per lane
+// (64 per item: half the shared-memory reads per pair term, two independent chains);
+// smaller ones one slot per lane (32 per item: more items to spread over the CTAs).
+constexpr int FUSED_IPT2_NA = 256;
 constexpr int FUSED_TILE_FOLD = 8;  // tiles per FP32 partial sum (8 x 16 terms per half)
 
-template <bool DS>
+template <bool DS, int IPT>
 __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, int j0, int j1,
                                           int chunk, float4 (*s_tile)[DS_REC * FUSED_TILE])
 {
     constexpr int NT = FUSED_THREADS, NW = NT / 32, PF = (DS_REC * FUSED_TILE + NT - 1) / NT;
     constexpr int NPAIR = FUSED_TILE / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float4 *ir = a.irec + (size_t)DS_REC * min(k0 + lane, na - 1);
-    const float4 I0 = __ldcg(ir), I1 = __ldcg(ir + 1), I2 = __ldcg(ir + 2);
-    // the due particle, negated, in both halves
-    const float2 nxh = make_float2(-I0.x, -I0.x), nyh = make_float2(-I0.y, -I0.y);
-    const float2 nzh = make_float2(-I0.z, -I0.z), nxl = make_float2(-I1.x, -I1.x);
-    const float2 nyl = make_float2(-I1.y, -I1.y), nzl = make_float2(-I1.z, -I1.z);
-    const float2 nvx = make_float2(-I2.x, -I2.x), nvy = make_float2(-I2.y, -I2.y);
-    const float2 nvz = make_float2(-I2.z, -I2.z), e2 = make_float2(a.eps2f, a.eps2f);
-    const int iid = __float_as_int(I1.w);
-    float A_h[3], A_l[3], J_h[3], J_l[3], P_h = 0.f, P_l = 0.f;
+    // the lane's due particles (slots k0 + 32 p + lane), negated, in both halves
+    float2 nxh[IPT], nyh[IPT], nzh[IPT], nxl[IPT], nyl[IPT], nzl[IPT], nvx[IPT], nvy[IPT],
+        nvz[IPT];
+    int iid[IPT];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) A_h[c] = A_l[c] = J_h[c] = J_l[c] = 0.f;
-    float2 ta[3], tja[3], tjb[3], tp = make_float2(0.f, 0.f);
+    for (int p = 0; p < IPT; ++p) {
+        const float4 *ir = a.irec + (size_t)DS_REC * min(k0 + 32 * p + lane, na - 1);
+        const float4 I0 = __ldcg(ir), I1 = __ldcg(ir + 1), I2 = __ldcg(ir + 2);
+        nxh[p] = make_float2(-I0.x, -I0.x);
+        nyh[p] = make_float2(-I0.y, -I0.y);
+        nzh[p] = make_float2(-I0.z, -I0.z);
+        nxl[p] = make_float2(-I1.x, -I1.x);
+        nyl[p] = make_float2(-I1.y, -I1.y);
+        nzl[p] = make_float2(-I1.z, -I1.z);
+        nvx[p] = make_float2(-I2.x, -I2.x);
+        nvy[p] = make_float2(-I2.y, -I2.y);
+        nvz[p] = make_float2(-I2.z, -I2.z);
+        iid[p] = __float_as_int(I1.w);
+    }
+    const float2 e2 = make_float2(a.eps2f, a.eps2f);
+    float A_h[IPT][3], A_l[IPT][3], J_h[IPT][3], J_l[IPT][3], P_h[IPT], P_l[IPT];
+    float2 ta[IPT][3], tja[IPT][3], tjb[IPT][3], tp[IPT];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ta[c] = tja[c] = tjb[c] = make_float2(0.f, 0.f);
+    for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A_h[p][c] = A_l[p][c] = J_h[p][c] = J_l[p][c] = 0.f;
+            ta[p][c] = tja[p][c] = tjb[p][c] = make_float2(0.f, 0.f);
+        }
+        P_h[p] = P_l[p] = 0.f;
+        tp[p] = make_float2(0.f, 0.f);
+    }
     const float4 *jr = a.s.rec;
     const int ntile = (j1 - j0 + FUSED_TILE - 1) / FUSED_TILE;
     float4 pf[PF];
@@ -178,108 +199,125 @@ __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, in
         if (t + 1 < ntile) fetch(t + 1);
         const float4 *T = s_tile[t & 1];
         // a tile with a lane's own particle or a ragged end masks per half (warp-uniform)
-        const bool masked =
-            __any_sync(0xffffffffu, iid >= tb && iid < tb + cnt) || cnt < FUSED_TILE;
+        bool own = false;
+#pragma unroll
+        for (int p = 0; p < IPT; ++p) own = own || (iid[p] >= tb && iid[p] < tb + cnt);
+        const bool masked = __any_sync(0xffffffffu, own) || cnt < FUSED_TILE;
         auto body = [&](int q, bool msk) {
             const float4 *P = T + 6 * q;
             const float4 q0 = P[0], q1 = P[1], q4 = P[4], q5 = P[5];
-            float2 dx, dy, dz;
+            float4 q2, q3;
             if (DS) {
-                const float4 q2 = P[2], q3 = P[3];
-                dx = __fadd2_rn(__fadd2_rn(make_float2(q0.x, q0.y), nxh),
-                                __fadd2_rn(make_float2(q2.x, q2.y), nxl));
-                dy = __fadd2_rn(__fadd2_rn(make_float2(q0.z, q0.w), nyh),
-                                __fadd2_rn(make_float2(q2.z, q2.w), nyl));
-                dz = __fadd2_rn(__fadd2_rn(make_float2(q1.x, q1.y), nzh),
-                                __fadd2_rn(make_float2(q3.x, q3.y), nzl));
-            } else {
-                dx = __fadd2_rn(make_float2(q0.x, q0.y), nxh);
-                dy = __fadd2_rn(make_float2(q0.z, q0.w), nyh);
-                dz = __fadd2_rn(make_float2(q1.x, q1.y), nzh);
+                q2 = P[2];
+                q3 = P[3];
             }
-            const float2 dvx = __fadd2_rn(make_float2(q4.x, q4.y), nvx);
-            const float2 dvy = __fadd2_rn(make_float2(q4.z, q4.w), nvy);
-            const float2 dvz = __fadd2_rn(make_float2(q5.x, q5.y), nvz);
-            float2 r2 = __ffma2_rn(dx, dx, e2);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            float2 rv = __fmul2_rn(dx, dvx);
-            rv = __ffma2_rn(dy, dvy, rv);
-            rv = __ffma2_rn(dz, dvz, rv);
-            float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-            if (msk) {
-                const int ja = tb + 2 * q;  // the self pair and records past the end: nothing
-                rinv.x = (ja == iid || 2 * q >= cnt) ? 0.f : rinv.x;
-                rinv.y = (ja + 1 == iid || 2 * q + 1 >= cnt) ? 0.f : rinv.y;
+#pragma unroll
+            for (int p = 0; p < IPT; ++p) {
+                float2 dx, dy, dz;
+                if (DS) {
+                    dx = __fadd2_rn(__fadd2_rn(make_float2(q0.x, q0.y), nxh[p]),
+                                    __fadd2_rn(make_float2(q2.x, q2.y), nxl[p]));
+                    dy = __fadd2_rn(__fadd2_rn(make_float2(q0.z, q0.w), nyh[p]),
+                                    __fadd2_rn(make_float2(q2.z, q2.w), nyl[p]));
+                    dz = __fadd2_rn(__fadd2_rn(make_float2(q1.x, q1.y), nzh[p]),
+                                    __fadd2_rn(make_float2(q3.x, q3.y), nzl[p]));
+                } else {
+                    dx = __fadd2_rn(make_float2(q0.x, q0.y), nxh[p]);
+                    dy = __fadd2_rn(make_float2(q0.z, q0.w), nyh[p]);
+                    dz = __fadd2_rn(make_float2(q1.x, q1.y), nzh[p]);
+                }
+                const float2 dvx = __fadd2_rn(make_float2(q4.x, q4.y), nvx[p]);
+                const float2 dvy = __fadd2_rn(make_float2(q4.z, q4.w), nvy[p]);
+                const float2 dvz = __fadd2_rn(make_float2(q5.x, q5.y), nvz[p]);
+                float2 r2 = __ffma2_rn(dx, dx, e2);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                float2 rv = __fmul2_rn(dx, dvx);
+                rv = __ffma2_rn(dy, dvy, rv);
+                rv = __ffma2_rn(dz, dvz, rv);
+                float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                if (msk) {
+                    const int ja = tb + 2 * q;  // the self pair and records past the end: nothing
+                    rinv.x = (ja == iid[p] || 2 * q >= cnt) ? 0.f : rinv.x;
+                    rinv.y = (ja + 1 == iid[p] || 2 * q + 1 >= cnt) ? 0.f : rinv.y;
+                }
+                const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                const float2 mrinv = __fmul2_rn(make_float2(q1.z, q1.w), rinv);
+                const float2 mr3 = __fmul2_rn(mrinv, rinv2);
+                const float2 beta = __fmul2_rn(__fmul2_rn(mr3, rinv2), rv);
+                tp[p] = __fadd2_rn(tp[p], mrinv);
+                ta[p][0] = __ffma2_rn(mr3, dx, ta[p][0]);
+                ta[p][1] = __ffma2_rn(mr3, dy, ta[p][1]);
+                ta[p][2] = __ffma2_rn(mr3, dz, ta[p][2]);
+                tja[p][0] = __ffma2_rn(mr3, dvx, tja[p][0]);
+                tja[p][1] = __ffma2_rn(mr3, dvy, tja[p][1]);
+                tja[p][2] = __ffma2_rn(mr3, dvz, tja[p][2]);
+                tjb[p][0] = __ffma2_rn(beta, dx, tjb[p][0]);
+                tjb[p][1] = __ffma2_rn(beta, dy, tjb[p][1]);
+                tjb[p][2] = __ffma2_rn(beta, dz, tjb[p][2]);
             }
-            const float2 rinv2 = __fmul2_rn(rinv, rinv);
-            const float2 mrinv = __fmul2_rn(make_float2(q1.z, q1.w), rinv);
-            const float2 mr3 = __fmul2_rn(mrinv, rinv2);
-            const float2 beta = __fmul2_rn(__fmul2_rn(mr3, rinv2), rv);
-            tp = __fadd2_rn(tp, mrinv);
-            ta[0] = __ffma2_rn(mr3, dx, ta[0]);
-            ta[1] = __ffma2_rn(mr3, dy, ta[1]);
-            ta[2] = __ffma2_rn(mr3, dz, ta[2]);
-            tja[0] = __ffma2_rn(mr3, dvx, tja[0]);
-            tja[1] = __ffma2_rn(mr3, dvy, tja[1]);
-            tja[2] = __ffma2_rn(mr3, dvz, tja[2]);
-            tjb[0] = __ffma2_rn(beta, dx, tjb[0]);
-            tjb[1] = __ffma2_rn(beta, dy, tjb[1]);
-            tjb[2] = __ffma2_rn(beta, dz, tjb[2]);
         };
         const int npair = (cnt + 1) / 2;
         if (masked) {
             for (int q = warp; q < npair; q += NW) body(q, true);
         } else {
-#pragma unroll 4
+#pragma unroll 2
             for (int q = warp; q < NPAIR; q += NW) body(q, false);
         }
         if ((t + 1) % FUSED_TILE_FOLD == 0 || t + 1 == ntile) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float sa = ta[c].x + ta[c].y;
-                const float jt = fmaf(-3.f, tjb[c].x + tjb[c].y, tja[c].x + tja[c].y);
-                if (DS) {
-                    ds_add(A_h[c], A_l[c], sa);
-                    ds_add(J_h[c], J_l[c], jt);
-                } else {
-                    A_h[c] += sa;
-                    J_h[c] += jt;
+            for (int p = 0; p < IPT; ++p) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float sa = ta[p][c].x + ta[p][c].y;
+                    const float jt = fmaf(-3.f, tjb[p][c].x + tjb[p][c].y, tja[p][c].x + tja[p][c].y);
+                    if (DS) {
+                        ds_add(A_h[p][c], A_l[p][c], sa);
+                        ds_add(J_h[p][c], J_l[p][c], jt);
+                    } else {
+                        A_h[p][c] += sa;
+                        J_h[p][c] += jt;
+                    }
+                    ta[p][c] = tja[p][c] = tjb[p][c] = make_float2(0.f, 0.f);
                 }
-                ta[c] = tja[c] = tjb[c] = make_float2(0.f, 0.f);
+                const float sp = tp[p].x + tp[p].y;
+                if (DS)
+                    ds_add(P_h[p], P_l[p], sp);
+                else
+                    P_h[p] += sp;
+                tp[p] = make_float2(0.f, 0.f);
             }
-            const float sp = tp.x + tp.y;
-            if (DS)
-                ds_add(P_h, P_l, sp);
-            else
-                P_h += sp;
-            tp = make_float2(0.f, 0.f);
         }
         if (t + 1 < ntile) stash((t + 1) & 1);
         __syncthreads();
     }
-    // the warps' totals, added in order 0..7 (the tile buffers are free now)
+    // the warps' totals, added in order 0..7, one group of 32 slots at a time (the tile
+    // buffers are free now)
     float2 *s_red = reinterpret_cast<float2 *>(&s_tile[0][0]);  // [NW][7][32]
-    const float2 mine[7] = {make_float2(A_h[0], A_l[0]), make_float2(A_h[1], A_l[1]),
-                            make_float2(A_h[2], A_l[2]), make_float2(J_h[0], J_l[0]),
-                            make_float2(J_h[1], J_l[1]), make_float2(J_h[2], J_l[2]),
-                            make_float2(P_h, P_l)};
 #pragma unroll
-    for (int c = 0; c < 7; ++c) s_red[(warp * 7 + c) * 32 + lane] = mine[c];
-    __syncthreads();
-    if (warp == 0 && k0 + lane < na) {
+    for (int p = 0; p < IPT; ++p) {
+        const float2 mine[7] = {make_float2(A_h[p][0], A_l[p][0]), make_float2(A_h[p][1], A_l[p][1]),
+                                make_float2(A_h[p][2], A_l[p][2]), make_float2(J_h[p][0], J_l[p][0]),
+                                make_float2(J_h[p][1], J_l[p][1]), make_float2(J_h[p][2], J_l[p][2]),
+                                make_float2(P_h[p], P_l[p])};
 #pragma unroll
-        for (int c = 0; c < 7; ++c) {
-            dsf v{mine[c].x, mine[c].y};
+        for (int c = 0; c < 7; ++c) s_red[(warp * 7 + c) * 32 + lane] = mine[c];
+        __syncthreads();
+        const int k = k0 + 32 * p + lane;
+        if (warp == 0 && k < na) {
 #pragma unroll
-            for (int w = 1; w < NW; ++w) {
-                const float2 x = s_red[(w * 7 + c) * 32 + lane];
-                ds_acc(v, dsf{x.x, x.y});
+            for (int c = 0; c < 7; ++c) {
+                dsf v{mine[c].x, mine[c].y};
+#pragma unroll
+                for (int w = 1; w < NW; ++w) {
+                    const float2 x = s_red[(w * 7 + c) * 32 + lane];
+                    ds_acc(v, dsf{x.x, x.y});
+                }
+                a.part[((size_t)chunk * 7 + c) * na + k] = make_float2(v.hi, v.lo);
             }
-            a.part[((size_t)chunk * 7 + c) * na + k0 + lane] = make_float2(v.hi, v.lo);
         }
+        __syncthreads();  // s_red is free for the next group (or the next item's tiles)
     }
-    __syncthreads();  // s_red is the tile buffer of the next item
 }
 
 // The j-chunks of a step with na (> FUSED_SMALL_NA) due particles on n (a
@@ -288,9 +326,10 @@ __device__ __forceinline__ void tile_item(const FusedArgs &a, int na, int k0, in
 // FUSED_TILE j.
 constexpr int FUSED_MAX_CHUNKS = 128;
 
-__device__ __forceinline__ void tile_chunking(int na, int n, int grid, int &nchunk, int &jc)
+__device__ __forceinline__ void tile_chunking(int na, int n, int grid, int ib, int &nchunk,
+                                              int &jc)
 {
-    const int nib = (na + FUSED_IB - 1) / FUSED_IB;
+    const int nib = (na + ib - 1) / ib;
     int nc = max(1, grid / nib);
     nc = max(1, min(min(nc, (n + FUSED_TILE - 1) / FUSED_TILE), FUSED_MAX_CHUNKS));
     jc = (n + nc - 1) / nc;
@@ -763,13 +802,18 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             mark(1);
         } else {
             // C: pair force, tile items (32 due slots x one j-chunk)
+            const bool two = na >= FUSED_IPT2_NA;
+            const int IB = two ? 64 : 32;
             int nchunk, jc;
-            tile_chunking(na, n, G, nchunk, jc);
-            const int nib = (na + FUSED_IB - 1) / FUSED_IB;
+            tile_chunking(na, n, G, IB, nchunk, jc);
+            const int nib = (na + IB - 1) / IB;
             for (int it = bid; it < nib * nchunk; it += G) {
                 const int ib = it / nchunk, c = it - ib * nchunk;
                 const int j0 = c * jc;
-                tile_item<DS>(a, na, FUSED_IB * ib, j0, min(n, j0 + jc), c, s_tile);
+                if (two)
+                    tile_item<DS, 2>(a, na, IB * ib, j0, min(n, j0 + jc), c, s_tile);
+                else
+                    tile_item<DS, 1>(a, na, IB * ib, j0, min(n, j0 + jc), c, s_tile);
             }
             if (!(ok = grid_barrier(a.bar, gen))) break;
             mark(1);
