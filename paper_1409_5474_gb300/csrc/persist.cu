@@ -14,7 +14,7 @@
 //      j); the CTA that completes a group's last chunk (a ticket) sums its
 //      double-single partials in chunk order (K3) and corrects its particles
 //      (K4), three lanes for the three components; larger due sets (order 4):
-//      CTA items of 32 due slots whose j-chunk is staged through shared memory
+//      CTA items of 32 (64) due slots whose j-chunk is staged through shared memory
 //      as j-pairs, double-single partials per chunk;   -- barrier
 //   D  (larger due sets) one warp per due particle sums its chunk partials in
 //      chunk order (K3) and corrects it (K4: Hermite corrector, Aarseth step,
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
             }
             mark(1);
         } else {
-            // C: pair force, tile items (32 due slots x one j-chunk)
+            // C: pair force, tile items (32 or 64 due slots x one j-chunk)
             const bool two = na >= FUSED_IPT2_NA;
             const int IB = two ? 64 : 32;
             int nchunk, jc;
